@@ -1,0 +1,413 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+* the classical 19-point fourth-order ("Mehrstellen") Poisson stencil, a special case of Eq. (5);
+* fourth-order spatial / second-order temporal convergence on a manufactured solution of Eq. (1)
+  (the order the paper claims for the scheme, Sec. 2.2);
+* the printed stencil weights L1..L7 and Q1..Q19 of Eq. (6), an independent expansion of Eq. (5);
+* BiCGSTAB against a direct sparse LU solve;
+* the exact conduction fixed point at Ra = 0 (Nu = 1, E_total = 1, Be = 1);
+* centro- and z-mirror symmetry of the coupled step, hot/cold Nusselt balance and the sign and
+  range of the entropy quantities (Sec. 4.3).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hosc_oracle as O
+
+
+# ------------------------------------------------------------------ Mehrstellen special case
+
+def _stencil_of_B(g, c, node):
+    """Weights of the level-n operator at ``node`` (flattened), by applying it to unit vectors
+    restricted to the 3x3x3 neighbourhood."""
+    N = g.N
+    i, j, k = node
+    w = {}
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                e = np.zeros(N ** 3)
+                e[(i + dx) + N * ((j + dy) + N * (k + dz))] = 1.0
+                w[(dx, dy, dz)] = O.apply_B(g, c, e)[i + N * (j + N * k)]
+    return w
+
+
+def test_mehrstellen_special_case():
+    """L=1, G*=H*=I*=K*=0, no time change: B must be the classical 19-point fourth-order
+    Laplacian (1/(6h^2)) [24 centre - 2 faces - 1 edges, 0 corners] (negated Laplacian)."""
+    N = 7
+    g = O.Grid(N)
+    one, zero = np.ones(N ** 3), np.zeros(N ** 3)
+    c = O.scalar_coefficients(g, 0.01, one, zero, zero, zero, zero, zero)
+    w = _stencil_of_B(g, c, (3, 3, 3))
+    h2 = g.h ** 2
+    for off, val in w.items():
+        nz = sum(abs(a) for a in off)
+        expect = {0: 24.0, 1: -2.0, 2: -1.0, 3: 0.0}[nz] / (6.0 * h2)
+        assert val == pytest.approx(expect, rel=1e-12, abs=1e-9), off
+    # R = (1 + h^2/12 lap_h) E  for that special case
+    rng = np.random.default_rng(1)
+    E = rng.standard_normal(N ** 3)
+    c = O.scalar_coefficients(g, 0.01, one, zero, zero, zero, zero, E)
+    lap = (g.Dxx + g.Dyy + g.Dzz) @ E
+    ii = g.int_idx
+    np.testing.assert_allclose(c["R"][ii], (E + h2 / 12.0 * lap)[ii], rtol=1e-13, atol=1e-12)
+
+
+# ------------------------------------------------------------------ manufactured solution
+
+PI = math.pi
+
+
+def _mms_fields(g, t, with_K=True):
+    x, y, z = (a.ravel() for a in g.coords())
+    S = np.sin(PI * x) * np.sin(PI * y) * np.sin(PI * z)
+    e = math.exp(-t)
+    chi = e * S + x * x * y * z
+    chi_t = -e * S
+    chi_x = e * PI * np.cos(PI * x) * np.sin(PI * y) * np.sin(PI * z) + 2 * x * y * z
+    chi_y = e * PI * np.sin(PI * x) * np.cos(PI * y) * np.sin(PI * z) + x * x * z
+    chi_z = e * PI * np.sin(PI * x) * np.sin(PI * y) * np.cos(PI * z) + x * x * y
+    lap = -3 * PI * PI * e * S + 2 * y * z
+    L = 1.0 + 0.5 * np.sin(x + y + z + t)
+    G = 2.0 * np.cos(x - y + t)
+    H = 1.5 * np.sin(y + 2 * z - t)
+    I = 1.8 * np.cos(z + x + 0.5 * t)
+    K = (0.5 + 0.3 * np.sin(x * y * z + t)) if with_K else np.zeros_like(x)
+    E = L * chi_t + G * chi_x + H * chi_y + I * chi_z + K * chi - lap
+    return chi, dict(L=L, G=G, H=H, I=I, K=K, E=E)
+
+
+def _mms_run(N, dt, T, with_K=True):
+    g = O.Grid(N)
+    steps = int(round(T / dt))
+    chi, _ = _mms_fields(g, 0.0, with_K)
+    chi = chi.reshape(N, N, N)
+    for n in range(steps):
+        t = n * dt
+        _, cf = _mms_fields(g, t, with_K)
+        _, cp = _mms_fields(g, t - dt, with_K)
+        c = O.scalar_coefficients(g, dt, prev=cp, **cf)
+        A = O.assemble_A(g, dt, c)
+        wall, _ = _mms_fields(g, t + dt, with_K)
+        chi, its, st = O.solve_system(g, dt, c, A, chi, 1e-13, 500,
+                                      chi_wall_new=wall.reshape(N, N, N))
+        assert st == 0
+    exact, _ = _mms_fields(g, steps * dt, with_K)
+    return float(np.max(np.abs(chi.ravel() - exact)[g.int_idx]))
+
+
+@pytest.mark.parametrize("with_K", [True, False])
+def test_mms_fourth_order_space(with_K):
+    """dt = h^2: the error at fixed T must fall as h^4 (Sec. 2.2 claims O(dt^2, h^4))."""
+    errs = []
+    for N in (9, 17, 33):
+        h = 1.0 / (N - 1)
+        errs.append(_mms_run(N, 2.0 * h * h, 1.0 / 16.0, with_K))
+    order = math.log2(errs[1] / errs[2])
+    assert 3.6 < order < 4.6, (errs, order)
+
+
+def test_mms_second_order_time():
+    """Fixed grid: the change against a fine-dt run must fall as dt^2."""
+    N, T = 11, 0.4
+    ref = None
+    g = O.Grid(N)
+    sols = {}
+    for m in (2, 4, 8, 64):
+        dt = T / m
+        chi, _ = _mms_fields(g, 0.0)
+        chi = chi.reshape(N, N, N)
+        for n in range(m):
+            t = n * dt
+            _, cf = _mms_fields(g, t)
+            _, cp = _mms_fields(g, t - dt)
+            c = O.scalar_coefficients(g, dt, prev=cp, **cf)
+            A = O.assemble_A(g, dt, c)
+            wall, _ = _mms_fields(g, t + dt)
+            chi, _, st = O.solve_system(g, dt, c, A, chi, 1e-14, 500,
+                                        chi_wall_new=wall.reshape(N, N, N))
+            assert st == 0
+        sols[m] = chi.ravel()[g.int_idx]
+    ref = sols[64]
+    e = [np.max(np.abs(sols[m] - ref)) for m in (2, 4, 8)]
+    o1, o2 = math.log2(e[0] / e[1]), math.log2(e[1] / e[2])
+    assert 1.7 < o2 < 2.5 and 1.5 < o1 < 2.6, (e, o1, o2)
+
+
+# ------------------------------------------------------------------ printed weights of Eq. (6)
+
+def test_printed_stencil_weights_eq6():
+    """Q = A - dt B from the operator composition must equal the expanded weights printed with
+    Eq. (6) (readings: the operator missing in Q1/Q3 is a '+'; the N4, N5 terms change sign
+    between the +/- neighbours; '2l^h' is 2 l^2 h; h = k = l here)."""
+    N, dt = 7, 0.013
+    g = O.Grid(N)
+    rng = np.random.default_rng(7)
+    f = lambda s=1.0, o=0.0: o + s * rng.standard_normal(N ** 3)
+    L, G, H, I, K, E = f(0.2, 1.3), f(), f(), f(), f(0.3), f()
+    prev = dict(L=L + f(0.05), G=G + f(0.05), H=H + f(0.05), I=I + f(0.05), K=K + f(0.05),
+                E=E + f(0.05))
+    c = O.scalar_coefficients(g, dt, L, G, H, I, K, E, prev=prev)
+    A = O.assemble_A(g, dt, c)
+    node = (3, 2, 4)
+    i, j, k = node
+    n0 = i + N * (j + N * k)
+    wB = _stencil_of_B(g, c, node)
+    Arow = A[n0].toarray().ravel()
+    Q = {}
+    for off, b in wB.items():
+        col = (i + off[0]) + N * ((j + off[1]) + N * (k + off[2]))
+        Q[off] = Arow[col] - dt * b
+    h = k_ = l = g.h
+    at = lambda a: a[n0]
+    Lc, Gc, Hc, Ic, Kc = at(L), at(G), at(H), at(I), at(K)
+    Mx = -dt / (2 * Lc) + h * h / 12
+    My = -dt / (2 * Lc) + k_ * k_ / 12
+    Mz = -dt / (2 * Lc) + l * l / 12
+    M4L = dt / (2 * Lc)
+    M15 = at(g.Dx @ L) * h * h / (6 * Lc)
+    M16 = at(g.Dy @ L) * k_ * k_ / (6 * Lc)
+    M17 = at(g.Dz @ L) * l * l / (6 * Lc)
+    # M18 read from the delta_t^+ bracket of Eq. (5) (reading R9)
+    M18 = (0.5 * dt * (Lc - at(prev["L"])) / dt
+           + h * h / 12 * (at(g.Dxx @ L) - Gc * at(g.Dx @ L))
+           + k_ * k_ / 12 * (at(g.Dyy @ L) - Hc * at(g.Dy @ L))
+           + l * l / 12 * (at(g.Dzz @ L) - Ic * at(g.Dz @ L)))
+    # printed L1..L7
+    Lw = {
+        (1, 0, 0): (-Mx * Gc / (2 * h) + Mx / h ** 2 + M15 / (2 * h)) * Lc,
+        (-1, 0, 0): (Mx * Gc / (2 * h) + Mx / h ** 2 - M15 / (2 * h)) * Lc,
+        (0, 1, 0): (-My * Hc / (2 * k_) + My / k_ ** 2 + M16 / (2 * k_)) * Lc,
+        (0, -1, 0): (My * Hc / (2 * k_) + My / k_ ** 2 - M16 / (2 * k_)) * Lc,
+        (0, 0, 1): (-Mz * Ic / (2 * l) + Mz / l ** 2 + M17 / (2 * l)) * Lc,
+        (0, 0, -1): (Mz * Ic / (2 * l) + Mz / l ** 2 - M17 / (2 * l)) * Lc,
+        (0, 0, 0): (1 - 2 * My / k_ ** 2 - 2 * Mx / h ** 2 + 2 * M4L * M18 / dt + M4L * Kc
+                    - 2 * Mz / l ** 2) * Lc,
+    }
+    for off, val in Lw.items():
+        col = (i + off[0]) + N * ((j + off[1]) + N * (k + off[2]))
+        assert Arow[col] == pytest.approx(val, rel=1e-11, abs=1e-9), ("L", off)
+    # printed Q1..Q19
+    al, be, ga = at(c["alpha"]), at(c["beta"]), at(c["gamma"])
+    M1, M2, M3, M4 = at(c["M1"]), at(c["M2"]), at(c["M3"]), at(c["M4"])
+    p1, q1, r1 = at(c["p1"]), at(c["q1"]), at(c["r1"])
+    M5 = (h * h + k_ * k_) / 12
+    M6 = (k_ * k_ + l * l) / 12
+    M7 = (l * l + h * h) / 12
+    N1 = dt * al + Lc * Mx
+    N2 = dt * be + Lc * My
+    N3 = dt * ga + Lc * Mz
+    N4 = -dt * M1 - Lc * Mx * Gc
+    N5 = -dt * M2 - Lc * My * Hc
+    N6 = -dt * M3 - Lc * Mz * Ic
+    N7 = M4L * Lc
+    N8 = -dt
+    h2, k2, l2 = h * h, k_ * k_, l * l
+    Qp = {
+        (1, 0, 0): Lc * M15 / (2 * h) + N1 / h2 - 2 * dt * M5 / (h2 * k2) + 2 * dt * M5 * Gc / (2 * h * k2)
+        + N4 / (2 * h) - 2 * dt * M7 / (l2 * h2) + 2 * dt * M7 * Gc / (2 * h * l2),
+        (0, 0, 0): Lc - 2 * (N2 / k2 + N1 / h2 + N3 / l2) + (N8 * M4 + N7 * Kc)
+        + 4 * dt * M5 / (h2 * k2) + 4 * dt * M6 / (k2 * l2) + 2 * N7 * M18 / dt
+        + 4 * dt * M7 / (h2 * l2),
+        (-1, 0, 0): -Lc * M15 / (2 * h) + N1 / h2 - 2 * dt * M5 / (h2 * k2)
+        - 2 * dt * M5 * Gc / (2 * h * k2) - N4 / (2 * h) - 2 * dt * M7 / (l2 * h2)
+        - 2 * dt * M7 * Gc / (2 * h * l2),
+        (0, 1, 0): Lc * M16 / (2 * k_) + N2 / k2 - 2 * dt * M5 / (h2 * k2) + N5 / (2 * k_)
+        + 2 * dt * M5 * Hc / (2 * h2 * k_) - 2 * dt * M6 / (l2 * k2) + 2 * dt * M6 * Hc / (2 * k_ * l2),
+        (0, -1, 0): -Lc * M16 / (2 * k_) + N2 / k2 - 2 * dt * M5 / (h2 * k2) - N5 / (2 * k_)
+        - 2 * dt * M5 * Hc / (2 * h2 * k_) - 2 * dt * M6 / (l2 * k2) - 2 * dt * M6 * Hc / (2 * k_ * l2),
+        (0, 0, 1): Lc * M17 / (2 * l) + N3 / l2 - 2 * dt * M6 / (l2 * k2) + N6 / (2 * l)
+        - 2 * dt * M7 / (l2 * h2) + 2 * dt * M6 * Ic / (2 * k2 * l) + 2 * dt * M7 * Ic / (2 * l * h2),
+        (0, 0, -1): -2 * dt * M7 * Ic / (2 * l * h2) - Lc * M17 / (2 * l) + N3 / l2
+        - 2 * dt * M6 / (l2 * k2) - N6 / (2 * l) - 2 * dt * M6 * Ic / (2 * k2 * l) - 2 * dt * M7 / (l2 * h2),
+        (1, 1, 0): -dt * M5 * p1 / (4 * h * k_) + dt * M5 / (h2 * k2) - dt * M5 * Hc / (2 * h2 * k_)
+        - dt * M5 * Gc / (2 * h * k2),
+        (-1, 1, 0): dt * M5 * p1 / (4 * h * k_) + dt * M5 / (h2 * k2) - dt * M5 * Hc / (2 * h2 * k_)
+        + dt * M5 * Gc / (2 * h * k2),
+        (1, -1, 0): dt * M5 * p1 / (4 * h * k_) + dt * M5 / (h2 * k2) + dt * M5 * Hc / (2 * h2 * k_)
+        - dt * M5 * Gc / (2 * h * k2),
+        (-1, -1, 0): -dt * M5 * p1 / (4 * h * k_) + dt * M5 / (h2 * k2) + dt * M5 * Hc / (2 * h2 * k_)
+        + dt * M5 * Gc / (2 * h * k2),
+        (0, 1, 1): -dt * M6 * q1 / (4 * k_ * l) + dt * M6 / (l2 * k2) - dt * M6 * Ic / (2 * k2 * l)
+        - dt * M6 * Hc / (2 * k_ * l2),
+        (0, -1, 1): dt * M6 * q1 / (4 * k_ * l) + dt * M6 / (l2 * k2) - dt * M6 * Ic / (2 * k2 * l)
+        + dt * M6 * Hc / (2 * k_ * l2),
+        (0, 1, -1): dt * M6 * q1 / (4 * k_ * l) + dt * M6 / (l2 * k2) + dt * M6 * Ic / (2 * k2 * l)
+        - dt * M6 * Hc / (2 * k_ * l2),
+        (0, -1, -1): -dt * M6 * q1 / (4 * k_ * l) + dt * M6 / (l2 * k2) + dt * M6 * Ic / (2 * k2 * l)
+        + dt * M6 * Hc / (2 * k_ * l2),
+        (1, 0, 1): -dt * M7 * r1 / (4 * l * h) + dt * M7 / (l2 * h2) - dt * M7 * Gc / (2 * l2 * h)
+        - dt * M7 * Ic / (2 * l * h2),
+        (1, 0, -1): dt * M7 * r1 / (4 * l * h) + dt * M7 / (l2 * h2) - dt * M7 * Gc / (2 * l2 * h)
+        + dt * M7 * Ic / (2 * l * h2),
+        (-1, 0, 1): dt * M7 * r1 / (4 * l * h) + dt * M7 / (l2 * h2) + dt * M7 * Gc / (2 * l2 * h)
+        - dt * M7 * Ic / (2 * l * h2),
+        (-1, 0, -1): -dt * M7 * r1 / (4 * l * h) + dt * M7 / (l2 * h2) + dt * M7 * Gc / (2 * l2 * h)
+        + dt * M7 * Ic / (2 * l * h2),
+    }
+    scale = max(abs(v) for v in Qp.values())
+    for off, val in Qp.items():
+        assert Q[off] == pytest.approx(val, abs=1e-11 * scale), ("Q", off)
+    corners = [o for o in Q if all(a != 0 for a in o)]
+    assert len(corners) == 8 and all(abs(Q[o]) < 1e-12 * scale for o in corners)
+
+
+# ------------------------------------------------------------------ BiCGSTAB vs direct
+
+def test_bicgstab_matches_direct_solve():
+    prm = O.Params(N=7, Ra=2e3, n=0.8, tol_lin=1e-13)
+    g = O.Grid(7)
+    rng = np.random.default_rng(3)
+    st = O.initial_state(prm)
+    for key in ("u", "v", "w"):
+        f = np.zeros((7, 7, 7))
+        f[1:-1, 1:-1, 1:-1] = rng.standard_normal((5, 5, 5))
+        st[key] = f
+    st["th"] = O.apply_theta_bc(rng.random((7, 7, 7)))
+    a, _ = O.step(st, prm, g)
+    b, _ = O.step(st, prm, g, direct=True)
+    for key in ("u", "v", "w", "th", "p"):
+        np.testing.assert_allclose(a[key], b[key], rtol=0, atol=1e-10 * max(1.0, np.abs(b[key]).max()))
+
+
+# ------------------------------------------------------------------ coupled-system invariants
+
+def test_conduction_fixed_point_ra0():
+    """Ra = 0: theta = 1 - x, V = 0, p = 0 is an exact discrete steady state; Nu = 1,
+    E_total = 1 and Be = 1 (Sec. 4.2-4.3 definitions applied to pure conduction)."""
+    for n in (0.75, 1.0, 1.25):
+        prm = O.Params(N=9, Ra=0.0, n=n)
+        g = O.Grid(9)
+        st = O.initial_state(prm)
+        x, _, _ = g.coords()
+        st["th"] = 1.0 - x
+        for _ in range(2):
+            st, info = O.step(st, prm, g)
+        assert info["res"] < 1e-13 and info["div_max"] == 0.0
+        d = O.diagnostics(st, prm)
+        assert d["Nu_hot_max"] == pytest.approx(1.0, abs=1e-12)
+        assert d["Nu_hot_mean"] == pytest.approx(1.0, abs=1e-12)
+        assert d["Nu_cold_mean"] == pytest.approx(1.0, abs=1e-12)
+        assert d["E_total"] == pytest.approx(1.0, abs=1e-12)
+        assert d["Be"] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_conduction_reached_from_rest_ra0():
+    prm = O.Params(N=9, Ra=0.0, n=0.75, tol_lin=1e-10)
+    st, info = O.solve_steady(prm, 400, tol_steady=1e-10)
+    x, _, _ = O.Grid(9).coords()
+    assert np.max(np.abs(st["th"] - (1.0 - x))) < 1e-8
+    assert np.max(np.abs(st["u"])) == 0.0
+
+
+def _mirror_all(f):
+    return f[::-1, ::-1, ::-1]
+
+
+@pytest.mark.parametrize("n", [0.75, 1.0, 1.25])
+def test_centro_and_z_symmetry_of_the_step(n):
+    """With theta_ref = 1/2 the coupled step maps a centro-symmetric state (theta + theta' = 1,
+    V = -V', p = p' about the cavity centre) to a centro-symmetric state, and a z-mirror-symmetric
+    state (w odd, the rest even in z) to a z-mirror-symmetric state."""
+    N = 9
+    prm = O.Params(N=N, Ra=5e3, n=n)
+    g = O.Grid(N)
+    rng = np.random.default_rng(11)
+    # build a state with both symmetries
+    base = {}
+    for key in ("u", "v", "w"):
+        f = np.zeros((N, N, N))
+        f[1:-1, 1:-1, 1:-1] = rng.standard_normal((N - 2,) * 3)
+        f = f - _mirror_all(f)                    # centro-odd
+        f = 0.5 * (f + (-1 if key == "w" else 1) * f[::-1, :, :])   # z parity (keeps centro-odd)
+        base[key] = f
+    th = rng.random((N, N, N))
+    th = 0.5 * (th + 1.0 - _mirror_all(th))
+    th = 0.5 * (th + th[::-1, :, :])
+    st = O.initial_state(prm)
+    st.update(u=base["u"], v=base["v"], w=base["w"], th=O.apply_theta_bc(th))
+    for _ in range(3):
+        st, info = O.step(st, prm, g)
+        assert info["status"] == 0
+        tol = 1e-9 * max(1.0, np.abs(st["v"]).max())
+        assert np.max(np.abs(st["th"] + _mirror_all(st["th"]) - 1.0)) < 1e-11
+        for key in ("u", "v", "w"):
+            assert np.max(np.abs(st[key] + _mirror_all(st[key]))) < tol
+            par = -1.0 if key == "w" else 1.0
+            assert np.max(np.abs(st[key] - par * st[key][::-1, :, :])) < tol
+        assert np.max(np.abs(st["th"] - st["th"][::-1, :, :])) < 1e-11
+        ptol = 1e-9 * max(1.0, np.abs(st["p"]).max())
+        assert np.max(np.abs(st["p"] - _mirror_all(st["p"]))) < ptol
+        assert np.max(np.abs(st["p"] - st["p"][::-1, :, :])) < ptol
+
+
+def _midplane_heat_flux(st, h):
+    """Heat flux through the plane x = 1/2: int int (u theta - theta_x) dy dz (trapezoid)."""
+    N = st["th"].shape[0]
+    m = (N - 1) // 2
+    th, u = st["th"], st["u"]
+    q = u[:, :, m] * th[:, :, m] - (th[:, :, m + 1] - th[:, :, m - 1]) / (2 * h)
+    w = np.full(N, h)
+    w[0] = w[-1] = h / 2
+    return float(w @ q @ w)
+
+
+def test_steady_state_balance_entropy_and_certificate():
+    """A converged small power-law cavity: the hot and cold wall means agree, div V -> 0, the dt-free steady
+    residual B chi - R vanishes, entropy terms are non-negative, 0 <= Be <= 1, and the steady
+    state is centro-symmetric."""
+    prm = O.Params(N=9, Ra=1e3, n=0.75, dt=0.01, tol_lin=1e-11, tol_div=1e-7)
+    g = O.Grid(9)
+    st, info = O.solve_steady(prm, 4000, tol_steady=1e-9, g=g)
+    assert info["status"] == 0 and info["res"] < 1e-9 and info["div_max"] < 1e-7
+    d = O.diagnostics(st, prm)
+    assert d["Nu_hot_mean"] > 1.2
+    assert abs(d["Nu_hot_mean"] - d["Nu_cold_mean"]) < 1e-8
+    cert, dmax = O.steady_certificate(st, prm, g)
+    assert cert < 1e-5 and dmax < 1e-7
+    for key in ("E_HT", "E_FF", "E_local"):
+        assert np.all(d[key] >= 0.0)
+    assert 0.0 < d["Be"] < 1.0
+    assert np.all((d["Be_local"] >= 0.0) & (d["Be_local"] <= 1.0))
+    assert np.max(np.abs(st["th"] + _mirror_all(st["th"]) - 1.0)) < 1e-10
+    # the steady state does not depend on the pseudo-time step
+    prm2 = O.Params(N=9, Ra=1e3, n=0.75, dt=0.005, tol_lin=1e-11, tol_div=1e-7)
+    st2, info2 = O.solve_steady(prm2, 8000, tol_steady=1e-9, g=g)
+    for key in ("u", "v", "w", "th"):
+        assert np.max(np.abs(st2[key] - st[key])) < 1e-5 * max(1.0, np.abs(st[key]).max())
+
+
+def test_newtonian_limit_table2_ra1e3_coarse():
+    """n = 1, Pr = 0.71, Ra = 1e3: Table 2 prints max Nu_avg = 1.098 on 51^3 (the cited 3D
+    benchmarks: 1.091, 1.088). A 17^3 grid of a fourth-order scheme is within 1 % of it."""
+    N = 17
+    h = 1.0 / (N - 1)
+    prm = O.Params(N=N, Ra=1e3, Pr=0.71, n=1.0, dt=0.02, lam=0.9 * h * h / 0.02, tol_lin=1e-9)
+    st, info = O.solve_steady(prm, 3000, tol_steady=1e-6, div_stop=np.inf)
+    assert info["status"] == 0 and info["res"] < 1e-6
+    d = O.diagnostics(st, prm)
+    assert d["Nu_hot_max"] == pytest.approx(1.098, rel=1e-2)
+    assert 1.0 < d["Nu_hot_mean"] < d["Nu_hot_max"]
+    # steady heat balance: the flux through the mid-plane x = 1/2 matches the wall Nusselt number
+    flux = _midplane_heat_flux(st, 1.0 / (N - 1))
+    print("midplane", flux, d["Nu_hot_mean"])
+    assert abs(flux - d["Nu_hot_mean"]) / d["Nu_hot_mean"] < 2e-2
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("Ra,expect,dt", [(1e3, 1.098, 0.02), (1e4, 2.256, 0.004),
+                                          (1e5, 4.638, 5e-4)])
+def test_newtonian_limit_table2_51(Ra, expect, dt):
+    """Table 2 on its own grid (51^3, n = 1, Pr = 0.71): within 1.5 % of the printed values
+    (the paper's own gap to the two cited benchmarks is up to 0.99 %)."""
+    N = 51
+    h = 1.0 / (N - 1)
+    prm = O.Params(N=N, Ra=Ra, Pr=0.71, n=1.0, dt=dt, lam=0.9 * h * h / dt, tol_lin=1e-8)
+    st, info = O.solve_steady(prm, 200000, tol_steady=1e-6 * dt / 0.02, div_stop=np.inf)
+    assert info["status"] == 0
+    d = O.diagnostics(st, prm)
+    assert d["Nu_hot_max"] == pytest.approx(expect, rel=1.5e-2)
