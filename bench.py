@@ -1,0 +1,304 @@
+#!/usr/bin/env python
+"""Benchmark of the HOSC pseudo-time step on GB300: grid-point updates per second (GPUPS).
+
+One "step" is one pass of the whole hot path (viscosity, sources, compact right-hand sides,
+BiCGSTAB on the four systems, walls, divergence and pressure correction, steady-state change)
+over one cavity. GPUPS = (N - 2)^3 interior nodes x steps / second, summed over ranks.
+
+Workload (default): the single large cavity of the headline configuration, 101^3 nodes,
+n = 0.75, Ra = 1e5, Pr = 1, marched from rest (fluid at rest, theta = 1/2 inside) through a
+spin-up before the timed steps. The working set (> 500 MB of device arrays) is larger than the
+129 MB L2, so no flush is needed between steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "cavity101": dict(N=101, Ra=1e5, Pr=1.0, n=0.75, dt=5e-5, spinup=200,
+                      desc="single cavity 101^3, n=0.75, Ra=1e5, Pr=1 (power-law, shear-thinning)"),
+    "cavity41": dict(N=41, Ra=1e4, Pr=1.0, n=0.75, dt=5e-4, spinup=200,
+                     desc="cavity 41^3, n=0.75, Ra=1e4, Pr=1"),
+}
+ALG_WORDS = {  # algorithmic 8-byte words per interior node of one launch, all four systems active
+    "k_bicg_pv": 38, "k_bicg_st": 26, "k_bicg_xr": 32,
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for _, _, r in rows for q in range(4) if r[q].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args, wl):
+    """The oracle (plain FP64 CPU implementation) timed on the host cores: each step is one
+    pseudo-time step of a 51^3 cavity with the workload's physics (a bounded sample)."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import hosc_oracle as O
+    Ns = 51
+    h = 1.0 / (Ns - 1)
+    prm = O.Params(N=Ns, Ra=wl["Ra"], Pr=wl["Pr"], n=wl["n"], dt=wl["dt"] * 4,
+                   lam=0.25 * h * h / (wl["dt"] * 4), tol_lin=1e-10)
+    g = O.Grid(Ns)
+    st = O.initial_state(prm)
+    for _ in range(args.warmup):
+        st, _ = O.step(st, prm, g)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st, _ = O.step(st, prm, g)
+    dt = time.perf_counter() - t0
+    val = (Ns - 2) ** 3 * args.steps / dt
+    out = {"impl": "reference", "metric": "grid-point updates/s", "value": val, "unit": "GPUPS",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": wl["desc"], "sample": "%d^3 cavity, same physics" % Ns},
+           "cpu_baseline": {"value": val, "unit": "GPUPS", "cores": 1, "kind": "oracle",
+                            "sample": "%d oracle steps of a %d^3 cavity" % (args.steps, Ns)},
+           "e2e": {"value": val, "unit": "GPUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def cpu_baseline(cav, H, wl):
+    """One oracle step of the same 101^3 workload from the GPU's current state (with history)."""
+    import numpy as np
+    from oracle import hosc_oracle as O
+    N = wl["N"]
+    prm = O.Params(N=N, Ra=wl["Ra"], Pr=wl["Pr"], n=wl["n"], dt=wl["dt"],
+                   lam=cav.params.lambda_, tol_lin=cav.params.tol_lin)
+    st = dict(u=cav.get(H.HOSC_U), v=cav.get(H.HOSC_V), w=cav.get(H.HOSC_W),
+              th=cav.get(H.HOSC_THETA), p=cav.get(H.HOSC_P), steps=0,
+              prev=dict(L=cav.get(H.HOSC_PREV_L), u=cav.get(H.HOSC_PREV_U),
+                        v=cav.get(H.HOSC_PREV_V), w=cav.get(H.HOSC_PREV_W),
+                        Eu=cav.get(H.HOSC_PREV_EU), Ev=cav.get(H.HOSC_PREV_EV),
+                        Ew=cav.get(H.HOSC_PREV_EW)))
+    g = O.Grid(N)
+    t0 = time.perf_counter()
+    O.step(st, prm, g)
+    dt = time.perf_counter() - t0
+    return {"value": (N - 2) ** 3 / dt, "unit": "GPUPS", "cores": 1, "kind": "oracle",
+            "sample": "1 oracle step of the %d^3 workload from the GPU state (%.1f s)" % (N, dt)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cavity101", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2411_06563_gb300 import hosc as H
+
+    N = wl["N"]
+    h = 1.0 / (N - 1)
+    stream = torch.cuda.current_stream()
+    p = H.hosc_default_params(N, wl["Ra"], wl["Pr"], wl["n"])
+    p.dt = wl["dt"]
+    p.lambda_ = 0.25 * h * h / p.dt
+    p.tol_lin = 1e-10
+    p.cuda_stream = stream.cuda_stream
+    cav = H.Cavity(p, workspace="torch")
+    # spin-up from rest (untimed), then warm-up steps
+    info = cav.step(wl["spinup"])
+    assert info["call_status"] == 0, info
+    cav.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # ------------------------------------------------------------- timed region (device-resident)
+    l0 = cav.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        info = cav.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    launches = cav.kernel_launches() - l0
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    units = (N - 2) ** 3 * args.steps * ws
+    value = units / (ms * 1e-3)
+    lin_iters = info["lin_iters"]
+
+    # ------------------------------------------------------------- kernel breakdown (events)
+    H.hosc_profile_enable(cav.h, 1)
+    prof_steps = max(5, min(args.steps, 50))
+    cav.step(prof_steps)
+    names = ["k_viscosity", "k_sources", "k_rhs", "k_bicg_pv", "k_bicg_st", "k_bicg_xr", "update"]
+    kern = {}
+    for kid, name in enumerate(names):
+        _, kms, kl, kb = H.hosc_profile_read(cav.h, kid)
+        kern[name] = dict(ms=kms, launches=kl, bytes=kb)
+    H.hosc_profile_enable(cav.h, 0)
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    peak, peak_kind = _peaks()
+    d = kern[dom]
+    achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9 if d["ms"] > 0 else 0.0
+    total_ms = sum(k["ms"] for k in kern.values())
+
+    # ------------------------------------------------------------- end to end through host buffers
+    e2e_steps = max(3, min(args.steps // 10, 20))
+    n3 = N ** 3
+    which = [H.HOSC_U, H.HOSC_V, H.HOSC_W, H.HOSC_THETA, H.HOSC_P]
+    host = [torch.empty((N, N, N), dtype=torch.float64, pin_memory=True).numpy() for _ in which]
+    for a, w_ in zip(host, which):
+        H.hosc_get_field(cav.h, w_, a)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        for a, w_ in zip(host, which):
+            H.hosc_set_field(cav.h, w_, a)
+        H.hosc_step(cav.h, 1)
+        for a, w_ in zip(host, which):
+            H.hosc_get_field(cav.h, w_, a)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = (N - 2) ** 3 * e2e_steps * ws / e2e_s
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(cav, H, wl)
+
+    if rank == 0:
+        out = {
+            "metric": "grid-point updates/s", "value": value, "unit": "GPUPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl["desc"], "N": N, "Ra": wl["Ra"], "n": wl["n"],
+                       "Pr": wl["Pr"], "dt": wl["dt"], "precision": "fp64",
+                       "spinup_steps": wl["spinup"], "tol_lin": p.tol_lin,
+                       "bicgstab_iters_per_step": lin_iters / (4.0 * args.steps),
+                       "l2": "no flush: device working set %.0f MB > 129 MB L2"
+                             % (H.hosc_workspace_bytes(p) / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "peak_kind": peak_kind,
+                         "share": d["ms"] / total_ms if total_ms else None},
+            "kernels": {k: {"ms_per_step": v["ms"] / prof_steps, "launches": v["launches"],
+                            "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else 0.0}
+                        for k, v in kern.items()},
+            "clocks": clk.summary(),
+            "e2e": {"value": e2e_val, "unit": "GPUPS", "h2d_bytes_per_step": 5 * n3 * 8,
+                    "d2h_bytes_per_step": 5 * n3 * 8 + 64},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out))
+    cav.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

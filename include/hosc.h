@@ -1,0 +1,200 @@
+/*
+ * hosc.h -- C ABI of the GB300 (sm_103a) implementation of the higher-order super-compact (HOSC)
+ * implicit finite-difference scheme for 3D natural convection of power-law fluids in a
+ * differentially heated cubic cavity (Punia & Ray, arXiv:2411.06563).
+ *
+ * Problem (Sec. 2.1): dimensionless Boussinesq momentum, energy and continuity equations with the
+ * power-law stress tau* = 2 eta eps, eta = I2^((n-1)/2) (Eqs. 6-8), gravity along -y; hot wall
+ * theta = 1 at x = 0, cold wall theta = 0 at x = 1, the other walls adiabatic, no slip on every
+ * wall, zero normal pressure gradient on every wall. Parameters Ra, Pr and n (Sec. 2.1), the
+ * uniform N^3 node grid with h = k = l = 1/(N-1) and the pseudo-time step dt (Sec. 3.1).
+ *
+ * One pseudo-time step (Sec. 2.2):
+ *   S1  power-law viscosity eta and L = 1/(Pr eta) from the local strain rate (Eqs. 7-8);
+ *   S2  momentum sources E* (pressure gradient, eps . grad eta, buoyancy);
+ *   S3  the fourth-order compact right-hand sides of Eq. (5)/(6) for u, v, w and theta;
+ *   S4  the seven-point level-(n+1) operator of Eq. (5) (weights L1..L7 of Eq. 6);
+ *   S5  unpreconditioned BiCGSTAB on the four systems;
+ *   S6  wall conditions; S7 div V and the modified artificial-compressibility correction
+ *       p <- p - lambda div V (Sec. 2.2, last paragraph); S8 the steady-state change max|chi^{n+1}-chi^n|.
+ * Diagnostics (Sec. 4.2-4.3): local / average Nusselt numbers, entropy generation, Bejan number.
+ *
+ * Conventions
+ *  - Every call returns an hosc_status; nothing aborts and no C++ exception crosses the ABI.
+ *  - Fields are N^3 arrays of double, x fastest: node (i, j, k) at index i + N*(j + N*k),
+ *    x_i = i/(N-1), y_j = j/(N-1), z_k = k/(N-1).
+ *  - Host buffers passed in are owned by the caller and only read/written during the call.
+ *  - A context owns its device memory (or uses a caller-supplied device workspace) and all work
+ *    is enqueued on one CUDA stream (the caller's, or one it creates). A context must not be used
+ *    from two host threads at once; different contexts may run concurrently.
+ *  - Errors: HOSC_EINVAL for bad arguments (the context is unchanged), HOSC_ECUDA when a CUDA call
+ *    fails (the context should be destroyed), HOSC_ENOCONV / HOSC_EDIVERGED are numerical outcomes
+ *    reported by a step (the fields hold the state after that step).
+ */
+#ifndef HOSC_H
+#define HOSC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HOSC_OK = 0,
+  HOSC_EINVAL = 1,     /* invalid argument or parameter */
+  HOSC_ENOMEM = 2,     /* device or host allocation failed, or workspace too small */
+  HOSC_ECUDA = 3,      /* a CUDA runtime call failed */
+  HOSC_ENOCONV = 4,    /* BiCGSTAB reached max_lin_iter or broke down */
+  HOSC_EDIVERGED = 5,  /* a field became NaN or Inf */
+  HOSC_ESTEPLIMIT = 6, /* hosc_solve_steady reached max_steps before the steady criterion */
+  HOSC_ESTATE = 7      /* call not valid in the current state */
+} hosc_status;
+
+/* Arithmetic of the step. HOSC_FP64: every kernel in double. */
+typedef enum { HOSC_FP64 = 0, HOSC_MIXED = 1 } hosc_precision;
+
+/* Field selectors for hosc_get_field / hosc_set_field. */
+typedef enum {
+  HOSC_U = 0, HOSC_V = 1, HOSC_W = 2, HOSC_THETA = 3, HOSC_P = 4,
+  /* level-n quantities computed by a step (read-only) */
+  HOSC_ETA = 5,    /* apparent viscosity eta (S1) */
+  HOSC_LCOEF = 6,  /* L = 1/(Pr eta) (S1) */
+  HOSC_EU = 7, HOSC_EV = 8, HOSC_EW = 9, /* momentum sources E* (S2) */
+  HOSC_RHS_U = 10, HOSC_RHS_V = 11, HOSC_RHS_W = 12, HOSC_RHS_THETA = 13,
+      /* dt (R - B chi^n) at interior nodes, the right-hand side of the increment form of Eq. (6) (S3) */
+  HOSC_DX_U = 14, HOSC_DX_V = 15, HOSC_DX_W = 16, HOSC_DX_THETA = 17,
+      /* BiCGSTAB solution chi^{n+1} - chi^n of the last solve (S5) */
+  /* level n-1 history used by delta_t^- (settable, for restart / checkpoint) */
+  HOSC_PREV_L = 18, HOSC_PREV_U = 19, HOSC_PREV_V = 20, HOSC_PREV_W = 21,
+  HOSC_PREV_EU = 22, HOSC_PREV_EV = 23, HOSC_PREV_EW = 24,
+  HOSC_DIV = 25,   /* central div V^{n+1} at interior nodes (S7) */
+  HOSC_NFIELDS = 26
+} hosc_field;
+
+/* Stages of one step, for stage-by-stage use (tests, checkpointing). */
+typedef enum {
+  HOSC_STAGE_VISCOSITY = 0, /* S1: eta, L */
+  HOSC_STAGE_SOURCES = 1,   /* S2: E* of the three momentum equations */
+  HOSC_STAGE_RHS = 2,       /* S3/S4: right-hand sides and the level-(n+1) operators */
+  HOSC_STAGE_SOLVE = 3,     /* S5: BiCGSTAB on the four systems */
+  HOSC_STAGE_UPDATE = 4     /* S6-S8: increments, walls, div V, pressure, history */
+} hosc_stage;
+
+typedef struct {
+  int N;              /* nodes per side including walls, 5 <= N <= 1025 */
+  double Ra;          /* Rayleigh number (Sec. 2.1), >= 0 */
+  double Pr;          /* Prandtl number (Sec. 2.1), > 0 */
+  double n;           /* power-law index (Eq. 7), > 0 */
+  double dt;          /* pseudo-time step (Sec. 3.1 uses 0.02), > 0 */
+  double lambda;      /* relaxation of p <- p - lambda div V (Sec. 2.2), > 0 */
+  double theta_ref;   /* buoyancy reference temperature: the y source has Ra (theta - theta_ref)/eta */
+  double theta_init;  /* initial interior temperature (fluid at rest, constant pressure) */
+  double I2_eps;      /* regulariser: eta = (I2 + I2_eps)^((n-1)/2); unused when n == 1 */
+  double phi;         /* irreversibility distribution ratio of E_FF (Sec. 4.3), 1e-4 */
+  double tol_steady;  /* hosc_solve_steady stops when max|chi^{n+1}-chi^n| < tol_steady ... */
+  double tol_div;     /* ... and max|div V| < tol_div; the pressure is corrected when above it */
+  double tol_lin;     /* BiCGSTAB stops when ||r_k||_2 <= tol_lin ||r_0||_2 */
+  int max_lin_iter;   /* BiCGSTAB iteration limit per system and step, >= 1 */
+  int precision;      /* hosc_precision */
+  void* cuda_stream;  /* cudaStream_t to enqueue on, or NULL for a stream owned by the context */
+} hosc_params;
+
+typedef struct {
+  long steps;         /* steps taken by this call */
+  long lin_iters;     /* BiCGSTAB iterations summed over systems and steps of this call */
+  int last_iters[4];  /* iterations of the last step's u, v, w, theta solves */
+  double res_steady;  /* max over u, v, w, theta of max|chi^{n+1} - chi^n| of the last step */
+  double div_max;     /* max|div V^{n+1}| at interior nodes of the last step */
+  double lin_res;     /* largest ||r_k|| / ||r_0|| of the last step's four solves */
+  int status;         /* hosc_status of the last step */
+} hosc_info;
+
+typedef struct {
+  double Nu_hot_max;   /* max over z of Nu_avg(z) at x = 0 (the quantity of Table 2) */
+  double Nu_hot_mean;  /* surface mean of Nu_local at x = 0 */
+  double Nu_cold_mean; /* surface mean of -d theta/dx at x = 1 */
+  double E_total;      /* volume integral of E_local = E_HT + E_FF (Simpson) */
+  double E_HT;         /* volume integral of |grad theta|^2 */
+  double E_FF;         /* volume integral of phi eta I2 */
+  double Be;           /* E_HT / E_total */
+} hosc_diag;
+
+/* Fill *p with defaults for grid N and (Ra, Pr, n): dt = 0.02, lambda = 0.25 h^2/dt,
+ * theta_ref = theta_init = 0.5, I2_eps = 1e-10, phi = 1e-4, tol_steady = 1e-6, tol_div = 1e-6,
+ * tol_lin = 1e-10, max_lin_iter = 1000, HOSC_FP64, own stream. */
+hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, double n);
+
+/* Bytes of device workspace a context with these parameters needs (0 if invalid). */
+size_t hosc_workspace_bytes(const hosc_params* p);
+
+/* Create a context: validates *p, allocates device memory with cudaMalloc, sets the initial
+ * state (V = 0, p = 0, theta = theta_init inside with the wall temperatures). */
+hosc_status hosc_create(const hosc_params* p, void** ctx_out);
+
+/* As hosc_create but carves all device arrays out of a caller-owned device buffer of at least
+ * hosc_workspace_bytes(p) bytes, aligned to 256 bytes (e.g. a PyTorch allocation). The buffer
+ * must outlive the context. */
+hosc_status hosc_create_in(const hosc_params* p, void* dev_workspace, size_t bytes, void** ctx_out);
+
+/* Free everything the context owns. NULL is accepted. */
+void hosc_destroy(void* ctx);
+
+/* Back to the initial state (fields, history and step counter). */
+hosc_status hosc_reset(void* ctx);
+
+/* Take nsteps >= 1 pseudo-time steps. Enqueues the work and waits for it once at the end.
+ * Stops early at the first step whose status is not HOSC_OK and returns that status. */
+hosc_status hosc_step(void* ctx, int nsteps, hosc_info* out);
+
+/* Step until max|chi^{n+1}-chi^n| < tol_steady and max|div V| < tol_div (HOSC_OK) or max_steps
+ * (HOSC_ESTEPLIMIT) or a numerical failure. */
+hosc_status hosc_solve_steady(void* ctx, long max_steps, hosc_info* out);
+
+/* Run a single stage of the next step (see hosc_stage); stages must be run in order. */
+hosc_status hosc_run_stage(void* ctx, int stage, hosc_info* out);
+
+/* Diagnostics of the current fields (Sec. 4.2-4.3). nu_avg_z (N doubles) and fields (3 N^3
+ * doubles: E_HT, E_FF, E_local) are optional host outputs. */
+hosc_status hosc_diagnostics(void* ctx, hosc_diag* out, double* nu_avg_z, double* fields);
+
+/* Copy a field (hosc_field) to / from a host buffer of N^3 doubles. Setting U, V, W, THETA or P
+ * replaces the state as given (walls included); setting a PREV_* field marks the level n-1
+ * history as present (hosc_clear_history removes it, so delta_t^- = 0 at the next step). */
+hosc_status hosc_get_field(void* ctx, int which, double* host_out);
+hosc_status hosc_set_field(void* ctx, int which, const double* host_in);
+hosc_status hosc_clear_history(void* ctx);
+
+/* Copy a state field between the context and a device buffer of N^3 doubles on the context's
+ * stream (no synchronisation). */
+hosc_status hosc_get_field_device(void* ctx, int which, double* dev_out);
+hosc_status hosc_set_field_device(void* ctx, int which, const double* dev_in);
+
+/* Parameters the context runs with, and its stream (cudaStream_t). */
+hosc_status hosc_get_params(void* ctx, hosc_params* out);
+
+/* Per-launch timing of every kernel class with CUDA events on the context's stream (adds two event
+ * records per launch). enable(on != 0) resets the accumulators; read returns, for one kernel
+ * class, the summed event milliseconds, the launch count and the algorithmic bytes those launches
+ * moved (each array element read or written once per launch, counting only the systems still
+ * iterating). The algorithmic-byte counters run whether or not timing is on. Outputs may be NULL. */
+hosc_status hosc_profile_enable(void* ctx, int on);
+hosc_status hosc_profile_read(void* ctx, int kernel_id, double* total_ms, long* launches,
+                              double* alg_bytes);
+
+/* Kernel classes for hosc_profile_read. */
+enum { HOSC_K_VISC = 0, HOSC_K_SOURCES = 1, HOSC_K_RHS = 2, HOSC_K_BICG_PV = 3,
+       HOSC_K_BICG_ST = 4, HOSC_K_BICG_XR = 5, HOSC_K_UPDATE = 6, HOSC_K_COUNT = 7 };
+
+/* Number of kernel launches the library has made since the context was created. */
+long hosc_kernel_launches(void* ctx);
+
+const char* hosc_strerror(int status);
+
+/* Text of the last CUDA failure seen by this host thread (for HOSC_ECUDA / HOSC_ENOMEM). */
+const char* hosc_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HOSC_H */

@@ -1,0 +1,695 @@
+// C ABI of libhosc.so (declared in include/hosc.h): context lifetime, parameter validation, the
+// step driver (S1-S8 of one pseudo-time step of Punia & Ray, arXiv:2411.06563, Sec. 2.2), field
+// transfer and diagnostics. Host code only; the kernels live in hosc_step.cu, hosc_krylov.cu and
+// hosc_diag.cu.
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "hosc.h"
+#include "hosc_internal.h"
+
+using namespace hosc;
+
+namespace {
+
+thread_local char g_detail[256] = "";
+
+#define CU(call)                                                                  \
+  do {                                                                            \
+    cudaError_t e_ = (call);                                                      \
+    if (e_ != cudaSuccess) {                                                      \
+      snprintf(g_detail, sizeof(g_detail), "%s: %s", #call, cudaGetErrorString(e_)); \
+      return HOSC_ECUDA;                                                          \
+    }                                                                             \
+  } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kProfEvents = 8192;
+
+struct Ctx {
+  hosc_params prm;
+  DevParams P;
+  Fields F;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int cur = 0;
+  int stage = 0;            // next stage of the step in progress
+  long launches = 0;
+  KrylovScalars* h_ks = nullptr;
+  StepRecord* h_rec = nullptr;
+  double* h_scal = nullptr;
+  // per-launch event timing of every kernel class
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kid;                 // kernel class of each recorded pair
+  int ev_used = 0;
+  double prof_ms[HOSC_K_COUNT] = {0};
+  long prof_launches[HOSC_K_COUNT] = {0};
+  double host_bytes[HOSC_K_COUNT] = {0};   // algorithmic bytes of the fixed-work kernels
+};
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+hosc_status validate(const hosc_params* p) {
+  if (!p) return HOSC_EINVAL;
+  if (p->N < 5 || p->N > 1025) return HOSC_EINVAL;
+  if (!(p->Ra >= 0.0) || !(p->Pr > 0.0) || !(p->n > 0.0) || !(p->dt > 0.0)) return HOSC_EINVAL;
+  if (!(p->lambda > 0.0) || !(p->tol_lin > 0.0) || p->max_lin_iter < 1) return HOSC_EINVAL;
+  if (!(p->I2_eps >= 0.0) || (p->n != 1.0 && p->n < 1.0 && !(p->I2_eps > 0.0))) return HOSC_EINVAL;
+  if (!(p->phi >= 0.0) || !(p->tol_div >= 0.0) || !(p->tol_steady >= 0.0)) return HOSC_EINVAL;
+  if (!isfinite(p->theta_ref) || !isfinite(p->theta_init)) return HOSC_EINVAL;
+  if (p->precision != HOSC_FP64) return HOSC_EINVAL;
+  return HOSC_OK;
+}
+
+DevParams device_params(const hosc_params& p, int have_prev) {
+  DevParams d;
+  d.N = p.N;
+  d.newtonian = (p.n == 1.0);
+  d.have_prev = have_prev;
+  d.max_lin_iter = p.max_lin_iter;
+  d.h = 1.0 / (p.N - 1);
+  d.h2 = d.h * d.h;
+  d.Ra = p.Ra;
+  d.Pr = p.Pr;
+  d.n = p.n;
+  d.dt = p.dt;
+  d.lambda = p.lambda;
+  d.theta_ref = p.theta_ref;
+  d.I2_eps = p.I2_eps;
+  d.phi = p.phi;
+  d.tol_div = p.tol_div;
+  d.tol_lin = p.tol_lin;
+  return d;
+}
+
+double* field_ptr(Ctx* c, int which) {
+  Fields& F = c->F;
+  const int o = 1 - c->cur;
+  switch (which) {
+    case HOSC_U: return F.u[c->cur];
+    case HOSC_V: return F.v[c->cur];
+    case HOSC_W: return F.w[c->cur];
+    case HOSC_THETA: return F.th;
+    case HOSC_P: return F.p;
+    case HOSC_ETA: return F.eta;
+    case HOSC_LCOEF: return F.L[c->cur];
+    case HOSC_EU: return F.Eu[c->cur];
+    case HOSC_EV: return F.Ev[c->cur];
+    case HOSC_EW: return F.Ew[c->cur];
+    case HOSC_RHS_U: case HOSC_RHS_V: case HOSC_RHS_W: case HOSC_RHS_THETA:
+      return F.rhs[which - HOSC_RHS_U];
+    case HOSC_DX_U: case HOSC_DX_V: case HOSC_DX_W: case HOSC_DX_THETA:
+      return F.x[which - HOSC_DX_U];
+    case HOSC_PREV_L: return F.L[o];
+    case HOSC_PREV_U: return F.u[o];
+    case HOSC_PREV_V: return F.v[o];
+    case HOSC_PREV_W: return F.w[o];
+    case HOSC_PREV_EU: return F.Eu[o];
+    case HOSC_PREV_EV: return F.Ev[o];
+    case HOSC_PREV_EW: return F.Ew[o];
+    case HOSC_DIV: return F.div;
+    default: return nullptr;
+  }
+}
+
+bool settable(int which) {
+  return (which >= HOSC_U && which <= HOSC_P) || (which >= HOSC_PREV_L && which <= HOSC_PREV_EW);
+}
+
+hosc_status prof_fold(Ctx* c);
+
+void prof_begin(Ctx* c, int kid) {
+  if (!c->prof_on) return;
+  if (c->ev_used + 2 > (int)c->ev.size()) prof_fold(c);   // pool full: fold (waits) and reuse
+  c->ev_kid[c->ev_used / 2] = kid;
+  cudaEventRecord(c->ev[c->ev_used], c->stream);
+}
+void prof_end(Ctx* c, int kid) {
+  if (!c->prof_on) return;
+  cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
+  c->ev_used += 2;
+}
+
+// Fold recorded event pairs into the accumulators (waits for them).
+hosc_status prof_fold(Ctx* c) {
+  for (int q = 0; q + 1 < c->ev_used; q += 2) {
+    CU(cudaEventSynchronize(c->ev[q + 1]));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev[q], c->ev[q + 1]));
+    const int kid = c->ev_kid[q / 2];
+    c->prof_ms[kid] += ms;
+    c->prof_launches[kid] += 1;
+  }
+  c->ev_used = 0;
+  return HOSC_OK;
+}
+
+hosc_status set_initial_state(Ctx* c) {
+  CU(cudaSetDevice(c->device));
+  CU(cudaMemsetAsync(c->ws, 0, c->ws_bytes, c->stream));
+  const int N = c->prm.N;
+  std::vector<double> th((size_t)N * N * N);
+  for (int k = 0; k < N; ++k)
+    for (int j = 0; j < N; ++j)
+      for (int i = 0; i < N; ++i) {
+        double v = c->prm.theta_init;
+        if (i == 0) v = 1.0;
+        if (i == N - 1) v = 0.0;
+        th[i + (size_t)N * (j + (size_t)N * k)] = v;
+      }
+  CU(cudaMemcpyAsync(c->F.th, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  c->cur = 0;
+  c->stage = 0;
+  c->P = device_params(c->prm, 0);
+  return HOSC_OK;
+}
+
+hosc_status check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_detail, sizeof(g_detail), "kernel launch: %s", cudaGetErrorString(e));
+    return HOSC_ECUDA;
+  }
+  return HOSC_OK;
+}
+
+// BiCGSTAB on the four systems; the host checks the done flags every few iterations.
+hosc_status solve(Ctx* c) {
+  const DevParams& P = c->P;
+  const Fields& F = c->F;
+  launch_bicg_init(P, F, c->stream);
+  c->launches += 1;
+  int pp = 0, it = 0, check = 4;
+  while (it < P.max_lin_iter) {
+    const int chunk = (P.max_lin_iter - it < check) ? P.max_lin_iter - it : check;
+    for (int q = 0; q < chunk; ++q) {
+      prof_begin(c, HOSC_K_BICG_PV);
+      launch_bicg_pv(P, F, pp, c->stream);
+      prof_end(c, HOSC_K_BICG_PV);
+      prof_begin(c, HOSC_K_BICG_ST);
+      launch_bicg_st(P, F, pp, c->stream);
+      prof_end(c, HOSC_K_BICG_ST);
+      prof_begin(c, HOSC_K_BICG_XR);
+      launch_bicg_xr(P, F, pp, c->stream);
+      prof_end(c, HOSC_K_BICG_XR);
+      pp ^= 1;
+    }
+    c->launches += 3L * chunk;
+    it += chunk;
+    hosc_status st = check_launch();
+    if (st) return st;
+    CU(cudaMemcpyAsync(c->h_ks, F.ks, 4 * sizeof(KrylovScalars), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (c->h_ks[0].done && c->h_ks[1].done && c->h_ks[2].done && c->h_ks[3].done) break;
+    if (check < 16) check *= 2;
+  }
+  return HOSC_OK;
+}
+
+hosc_status run_stage(Ctx* c, int stage) {
+  if (stage != c->stage) return HOSC_ESTATE;
+  const Fields& F = c->F;
+  const double N = c->P.N, n3 = N * N * N, ni3 = (N - 2) * (N - 2) * (N - 2);
+  hosc_status st = HOSC_OK;
+  switch (stage) {
+    case HOSC_STAGE_VISCOSITY:
+      prof_begin(c, HOSC_K_VISC);
+      launch_viscosity(c->P, F, c->cur, c->stream);
+      prof_end(c, HOSC_K_VISC);
+      c->launches += 1;
+      c->host_bytes[HOSC_K_VISC] += 8.0 * n3 * 5;          // u, v, w -> eta, L
+      break;
+    case HOSC_STAGE_SOURCES:
+      prof_begin(c, HOSC_K_SOURCES);
+      launch_sources(c->P, F, c->cur, c->stream);
+      prof_end(c, HOSC_K_SOURCES);
+      c->launches += 1;
+      c->host_bytes[HOSC_K_SOURCES] += 8.0 * n3 * 9;       // u, v, w, theta, p, eta -> E*x3
+      break;
+    case HOSC_STAGE_RHS:
+      prof_begin(c, HOSC_K_RHS);
+      launch_rhs(c->P, F, c->cur, c->stream);
+      prof_end(c, HOSC_K_RHS);
+      c->launches += 1;
+      // reads L, u, v, w, theta, E*x3 (+ 7 history arrays), writes rhs x4 and 14 weights
+      c->host_bytes[HOSC_K_RHS] += 8.0 * ni3 * (8 + (c->P.have_prev ? 7 : 0) + 18);
+      break;
+    case HOSC_STAGE_SOLVE:
+      st = solve(c);
+      break;
+    case HOSC_STAGE_UPDATE:
+      prof_begin(c, HOSC_K_UPDATE);
+      launch_update(c->P, F, c->cur, c->stream);
+      prof_end(c, HOSC_K_UPDATE);
+      c->launches += 6;
+      // increments: x4 + u, v, w, theta read, u, v, w, theta written; div: V read, div written;
+      // pressure: p, div read, p written
+      c->host_bytes[HOSC_K_UPDATE] += 8.0 * (n3 * 12 + ni3 * 4 + ni3 * 3);
+      break;
+    default:
+      return HOSC_EINVAL;
+  }
+  if (st) return st;
+  st = check_launch();
+  if (st) return st;
+  if (stage == HOSC_STAGE_UPDATE) {
+    c->cur = 1 - c->cur;
+    c->P.have_prev = 1;
+    c->stage = 0;
+  } else {
+    c->stage = stage + 1;
+  }
+  return HOSC_OK;
+}
+
+hosc_status read_record(Ctx* c, hosc_info* info) {
+  CU(cudaMemcpyAsync(c->h_rec, c->F.rec, sizeof(StepRecord), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (info) {
+    for (int s = 0; s < 4; ++s) info->last_iters[s] = c->h_rec->iters[s];
+    info->res_steady = c->h_rec->res;
+    info->div_max = c->h_rec->div_max;
+    info->lin_res = c->h_rec->lin_res;
+    info->status = c->h_rec->status;
+  }
+  return HOSC_OK;
+}
+
+hosc_status one_step(Ctx* c, hosc_info* info) {
+  for (int s = 0; s < 5; ++s) {
+    hosc_status st = run_stage(c, s);
+    if (st) return st;
+  }
+  hosc_status st = read_record(c, info);
+  if (st) return st;
+  if (info) {
+    info->steps += 1;
+    for (int s = 0; s < 4; ++s) info->lin_iters += c->h_rec->iters[s];
+  }
+  return (hosc_status)c->h_rec->status;
+}
+
+hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** out) {
+  if (!out) return HOSC_EINVAL;
+  *out = nullptr;
+  hosc_status st = validate(p);
+  if (st) return st;
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return HOSC_ENOMEM;
+  c->prm = *p;
+  const size_t need = workspace_layout(p->N, nullptr, nullptr);
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) {
+    if (dev_ws) {
+      if (bytes < need || ((uintptr_t)dev_ws % kAlign) != 0) {
+        delete c;
+        return bytes < need ? HOSC_ENOMEM : HOSC_EINVAL;
+      }
+      c->ws = (char*)dev_ws;
+      c->own_ws = false;
+    } else {
+      e = cudaMalloc(&c->ws, need);
+      if (e != cudaSuccess) {
+        snprintf(g_detail, sizeof(g_detail), "cudaMalloc(%zu): %s", need, cudaGetErrorString(e));
+        delete c;
+        return HOSC_ENOMEM;
+      }
+      c->own_ws = true;
+    }
+    c->ws_bytes = need;
+    workspace_layout(p->N, &c->F, c->ws);
+    if (p->cuda_stream) {
+      c->stream = (cudaStream_t)p->cuda_stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+      c->own_stream = (e == cudaSuccess);
+    }
+  }
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_ks, 4 * sizeof(KrylovScalars));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_rec, sizeof(StepRecord));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_scal, 8 * sizeof(double));
+  if (e != cudaSuccess) {
+    snprintf(g_detail, sizeof(g_detail), "create: %s", cudaGetErrorString(e));
+    hosc_destroy(c);
+    return HOSC_ECUDA;
+  }
+  st = set_initial_state(c);
+  if (st) {
+    hosc_destroy(c);
+    return st;
+  }
+  *out = c;
+  return HOSC_OK;
+}
+
+}  // namespace
+
+namespace hosc {
+
+size_t workspace_layout(int N, Fields* f, char* base) {
+  const size_t n3 = (size_t)N * N * N;
+  const size_t fb = align_up(n3 * sizeof(double));
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  Fields tmp;
+  Fields& F = f ? *f : tmp;
+  auto fld = [&]() { return (double*)take(fb); };
+  for (int b = 0; b < 2; ++b) {
+    F.u[b] = fld();
+    F.v[b] = fld();
+    F.w[b] = fld();
+    F.L[b] = fld();
+    F.Eu[b] = fld();
+    F.Ev[b] = fld();
+    F.Ew[b] = fld();
+  }
+  F.th = fld();
+  F.p = fld();
+  F.eta = fld();
+  for (int q = 0; q < 7; ++q) F.Am[q] = fld();
+  for (int q = 0; q < 7; ++q) F.Ae[q] = fld();
+  for (int s = 0; s < 4; ++s) {
+    F.rhs[s] = fld();
+    F.x[s] = fld();
+    F.r[s] = fld();
+    F.t[s] = fld();
+    for (int b = 0; b < 2; ++b) {
+      F.pk[b][s] = fld();
+      F.vk[b][s] = fld();
+    }
+  }
+  F.div = fld();
+  F.eloc = (double*)take(3 * n3 * sizeof(double));
+  F.red = (double*)take((size_t)red_blocks((long)n3) * kRedSlots * sizeof(double));
+  F.counter = (unsigned int*)take(sizeof(unsigned int));
+  F.ks = (KrylovScalars*)take(4 * sizeof(KrylovScalars));
+  F.rec = (StepRecord*)take(sizeof(StepRecord));
+  F.diag_scal = (double*)take(8 * sizeof(double));
+  F.nu_hot = (double*)take((size_t)N * N * sizeof(double));
+  F.nu_cold = (double*)take((size_t)N * N * sizeof(double));
+  F.nu_avg = (double*)take((size_t)N * sizeof(double));
+  F.alg_bytes = (double*)take(HOSC_K_COUNT * sizeof(double));
+  return off;
+}
+
+}  // namespace hosc
+
+extern "C" {
+
+hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, double n) {
+  if (!p || N < 5) return HOSC_EINVAL;
+  memset(p, 0, sizeof(*p));
+  const double h = 1.0 / (N - 1);
+  p->N = N;
+  p->Ra = Ra;
+  p->Pr = Pr;
+  p->n = n;
+  p->dt = 0.02;
+  p->lambda = 0.25 * h * h / p->dt;
+  p->theta_ref = 0.5;
+  p->theta_init = 0.5;
+  p->I2_eps = 1e-10;
+  p->phi = 1e-4;
+  p->tol_steady = 1e-6;
+  p->tol_div = 1e-6;
+  p->tol_lin = 1e-10;
+  p->max_lin_iter = 1000;
+  p->precision = HOSC_FP64;
+  p->cuda_stream = nullptr;
+  return HOSC_OK;
+}
+
+size_t hosc_workspace_bytes(const hosc_params* p) {
+  if (validate(p) != HOSC_OK) return 0;
+  return workspace_layout(p->N, nullptr, nullptr);
+}
+
+hosc_status hosc_create(const hosc_params* p, void** ctx_out) {
+  return make_ctx(p, nullptr, 0, ctx_out);
+}
+
+hosc_status hosc_create_in(const hosc_params* p, void* dev_workspace, size_t bytes,
+                           void** ctx_out) {
+  if (!dev_workspace) return HOSC_EINVAL;
+  return make_ctx(p, dev_workspace, bytes, ctx_out);
+}
+
+void hosc_destroy(void* ctx) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  if (c->own_ws && c->ws) cudaFree(c->ws);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  if (c->h_ks) cudaFreeHost(c->h_ks);
+  if (c->h_rec) cudaFreeHost(c->h_rec);
+  if (c->h_scal) cudaFreeHost(c->h_scal);
+  delete c;
+}
+
+hosc_status hosc_reset(void* ctx) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  return set_initial_state(c);
+}
+
+hosc_status hosc_step(void* ctx, int nsteps, hosc_info* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || nsteps < 1) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  hosc_info info;
+  memset(&info, 0, sizeof(info));
+  hosc_status st = HOSC_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    st = one_step(c, &info);
+    if (st) break;
+  }
+  if (out) *out = info;
+  return st;
+}
+
+hosc_status hosc_solve_steady(void* ctx, long max_steps, hosc_info* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || max_steps < 1) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  hosc_info info;
+  memset(&info, 0, sizeof(info));
+  hosc_status st = HOSC_ESTEPLIMIT;
+  for (long s = 0; s < max_steps; ++s) {
+    hosc_status q = one_step(c, &info);
+    if (q) {
+      st = q;
+      break;
+    }
+    if (info.res_steady < c->prm.tol_steady && info.div_max < c->prm.tol_div) {
+      st = HOSC_OK;
+      break;
+    }
+  }
+  if (out) *out = info;
+  return st;
+}
+
+hosc_status hosc_run_stage(void* ctx, int stage, hosc_info* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || stage < 0 || stage > HOSC_STAGE_UPDATE) return HOSC_EINVAL;
+  CU(cudaSetDevice(c->device));
+  hosc_status st = run_stage(c, stage);
+  if (st) return st;
+  if (stage == HOSC_STAGE_SOLVE) {
+    CU(cudaMemcpyAsync(c->h_ks, c->F.ks, 4 * sizeof(KrylovScalars), cudaMemcpyDeviceToHost,
+                       c->stream));
+  }
+  CU(cudaStreamSynchronize(c->stream));
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    if (stage == HOSC_STAGE_SOLVE) {
+      for (int s = 0; s < 4; ++s) {
+        out->last_iters[s] = c->h_ks[s].iters;
+        out->lin_iters += c->h_ks[s].iters;
+        if (c->h_ks[s].status) out->status = HOSC_ENOCONV;
+      }
+    }
+    if (stage == HOSC_STAGE_UPDATE) {
+      st = read_record(c, out);
+      if (st) return st;
+      out->steps = 1;
+    }
+  }
+  return HOSC_OK;
+}
+
+hosc_status hosc_diagnostics(void* ctx, hosc_diag* out, double* nu_avg_z, double* fields) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !out) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  const int N = c->prm.N;
+  launch_diagnostics(c->P, c->F, c->cur, fields != nullptr, c->stream);
+  c->launches += 3;
+  hosc_status st = check_launch();
+  if (st) return st;
+  CU(cudaMemcpyAsync(c->h_scal, c->F.diag_scal, 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                     c->stream));
+  if (nu_avg_z)
+    CU(cudaMemcpyAsync(nu_avg_z, c->F.nu_avg, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (fields)
+    CU(cudaMemcpyAsync(fields, c->F.eloc, 3 * (size_t)N * N * N * sizeof(double),
+                       cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  const double* s = c->h_scal;
+  out->Nu_hot_max = s[0];
+  out->Nu_hot_mean = s[1];
+  out->Nu_cold_mean = s[2];
+  out->E_HT = s[3];
+  out->E_FF = s[4];
+  out->E_total = s[3] + s[4];
+  out->Be = s[3] / (s[3] + s[4]);
+  return HOSC_OK;
+}
+
+hosc_status hosc_get_field(void* ctx, int which, double* host_out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !host_out) return HOSC_EINVAL;
+  double* d = field_ptr(c, which);
+  if (!d) return HOSC_EINVAL;
+  CU(cudaSetDevice(c->device));
+  const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
+  CU(cudaMemcpyAsync(host_out, d, n3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return HOSC_OK;
+}
+
+hosc_status hosc_set_field(void* ctx, int which, const double* host_in) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !host_in || !settable(which)) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
+  CU(cudaMemcpyAsync(field_ptr(c, which), host_in, n3 * sizeof(double), cudaMemcpyHostToDevice,
+                     c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  if (which >= HOSC_PREV_L) c->P.have_prev = 1;
+  return HOSC_OK;
+}
+
+hosc_status hosc_clear_history(void* ctx) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  c->P.have_prev = 0;
+  return HOSC_OK;
+}
+
+hosc_status hosc_get_field_device(void* ctx, int which, double* dev_out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !dev_out) return HOSC_EINVAL;
+  double* d = field_ptr(c, which);
+  if (!d) return HOSC_EINVAL;
+  CU(cudaSetDevice(c->device));
+  const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
+  CU(cudaMemcpyAsync(dev_out, d, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  return HOSC_OK;
+}
+
+hosc_status hosc_set_field_device(void* ctx, int which, const double* dev_in) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !dev_in || !settable(which)) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
+  CU(cudaMemcpyAsync(field_ptr(c, which), dev_in, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                     c->stream));
+  if (which >= HOSC_PREV_L) c->P.have_prev = 1;
+  return HOSC_OK;
+}
+
+hosc_status hosc_get_params(void* ctx, hosc_params* out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !out) return HOSC_EINVAL;
+  *out = c->prm;
+  out->cuda_stream = (void*)c->stream;
+  return HOSC_OK;
+}
+
+hosc_status hosc_profile_enable(void* ctx, int on) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  CU(cudaMemsetAsync(c->F.alg_bytes, 0, HOSC_K_COUNT * sizeof(double), c->stream));
+  if (on && c->ev.empty()) {
+    c->ev.resize(kProfEvents);
+    c->ev_kid.resize(kProfEvents / 2);
+    for (auto& e : c->ev) CU(cudaEventCreate(&e));
+  }
+  c->prof_on = on != 0;
+  c->ev_used = 0;
+  for (int k = 0; k < HOSC_K_COUNT; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_launches[k] = 0;
+    c->host_bytes[k] = 0.0;
+  }
+  return HOSC_OK;
+}
+
+hosc_status hosc_profile_read(void* ctx, int kernel_id, double* total_ms, long* launches,
+                              double* alg_bytes) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || kernel_id < 0 || kernel_id >= HOSC_K_COUNT) return HOSC_EINVAL;
+  CU(cudaSetDevice(c->device));
+  hosc_status st = prof_fold(c);
+  if (st) return st;
+  if (total_ms) *total_ms = c->prof_ms[kernel_id];
+  if (launches) *launches = c->prof_launches[kernel_id];
+  if (alg_bytes) {
+    double b[HOSC_K_COUNT];
+    CU(cudaMemcpyAsync(b, c->F.alg_bytes, sizeof(b), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    *alg_bytes = b[kernel_id] + c->host_bytes[kernel_id];
+  }
+  return HOSC_OK;
+}
+
+long hosc_kernel_launches(void* ctx) {
+  Ctx* c = (Ctx*)ctx;
+  return c ? c->launches : -1;
+}
+
+const char* hosc_last_error_detail(void) { return g_detail; }
+
+const char* hosc_strerror(int status) {
+  switch (status) {
+    case HOSC_OK: return "ok";
+    case HOSC_EINVAL: return "invalid argument";
+    case HOSC_ENOMEM: return "out of memory or workspace too small";
+    case HOSC_ECUDA: return "CUDA runtime error";
+    case HOSC_ENOCONV: return "BiCGSTAB did not converge (iteration limit or breakdown)";
+    case HOSC_EDIVERGED: return "a field became NaN or Inf";
+    case HOSC_ESTEPLIMIT: return "step limit reached before steady state";
+    case HOSC_ESTATE: return "call not valid in the current state";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

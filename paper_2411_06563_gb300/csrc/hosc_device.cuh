@@ -1,0 +1,129 @@
+// Device helpers shared by the kernels of libhosc.so: indexing, one-sided / central gradients,
+// block reductions and the last-block reduction of per-block partials.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "hosc_internal.h"
+
+namespace hosc {
+
+__device__ __forceinline__ long node(int i, int j, int k, int N) {
+  return (long)i + (long)N * ((long)j + (long)N * (long)k);
+}
+
+// Derivative along one axis at a node whose coordinate along that axis is a (0..N-1); st is the
+// memory stride of that axis. Central inside, second-order one-sided at the two walls.
+__device__ __forceinline__ double grad_axis(const double* __restrict__ f, long c, int a, int N,
+                                            long st, double inv2h) {
+  if (a == 0) return (-3.0 * f[c] + 4.0 * f[c + st] - f[c + 2 * st]) * inv2h;
+  if (a == N - 1) return (3.0 * f[c] - 4.0 * f[c - st] + f[c - 2 * st]) * inv2h;
+  return (f[c + st] - f[c - st]) * inv2h;
+}
+
+struct Grad9 {
+  double ux, uy, uz, vx, vy, vz, wx, wy, wz;
+};
+
+__device__ __forceinline__ Grad9 velocity_gradients(const double* __restrict__ u,
+                                                    const double* __restrict__ v,
+                                                    const double* __restrict__ w, int i, int j,
+                                                    int k, int N, double inv2h) {
+  const long c = node(i, j, k, N);
+  const long sy = N, sz = (long)N * N;
+  Grad9 g;
+  g.ux = grad_axis(u, c, i, N, 1, inv2h);
+  g.uy = grad_axis(u, c, j, N, sy, inv2h);
+  g.uz = grad_axis(u, c, k, N, sz, inv2h);
+  g.vx = grad_axis(v, c, i, N, 1, inv2h);
+  g.vy = grad_axis(v, c, j, N, sy, inv2h);
+  g.vz = grad_axis(v, c, k, N, sz, inv2h);
+  g.wx = grad_axis(w, c, i, N, 1, inv2h);
+  g.wy = grad_axis(w, c, j, N, sy, inv2h);
+  g.wz = grad_axis(w, c, k, N, sz, inv2h);
+  return g;
+}
+
+// Second invariant of the strain-rate tensor, Eq. (8).
+__device__ __forceinline__ double second_invariant(const Grad9& g) {
+  const double a = g.uz + g.wx, b = g.uy + g.vx, c = g.vz + g.wy;
+  return 2.0 * (g.ux * g.ux + g.vy * g.vy + g.wz * g.wz) + a * a + b * b + c * c;
+}
+
+// ----------------------------------------------------------------------------- reductions
+
+template <int M>
+__device__ __forceinline__ void warp_sum(double (&v)[M]) {
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[m] += __shfl_down_sync(0xffffffffu, v[m], off);
+}
+
+template <int M>
+__device__ __forceinline__ void warp_max(double (&v)[M]) {
+#pragma unroll
+  for (int m = 0; m < M; ++m)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[m] = fmax(v[m], __shfl_down_sync(0xffffffffu, v[m], off));
+}
+
+// Sum (or max) of M values over the block; the result is valid in thread 0. Fixed order, so the
+// result is the same run to run for the same launch shape. smem: >= 32*M doubles.
+template <int M, bool IsMax>
+__device__ __forceinline__ void block_reduce(double (&v)[M], double* smem) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  if (IsMax) warp_max<M>(v); else warp_sum<M>(v);
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) smem[wid * M + m] = v[m];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = (lane < nw) ? smem[lane * M + m] : (IsMax ? 0.0 : 0.0);
+    if (IsMax) warp_max<M>(v); else warp_sum<M>(v);
+  }
+  __syncthreads();
+}
+
+// Publish this block's M partials (valid in thread 0) and report whether this block is the last
+// one of the grid to do so. No thread waits on another block: the last block to take a ticket
+// does the final reduction, every other block simply exits.
+template <int M>
+__device__ __forceinline__ bool publish_is_last(const double (&v)[M], double* red,
+                                                unsigned int* counter) {
+  __shared__ int s_last;
+  if (threadIdx.x == 0) {
+    const unsigned int b = blockIdx.x;
+#pragma unroll
+    for (int m = 0; m < M; ++m) red[(long)b * kRedSlots + m] = v[m];
+    __threadfence();
+    const unsigned int ticket = atomicAdd(counter, 1u);
+    s_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  return s_last != 0;
+}
+
+// In the last block: reduce the partials of all blocks in a fixed order (valid in thread 0) and
+// re-arm the ticket counter for the next kernel.
+template <int M, bool IsMax>
+__device__ __forceinline__ void reduce_partials(double (&tot)[M], const double* red, int nblocks,
+                                                unsigned int* counter, double* smem) {
+  __threadfence();
+#pragma unroll
+  for (int m = 0; m < M; ++m) tot[m] = 0.0;
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const double x = __ldcg(red + (long)b * kRedSlots + m);
+      tot[m] = IsMax ? fmax(tot[m], x) : tot[m] + x;
+    }
+  }
+  block_reduce<M, IsMax>(tot, smem);
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
+}  // namespace hosc

@@ -1,0 +1,256 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element, on
+seeded synthetic states. One row of the hot path per check:
+
+  S1 viscosity eta, L      S2 momentum sources E*      S3 right-hand sides dt (R - B chi^n)
+  S4/S5 the level-(n+1) operator and BiCGSTAB (GPU increment vs oracle direct solve; oracle
+        operator applied to the GPU increment reproduces the GPU right-hand side)
+  S6-S8 one full step (u, v, w, theta, p), multi-step trajectories, diagnostics.
+
+Tolerances (FP64 both sides): relative to the largest magnitude of the compared quantity,
+1e-13 for eta and L, 1e-12 for E* (one division and a few products), 1e-11 for the right-hand
+sides (19-point sums of O(1/h^4)-weighted terms), 1e-9 for the BiCGSTAB increment solved to
+1e-13 against a direct solve, and 1e-10 for the fields after a step (the all-FP64 target).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import hosc_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+hosc = pytest.importorskip("paper_2411_06563_gb300.hosc")
+from paper_2411_06563_gb300 import inputs  # noqa: E402
+
+H = hosc
+
+
+def _rel(a, b):
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return float(np.max(np.abs(a - b)) / scale)
+
+
+def _params(N, Ra, n, dt=0.01, Pr=1.0, tol_lin=1e-13, **kw):
+    p = H.hosc_default_params(N, Ra, Pr, n)
+    p.dt = dt
+    p.lambda_ = 0.25 / (N - 1) ** 2 / dt
+    p.tol_lin = tol_lin
+    p.max_lin_iter = 3000
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def _oracle_params(p):
+    return O.Params(N=p.N, Ra=p.Ra, Pr=p.Pr, n=p.n, dt=p.dt, lam=p.lambda_,
+                    theta_ref=p.theta_ref, I2_eps=p.I2_eps, phi=p.phi, tol_div=p.tol_div,
+                    tol_lin=p.tol_lin, max_lin_iter=p.max_lin_iter, theta_init=p.theta_init)
+
+
+def _setup(N, Ra, n, seed, history, **kw):
+    p = _params(N, Ra, n, **kw)
+    op = _oracle_params(p)
+    st = inputs.cavity_state(N, Ra, seed)
+    state = dict(st, prev=None, steps=0)
+    cav = H.Cavity(p)
+    for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W), ("th", H.HOSC_THETA),
+                        ("p", H.HOSC_P)):
+        cav.set(which, st[name])
+    if history:
+        old = inputs.perturbed(st, seed + 1000)
+        lev = O.level_coefficients(dict(old, prev=None), op)
+        prev = dict(L=lev["L"], u=old["u"], v=old["v"], w=old["w"], Eu=lev["Eu"], Ev=lev["Ev"],
+                    Ew=lev["Ew"])
+        state["prev"] = prev
+        for key, which in (("L", H.HOSC_PREV_L), ("u", H.HOSC_PREV_U), ("v", H.HOSC_PREV_V),
+                           ("w", H.HOSC_PREV_W), ("Eu", H.HOSC_PREV_EU), ("Ev", H.HOSC_PREV_EV),
+                           ("Ew", H.HOSC_PREV_EW)):
+            cav.set(which, prev[key])
+    return p, op, state, cav
+
+
+CASES = [(7, 1e3, 1.0, True), (13, 1e4, 0.75, True), (13, 5e3, 1.25, False),
+         (22, 1e4, 0.8, True), (22, 2e3, 1.0, False)]
+
+
+@pytest.mark.parametrize("N,Ra,n,history", CASES)
+def test_stage_parity(N, Ra, n, history):
+    p, op, state, cav = _setup(N, Ra, n, seed=N * 7 + int(n * 100), history=history, dt=0.004)
+    g = O.Grid(N)
+    ii = g.int_idx
+    with cav:
+        # S1
+        cav.run_stage(H.HOSC_STAGE_VISCOSITY)
+        eta_o, _, gr = O.viscosity(state["u"], state["v"], state["w"], op)
+        assert _rel(cav.get(H.HOSC_ETA), eta_o) < 1e-13
+        assert _rel(cav.get(H.HOSC_LCOEF), 1.0 / (op.Pr * eta_o)) < 1e-13
+        # S2
+        cav.run_stage(H.HOSC_STAGE_SOURCES)
+        Eu, Ev, Ew = O.momentum_sources(state["u"], state["v"], state["w"], state["th"],
+                                        state["p"], eta_o, gr, op)
+        for which, ref in ((H.HOSC_EU, Eu), (H.HOSC_EV, Ev), (H.HOSC_EW, Ew)):
+            assert _rel(cav.get(which), ref) < 1e-12
+        # S3
+        cav.run_stage(H.HOSC_STAGE_RHS)
+        lev = O.level_coefficients(state, op)
+        coefs = O._system_coefficients(g, op, lev, state["prev"])
+        rhs_o = {}
+        for name, which in (("u", H.HOSC_RHS_U), ("v", H.HOSC_RHS_V), ("w", H.HOSC_RHS_W),
+                            ("th", H.HOSC_RHS_THETA)):
+            c = coefs[name]
+            R = c["R"]
+            Bx = O.apply_B(g, c, state[name].ravel())
+            ref = (op.dt * (R - Bx))[ii]
+            got = cav.get(which).ravel()[ii]
+            scale = op.dt * max(np.max(np.abs(R[ii])), np.max(np.abs(Bx[ii])))
+            assert np.max(np.abs(got - ref)) / scale < 1e-11, name
+            rhs_o[name] = got
+        # S4/S5: GPU increment vs direct solve of the oracle operator; oracle A x_gpu = rhs_gpu
+        info = cav.run_stage(H.HOSC_STAGE_SOLVE)
+        assert info["status"] == 0
+        A_m = O.assemble_A(g, op.dt, coefs["u"])
+        A_e = O.assemble_A(g, op.dt, coefs["th"])
+        import scipy.sparse.linalg as spla
+        for name, which in (("u", H.HOSC_DX_U), ("v", H.HOSC_DX_V), ("w", H.HOSC_DX_W),
+                            ("th", H.HOSC_DX_THETA)):
+            A = (A_e if name == "th" else A_m)[ii][:, ii].tocsc()
+            x_gpu = cav.get(which).ravel()[ii]
+            b = rhs_o[name]
+            assert np.linalg.norm(A @ x_gpu - b) <= 1e-11 * max(np.linalg.norm(b), 1e-300)
+            x_ref = spla.spsolve(A, b)
+            assert _rel(x_gpu, x_ref) < 1e-9, name
+        # S6-S8: the full step against the oracle's step
+        cav.run_stage(H.HOSC_STAGE_UPDATE)
+        new, oinfo = O.step(state, op, g)
+        for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
+                            ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
+            assert _rel(cav.get(which), new[name]) < 1e-10, name
+        div_o = O.divergence(new["u"], new["v"], new["w"], g.h)
+        assert _rel(cav.get(H.HOSC_DIV).ravel()[ii], div_o.ravel()[ii]) < 1e-9
+
+
+@pytest.mark.parametrize("N,n", [(21, 1.0), (21, 0.75), (16, 1.25)])
+def test_trajectory_from_rest(N, n):
+    """Several steps from the initial state (fluid at rest), the configuration marched to
+    steady state: fields, step change and divergence agree after every step."""
+    p = _params(N, 1e3, n, dt=0.005)
+    op = _oracle_params(p)
+    g = O.Grid(N)
+    st = O.initial_state(op)
+    with H.Cavity(p) as cav:
+        assert _rel(cav.get(H.HOSC_THETA), st["th"]) == 0.0
+        for _ in range(6):
+            info = cav.step(1)
+            st, oinfo = O.step(st, op, g)
+            assert info["call_status"] == 0
+            for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
+                                ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
+                assert _rel(cav.get(which), st[name]) < 1e-10, name
+            assert abs(info["res"] - oinfo["res"]) <= 1e-9 * oinfo["res"]
+            assert abs(info["div_max"] - oinfo["div_max"]) <= 1e-9 * oinfo["div_max"]
+            for s, name in enumerate(("u", "v", "w", "th")):
+                assert abs(info["last_iters"][s] - oinfo["iters"][name]) <= 1
+
+
+def test_diagnostics_parity():
+    for N, n in ((13, 0.75), (14, 1.0), (21, 1.25)):
+        p = _params(N, 1e4, n)
+        op = _oracle_params(p)
+        st = inputs.cavity_state(N, 1e4, seed=N)
+        with H.Cavity(p) as cav:
+            for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
+                                ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
+                cav.set(which, st[name])
+            d = cav.diagnostics(with_fields=True)
+        o = O.diagnostics(st, op)
+        for k_gpu, k_ora in (("Nu_hot_max", "Nu_hot_max"), ("Nu_hot_mean", "Nu_hot_mean"),
+                             ("Nu_cold_mean", "Nu_cold_mean"), ("E_total", "E_total"),
+                             ("E_HT", "E_HT_total"), ("E_FF", "E_FF_total"), ("Be", "Be")):
+            assert d[k_gpu] == pytest.approx(o[k_ora], rel=1e-12, abs=1e-14), k_gpu
+        assert _rel(d["Nu_avg_z"], o["Nu_avg_z"]) < 1e-12
+        for k in ("E_HT", "E_FF", "E_local"):
+            assert _rel(d[k + "_field"], o[k]) < 1e-12
+
+
+def test_conduction_fixed_point_and_zero_rhs():
+    """Ra = 0 with theta = 1 - x: every right-hand side is zero, BiCGSTAB takes no iteration, the
+    state is unchanged and Nu = E_total = Be = 1."""
+    N = 11
+    p = _params(N, 0.0, 0.75)
+    x = np.linspace(0, 1, N)
+    th = np.broadcast_to(1.0 - x, (N, N, N)).copy()
+    with H.Cavity(p) as cav:
+        cav.set(H.HOSC_THETA, th)
+        info = cav.step(2)
+        assert info["call_status"] == 0 and info["last_iters"] == [0, 0, 0, 0]
+        assert info["res"] == 0.0 and info["div_max"] == 0.0
+        assert np.max(np.abs(cav.get(H.HOSC_THETA) - th)) == 0.0
+        d = cav.diagnostics()
+        for k in ("Nu_hot_max", "Nu_hot_mean", "Nu_cold_mean", "E_total", "Be"):
+            assert d[k] == pytest.approx(1.0, abs=1e-12), k
+
+
+def test_torch_workspace_matches_library_allocation():
+    torch = pytest.importorskip("torch")
+    p = _params(13, 1e4, 0.75)
+    st = inputs.cavity_state(13, 1e4, seed=5)
+    outs = []
+    for ws in (None, "torch"):
+        with H.Cavity(p, workspace=ws) as cav:
+            for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
+                                ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
+                cav.set(which, st[name])
+            cav.step(3)
+            outs.append([cav.get(w) for w in (H.HOSC_U, H.HOSC_V, H.HOSC_THETA, H.HOSC_P)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert torch.cuda.is_available()
+
+
+def test_errors_and_limits():
+    p = _params(9, 1e3, 1.0)
+    p.max_lin_iter = 1
+    st = inputs.cavity_state(9, 1e3, seed=2)
+    with H.Cavity(p) as cav:
+        cav.set(H.HOSC_V, st["v"])
+        info = cav.step(1)
+        assert info["call_status"] == H.HOSC_ENOCONV
+        assert max(info["last_iters"]) == 1
+        # stages out of order
+        st_, _ = H.hosc_run_stage(cav.h, H.HOSC_STAGE_RHS)
+        assert st_ == H.HOSC_ESTATE
+        # read-only field, bad selector
+        assert H.hosc_set_field(cav.h, H.HOSC_ETA, np.zeros((9, 9, 9))) == H.HOSC_EINVAL
+        assert H.hosc_get_field(cav.h, 99, np.zeros((9, 9, 9))) == H.HOSC_EINVAL
+    # a NaN in the state is reported as divergence, not hidden
+    p = _params(9, 1e3, 1.0)
+    with H.Cavity(p) as cav:
+        u = st["u"].copy()
+        u[4, 4, 4] = np.nan
+        cav.set(H.HOSC_U, u)
+        info = cav.step(1)
+        assert info["call_status"] == H.HOSC_EDIVERGED
+    bad = _params(9, 1e3, 1.0)
+    bad.dt = -1.0
+    st_, h = H.hosc_create(bad)
+    assert st_ == H.HOSC_EINVAL and not h.value
+
+
+def test_small_and_even_grids():
+    """N = 5 (one interior plane of 3^3) and even N (trapezoid diagnostics) against the oracle."""
+    for N in (5, 6, 8):
+        p = _params(N, 1e3, 0.9, dt=0.002)
+        op = _oracle_params(p)
+        st = O.initial_state(op)
+        g = O.Grid(N)
+        with H.Cavity(p) as cav:
+            for _ in range(3):
+                cav.step(1)
+                st, _ = O.step(st, op, g)
+            for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("th", H.HOSC_THETA),
+                                ("p", H.HOSC_P)):
+                assert _rel(cav.get(which), st[name]) < 1e-10, (N, name)
+            d = cav.diagnostics()
+        o = O.diagnostics(st, op)
+        assert d["Nu_hot_mean"] == pytest.approx(o["Nu_hot_mean"], rel=1e-12)
+        assert d["Be"] == pytest.approx(o["Be"], rel=1e-12)
