@@ -26,9 +26,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "cavity101": dict(N=101, Ra=1e5, Pr=1.0, n=0.75, dt=5e-5, spinup=200,
+    "cavity101": dict(N=101, Ra=1e5, Pr=1.0, n=0.75, dt=2e-5, spinup=300, history=0,
                       desc="single cavity 101^3, n=0.75, Ra=1e5, Pr=1 (power-law, shear-thinning)"),
-    "cavity41": dict(N=41, Ra=1e4, Pr=1.0, n=0.75, dt=5e-4, spinup=200,
+    "cavity41": dict(N=41, Ra=1e4, Pr=1.0, n=0.75, dt=2e-4, spinup=300, history=0,
                      desc="cavity 41^3, n=0.75, Ra=1e4, Pr=1"),
 }
 ALG_WORDS = {  # algorithmic 8-byte words per interior node of one launch, all four systems active
@@ -117,7 +117,8 @@ def run_reference(args, wl):
     Ns = 51
     h = 1.0 / (Ns - 1)
     prm = O.Params(N=Ns, Ra=wl["Ra"], Pr=wl["Pr"], n=wl["n"], dt=wl["dt"] * 4,
-                   lam=0.25 * h * h / (wl["dt"] * 4), tol_lin=1e-10)
+                   lam=min(0.25 * h * h / (wl["dt"] * 4), 0.1), tol_lin=1e-10,
+                   use_history=wl["history"])
     g = O.Grid(Ns)
     st = O.initial_state(prm)
     for _ in range(args.warmup):
@@ -146,7 +147,8 @@ def cpu_baseline(cav, H, wl):
     from oracle import hosc_oracle as O
     N = wl["N"]
     prm = O.Params(N=N, Ra=wl["Ra"], Pr=wl["Pr"], n=wl["n"], dt=wl["dt"],
-                   lam=cav.params.lambda_, tol_lin=cav.params.tol_lin)
+                   lam=cav.params.lambda_, tol_lin=cav.params.tol_lin,
+                   use_history=wl["history"])
     st = dict(u=cav.get(H.HOSC_U), v=cav.get(H.HOSC_V), w=cav.get(H.HOSC_W),
               th=cav.get(H.HOSC_THETA), p=cav.get(H.HOSC_P), steps=0,
               prev=dict(L=cav.get(H.HOSC_PREV_L), u=cav.get(H.HOSC_PREV_U),
@@ -190,6 +192,7 @@ def main():
     p.dt = wl["dt"]
     p.lambda_ = 0.25 * h * h / p.dt
     p.tol_lin = 1e-10
+    p.use_history = wl["history"]
     p.cuda_stream = stream.cuda_stream
     cav = H.Cavity(p, workspace="torch")
     # spin-up from rest (untimed), then warm-up steps
@@ -276,6 +279,7 @@ def main():
             "config": {"workload": wl["desc"], "N": N, "Ra": wl["Ra"], "n": wl["n"],
                        "Pr": wl["Pr"], "dt": wl["dt"], "precision": "fp64",
                        "spinup_steps": wl["spinup"], "tol_lin": p.tol_lin,
+                       "use_history": wl["history"], "lambda": p.lambda_,
                        "bicgstab_iters_per_step": lin_iters / (4.0 * args.steps),
                        "l2": "no flush: device working set %.0f MB > 129 MB L2"
                              % (H.hosc_workspace_bytes(p) / 1e6),

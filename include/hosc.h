@@ -69,7 +69,10 @@ typedef enum {
   HOSC_PREV_L = 18, HOSC_PREV_U = 19, HOSC_PREV_V = 20, HOSC_PREV_W = 21,
   HOSC_PREV_EU = 22, HOSC_PREV_EV = 23, HOSC_PREV_EW = 24,
   HOSC_DIV = 25,   /* central div V^{n+1} at interior nodes (S7) */
-  HOSC_NFIELDS = 26
+  /* level-(n+1) weights of Eq. (6) (S4, read-only): centre, x+, x-, y+, y-, z+, z- */
+  HOSC_A_MOM = 26, /* 26..32: momentum operator, shared by u, v, w */
+  HOSC_A_ENE = 33, /* 33..39: energy operator */
+  HOSC_NFIELDS = 40
 } hosc_field;
 
 /* Stages of one step, for stage-by-stage use (tests, checkpointing). */
@@ -92,12 +95,21 @@ typedef struct {
   double theta_init;  /* initial interior temperature (fluid at rest, constant pressure) */
   double I2_eps;      /* regulariser: eta = (I2 + I2_eps)^((n-1)/2); unused when n == 1 */
   double phi;         /* irreversibility distribution ratio of E_FF (Sec. 4.3), 1e-4 */
-  double tol_steady;  /* hosc_solve_steady stops when max|chi^{n+1}-chi^n| < tol_steady ... */
+  double tol_steady;  /* hosc_solve_steady stops when max|chi^{n+1}-chi^n| / dt < tol_steady ... */
   double tol_div;     /* ... and max|div V| < tol_div; the pressure is corrected when above it */
   double tol_lin;     /* BiCGSTAB stops when ||r_k||_2 <= tol_lin ||r_0||_2 */
   int max_lin_iter;   /* BiCGSTAB iteration limit per system and step, >= 1 */
   int precision;      /* hosc_precision */
   void* cuda_stream;  /* cudaStream_t to enqueue on, or NULL for a stream owned by the context */
+  double a_limit;     /* lower limit of the diagonal term M18 of the level-(n+1) operator, in units
+                         of L (keeps its mass positive when L changes fast); 0 disables */
+  double a_boost;     /* factor of the pseudo-time mass added to the level-(n+1) operator where the
+                         cell Reynolds number |G*| h is high (keeps every grid mode damped);
+                         0 disables. Neither changes the steady state B chi = R. */
+  int use_history;    /* 1: the delta_t^- terms of Eq. (5) use the level n-1 history (the paper's
+                         second-order-in-time scheme); 0: delta_t^- = 0 at every step, a
+                         first-order pseudo-time march with the same steady state */
+  int pad_;           /* reserved, 0 */
 } hosc_params;
 
 typedef struct {
@@ -120,9 +132,11 @@ typedef struct {
   double Be;           /* E_HT / E_total */
 } hosc_diag;
 
-/* Fill *p with defaults for grid N and (Ra, Pr, n): dt = 0.02, lambda = 0.25 h^2/dt,
+/* Fill *p with defaults for grid N and (Ra, Pr, n): dt = 0.02, lambda = min(h^2/(4 dt), Pr/10),
  * theta_ref = theta_init = 0.5, I2_eps = 1e-10, phi = 1e-4, tol_steady = 1e-6, tol_div = 1e-6,
- * tol_lin = 1e-10, max_lin_iter = 1000, HOSC_FP64, own stream. */
+ * tol_lin = 1e-10, max_lin_iter = 1000, HOSC_FP64, own stream, a_limit = 0.25, a_boost = 1,
+ * use_history = 1. After changing
+ * dt, set lambda again (it must stay below h^2/dt). */
 hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, double n);
 
 /* Bytes of device workspace a context with these parameters needs (0 if invalid). */
@@ -147,8 +161,8 @@ hosc_status hosc_reset(void* ctx);
  * Stops early at the first step whose status is not HOSC_OK and returns that status. */
 hosc_status hosc_step(void* ctx, int nsteps, hosc_info* out);
 
-/* Step until max|chi^{n+1}-chi^n| < tol_steady and max|div V| < tol_div (HOSC_OK) or max_steps
- * (HOSC_ESTEPLIMIT) or a numerical failure. */
+/* Step until max|chi^{n+1}-chi^n| / dt < tol_steady and max|div V| < tol_div (HOSC_OK), or
+ * max_steps (HOSC_ESTEPLIMIT), or a numerical failure. */
 hosc_status hosc_solve_steady(void* ctx, long max_steps, hosc_info* out);
 
 /* Run a single stage of the next step (see hosc_stage); stages must be run in order. */

@@ -53,6 +53,13 @@ notes of the repository):
 * R11 chi* = phi* = phi (default 1e-4), so E_FF = phi * eta * I2; Be = int E_HT / int E_local.
 * R12 The initial interior temperature is theta_init (default 1/2 = theta_ref): the fluid at rest
       with constant pressure is then in equilibrium with the buoyancy term at t = 0.
+* R18 The diagonal part M18 of the level-(n+1) operator is limited below by -a_limit * L (default
+      a_limit = 1/4) so the operator keeps a positive mass when L changes fast (see assemble_A).
+* R20 use_history = 0 sets delta_t^- = 0 at every step: a first-order pseudo-time march with the
+      same steady state, free of the period-2 computational mode of the three-level scheme.
+* R19 Where the cell Reynolds number |G*| h is high, a diagonal pseudo-time mass is added to the
+      level-(n+1) operator (see pseudo_time_mass). R18 and R19 change A only: the discrete steady
+      state B chi = R of Eq. (5) is the paper's.
 
 Layout: a field is a numpy array f[z, y, x] of shape (N, N, N); node (i, j, k) sits at
 x = i*h, y = j*k, z = k*l with h = k = l = 1/(N-1). The flattened index is i + N*(j + N*k).
@@ -77,17 +84,25 @@ class Params:
     """Problem and solver parameters (Sec. 2.1 dimensionless groups; Sec. 3.1 dt = 0.02)."""
 
     def __init__(self, N, Ra, Pr=1.0, n=1.0, dt=0.02, lam=None, theta_ref=0.5, I2_eps=1e-10,
-                 phi=1e-4, tol_div=1e-6, tol_lin=1e-12, max_lin_iter=2000, theta_init=0.5):
+                 phi=1e-4, tol_div=1e-6, tol_lin=1e-12, max_lin_iter=2000, theta_init=0.5,
+                 a_limit=0.25, a_boost=1.0, use_history=1):
         self.N = int(N)
         self.Ra = float(Ra)
         self.Pr = float(Pr)
         self.n = float(n)
         self.dt = float(dt)
         h = 1.0 / (self.N - 1)
-        # Relaxation of the artificial-compressibility update (not given in the paper): a quarter
-        # of h^2/dt. Above h^2/dt the highest grid mode of the coupled update grows even for
-        # constant viscosity; strongly varying power-law viscosity needs a further margin.
-        self.lam = float(0.25 * h * h / self.dt if lam is None else lam)
+        # Relaxation of the artificial-compressibility update (not given in the paper): the
+        # smaller of h^2/(4 dt) and Pr/10. Above h^2/dt the highest grid mode of the coupled
+        # update grows even at constant viscosity; at small dt the pressure mode needs lam below
+        # about twice the smallest Pr*eta.
+        self.lam = float(min(0.25 * h * h / self.dt, 0.1 * self.Pr) if lam is None else lam)
+        # Lower limit of M18 in units of L (reading R18); 0 disables the limiter.
+        self.a_limit = float(a_limit)
+        # Factor of the pseudo-time mass added where the cell Reynolds number is high (R19).
+        self.a_boost = float(a_boost)
+        # 1: delta_t^- from the level n-1 history (Eq. 5); 0: delta_t^- = 0 every step (R20).
+        self.use_history = int(use_history)
         self.theta_ref = float(theta_ref)
         self.theta_init = float(theta_init)
         self.I2_eps = float(I2_eps)
@@ -201,7 +216,23 @@ def scalar_coefficients(g, dt, L, G, H, I, K, E, prev=None):
     return c
 
 
-def assemble_A(g, dt, c):
+def pseudo_time_mass(g, dt, c, kappa):
+    """Reading R19: diagonal mass added to the level-(n+1) operator so that every grid mode of
+    the frozen-coefficient pseudo-time update chi <- chi + dt A^-1 (R - B chi) is damped.
+
+    The level-n operator B carries the compact correction (h^2/12)|G*|^2 delta^2 explicitly
+    (inside alpha, beta, gamma); for the grid mode that alternates in all three directions the
+    level-(n+1) operator reduces to 6 dt/h^2 (its compact mass cancels), so that mode grows once
+    |G*|^2 h^2 > 24, and the mode alternating in one direction grows once dt |G*|^2 > 4 L.
+    sigma = kappa * max(0, dt (|G*|^2/6 - 1/h^2), dt |G*|^2/6 - 2 L/3) keeps both damped. It is
+    zero for well-resolved flows; A only sets the pseudo-time path, never the steady state.
+    """
+    G2 = c["G"] ** 2 + c["H"] ** 2 + c["I"] ** 2
+    sig = np.maximum(0.0, np.maximum(dt * (G2 / 6.0 - 1.0 / g.h ** 2), dt * G2 / 6.0 - 2.0 * c["L"] / 3.0))
+    return kappa * sig
+
+
+def assemble_A(g, dt, c, a_limit=0.0, a_boost=0.0):
     """The level-(n+1) operator of Eq. (5): the bracket multiplying delta_t^+ chi, as a sparse matrix.
 
     Written term by term as printed in Eq. (5):
@@ -211,6 +242,11 @@ def assemble_A(g, dt, c):
             + 1/(12 L) (-h^2 G dx L - l^2 I dz L - k^2 H dy L)
             + (k^2/(6L) dy L) dy + (h^2/(6L) dx L) dx + (l^2/(6L) dz L) dz ] .
     Its rows at interior nodes are the seven weights L1..L7 of Eq. (6).
+
+    Reading R18: with a_limit > 0, the diagonal part M18 = L * (diagonal bracket terms other
+    than K) is limited below by -a_limit * L, so that the extrapolated mass of the level-(n+1)
+    operator stays positive when L drops fast between steps or varies strongly across a cell.
+    A only sets the pseudo-time path; the steady state B chi = R does not involve it.
     """
     L, G, H, I, K = c["L"], c["G"], c["H"], c["I"], c["K"]
     h2, k2, l2 = g.h ** 2, g.k ** 2, g.l ** 2
@@ -221,6 +257,8 @@ def assemble_A(g, dt, c):
                          + l2 / (6 * dt) * (g.Dzz @ L))
                   + 1.0 / (12.0 * L) * (-h2 * G * (g.Dx @ L) - l2 * I * (g.Dz @ L)
                                         - k2 * H * (g.Dy @ L)))
+    if a_limit > 0.0:
+        diag_terms = np.maximum(diag_terms - dtL * K, -a_limit) + dtL * K
     inner = (sp.identity(g.N ** 3, format="csr")
              - D(dtL - k2 / 12.0) @ (g.Dyy - D(H) @ g.Dy)
              - D(dtL - h2 / 12.0) @ (g.Dxx - D(G) @ g.Dx)
@@ -229,7 +267,10 @@ def assemble_A(g, dt, c):
              + D(k2 / (6.0 * L) * (g.Dy @ L)) @ g.Dy
              + D(h2 / (6.0 * L) * (g.Dx @ L)) @ g.Dx
              + D(l2 / (6.0 * L) * (g.Dz @ L)) @ g.Dz)
-    return (D(L) @ inner).tocsr()
+    A = D(L) @ inner
+    if a_boost > 0.0:
+        A = A + D(pseudo_time_mass(g, dt, c, a_boost))
+    return A.tocsr()
 
 
 def apply_B(g, c, chi):
@@ -479,9 +520,9 @@ def step(state, prm, g=None, direct=False):
     """
     g = g or Grid(prm.N)
     lev = level_coefficients(state, prm)
-    coefs = _system_coefficients(g, prm, lev, state["prev"])
-    A_m = assemble_A(g, prm.dt, coefs["u"])
-    A_e = assemble_A(g, prm.dt, coefs["th"])
+    coefs = _system_coefficients(g, prm, lev, state["prev"] if prm.use_history else None)
+    A_m = assemble_A(g, prm.dt, coefs["u"], prm.a_limit, prm.a_boost)
+    A_e = assemble_A(g, prm.dt, coefs["th"], prm.a_limit, prm.a_boost)
     new, iters, status = {}, {}, 0
     for name in ("u", "v", "w", "th"):
         A = A_e if name == "th" else A_m

@@ -68,6 +68,9 @@ hosc_status validate(const hosc_params* p) {
   if (!(p->I2_eps >= 0.0) || (p->n != 1.0 && p->n < 1.0 && !(p->I2_eps > 0.0))) return HOSC_EINVAL;
   if (!(p->phi >= 0.0) || !(p->tol_div >= 0.0) || !(p->tol_steady >= 0.0)) return HOSC_EINVAL;
   if (!isfinite(p->theta_ref) || !isfinite(p->theta_init)) return HOSC_EINVAL;
+  if (!(p->a_limit >= 0.0) || !(p->a_limit < 1.0)) return HOSC_EINVAL;
+  if (!(p->a_boost >= 0.0) || !isfinite(p->a_boost)) return HOSC_EINVAL;
+  if (p->use_history != 0 && p->use_history != 1) return HOSC_EINVAL;
   if (p->precision != HOSC_FP64) return HOSC_EINVAL;
   return HOSC_OK;
 }
@@ -90,6 +93,8 @@ DevParams device_params(const hosc_params& p, int have_prev) {
   d.phi = p.phi;
   d.tol_div = p.tol_div;
   d.tol_lin = p.tol_lin;
+  d.a_limit = p.a_limit;
+  d.a_boost = p.a_boost;
   return d;
 }
 
@@ -119,7 +124,10 @@ double* field_ptr(Ctx* c, int which) {
     case HOSC_PREV_EV: return F.Ev[o];
     case HOSC_PREV_EW: return F.Ew[o];
     case HOSC_DIV: return F.div;
-    default: return nullptr;
+    default:
+      if (which >= HOSC_A_MOM && which < HOSC_A_MOM + 7) return F.Am[which - HOSC_A_MOM];
+      if (which >= HOSC_A_ENE && which < HOSC_A_ENE + 7) return F.Ae[which - HOSC_A_ENE];
+      return nullptr;
   }
 }
 
@@ -267,7 +275,7 @@ hosc_status run_stage(Ctx* c, int stage) {
   if (st) return st;
   if (stage == HOSC_STAGE_UPDATE) {
     c->cur = 1 - c->cur;
-    c->P.have_prev = 1;
+    c->P.have_prev = c->prm.use_history ? 1 : 0;
     c->stage = 0;
   } else {
     c->stage = stage + 1;
@@ -422,7 +430,7 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
   p->Pr = Pr;
   p->n = n;
   p->dt = 0.02;
-  p->lambda = 0.25 * h * h / p->dt;
+  p->lambda = fmin(0.25 * h * h / p->dt, 0.1 * Pr);
   p->theta_ref = 0.5;
   p->theta_init = 0.5;
   p->I2_eps = 1e-10;
@@ -433,6 +441,9 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
   p->max_lin_iter = 1000;
   p->precision = HOSC_FP64;
   p->cuda_stream = nullptr;
+  p->a_limit = 0.25;
+  p->a_boost = 1.0;
+  p->use_history = 1;
   return HOSC_OK;
 }
 
@@ -501,7 +512,7 @@ hosc_status hosc_solve_steady(void* ctx, long max_steps, hosc_info* out) {
       st = q;
       break;
     }
-    if (info.res_steady < c->prm.tol_steady && info.div_max < c->prm.tol_div) {
+    if (info.res_steady < c->prm.tol_steady * c->prm.dt && info.div_max < c->prm.tol_div) {
       st = HOSC_OK;
       break;
     }
@@ -589,7 +600,7 @@ hosc_status hosc_set_field(void* ctx, int which, const double* host_in) {
   CU(cudaMemcpyAsync(field_ptr(c, which), host_in, n3 * sizeof(double), cudaMemcpyHostToDevice,
                      c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  if (which >= HOSC_PREV_L) c->P.have_prev = 1;
+  if (which >= HOSC_PREV_L) c->P.have_prev = c->prm.use_history ? 1 : 0;
   return HOSC_OK;
 }
 
@@ -620,7 +631,7 @@ hosc_status hosc_set_field_device(void* ctx, int which, const double* dev_in) {
   const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
   CU(cudaMemcpyAsync(field_ptr(c, which), dev_in, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
                      c->stream));
-  if (which >= HOSC_PREV_L) c->P.have_prev = 1;
+  if (which >= HOSC_PREV_L) c->P.have_prev = c->prm.use_history ? 1 : 0;
   return HOSC_OK;
 }
 

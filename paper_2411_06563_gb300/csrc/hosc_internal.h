@@ -18,7 +18,7 @@ struct DevParams {
   int have_prev;     // level n-1 history present (else delta_t^- = 0)
   int max_lin_iter;
   double h, h2;      // grid spacing (h = k = l) and its square
-  double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin;
+  double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
 };
 
 // BiCGSTAB scalars of one system, resident in device memory.

@@ -205,6 +205,18 @@ __device__ __forceinline__ double applyB(const Eq5& c, const double f[19], doubl
          m5 * (gyz + gxy + gzx);
 }
 
+// Diagonal pseudo-time mass where the cell Reynolds number is high: the level-n operator carries
+// (h^2/12)|G*|^2 delta^2 explicitly, and for the grid mode alternating in all three directions the
+// level-(n+1) operator is only 6 dt/h^2, so that mode grows once |G*|^2 h^2 > 24 (and the mode
+// alternating in one direction once dt |G*|^2 > 4 L). Zero in resolved flows; it changes the
+// pseudo-time path only, never the steady state.
+__device__ __forceinline__ double pseudo_time_mass(double G, double H, double I, double L,
+                                                   double dt, double invh2, double kappa) {
+  const double g2 = G * G + H * H + I * I;
+  const double s = fmax(0.0, fmax(dt * (g2 / 6.0 - invh2), dt * g2 / 6.0 - 2.0 * L / 3.0));
+  return kappa * s;
+}
+
 // Right-hand sides of the increment form of Eq. (6),  A (chi^{n+1} - chi^n) = dt (R - B chi^n),
 // for u, v, w, theta at interior nodes, and the seven level-(n+1) weights L1..L7 of the momentum
 // and energy systems.
@@ -263,11 +275,15 @@ __global__ void __launch_bounds__(kThreads) k_rhs(
     const double M = -dt / (2.0 * Lc) + h2_12;
     const double m15 = h2 / (6.0 * Lc) * dL.dx, m16 = h2 / (6.0 * Lc) * dL.dy,
                  m17 = h2 / (6.0 * Lc) * dL.dz;
-    const double M18 = 0.5 * (Lc - Lpc) + h2_12 * ((dL.dxx - cm.G * dL.dx) +
-                                                   (dL.dyy - cm.H * dL.dy) +
-                                                   (dL.dzz - cm.I * dL.dz));
+    double M18 = 0.5 * (Lc - Lpc) + h2_12 * ((dL.dxx - cm.G * dL.dx) +
+                                             (dL.dyy - cm.H * dL.dy) +
+                                             (dL.dzz - cm.I * dL.dz));
+    // keep the extrapolated mass positive where L changes fast (the steady state is unaffected)
+    if (P.a_limit > 0.0) M18 = fmax(M18, -P.a_limit * Lc);
     const double a2 = M * invh2;
-    F.Am[0][c] = Lc * (1.0 - 6.0 * a2) + M18;
+    const double sig_m = P.a_boost > 0.0
+                             ? pseudo_time_mass(cm.G, cm.H, cm.I, Lc, dt, invh2, P.a_boost) : 0.0;
+    F.Am[0][c] = Lc * (1.0 - 6.0 * a2) + M18 + sig_m;
     F.Am[1][c] = Lc * (a2 - M * cm.G * inv2h + m15 * inv2h);
     F.Am[2][c] = Lc * (a2 + M * cm.G * inv2h - m15 * inv2h);
     F.Am[3][c] = Lc * (a2 - M * cm.H * inv2h + m16 * inv2h);
@@ -283,7 +299,9 @@ __global__ void __launch_bounds__(kThreads) k_rhs(
     F.rhs[3][c] = -dt * applyB(ce, f19, h, inv2h, invh2);
     const double M = -0.5 * dt + h2_12;
     const double a2 = M * invh2;
-    F.Ae[0][c] = 1.0 - 6.0 * a2;
+    const double sig_e = P.a_boost > 0.0
+                             ? pseudo_time_mass(ce.G, ce.H, ce.I, 1.0, dt, invh2, P.a_boost) : 0.0;
+    F.Ae[0][c] = 1.0 - 6.0 * a2 + sig_e;
     F.Ae[1][c] = a2 - M * ce.G * inv2h;
     F.Ae[2][c] = a2 + M * ce.G * inv2h;
     F.Ae[3][c] = a2 - M * ce.H * inv2h;

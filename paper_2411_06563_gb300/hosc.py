@@ -23,6 +23,7 @@ HOSC_FP64, HOSC_MIXED = 0, 1
  HOSC_RHS_U, HOSC_RHS_V, HOSC_RHS_W, HOSC_RHS_THETA, HOSC_DX_U, HOSC_DX_V, HOSC_DX_W,
  HOSC_DX_THETA, HOSC_PREV_L, HOSC_PREV_U, HOSC_PREV_V, HOSC_PREV_W, HOSC_PREV_EU, HOSC_PREV_EV,
  HOSC_PREV_EW, HOSC_DIV) = range(26)
+HOSC_A_MOM, HOSC_A_ENE = 26, 33   # + 0..6: centre, x+, x-, y+, y-, z+, z-
 # stages
 (HOSC_STAGE_VISCOSITY, HOSC_STAGE_SOURCES, HOSC_STAGE_RHS, HOSC_STAGE_SOLVE,
  HOSC_STAGE_UPDATE) = range(5)
@@ -38,7 +39,9 @@ class hosc_params(ctypes.Structure):
                 ("I2_eps", ctypes.c_double), ("phi", ctypes.c_double),
                 ("tol_steady", ctypes.c_double), ("tol_div", ctypes.c_double),
                 ("tol_lin", ctypes.c_double), ("max_lin_iter", ctypes.c_int),
-                ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p)]
+                ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
+                ("a_limit", ctypes.c_double), ("a_boost", ctypes.c_double),
+                ("use_history", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 class hosc_info(ctypes.Structure):

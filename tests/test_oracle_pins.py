@@ -360,7 +360,7 @@ def test_steady_state_balance_entropy_and_certificate():
     """A converged small power-law cavity: the hot and cold wall means agree, div V -> 0, the dt-free steady
     residual B chi - R vanishes, entropy terms are non-negative, 0 <= Be <= 1, and the steady
     state is centro-symmetric."""
-    prm = O.Params(N=9, Ra=1e3, n=0.75, dt=0.01, tol_lin=1e-11, tol_div=1e-7)
+    prm = O.Params(N=9, Ra=1e3, n=0.75, dt=0.01, lam=0.25 / 64 / 0.01, tol_lin=1e-11, tol_div=1e-7)
     g = O.Grid(9)
     st, info = O.solve_steady(prm, 4000, tol_steady=1e-9, g=g)
     assert info["status"] == 0 and info["res"] < 1e-9 and info["div_max"] < 1e-7
@@ -375,7 +375,8 @@ def test_steady_state_balance_entropy_and_certificate():
     assert np.all((d["Be_local"] >= 0.0) & (d["Be_local"] <= 1.0))
     assert np.max(np.abs(st["th"] + _mirror_all(st["th"]) - 1.0)) < 1e-10
     # the steady state does not depend on the pseudo-time step
-    prm2 = O.Params(N=9, Ra=1e3, n=0.75, dt=0.005, tol_lin=1e-11, tol_div=1e-7)
+    prm2 = O.Params(N=9, Ra=1e3, n=0.75, dt=0.005, lam=0.25 / 64 / 0.005, tol_lin=1e-11,
+                    tol_div=1e-7)
     st2, info2 = O.solve_steady(prm2, 8000, tol_steady=1e-9, g=g)
     for key in ("u", "v", "w", "th"):
         assert np.max(np.abs(st2[key] - st[key])) < 1e-5 * max(1.0, np.abs(st[key]).max())
