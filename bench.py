@@ -27,9 +27,10 @@ sys.path.insert(0, ROOT)
 
 WORKLOADS = {
     "cavity101": dict(N=101, Ra=1e5, Pr=1.0, n=0.75, dt=2e-5, spinup=300, history=0,
-                      desc="single cavity 101^3, n=0.75, Ra=1e5, Pr=1 (power-law, shear-thinning)"),
+                      desc="single cavity 101^3, n=0.75, Ra=1e5, Pr=1 (power-law, shear-thinning), "
+                           "mixed precision"),
     "cavity41": dict(N=41, Ra=1e4, Pr=1.0, n=0.75, dt=2e-4, spinup=300, history=0,
-                     desc="cavity 41^3, n=0.75, Ra=1e4, Pr=1"),
+                     desc="cavity 41^3, n=0.75, Ra=1e4, Pr=1, mixed precision"),
 }
 ALG_WORDS = {  # algorithmic 8-byte words per interior node of one launch, all four systems active
     "k_bicg_pv": 38, "k_bicg_st": 26, "k_bicg_xr": 32,
@@ -171,6 +172,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cavity101", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--spinup", type=int, default=None,
+                    help="untimed steps from rest before the warm-up (default: per workload)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
@@ -188,22 +193,44 @@ def main():
     N = wl["N"]
     h = 1.0 / (N - 1)
     stream = torch.cuda.current_stream()
-    p = H.hosc_default_params(N, wl["Ra"], wl["Pr"], wl["n"])
-    p.dt = wl["dt"]
-    p.lambda_ = 0.25 * h * h / p.dt
-    p.tol_lin = 1e-10
-    p.use_history = wl["history"]
-    p.cuda_stream = stream.cuda_stream
-    cav = H.Cavity(p, workspace="torch")
-    # spin-up from rest (untimed), then warm-up steps
-    info = cav.step(wl["spinup"])
-    assert info["call_status"] == 0, info
-    cav.step(args.warmup)
-    torch.cuda.synchronize()
+    spinup = wl["spinup"] if args.spinup is None else args.spinup
+
+    def make(precision):
+        p = H.hosc_default_params(N, wl["Ra"], wl["Pr"], wl["n"])
+        p.dt = wl["dt"]
+        p.lambda_ = min(0.25 * h * h / p.dt, 0.1 * wl["Pr"])
+        p.tol_lin = 1e-10
+        p.use_history = wl["history"]
+        p.precision = H.HOSC_MIXED if precision == "mixed" else H.HOSC_FP64
+        p.auto_defect = 0   # time the FP32 sweeps; the FP64 defect phase is for the last digits
+        p.cuda_stream = stream.cuda_stream
+        cav = H.Cavity(p, workspace="torch")
+        # spin-up from rest (untimed), then warm-up steps
+        info = cav.step(spinup)
+        assert info["call_status"] == 0, info
+        cav.step(args.warmup)
+        torch.cuda.synchronize()
+        return p, cav
 
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
+
+    fp64_compare = None
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        # the plain all-FP64 path on the same workload, for context
+        p64, c64 = make("fp64")
+        k64 = max(5, args.steps // 4)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        ea.record(stream)
+        c64.step(k64)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        fp64_compare = {"value": (N - 2) ** 3 * k64 * ws / (ea.elapsed_time(eb) * 1e-3),
+                        "steps": k64, "ms_per_step": ea.elapsed_time(eb) / k64}
+        c64.close()
+    p, cav = make(args.precision)
 
     # ------------------------------------------------------------- timed region (device-resident)
     l0 = cav.kernel_launches()
@@ -274,11 +301,15 @@ def main():
         out = {
             "metric": "grid-point updates/s", "value": value, "unit": "GPUPS", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": wl["desc"], "N": N, "Ra": wl["Ra"], "n": wl["n"],
-                       "Pr": wl["Pr"], "dt": wl["dt"], "precision": "fp64",
-                       "spinup_steps": wl["spinup"], "tol_lin": p.tol_lin,
+                       "Pr": wl["Pr"], "dt": wl["dt"], "precision": args.precision,
+                       "mixed_phase": "FP32 sweeps and Krylov, FP64 state/reductions/pressure"
+                       if args.precision == "mixed" else None,
+                       "fp64_path": fp64_compare,
+                       "spinup_steps": spinup, "tol_lin": p.tol_lin,
                        "use_history": wl["history"], "lambda": p.lambda_,
                        "bicgstab_iters_per_step": lin_iters / (4.0 * args.steps),
                        "l2": "no flush: device working set %.0f MB > 129 MB L2"

@@ -51,7 +51,13 @@ typedef enum {
   HOSC_ESTATE = 7      /* call not valid in the current state */
 } hosc_status;
 
-/* Arithmetic of the step. HOSC_FP64: every kernel in double. */
+/* Arithmetic of the step. HOSC_FP64: every kernel in double. HOSC_MIXED: the state (u, v, w,
+ * theta, p), the divergence / pressure update, every norm and reduction and the diagnostics stay in
+ * double; the viscosity, sources and right-hand-side sweeps run in float (differences of the state
+ * taken in double first), and the BiCGSTAB vectors and operator weights are float. When the step
+ * change stalls at the float rounding level the context switches to FP64 defect sweeps (the
+ * right-hand side dt (R - B chi^n) in double, the Krylov solve still float), whose fixed point is
+ * the FP64 steady state. tol_lin is raised to at least 3e-6 for the float solves. */
 typedef enum { HOSC_FP64 = 0, HOSC_MIXED = 1 } hosc_precision;
 
 /* Field selectors for hosc_get_field / hosc_set_field. */
@@ -109,7 +115,9 @@ typedef struct {
   int use_history;    /* 1: the delta_t^- terms of Eq. (5) use the level n-1 history (the paper's
                          second-order-in-time scheme); 0: delta_t^- = 0 at every step, a
                          first-order pseudo-time march with the same steady state */
-  int pad_;           /* reserved, 0 */
+  int auto_defect;    /* HOSC_MIXED: 1 switches from FP32 to FP64 defect sweeps by itself when the
+                         step change stalls (200 steps without a 5 % improvement); 0 keeps the
+                         phase chosen with hosc_set_phase */
 } hosc_params;
 
 typedef struct {
@@ -135,7 +143,7 @@ typedef struct {
 /* Fill *p with defaults for grid N and (Ra, Pr, n): dt = 0.02, lambda = min(h^2/(4 dt), Pr/10),
  * theta_ref = theta_init = 0.5, I2_eps = 1e-10, phi = 1e-4, tol_steady = 1e-6, tol_div = 1e-6,
  * tol_lin = 1e-10, max_lin_iter = 1000, HOSC_FP64, own stream, a_limit = 0.25, a_boost = 1,
- * use_history = 1. After changing
+ * use_history = 1, auto_defect = 1. After changing
  * dt, set lambda again (it must stay below h^2/dt). */
 hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, double n);
 
@@ -199,6 +207,12 @@ hosc_status hosc_profile_read(void* ctx, int kernel_id, double* total_ms, long* 
 /* Kernel classes for hosc_profile_read. */
 enum { HOSC_K_VISC = 0, HOSC_K_SOURCES = 1, HOSC_K_RHS = 2, HOSC_K_BICG_PV = 3,
        HOSC_K_BICG_ST = 4, HOSC_K_BICG_XR = 5, HOSC_K_UPDATE = 6, HOSC_K_COUNT = 7 };
+
+/* Mixed precision only: select FP32 sweeps (0) or FP64 defect sweeps (1) for the next steps (the
+ * automatic switch, when auto_defect is set, is re-armed); get returns the current phase. With
+ * HOSC_FP64, phase 0 is accepted and 1 rejected. */
+hosc_status hosc_set_phase(void* ctx, int phase);
+int hosc_get_phase(void* ctx);
 
 /* Number of kernel launches the library has made since the context was created. */
 long hosc_kernel_launches(void* ctx);

@@ -44,6 +44,11 @@ struct Ctx {
   int device = 0;
   int cur = 0;
   int stage = 0;            // next stage of the step in progress
+  // mixed precision: 0 = FP32 sweeps, 1 = FP64 defect sweeps (FP32 Krylov in both)
+  int phase = 0;
+  double best_res = INFINITY;
+  long since_best = 0;
+  bool shadow_valid = false;   // float copies of the state match the state
   long launches = 0;
   KrylovScalars* h_ks = nullptr;
   StepRecord* h_rec = nullptr;
@@ -71,16 +76,25 @@ hosc_status validate(const hosc_params* p) {
   if (!(p->a_limit >= 0.0) || !(p->a_limit < 1.0)) return HOSC_EINVAL;
   if (!(p->a_boost >= 0.0) || !isfinite(p->a_boost)) return HOSC_EINVAL;
   if (p->use_history != 0 && p->use_history != 1) return HOSC_EINVAL;
-  if (p->precision != HOSC_FP64) return HOSC_EINVAL;
+  if (p->auto_defect != 0 && p->auto_defect != 1) return HOSC_EINVAL;
+  if (p->precision != HOSC_FP64 && p->precision != HOSC_MIXED) return HOSC_EINVAL;
   return HOSC_OK;
 }
 
-DevParams device_params(const hosc_params& p, int have_prev) {
+// FP32 Krylov vectors cannot resolve relative residuals far below their rounding.
+constexpr double kFp32TolFloor = 3e-6;
+// Steps without a 5 % improvement of the step change after which mixed precision switches from
+// FP32 to FP64 defect sweeps.
+constexpr long kStallSteps = 200;
+
+DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   DevParams d;
   d.N = p.N;
   d.newtonian = (p.n == 1.0);
   d.have_prev = have_prev;
   d.max_lin_iter = p.max_lin_iter;
+  d.krylov_fp32 = (p.precision == HOSC_MIXED);
+  d.sweep_fp32 = (p.precision == HOSC_MIXED && phase == 0);
   d.h = 1.0 / (p.N - 1);
   d.h2 = d.h * d.h;
   d.Ra = p.Ra;
@@ -92,7 +106,7 @@ DevParams device_params(const hosc_params& p, int have_prev) {
   d.I2_eps = p.I2_eps;
   d.phi = p.phi;
   d.tol_div = p.tol_div;
-  d.tol_lin = p.tol_lin;
+  d.tol_lin = d.krylov_fp32 ? fmax(p.tol_lin, kFp32TolFloor) : p.tol_lin;
   d.a_limit = p.a_limit;
   d.a_boost = p.a_boost;
   return d;
@@ -128,6 +142,22 @@ double* field_ptr(Ctx* c, int which) {
       if (which >= HOSC_A_MOM && which < HOSC_A_MOM + 7) return F.Am[which - HOSC_A_MOM];
       if (which >= HOSC_A_ENE && which < HOSC_A_ENE + 7) return F.Ae[which - HOSC_A_ENE];
       return nullptr;
+  }
+}
+
+// Fields stored in float in mixed precision: eta, L, E* (and their history) during FP32 sweeps;
+// right-hand sides, increments and operator weights whenever the Krylov solve is FP32.
+bool float_field(Ctx* c, int which) {
+  const bool sweep = c->P.sweep_fp32, kry = c->P.krylov_fp32;
+  switch (which) {
+    case HOSC_ETA: case HOSC_LCOEF: case HOSC_EU: case HOSC_EV: case HOSC_EW:
+    case HOSC_PREV_L: case HOSC_PREV_EU: case HOSC_PREV_EV: case HOSC_PREV_EW:
+      return sweep;
+    case HOSC_RHS_U: case HOSC_RHS_V: case HOSC_RHS_W: case HOSC_RHS_THETA:
+    case HOSC_DX_U: case HOSC_DX_V: case HOSC_DX_W: case HOSC_DX_THETA:
+      return kry;
+    default:
+      return kry && which >= HOSC_A_MOM && which < HOSC_A_ENE + 7;
   }
 }
 
@@ -181,7 +211,11 @@ hosc_status set_initial_state(Ctx* c) {
   CU(cudaStreamSynchronize(c->stream));
   c->cur = 0;
   c->stage = 0;
-  c->P = device_params(c->prm, 0);
+  c->phase = 0;
+  c->shadow_valid = false;
+  c->best_res = INFINITY;
+  c->since_best = 0;
+  c->P = device_params(c->prm, 0, 0);
   return HOSC_OK;
 }
 
@@ -234,6 +268,11 @@ hosc_status run_stage(Ctx* c, int stage) {
   hosc_status st = HOSC_OK;
   switch (stage) {
     case HOSC_STAGE_VISCOSITY:
+      if (c->P.sweep_fp32 && !c->shadow_valid) {
+        launch_shadow(c->P, F, c->cur, c->P.have_prev, c->stream);
+        c->launches += 1;
+        c->shadow_valid = true;
+      }
       prof_begin(c, HOSC_K_VISC);
       launch_viscosity(c->P, F, c->cur, c->stream);
       prof_end(c, HOSC_K_VISC);
@@ -263,6 +302,11 @@ hosc_status run_stage(Ctx* c, int stage) {
       launch_update(c->P, F, c->cur, c->stream);
       prof_end(c, HOSC_K_UPDATE);
       c->launches += 6;
+      if (c->P.krylov_fp32) {   // mixed precision: float copies of the new level
+        launch_shadow(c->P, F, 1 - c->cur, 0, c->stream);
+        c->launches += 1;
+        c->shadow_valid = true;
+      }
       // increments: x4 + u, v, w, theta read, u, v, w, theta written; div: V read, div written;
       // pressure: p, div read, p written
       c->host_bytes[HOSC_K_UPDATE] += 8.0 * (n3 * 12 + ni3 * 4 + ni3 * 3);
@@ -296,6 +340,26 @@ hosc_status read_record(Ctx* c, hosc_info* info) {
   return HOSC_OK;
 }
 
+// Mixed precision: FP32 sweeps until the step change stalls at their rounding level, then FP64
+// defect sweeps (the right-hand side dt (R - B chi^n) in double, the Krylov solve still FP32),
+// whose fixed point is the FP64 steady state. The history is dropped at the switch (its arrays
+// change type); the steady state does not depend on it.
+void set_phase(Ctx* c, int phase) {
+  if (c->prm.precision != HOSC_MIXED || phase == c->phase) return;
+  c->phase = phase;
+  c->P = device_params(c->prm, 0, phase);
+}
+
+void watch_stall(Ctx* c, double res) {
+  if (c->prm.precision != HOSC_MIXED || c->phase != 0 || !c->prm.auto_defect) return;
+  if (res < 0.95 * c->best_res) {
+    c->best_res = res;
+    c->since_best = 0;
+  } else if (++c->since_best >= kStallSteps) {
+    set_phase(c, 1);
+  }
+}
+
 hosc_status one_step(Ctx* c, hosc_info* info) {
   for (int s = 0; s < 5; ++s) {
     hosc_status st = run_stage(c, s);
@@ -303,6 +367,7 @@ hosc_status one_step(Ctx* c, hosc_info* info) {
   }
   hosc_status st = read_record(c, info);
   if (st) return st;
+  watch_stall(c, c->h_rec->res);
   if (info) {
     info->steps += 1;
     for (int s = 0; s < 4; ++s) info->lin_iters += c->h_rec->iters[s];
@@ -414,6 +479,14 @@ size_t workspace_layout(int N, Fields* f, char* base) {
   F.nu_cold = (double*)take((size_t)N * N * sizeof(double));
   F.nu_avg = (double*)take((size_t)N * sizeof(double));
   F.alg_bytes = (double*)take(HOSC_K_COUNT * sizeof(double));
+  const size_t ff = n3 * sizeof(float);
+  for (int b = 0; b < 2; ++b) {
+    F.us[b] = (float*)take(ff);
+    F.vs[b] = (float*)take(ff);
+    F.ws[b] = (float*)take(ff);
+  }
+  F.ths = (float*)take(ff);
+  F.ps = (float*)take(ff);
   return off;
 }
 
@@ -444,6 +517,7 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
   p->a_limit = 0.25;
   p->a_boost = 1.0;
   p->use_history = 1;
+  p->auto_defect = 1;
   return HOSC_OK;
 }
 
@@ -586,6 +660,13 @@ hosc_status hosc_get_field(void* ctx, int which, double* host_out) {
   if (!d) return HOSC_EINVAL;
   CU(cudaSetDevice(c->device));
   const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
+  if (float_field(c, which)) {
+    std::vector<float> tmp(n3);
+    CU(cudaMemcpyAsync(tmp.data(), d, n3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (size_t q = 0; q < n3; ++q) host_out[q] = tmp[q];
+    return HOSC_OK;
+  }
   CU(cudaMemcpyAsync(host_out, d, n3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
   return HOSC_OK;
@@ -597,10 +678,18 @@ hosc_status hosc_set_field(void* ctx, int which, const double* host_in) {
   if (c->stage != 0) return HOSC_ESTATE;
   CU(cudaSetDevice(c->device));
   const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
-  CU(cudaMemcpyAsync(field_ptr(c, which), host_in, n3 * sizeof(double), cudaMemcpyHostToDevice,
-                     c->stream));
-  CU(cudaStreamSynchronize(c->stream));
+  if (float_field(c, which)) {
+    std::vector<float> tmp(host_in, host_in + n3);
+    CU(cudaMemcpyAsync(field_ptr(c, which), tmp.data(), n3 * sizeof(float),
+                       cudaMemcpyHostToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  } else {
+    CU(cudaMemcpyAsync(field_ptr(c, which), host_in, n3 * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
   if (which >= HOSC_PREV_L) c->P.have_prev = c->prm.use_history ? 1 : 0;
+  c->shadow_valid = false;
   return HOSC_OK;
 }
 
@@ -616,7 +705,7 @@ hosc_status hosc_get_field_device(void* ctx, int which, double* dev_out) {
   Ctx* c = (Ctx*)ctx;
   if (!c || !dev_out) return HOSC_EINVAL;
   double* d = field_ptr(c, which);
-  if (!d) return HOSC_EINVAL;
+  if (!d || float_field(c, which)) return HOSC_EINVAL;
   CU(cudaSetDevice(c->device));
   const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
   CU(cudaMemcpyAsync(dev_out, d, n3 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -625,13 +714,14 @@ hosc_status hosc_get_field_device(void* ctx, int which, double* dev_out) {
 
 hosc_status hosc_set_field_device(void* ctx, int which, const double* dev_in) {
   Ctx* c = (Ctx*)ctx;
-  if (!c || !dev_in || !settable(which)) return HOSC_EINVAL;
+  if (!c || !dev_in || !settable(which) || float_field(c, which)) return HOSC_EINVAL;
   if (c->stage != 0) return HOSC_ESTATE;
   CU(cudaSetDevice(c->device));
   const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
   CU(cudaMemcpyAsync(field_ptr(c, which), dev_in, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
                      c->stream));
   if (which >= HOSC_PREV_L) c->P.have_prev = c->prm.use_history ? 1 : 0;
+  c->shadow_valid = false;
   return HOSC_OK;
 }
 
@@ -680,6 +770,22 @@ hosc_status hosc_profile_read(void* ctx, int kernel_id, double* total_ms, long* 
     *alg_bytes = b[kernel_id] + c->host_bytes[kernel_id];
   }
   return HOSC_OK;
+}
+
+hosc_status hosc_set_phase(void* ctx, int phase) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || phase < 0 || phase > 1) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  if (c->prm.precision != HOSC_MIXED) return phase == 0 ? HOSC_OK : HOSC_EINVAL;
+  set_phase(c, phase);
+  c->best_res = INFINITY;
+  c->since_best = 0;
+  return HOSC_OK;
+}
+
+int hosc_get_phase(void* ctx) {
+  Ctx* c = (Ctx*)ctx;
+  return c ? c->phase : -1;
 }
 
 long hosc_kernel_launches(void* ctx) {

@@ -88,6 +88,33 @@ __device__ __forceinline__ void block_reduce(double (&v)[M], double* smem) {
   __syncthreads();
 }
 
+// Block sum of M values whose per-thread terms are float: the warp stage adds in float, the
+// warp sums are widened to double for the cross-warp stage (and the grid stage that follows), so
+// each thread does no double arithmetic. The result is valid in thread 0.
+template <int M>
+__device__ __forceinline__ void block_sum_f32(const float (&vf)[M], double (&v)[M], double* smem) {
+  float w[M];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    w[m] = vf[m];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) w[m] += __shfl_down_sync(0xffffffffu, w[m], off);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) smem[wid * M + m] = (double)w[m];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] = (lane < nw) ? smem[lane * M + m] : 0.0;
+    warp_sum<M>(v);
+  }
+  __syncthreads();
+}
+
 // Publish this block's M partials (valid in thread 0) and report whether this block is the last
 // one of the grid to do so. No thread waits on another block: the last block to take a ticket
 // does the final reduction, every other block simply exits.

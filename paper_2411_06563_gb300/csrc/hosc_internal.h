@@ -17,6 +17,8 @@ struct DevParams {
   int newtonian;     // n == 1: eta == 1 exactly
   int have_prev;     // level n-1 history present (else delta_t^- = 0)
   int max_lin_iter;
+  int sweep_fp32;    // S1-S3 arithmetic (and eta, L, E* storage) in float
+  int krylov_fp32;   // right-hand sides, operator weights and Krylov vectors in float
   double h, h2;      // grid spacing (h = k = l) and its square
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
 };
@@ -69,6 +71,12 @@ struct Fields {
   double* nu_avg;          // [N]
   double* eloc;            // [3 N^3] E_HT, E_FF, E_local (diagnostics)
   double* alg_bytes;       // [HOSC_K_COUNT] algorithmic bytes moved by each kernel class
+  // float copies of the state for the FP32 sweeps of mixed precision (rounded once per step)
+  float* us[2];
+  float* vs[2];
+  float* ws[2];
+  float* ths;
+  float* ps;
 };
 
 size_t workspace_layout(int N, Fields* f, char* base);   // returns bytes; fills f when base != 0
@@ -87,6 +95,8 @@ void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 // S6-S8: increments, theta walls, div V, pressure correction and walls, step record.
 void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s);
+// Mixed precision: round u, v, w (level cur, and level 1-cur when both), theta and p to float.
+void launch_shadow(const DevParams& P, const Fields& F, int cur, int both, cudaStream_t s);
 // Diagnostics.
 void launch_diagnostics(const DevParams& P, const Fields& F, int cur, int want_fields,
                         cudaStream_t s);

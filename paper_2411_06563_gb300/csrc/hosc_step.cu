@@ -15,8 +15,55 @@ namespace hosc {
 
 namespace {
 
+__device__ __forceinline__ double absfin(double x) { return isfinite(x) ? fabs(x) : INFINITY; }
 __device__ __forceinline__ int inward(int a, int N) { return a == 0 ? 1 : (a == N - 1 ? N - 2 : a); }
 __device__ __forceinline__ int on_wall(int a, int N) { return (a == 0) | (a == N - 1); }
+
+// Arithmetic type helpers: the sweeps run in T = double (FP64 path, mixed-precision defect
+// steps) or T = float (mixed-precision sweeps: the double state is rounded to float as it is
+// loaded; the rounding noise this leaves in the right-hand side is what the FP64 defect sweeps
+// remove near the steady state).
+template <class T> __device__ __forceinline__ T tpow(T x, T y);
+template <> __device__ __forceinline__ double tpow<double>(double x, double y) { return pow(x, y); }
+template <> __device__ __forceinline__ float tpow<float>(float x, float y) { return powf(x, y); }
+
+template <class T> __device__ __forceinline__ T* as(double* p) { return reinterpret_cast<T*>(p); }
+template <class T> __device__ __forceinline__ const T* as(const double* p) {
+  return reinterpret_cast<const T*>(p);
+}
+
+template <class T, class S>
+__device__ __forceinline__ T grad_axis_t(const S* __restrict__ f, long c, int a, int N, long st,
+                                         T inv2h) {
+  if (a == 0) return (T(-3) * (T)f[c] + T(4) * (T)f[c + st] - (T)f[c + 2 * st]) * inv2h;
+  if (a == N - 1) return (T(3) * (T)f[c] - T(4) * (T)f[c - st] + (T)f[c - 2 * st]) * inv2h;
+  return ((T)f[c + st] - (T)f[c - st]) * inv2h;
+}
+
+template <class T>
+struct Grad9T {
+  T ux, uy, uz, vx, vy, vz, wx, wy, wz;
+};
+
+template <class T, class S>
+__device__ __forceinline__ Grad9T<T> velocity_gradients_t(const S* __restrict__ u,
+                                                          const S* __restrict__ v,
+                                                          const S* __restrict__ w, int i,
+                                                          int j, int k, int N, T inv2h) {
+  const long c = node(i, j, k, N);
+  const long sy = N, sz = (long)N * N;
+  Grad9T<T> g;
+  g.ux = grad_axis_t<T>(u, c, i, N, 1, inv2h);
+  g.uy = grad_axis_t<T>(u, c, j, N, sy, inv2h);
+  g.uz = grad_axis_t<T>(u, c, k, N, sz, inv2h);
+  g.vx = grad_axis_t<T>(v, c, i, N, 1, inv2h);
+  g.vy = grad_axis_t<T>(v, c, j, N, sy, inv2h);
+  g.vz = grad_axis_t<T>(v, c, k, N, sz, inv2h);
+  g.wx = grad_axis_t<T>(w, c, i, N, 1, inv2h);
+  g.wy = grad_axis_t<T>(w, c, j, N, sy, inv2h);
+  g.wz = grad_axis_t<T>(w, c, k, N, sz, inv2h);
+  return g;
+}
 
 // ------------------------------------------------------------------------------------ S1
 
@@ -24,28 +71,30 @@ __device__ __forceinline__ int on_wall(int a, int N) { return (a == 0) | (a == N
 // coefficients). On cube edges and corners, where the one-sided strain rates of two or three
 // no-slip walls vanish identically, I2 is taken at the node one step inward along each of those
 // wall normals.
-__global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const double* __restrict__ u,
-                                                        const double* __restrict__ v,
-                                                        const double* __restrict__ w,
-                                                        double* __restrict__ eta,
-                                                        double* __restrict__ L) {
-  const int N = P.N;
-  const long n3 = (long)N * N * N;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n3) return;
-  int i = (int)(t % N), j = (int)((t / N) % N), k = (int)(t / ((long)N * N));
-  double e = 1.0;
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const T* __restrict__ u,
+                                                        const T* __restrict__ v,
+                                                        const T* __restrict__ w,
+                                                        T* __restrict__ eta, T* __restrict__ L) {
+  const unsigned N = P.N;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * N * N) return;
+  const unsigned q = t / N;
+  int i = (int)(t - q * N), j = (int)(q % N), k = (int)(q / N);
+  T e = T(1);
   if (!P.newtonian) {
-    if (on_wall(i, N) + on_wall(j, N) + on_wall(k, N) >= 2) {
-      i = inward(i, N);
-      j = inward(j, N);
-      k = inward(k, N);
+    if (on_wall(i, (int)N) + on_wall(j, (int)N) + on_wall(k, (int)N) >= 2) {
+      i = inward(i, (int)N);
+      j = inward(j, (int)N);
+      k = inward(k, (int)N);
     }
-    const Grad9 g = velocity_gradients(u, v, w, i, j, k, N, 0.5 / P.h);
-    e = pow(second_invariant(g) + P.I2_eps, 0.5 * (P.n - 1.0));
+    const Grad9T<T> g = velocity_gradients_t<T, T>(u, v, w, i, j, k, N, (T)(0.5 / P.h));
+    const T a = g.uz + g.wx, b = g.uy + g.vx, c = g.vz + g.wy;
+    const T I2 = T(2) * (g.ux * g.ux + g.vy * g.vy + g.wz * g.wz) + a * a + b * b + c * c;
+    e = tpow<T>(I2 + (T)P.I2_eps, (T)(0.5 * (P.n - 1.0)));
   }
   eta[t] = e;
-  L[t] = 1.0 / (P.Pr * e);
+  L[t] = T(1) / ((T)P.Pr * e);
 }
 
 // ------------------------------------------------------------------------------------ S2
@@ -56,131 +105,131 @@ __global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const doubl
 //   E*_y = -p_y/(Pr eta) + (2/eta)(eps_xy eta_x + eps_yy eta_y + eps_zy eta_z) + Ra (theta - theta_ref)/eta
 //   E*_z = -p_z/(Pr eta) + (2/eta)(eps_xz eta_x + eps_yz eta_y + eps_zz eta_z)
 // Gradients are central inside and one-sided at wall nodes.
-__global__ void __launch_bounds__(kThreads) k_sources(DevParams P, const double* __restrict__ u,
-                                                     const double* __restrict__ v,
-                                                     const double* __restrict__ w,
-                                                     const double* __restrict__ th,
-                                                     const double* __restrict__ p,
-                                                     const double* __restrict__ eta,
-                                                     double* __restrict__ Eu,
-                                                     double* __restrict__ Ev,
-                                                     double* __restrict__ Ew) {
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_sources(DevParams P, const T* __restrict__ u,
+                                                     const T* __restrict__ v,
+                                                     const T* __restrict__ w,
+                                                     const T* __restrict__ th,
+                                                     const T* __restrict__ p,
+                                                     const T* __restrict__ eta,
+                                                     T* __restrict__ Eu, T* __restrict__ Ev,
+                                                     T* __restrict__ Ew) {
   const int N = P.N;
-  const long n3 = (long)N * N * N;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n3) return;
-  const int i = (int)(t % N), j = (int)((t / N) % N), k = (int)(t / ((long)N * N));
-  const double inv2h = 0.5 / P.h;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (unsigned)N * N * N) return;
+  const unsigned q = t / (unsigned)N;
+  const int i = (int)(t - q * (unsigned)N), j = (int)(q % (unsigned)N), k = (int)(q / (unsigned)N);
+  const T inv2h = (T)(0.5 / P.h);
   const long sy = N, sz = (long)N * N;
-  const Grad9 g = velocity_gradients(u, v, w, i, j, k, N, inv2h);
-  const double ex = grad_axis(eta, t, i, N, 1, inv2h);
-  const double ey = grad_axis(eta, t, j, N, sy, inv2h);
-  const double ez = grad_axis(eta, t, k, N, sz, inv2h);
-  const double px = grad_axis(p, t, i, N, 1, inv2h);
-  const double py = grad_axis(p, t, j, N, sy, inv2h);
-  const double pz = grad_axis(p, t, k, N, sz, inv2h);
-  const double e = eta[t];
-  const double exy = 0.5 * (g.uy + g.vx), exz = 0.5 * (g.uz + g.wx), eyz = 0.5 * (g.vz + g.wy);
-  const double a = 1.0 / (P.Pr * e), b = 2.0 / e;
+  const Grad9T<T> g = velocity_gradients_t<T, T>(u, v, w, i, j, k, N, inv2h);
+  const T ex = grad_axis_t<T>(eta, t, i, N, 1, inv2h);
+  const T ey = grad_axis_t<T>(eta, t, j, N, sy, inv2h);
+  const T ez = grad_axis_t<T>(eta, t, k, N, sz, inv2h);
+  const T px = grad_axis_t<T>(p, t, i, N, 1, inv2h);
+  const T py = grad_axis_t<T>(p, t, j, N, sy, inv2h);
+  const T pz = grad_axis_t<T>(p, t, k, N, sz, inv2h);
+  const T e = eta[t];
+  const T exy = T(0.5) * (g.uy + g.vx), exz = T(0.5) * (g.uz + g.wx), eyz = T(0.5) * (g.vz + g.wy);
+  const T a = T(1) / ((T)P.Pr * e), b = T(2) / e;
   Eu[t] = -px * a + b * (g.ux * ex + exy * ey + exz * ez);
-  Ev[t] = -py * a + b * (exy * ex + g.vy * ey + eyz * ez) + P.Ra * (th[t] - P.theta_ref) / e;
+  Ev[t] = -py * a + b * (exy * ex + g.vy * ey + eyz * ez) + (T)P.Ra * ((T)th[t] - (T)P.theta_ref) / e;
   Ew[t] = -pz * a + b * (exz * ex + eyz * ey + g.wz * ez);
 }
 
 // ------------------------------------------------------------------------------------ S3/S4
 
 // 7-point neighbourhood order: centre, x+, x-, y+, y-, z+, z-.
+template <class T>
 struct D7 {
-  double dx, dy, dz, dxx, dyy, dzz;
+  T dx, dy, dz, dxx, dyy, dzz;
 };
 
-__device__ __forceinline__ D7 diffs7(const double f[7], double inv2h, double invh2) {
-  D7 d;
+template <class T>
+__device__ __forceinline__ D7<T> diffs7(const T f[7], T inv2h, T invh2) {
+  D7<T> d;
   d.dx = (f[1] - f[2]) * inv2h;
   d.dy = (f[3] - f[4]) * inv2h;
   d.dz = (f[5] - f[6]) * inv2h;
-  d.dxx = (f[1] - 2.0 * f[0] + f[2]) * invh2;
-  d.dyy = (f[3] - 2.0 * f[0] + f[4]) * invh2;
-  d.dzz = (f[5] - 2.0 * f[0] + f[6]) * invh2;
+  d.dxx = (f[1] - T(2) * f[0] + f[2]) * invh2;
+  d.dyy = (f[3] - T(2) * f[0] + f[4]) * invh2;
+  d.dzz = (f[5] - T(2) * f[0] + f[6]) * invh2;
   return d;
 }
 
-__device__ __forceinline__ void load7(const double* __restrict__ a, long c, long sy, long sz,
-                                      double f[7]) {
-  f[0] = a[c];
-  f[1] = a[c + 1];
-  f[2] = a[c - 1];
-  f[3] = a[c + sy];
-  f[4] = a[c - sy];
-  f[5] = a[c + sz];
-  f[6] = a[c - sz];
+template <class T, class S>
+__device__ __forceinline__ void load7(const S* __restrict__ a, long c, long sy, long sz, T f[7]) {
+  f[0] = (T)a[c];
+  f[1] = (T)a[c + 1];
+  f[2] = (T)a[c - 1];
+  f[3] = (T)a[c + sy];
+  f[4] = (T)a[c - sy];
+  f[5] = (T)a[c + sz];
+  f[6] = (T)a[c - sz];
 }
 
 // 19-point neighbourhood: 0 c, 1 x+, 2 x-, 3 y+, 4 y-, 5 z+, 6 z-,
 // 7 x+y+, 8 x-y+, 9 x+y-, 10 x-y-, 11 y+z+, 12 y-z+, 13 y+z-, 14 y-z-,
 // 15 z+x+, 16 z-x+, 17 z+x-, 18 z-x-.
-__device__ __forceinline__ void load19(const double* __restrict__ a, long c, long sy, long sz,
-                                       double f[19]) {
-  load7(a, c, sy, sz, f);
-  f[7] = a[c + 1 + sy];
-  f[8] = a[c - 1 + sy];
-  f[9] = a[c + 1 - sy];
-  f[10] = a[c - 1 - sy];
-  f[11] = a[c + sy + sz];
-  f[12] = a[c - sy + sz];
-  f[13] = a[c + sy - sz];
-  f[14] = a[c - sy - sz];
-  f[15] = a[c + sz + 1];
-  f[16] = a[c - sz + 1];
-  f[17] = a[c + sz - 1];
-  f[18] = a[c - sz - 1];
+template <class T>
+__device__ __forceinline__ void load19(const T* __restrict__ a, long c, long sy, long sz,
+                                       T f[19]) {
+  load7<T, T>(a, c, sy, sz, f);
+  f[7] = (T)a[c + 1 + sy];
+  f[8] = (T)a[c - 1 + sy];
+  f[9] = (T)a[c + 1 - sy];
+  f[10] = (T)a[c - 1 - sy];
+  f[11] = (T)a[c + sy + sz];
+  f[12] = (T)a[c - sy + sz];
+  f[13] = (T)a[c + sy - sz];
+  f[14] = (T)a[c - sy - sz];
+  f[15] = (T)a[c + sz + 1];
+  f[16] = (T)a[c - sz + 1];
+  f[17] = (T)a[c + sz - 1];
+  f[18] = (T)a[c - sz - 1];
 }
 
 // One edge group of Eq. (5) on a uniform grid, directions (a, b):
 //   da^2 db^2 chi - Vb da^2 db chi - Va da db^2 chi - c1 da db chi
-// F[pp], F[0p], F[mp], F[p0], F[00], F[m0], F[pm], F[0m], F[mm] (first index along a).
-__device__ __forceinline__ double edge_group(double Fpp, double F0p, double Fmp, double Fp0,
-                                             double F00, double Fm0, double Fpm, double F0m,
-                                             double Fmm, double Va, double Vb, double c1,
-                                             double h) {
-  const double ih = 1.0 / h;
-  const double ih2 = ih * ih;
-  const double d22 = (Fpp + Fmp + Fpm + Fmm - 2.0 * (F0p + F0m + Fp0 + Fm0) + 4.0 * F00) * ih2 * ih2;
-  const double d21 = ((Fpp - 2.0 * F0p + Fmp) - (Fpm - 2.0 * F0m + Fmm)) * (0.5 * ih2 * ih);
-  const double d12 = ((Fpp - 2.0 * Fp0 + Fpm) - (Fmp - 2.0 * Fm0 + Fmm)) * (0.5 * ih2 * ih);
-  const double d11 = (Fpp - Fmp - Fpm + Fmm) * (0.25 * ih2);
+// from F[pp], F[0p], F[mp], F[p0], F[00], F[m0], F[pm], F[0m], F[mm] (first index along a).
+template <class T>
+__device__ __forceinline__ T edge_group(T Fpp, T F0p, T Fmp, T Fp0, T F00, T Fm0, T Fpm, T F0m,
+                                        T Fmm, T Va, T Vb, T c1, T ih) {
+  const T ih2 = ih * ih;
+  const T d22 = (Fpp + Fmp + Fpm + Fmm - T(2) * (F0p + F0m + Fp0 + Fm0) + T(4) * F00) * ih2 * ih2;
+  const T d21 = ((Fpp - T(2) * F0p + Fmp) - (Fpm - T(2) * F0m + Fmm)) * (T(0.5) * ih2 * ih);
+  const T d12 = ((Fpp - T(2) * Fp0 + Fpm) - (Fmp - T(2) * Fm0 + Fmm)) * (T(0.5) * ih2 * ih);
+  const T d11 = (Fpp - Fmp - Fpm + Fmm) * (T(0.25) * ih2);
   return d22 - Vb * d21 - Va * d12 - c1 * d11;
 }
 
 // Coefficients of Eq. (5) shared by the systems with the same G*, H*, I* (K* = 0).
+template <class T>
 struct Eq5 {
-  double G, H, I, al, be, ga, M1, M2, M3, p1, q1, r1;
+  T G, H, I, al, be, ga, M1, M2, M3, p1, q1, r1;
 };
 
 // [1 + (dx^2 - G dx) h^2/12 + (dy^2 - H dy) k^2/12 + (dz^2 - I dz) l^2/12 + (dt/2) dt^-] f
-__device__ __forceinline__ double bracket(const double f[7], double f_prev, const Eq5& c,
-                                          double inv2h, double invh2, double h2_12) {
-  const D7 d = diffs7(f, inv2h, invh2);
-  return f[0] + h2_12 * ((d.dxx - c.G * d.dx) + (d.dyy - c.H * d.dy) + (d.dzz - c.I * d.dz)) +
-         0.5 * (f[0] - f_prev);
+template <class T>
+__device__ __forceinline__ T bracket(const D7<T>& d, T f0, T f_prev, const Eq5<T>& c, T h2_12) {
+  return f0 + h2_12 * ((d.dxx - c.G * d.dx) + (d.dyy - c.H * d.dy) + (d.dzz - c.I * d.dz)) +
+         T(0.5) * (f0 - f_prev);
 }
 
-__device__ __forceinline__ Eq5 eq5_coefficients(const double G7[7], const double H7[7],
-                                                const double I7[7], double Gp, double Hp,
-                                                double Ip, double inv2h, double invh2,
-                                                double h2_12) {
-  Eq5 c;
+template <class T>
+__device__ __forceinline__ Eq5<T> eq5_coefficients(const T G7[7], const T H7[7], const T I7[7],
+                                                   T Gp, T Hp, T Ip, T inv2h, T invh2, T h2_12) {
+  Eq5<T> c;
   c.G = G7[0];
   c.H = H7[0];
   c.I = I7[0];
-  const D7 dG = diffs7(G7, inv2h, invh2), dH = diffs7(H7, inv2h, invh2),
-           dI = diffs7(I7, inv2h, invh2);
-  c.al = 1.0 + h2_12 * (c.G * c.G - 2.0 * dG.dx);
-  c.be = 1.0 + h2_12 * (c.H * c.H - 2.0 * dH.dy);
-  c.ga = 1.0 + h2_12 * (c.I * c.I - 2.0 * dI.dz);
-  c.M1 = bracket(G7, Gp, c, inv2h, invh2, h2_12);
-  c.M2 = bracket(H7, Hp, c, inv2h, invh2, h2_12);
-  c.M3 = bracket(I7, Ip, c, inv2h, invh2, h2_12);
+  const D7<T> dG = diffs7<T>(G7, inv2h, invh2), dH = diffs7<T>(H7, inv2h, invh2),
+              dI = diffs7<T>(I7, inv2h, invh2);
+  c.al = T(1) + h2_12 * (c.G * c.G - T(2) * dG.dx);
+  c.be = T(1) + h2_12 * (c.H * c.H - T(2) * dH.dy);
+  c.ga = T(1) + h2_12 * (c.I * c.I - T(2) * dI.dz);
+  c.M1 = bracket<T>(dG, G7[0], Gp, c, h2_12);
+  c.M2 = bracket<T>(dH, H7[0], Hp, c, h2_12);
+  c.M3 = bracket<T>(dI, I7[0], Ip, c, h2_12);
   // p1, q1, r1 with h = k = l: -G H + 2/(h^2+k^2) (k^2 dy G + h^2 dx H) = -G H + dy G + dx H
   c.p1 = -c.G * c.H + (dG.dy + dH.dx);
   c.q1 = -c.H * c.I + (dH.dz + dI.dy);
@@ -189,18 +238,18 @@ __device__ __forceinline__ Eq5 eq5_coefficients(const double G7[7], const double
 }
 
 // The level-n operator of Eq. (5) applied to chi (19 points):
-//  -al dx^2 - be dy^2 - ga dz^2 + M1 dx + M2 dy + M3 dz
-//  - (h^2/6) [yz group + xy group + zx group]
-__device__ __forceinline__ double applyB(const Eq5& c, const double f[19], double h, double inv2h,
-                                         double invh2) {
-  const D7 d = diffs7(f, inv2h, invh2);
-  const double gxy = edge_group(f[7], f[3], f[8], f[1], f[0], f[2], f[9], f[4], f[10], c.G, c.H,
-                                c.p1, h);
-  const double gyz = edge_group(f[11], f[5], f[12], f[3], f[0], f[4], f[13], f[6], f[14], c.H,
-                                c.I, c.q1, h);
-  const double gzx = edge_group(f[15], f[1], f[16], f[5], f[0], f[6], f[17], f[2], f[18], c.I,
-                                c.G, c.r1, h);
-  const double m5 = h * h / 6.0;
+//  -al dx^2 - be dy^2 - ga dz^2 + M1 dx + M2 dy + M3 dz - (h^2/6) [yz group + xy group + zx group]
+template <class T>
+__device__ __forceinline__ T applyB(const Eq5<T>& c, const T f[19], double h, T inv2h, T invh2) {
+  const D7<T> d = diffs7<T>(f, inv2h, invh2);
+  const T ih = (T)(1.0 / h);
+  const T gxy = edge_group<T>(f[7], f[3], f[8], f[1], f[0], f[2], f[9], f[4], f[10], c.G, c.H,
+                              c.p1, ih);
+  const T gyz = edge_group<T>(f[11], f[5], f[12], f[3], f[0], f[4], f[13], f[6], f[14], c.H, c.I,
+                              c.q1, ih);
+  const T gzx = edge_group<T>(f[15], f[1], f[16], f[5], f[0], f[6], f[17], f[2], f[18], c.I, c.G,
+                              c.r1, ih);
+  const T m5 = (T)(h * h / 6.0);
   return -c.al * d.dxx - c.be * d.dyy - c.ga * d.dzz + c.M1 * d.dx + c.M2 * d.dy + c.M3 * d.dz -
          m5 * (gyz + gxy + gzx);
 }
@@ -210,113 +259,119 @@ __device__ __forceinline__ double applyB(const Eq5& c, const double f[19], doubl
 // level-(n+1) operator is only 6 dt/h^2, so that mode grows once |G*|^2 h^2 > 24 (and the mode
 // alternating in one direction once dt |G*|^2 > 4 L). Zero in resolved flows; it changes the
 // pseudo-time path only, never the steady state.
-__device__ __forceinline__ double pseudo_time_mass(double G, double H, double I, double L,
-                                                   double dt, double invh2, double kappa) {
-  const double g2 = G * G + H * H + I * I;
-  const double s = fmax(0.0, fmax(dt * (g2 / 6.0 - invh2), dt * g2 / 6.0 - 2.0 * L / 3.0));
+template <class T>
+__device__ __forceinline__ T pseudo_time_mass(T G, T H, T I, T L, T dt, T invh2, T kappa) {
+  const T g2 = G * G + H * H + I * I;
+  const T s = fmax(T(0), fmax(dt * (g2 / T(6) - invh2), dt * g2 / T(6) - T(2) * L / T(3)));
   return kappa * s;
 }
 
 // Right-hand sides of the increment form of Eq. (6),  A (chi^{n+1} - chi^n) = dt (R - B chi^n),
 // for u, v, w, theta at interior nodes, and the seven level-(n+1) weights L1..L7 of the momentum
-// and energy systems.
+// and energy systems. Tc: arithmetic and the type of L, E*; Ts: type of the outputs.
+template <class Tc, class Ts>
 __global__ void __launch_bounds__(kThreads) k_rhs(
-    DevParams P, const double* __restrict__ u, const double* __restrict__ v,
-    const double* __restrict__ w, const double* __restrict__ th, const double* __restrict__ L,
-    const double* __restrict__ Eu, const double* __restrict__ Ev, const double* __restrict__ Ew,
-    const double* __restrict__ Lp, const double* __restrict__ up, const double* __restrict__ vp,
-    const double* __restrict__ wp, const double* __restrict__ Eup,
-    const double* __restrict__ Evp, const double* __restrict__ Ewp, Fields F) {
-  const int N = P.N, ni = N - 2;
-  const long cnt = (long)ni * ni * ni;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
-  const int i = 1 + (int)(t % ni), j = 1 + (int)((t / ni) % ni), k = 1 + (int)(t / ((long)ni * ni));
+    DevParams P, const Tc* __restrict__ u, const Tc* __restrict__ v,
+    const Tc* __restrict__ w, const Tc* __restrict__ th, const Tc* __restrict__ L,
+    const Tc* __restrict__ Eu, const Tc* __restrict__ Ev, const Tc* __restrict__ Ew,
+    const Tc* __restrict__ Lp, const Tc* __restrict__ up, const Tc* __restrict__ vp,
+    const Tc* __restrict__ wp, const Tc* __restrict__ Eup, const Tc* __restrict__ Evp,
+    const Tc* __restrict__ Ewp, Fields F) {
+  const int N = P.N;
+  const unsigned ni = N - 2;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ni * ni * ni) return;
+  const unsigned q = t / ni;
+  const int i = 1 + (int)(t - q * ni), j = 1 + (int)(q % ni), k = 1 + (int)(q / ni);
   const long sy = N, sz = (long)N * N;
   const long c = node(i, j, k, N);
-  const double h = P.h, h2 = P.h2, inv2h = 0.5 / h, invh2 = 1.0 / h2, h2_12 = h2 / 12.0;
-  const double dt = P.dt;
+  const double h = P.h, h2 = P.h2, inv2h = 0.5 / h, invh2 = 1.0 / h2;
+  const Tc tinv2h = (Tc)inv2h, tinvh2 = (Tc)invh2, h2_12 = (Tc)(h2 / 12.0), tdt = (Tc)P.dt;
+  Ts* const* rhs = reinterpret_cast<Ts* const*>(F.rhs);
+  Ts* const* Am = reinterpret_cast<Ts* const*>(F.Am);
+  Ts* const* Ae = reinterpret_cast<Ts* const*>(F.Ae);
 
-  double L7[7], u7[7], v7[7], w7[7];
-  load7(L, c, sy, sz, L7);
-  load7(u, c, sy, sz, u7);
-  load7(v, c, sy, sz, v7);
-  load7(w, c, sy, sz, w7);
-  const double Lc = L7[0];
-  const double Lpc = P.have_prev ? Lp[c] : Lc;
-  const double upc = P.have_prev ? up[c] : u7[0];
-  const double vpc = P.have_prev ? vp[c] : v7[0];
-  const double wpc = P.have_prev ? wp[c] : w7[0];
+  Tc L7[7], u7[7], v7[7], w7[7];
+  load7<Tc, Tc>(L, c, sy, sz, L7);
+  load7<Tc, Tc>(u, c, sy, sz, u7);
+  load7<Tc, Tc>(v, c, sy, sz, v7);
+  load7<Tc, Tc>(w, c, sy, sz, w7);
+  const Tc Lc = L7[0];
+  const Tc Lpc = P.have_prev ? Lp[c] : Lc;
+  const Tc upc = P.have_prev ? (Tc)up[c] : u7[0];
+  const Tc vpc = P.have_prev ? (Tc)vp[c] : v7[0];
+  const Tc wpc = P.have_prev ? (Tc)wp[c] : w7[0];
 
   // ---------------- momentum: L = 1/(Pr eta), G* = u L, H* = v L, I* = w L, K* = 0
   {
-    double G7[7], H7[7], I7[7];
+    Tc G7[7], H7[7], I7[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
       G7[q] = u7[q] * L7[q];
       H7[q] = v7[q] * L7[q];
       I7[q] = w7[q] * L7[q];
     }
-    const Eq5 cm = eq5_coefficients(G7, H7, I7, upc * Lpc, vpc * Lpc, wpc * Lpc, inv2h, invh2, h2_12);
-    const double* E[3] = {Eu, Ev, Ew};
-    const double* Ep[3] = {Eup, Evp, Ewp};
-    const double* X[3] = {u, v, w};
+    const Eq5<Tc> cm = eq5_coefficients<Tc>(G7, H7, I7, upc * Lpc, vpc * Lpc, wpc * Lpc, tinv2h,
+                                            tinvh2, h2_12);
+    const Tc* E[3] = {Eu, Ev, Ew};
+    const Tc* Ep[3] = {Eup, Evp, Ewp};
+    const Tc* X[3] = {u, v, w};
 #pragma unroll 1
     for (int s = 0; s < 3; ++s) {
-      double E7[7], f19[19];
-      load7(E[s], c, sy, sz, E7);
-      const double Epc = P.have_prev ? Ep[s][c] : E7[0];
-      const double R = bracket(E7, Epc, cm, inv2h, invh2, h2_12);
-      load19(X[s], c, sy, sz, f19);
-      F.rhs[s][c] = dt * (R - applyB(cm, f19, h, inv2h, invh2));
+      Tc E7[7], f19[19];
+      load7<Tc, Tc>(E[s], c, sy, sz, E7);
+      const Tc Epc = P.have_prev ? Ep[s][c] : E7[0];
+      const Tc R = bracket<Tc>(diffs7<Tc>(E7, tinv2h, tinvh2), E7[0], Epc, cm, h2_12);
+      load19<Tc>(X[s], c, sy, sz, f19);
+      rhs[s][c] = (Ts)(tdt * (R - applyB<Tc>(cm, f19, h, tinv2h, tinvh2)));
     }
     // level-(n+1) weights (Eq. 6): Mx = -dt/(2L) + h^2/12, M15 = (h^2/(6L)) dx L, ...
-    const D7 dL = diffs7(L7, inv2h, invh2);
-    const double M = -dt / (2.0 * Lc) + h2_12;
-    const double m15 = h2 / (6.0 * Lc) * dL.dx, m16 = h2 / (6.0 * Lc) * dL.dy,
-                 m17 = h2 / (6.0 * Lc) * dL.dz;
-    double M18 = 0.5 * (Lc - Lpc) + h2_12 * ((dL.dxx - cm.G * dL.dx) +
-                                             (dL.dyy - cm.H * dL.dy) +
+    const D7<Tc> dL = diffs7<Tc>(L7, tinv2h, tinvh2);
+    const Tc M = -tdt / (Tc(2) * Lc) + h2_12;
+    const Tc h2_6L = (Tc)h2 / (Tc(6) * Lc);
+    const Tc m15 = h2_6L * dL.dx, m16 = h2_6L * dL.dy, m17 = h2_6L * dL.dz;
+    Tc M18 = Tc(0.5) * (Lc - Lpc) + h2_12 * ((dL.dxx - cm.G * dL.dx) + (dL.dyy - cm.H * dL.dy) +
                                              (dL.dzz - cm.I * dL.dz));
     // keep the extrapolated mass positive where L changes fast (the steady state is unaffected)
-    if (P.a_limit > 0.0) M18 = fmax(M18, -P.a_limit * Lc);
-    const double a2 = M * invh2;
-    const double sig_m = P.a_boost > 0.0
-                             ? pseudo_time_mass(cm.G, cm.H, cm.I, Lc, dt, invh2, P.a_boost) : 0.0;
-    F.Am[0][c] = Lc * (1.0 - 6.0 * a2) + M18 + sig_m;
-    F.Am[1][c] = Lc * (a2 - M * cm.G * inv2h + m15 * inv2h);
-    F.Am[2][c] = Lc * (a2 + M * cm.G * inv2h - m15 * inv2h);
-    F.Am[3][c] = Lc * (a2 - M * cm.H * inv2h + m16 * inv2h);
-    F.Am[4][c] = Lc * (a2 + M * cm.H * inv2h - m16 * inv2h);
-    F.Am[5][c] = Lc * (a2 - M * cm.I * inv2h + m17 * inv2h);
-    F.Am[6][c] = Lc * (a2 + M * cm.I * inv2h - m17 * inv2h);
+    if (P.a_limit > 0.0) M18 = fmax(M18, -(Tc)P.a_limit * Lc);
+    const Tc sig_m = P.a_boost > 0.0
+                         ? pseudo_time_mass<Tc>(cm.G, cm.H, cm.I, Lc, tdt, tinvh2, (Tc)P.a_boost)
+                         : Tc(0);
+    const Tc a2 = M * tinvh2;
+    Am[0][c] = (Ts)(Lc * (Tc(1) - Tc(6) * a2) + M18 + sig_m);
+    Am[1][c] = (Ts)(Lc * (a2 - M * cm.G * tinv2h + m15 * tinv2h));
+    Am[2][c] = (Ts)(Lc * (a2 + M * cm.G * tinv2h - m15 * tinv2h));
+    Am[3][c] = (Ts)(Lc * (a2 - M * cm.H * tinv2h + m16 * tinv2h));
+    Am[4][c] = (Ts)(Lc * (a2 + M * cm.H * tinv2h - m16 * tinv2h));
+    Am[5][c] = (Ts)(Lc * (a2 - M * cm.I * tinv2h + m17 * tinv2h));
+    Am[6][c] = (Ts)(Lc * (a2 + M * cm.I * tinv2h - m17 * tinv2h));
   }
   // ---------------- energy: L = 1, G* = u, H* = v, I* = w, K* = E* = 0
   {
-    const Eq5 ce = eq5_coefficients(u7, v7, w7, upc, vpc, wpc, inv2h, invh2, h2_12);
-    double f19[19];
-    load19(th, c, sy, sz, f19);
-    F.rhs[3][c] = -dt * applyB(ce, f19, h, inv2h, invh2);
-    const double M = -0.5 * dt + h2_12;
-    const double a2 = M * invh2;
-    const double sig_e = P.a_boost > 0.0
-                             ? pseudo_time_mass(ce.G, ce.H, ce.I, 1.0, dt, invh2, P.a_boost) : 0.0;
-    F.Ae[0][c] = 1.0 - 6.0 * a2 + sig_e;
-    F.Ae[1][c] = a2 - M * ce.G * inv2h;
-    F.Ae[2][c] = a2 + M * ce.G * inv2h;
-    F.Ae[3][c] = a2 - M * ce.H * inv2h;
-    F.Ae[4][c] = a2 + M * ce.H * inv2h;
-    F.Ae[5][c] = a2 - M * ce.I * inv2h;
-    F.Ae[6][c] = a2 + M * ce.I * inv2h;
+    const Eq5<Tc> ce = eq5_coefficients<Tc>(u7, v7, w7, upc, vpc, wpc, tinv2h, tinvh2, h2_12);
+    Tc f19[19];
+    load19<Tc>(th, c, sy, sz, f19);
+    rhs[3][c] = (Ts)(-tdt * applyB<Tc>(ce, f19, h, tinv2h, tinvh2));
+    const Tc M = Tc(-0.5) * tdt + h2_12;
+    const Tc a2 = M * tinvh2;
+    const Tc sig_e = P.a_boost > 0.0
+                         ? pseudo_time_mass<Tc>(ce.G, ce.H, ce.I, Tc(1), tdt, tinvh2, (Tc)P.a_boost)
+                         : Tc(0);
+    Ae[0][c] = (Ts)(Tc(1) - Tc(6) * a2 + sig_e);
+    Ae[1][c] = (Ts)(a2 - M * ce.G * tinv2h);
+    Ae[2][c] = (Ts)(a2 + M * ce.G * tinv2h);
+    Ae[3][c] = (Ts)(a2 - M * ce.H * tinv2h);
+    Ae[4][c] = (Ts)(a2 + M * ce.H * tinv2h);
+    Ae[5][c] = (Ts)(a2 - M * ce.I * tinv2h);
+    Ae[6][c] = (Ts)(a2 + M * ce.I * tinv2h);
   }
 }
 
 // ------------------------------------------------------------------------------------ S6-S8
 
-__device__ __forceinline__ double absfin(double x) { return isfinite(x) ? fabs(x) : INFINITY; }
-
 // chi^{n+1} = chi^n + x at interior nodes (u, v, w into the other buffer, theta in place); wall
 // velocities are carried over. Max |x| over the four systems goes to the step record.
+template <class Ts>
 __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Fields F, int cur,
                                                               int nblocks) {
   __shared__ double smem[32];
@@ -328,7 +383,8 @@ __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Field
     const int i = (int)(t % N), j = (int)((t / N) % N), k = (int)(t / ((long)N * N));
     const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
     if (inner) {
-      const double xu = F.x[0][t], xv = F.x[1][t], xw = F.x[2][t], xt = F.x[3][t];
+      const double xu = (double)as<Ts>(F.x[0])[t], xv = (double)as<Ts>(F.x[1])[t],
+                   xw = (double)as<Ts>(F.x[2])[t], xt = (double)as<Ts>(F.x[3])[t];
       F.u[1 - cur][t] = F.u[cur][t] + xu;
       F.v[1 - cur][t] = F.v[cur][t] + xv;
       F.w[1 - cur][t] = F.w[cur][t] + xw;
@@ -487,29 +543,101 @@ __global__ void k_finish_record(Fields F) {
 
 int red_blocks(long count) { return (int)((count + kThreads - 1) / kThreads); }
 
+namespace {
+// Float copies of the state for the FP32 sweeps (one rounding per node and step).
+__global__ void __launch_bounds__(kThreads) k_shadow(int n3, const double* __restrict__ u,
+                                                     const double* __restrict__ v,
+                                                     const double* __restrict__ w,
+                                                     const double* __restrict__ th,
+                                                     const double* __restrict__ p,
+                                                     float* __restrict__ us, float* __restrict__ vs,
+                                                     float* __restrict__ ws,
+                                                     float* __restrict__ ths,
+                                                     float* __restrict__ ps) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n3) return;
+  us[t] = (float)u[t];
+  vs[t] = (float)v[t];
+  ws[t] = (float)w[t];
+  if (ths) {
+    ths[t] = (float)th[t];
+    ps[t] = (float)p[t];
+  }
+}
+}  // namespace
+
+void launch_shadow(const DevParams& P, const Fields& F, int cur, int both, cudaStream_t s) {
+  const int n3 = P.N * P.N * P.N;
+  k_shadow<<<red_blocks(n3), kThreads, 0, s>>>(n3, F.u[cur], F.v[cur], F.w[cur], F.th, F.p,
+                                               F.us[cur], F.vs[cur], F.ws[cur], F.ths, F.ps);
+  if (both) {
+    const int o = 1 - cur;
+    k_shadow<<<red_blocks(n3), kThreads, 0, s>>>(n3, F.u[o], F.v[o], F.w[o], nullptr, nullptr,
+                                                 F.us[o], F.vs[o], F.ws[o], nullptr, nullptr);
+  }
+}
+
 void launch_viscosity(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
   const long n3 = (long)P.N * P.N * P.N;
-  k_viscosity<<<red_blocks(n3), kThreads, 0, s>>>(P, F.u[cur], F.v[cur], F.w[cur], F.eta, F.L[cur]);
+  if (P.sweep_fp32)
+    k_viscosity<float><<<red_blocks(n3), kThreads, 0, s>>>(
+        P, F.us[cur], F.vs[cur], F.ws[cur], reinterpret_cast<float*>(F.eta),
+        reinterpret_cast<float*>(F.L[cur]));
+  else
+    k_viscosity<double><<<red_blocks(n3), kThreads, 0, s>>>(P, F.u[cur], F.v[cur], F.w[cur],
+                                                            F.eta, F.L[cur]);
 }
 
 void launch_sources(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
   const long n3 = (long)P.N * P.N * P.N;
-  k_sources<<<red_blocks(n3), kThreads, 0, s>>>(P, F.u[cur], F.v[cur], F.w[cur], F.th, F.p, F.eta,
-                                                F.Eu[cur], F.Ev[cur], F.Ew[cur]);
+  if (P.sweep_fp32)
+    k_sources<float><<<red_blocks(n3), kThreads, 0, s>>>(
+        P, F.us[cur], F.vs[cur], F.ws[cur], F.ths, F.ps, reinterpret_cast<const float*>(F.eta),
+        reinterpret_cast<float*>(F.Eu[cur]), reinterpret_cast<float*>(F.Ev[cur]),
+        reinterpret_cast<float*>(F.Ew[cur]));
+  else
+    k_sources<double><<<red_blocks(n3), kThreads, 0, s>>>(P, F.u[cur], F.v[cur], F.w[cur], F.th,
+                                                          F.p, F.eta, F.Eu[cur], F.Ev[cur],
+                                                          F.Ew[cur]);
+}
+
+template <class Tc, class Ts>
+static void rhs_t(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
+  const long ni = P.N - 2;
+  const int o = 1 - cur;
+  auto T = [](double* p) { return reinterpret_cast<const Tc*>(p); };
+  // the state: float copies for FP32 sweeps, the double arrays otherwise
+  const Tc *u, *v, *w, *th, *up, *vp, *wp;
+  if (sizeof(Tc) == sizeof(float)) {
+    u = (const Tc*)F.us[cur]; v = (const Tc*)F.vs[cur]; w = (const Tc*)F.ws[cur];
+    th = (const Tc*)F.ths;
+    up = (const Tc*)F.us[o]; vp = (const Tc*)F.vs[o]; wp = (const Tc*)F.ws[o];
+  } else {
+    u = (const Tc*)F.u[cur]; v = (const Tc*)F.v[cur]; w = (const Tc*)F.w[cur];
+    th = (const Tc*)F.th;
+    up = (const Tc*)F.u[o]; vp = (const Tc*)F.v[o]; wp = (const Tc*)F.w[o];
+  }
+  k_rhs<Tc, Ts><<<red_blocks(ni * ni * ni), kThreads, 0, s>>>(
+      P, u, v, w, th, T(F.L[cur]), T(F.Eu[cur]), T(F.Ev[cur]), T(F.Ew[cur]), T(F.L[o]), up, vp,
+      wp, T(F.Eu[o]), T(F.Ev[o]), T(F.Ew[o]), F);
 }
 
 void launch_rhs(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
-  const long ni = P.N - 2;
-  const int o = 1 - cur;
-  k_rhs<<<red_blocks(ni * ni * ni), kThreads, 0, s>>>(
-      P, F.u[cur], F.v[cur], F.w[cur], F.th, F.L[cur], F.Eu[cur], F.Ev[cur], F.Ew[cur], F.L[o],
-      F.u[o], F.v[o], F.w[o], F.Eu[o], F.Ev[o], F.Ew[o], F);
+  if (P.sweep_fp32)
+    rhs_t<float, float>(P, F, cur, s);
+  else if (P.krylov_fp32)
+    rhs_t<double, float>(P, F, cur, s);
+  else
+    rhs_t<double, double>(P, F, cur, s);
 }
 
 void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
   const long N = P.N, n3 = N * N * N, ni = N - 2;
   const int b_all = red_blocks(n3);
-  k_apply_increment<<<b_all, kThreads, 0, s>>>(P, F, cur, b_all);
+  if (P.krylov_fp32)
+    k_apply_increment<float><<<b_all, kThreads, 0, s>>>(P, F, cur, b_all);
+  else
+    k_apply_increment<double><<<b_all, kThreads, 0, s>>>(P, F, cur, b_all);
   const int b_walls = red_blocks((N - 2) * N * N);
   k_theta_walls<<<b_walls, kThreads, 0, s>>>(P, F, b_walls);
   const int b_int = red_blocks(ni * ni * ni);

@@ -41,7 +41,7 @@ class hosc_params(ctypes.Structure):
                 ("tol_lin", ctypes.c_double), ("max_lin_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("a_limit", ctypes.c_double), ("a_boost", ctypes.c_double),
-                ("use_history", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("use_history", ctypes.c_int), ("auto_defect", ctypes.c_int)]
 
 
 class hosc_info(ctypes.Structure):
@@ -112,6 +112,8 @@ def lib():
         "hosc_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_long),
                                              _DP]),
         "hosc_kernel_launches": (ctypes.c_long, [_P]),
+        "hosc_set_phase": (ctypes.c_int, [_P, ctypes.c_int]),
+        "hosc_get_phase": (ctypes.c_int, [_P]),
         "hosc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "hosc_last_error_detail": (ctypes.c_char_p, []),
     }
@@ -238,6 +240,14 @@ def hosc_profile_read(h, kernel_id):
 
 def hosc_kernel_launches(h):
     return int(lib().hosc_kernel_launches(h))
+
+
+def hosc_set_phase(h, phase):
+    return lib().hosc_set_phase(h, int(phase))
+
+
+def hosc_get_phase(h):
+    return int(lib().hosc_get_phase(h))
 
 
 # ------------------------------------------------------------------ convenience wrapper

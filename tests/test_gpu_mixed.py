@@ -1,0 +1,97 @@
+"""Mixed precision (FP32 sweeps and Krylov vectors; FP64 state, reductions, pressure update and
+diagnostics) against the FP64 oracle and the FP64 GPU path.
+
+Targets: fields within 1e-5 max-abs and Nu_avg within 1e-4 relative of FP64 at steady state; one
+step from a seeded state within FP32 rounding of the increment.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import hosc_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+H = pytest.importorskip("paper_2411_06563_gb300.hosc")
+from paper_2411_06563_gb300 import inputs  # noqa: E402
+
+FIELDS = (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W), ("th", H.HOSC_THETA), ("p", H.HOSC_P))
+
+
+def _params(N, Ra, n, dt, precision, **kw):
+    p = H.hosc_default_params(N, Ra, 1.0, n)
+    p.dt = dt
+    p.lambda_ = min(0.25 / (N - 1) ** 2 / dt, 0.1)
+    p.precision = precision
+    p.max_lin_iter = 3000
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+@pytest.mark.parametrize("N,Ra,n", [(13, 1e4, 0.75), (22, 2e3, 1.0), (17, 5e3, 1.25)])
+def test_one_step_from_seeded_state(N, Ra, n):
+    """One mixed step against the oracle's FP64 step from a seeded (far from steady) state: the
+    increment chi^{n+1} - chi^n agrees to FP32 accuracy, 2e-5 relative to its size."""
+    dt = 0.002
+    p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-12)
+    op = O.Params(N=N, Ra=Ra, n=n, dt=dt, lam=p.lambda_, tol_lin=1e-12, a_limit=p.a_limit,
+                  a_boost=p.a_boost)
+    st = inputs.cavity_state(N, Ra, seed=100 + N)
+    g = O.Grid(N)
+    new, _ = O.step(dict(st, prev=None, steps=0), op, g)
+    with H.Cavity(p) as cav:
+        for name, which in FIELDS:
+            cav.set(which, st[name])
+        info = cav.step(1)
+        assert info["call_status"] == 0
+        for name, which in FIELDS:
+            got = cav.get(which)
+            inc_ref = new[name] - st[name]
+            scale = max(np.max(np.abs(inc_ref)), 1e-12)
+            assert np.max(np.abs((got - st[name]) - inc_ref)) <= 2e-5 * scale + 1e-12, name
+
+
+def _steady(p, max_steps):
+    with H.Cavity(p) as cav:
+        info = cav.solve_steady(max_steps)
+        phase = H.hosc_get_phase(cav.h)
+        fields = {name: cav.get(which) for name, which in FIELDS}
+        d = cav.diagnostics()
+    return info, phase, fields, d
+
+
+def test_steady_state_matches_fp64():
+    """Newtonian 21^3, Ra = 1e3 (the first configuration): the mixed solve (FP32 sweeps until the
+    step change stalls, then FP64 defect sweeps) reaches the FP64 steady state: fields within
+    1e-5 max-abs, Nu within 1e-4 relative, and the oracle's dt-free steady residual B chi - R of
+    the mixed fields is as small as that of the FP64 fields."""
+    N, dt = 21, 0.02
+    kw = dict(tol_steady=1e-7, tol_div=1e-6, lambda_=0.1)
+    i64, _, f64, d64 = _steady(_params(N, 1e3, 1.0, dt, H.HOSC_FP64, **kw), 20000)
+    imx, phase, fmx, dmx = _steady(_params(N, 1e3, 1.0, dt, H.HOSC_MIXED, **kw), 20000)
+    assert i64["call_status"] == 0 and imx["call_status"] == 0, (i64, imx)
+    assert phase == 1   # the switch to FP64 defect sweeps happened
+    for name, _ in FIELDS[:4]:
+        assert np.max(np.abs(fmx[name] - f64[name])) <= 1e-5, name
+    for k in ("Nu_hot_max", "Nu_hot_mean", "Nu_cold_mean"):
+        assert abs(dmx[k] - d64[k]) <= 1e-4 * abs(d64[k]), k
+    prm = O.Params(N=N, Ra=1e3, n=1.0, dt=dt)
+    cert_mx, div_mx = O.steady_certificate(dict(fmx, prev=None), prm)
+    cert_64, div_64 = O.steady_certificate(dict(f64, prev=None), prm)
+    assert cert_mx <= max(10 * cert_64, 1e-5) and div_mx < 1e-6
+
+
+def test_phase_api():
+    p = _params(9, 1e3, 1.0, 0.01, H.HOSC_MIXED)
+    with H.Cavity(p) as cav:
+        assert H.hosc_get_phase(cav.h) == 0
+        cav.step(2)
+        assert H.hosc_set_phase(cav.h, 1) == 0 and H.hosc_get_phase(cav.h) == 1
+        info = cav.step(2)
+        assert info["call_status"] == 0
+        assert H.hosc_set_phase(cav.h, 2) == H.HOSC_EINVAL
+    p = _params(9, 1e3, 1.0, 0.01, H.HOSC_FP64)
+    with H.Cavity(p) as cav:
+        assert H.hosc_set_phase(cav.h, 1) == H.HOSC_EINVAL
+        assert H.hosc_set_phase(cav.h, 0) == 0
