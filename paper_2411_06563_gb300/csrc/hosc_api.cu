@@ -49,6 +49,11 @@ struct Ctx {
   double best_res = INFINITY;
   long since_best = 0;
   bool shadow_valid = false;   // float copies of the state match the state
+  // one captured step per (phase, cur, have_prev); BiCGSTAB runs as a device-side while loop
+  cudaGraphExec_t graph[2][2][2] = {};
+  cudaStream_t cap[2] = {nullptr, nullptr};   // private streams used only for capture
+  bool graphs_ok = true;                      // capture or instantiation failed once: stay off
+  StepRecord* h_ring = nullptr;
   long launches = 0;
   KrylovScalars* h_ks = nullptr;
   StepRecord* h_rec = nullptr;
@@ -109,6 +114,7 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   d.tol_lin = d.krylov_fp32 ? fmax(p.tol_lin, kFp32TolFloor) : p.tol_lin;
   d.a_limit = p.a_limit;
   d.a_boost = p.a_boost;
+  d.steady_res = p.tol_steady * p.dt;
   return d;
 }
 
@@ -268,6 +274,7 @@ hosc_status run_stage(Ctx* c, int stage) {
   hosc_status st = HOSC_OK;
   switch (stage) {
     case HOSC_STAGE_VISCOSITY:
+      CU(cudaMemsetAsync(F.halt, 0, sizeof(int), c->stream));
       if (c->P.sweep_fp32 && !c->shadow_valid) {
         launch_shadow(c->P, F, c->cur, c->P.have_prev, c->stream);
         c->launches += 1;
@@ -375,6 +382,177 @@ hosc_status one_step(Ctx* c, hosc_info* info) {
   return (hosc_status)c->h_rec->status;
 }
 
+// ------------------------------------------------------------------ captured steps (CUDA graphs)
+
+// Capture one whole step: S1-S4 kernels, then a conditional WHILE node whose body runs two
+// BiCGSTAB iterations (the ping-pong buffers return to their parity) and sets the condition on
+// the device, then the update kernels (and the float state copy in mixed precision). Nothing in
+// the step waits on the host.
+hosc_status capture_step(Ctx* c, cudaGraphExec_t* out) {
+  const DevParams& P = c->P;
+  const Fields& F = c->F;
+  cudaStream_t s0 = c->cap[0], s1 = c->cap[1];
+  cudaGraph_t g = nullptr;
+  CU(cudaGraphCreate(&g, 0));
+  cudaError_t e = cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    CU(e);
+  }
+  launch_viscosity(P, F, c->cur, s0);
+  launch_sources(P, F, c->cur, s0);
+  launch_rhs(P, F, c->cur, s0);
+  launch_bicg_init(P, F, s0);
+  cudaStreamCaptureStatus cs;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  cudaGraph_t cg = nullptr;
+  e = cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, &deps, nullptr, &nd);
+  cudaGraphConditionalHandle h = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cn = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp);
+  if (e == cudaSuccess)
+    e = cudaStreamUpdateCaptureDependencies(s0, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (e == cudaSuccess) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      for (int pp = 0; pp < 2; ++pp) {
+        launch_bicg_pv(P, F, pp, s1);
+        launch_bicg_st(P, F, pp, s1);
+        launch_bicg_xr(P, F, pp, s1);
+      }
+      launch_loop_cond(F, (unsigned long long)h, s1);
+      cudaGraph_t bo = nullptr;
+      e = cudaStreamEndCapture(s1, &bo);
+    }
+  }
+  launch_update(P, F, c->cur, s0);
+  if (P.krylov_fp32) launch_shadow(P, F, 1 - c->cur, 0, s0);
+  cudaGraph_t go = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(s0, &go);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_detail, sizeof(g_detail), "step capture: %s", cudaGetErrorString(e));
+    return HOSC_ECUDA;
+  }
+  return HOSC_OK;
+}
+
+bool graphs_usable(Ctx* c) { return c->graphs_ok && !c->prof_on && c->stage == 0; }
+
+void drop_graphs(Ctx* c) {
+  for (auto& a : c->graph)
+    for (auto& b : a)
+      for (auto& g : b)
+        if (g) {
+          cudaGraphExecDestroy(g);
+          g = nullptr;
+        }
+}
+
+void watch_stall(Ctx* c, double res);
+
+// Fold n device step records (ring) into info; returns the status of the first failing step.
+hosc_status fold_records(Ctx* c, unsigned n, hosc_info* info, bool* steady) {
+  hosc_status st = HOSC_OK;
+  for (unsigned q = 0; q < n; ++q) {
+    const StepRecord& r = c->h_ring[q % kRing];
+    if (info) {
+      info->steps += 1;
+      for (int s = 0; s < 4; ++s) {
+        info->lin_iters += r.iters[s];
+        info->last_iters[s] = r.iters[s];
+      }
+      info->res_steady = r.res;
+      info->div_max = r.div_max;
+      info->lin_res = r.lin_res;
+      info->status = r.status;
+    }
+    int most = 0;
+    for (int s = 0; s < 4; ++s) most = r.iters[s] > most ? r.iters[s] : most;
+    c->launches += 4 + 6 + (c->P.krylov_fp32 ? 1 : 0) + 7L * ((most + 1) / 2 > 0 ? (most + 1) / 2 : 1);
+    if (r.status != HOSC_OK) {
+      st = (hosc_status)r.status;
+      break;
+    }
+    if (steady && r.res < c->P.steady_res && r.div_max < c->P.tol_div) *steady = true;
+    watch_stall(c, r.res);
+  }
+  return st;
+}
+
+// Enqueue up to nsteps captured steps without host synchronisation, then read their records.
+// The device halts the sequence at a failed step (or at the first steady step when stop_steady);
+// the host then knows from the records how many steps ran. Returns the first non-OK status.
+hosc_status graph_steps(Ctx* c, long nsteps, bool stop_steady, hosc_info* info, bool* steady) {
+  const Fields& F = c->F;
+  long done = 0;
+  while (done < nsteps) {
+    const long batch = (nsteps - done) < kRing ? (nsteps - done) : kRing;
+    const int stop = stop_steady ? 1 : 0;
+    CU(cudaMemsetAsync(F.halt, 0, sizeof(int), c->stream));
+    CU(cudaMemsetAsync(F.ring_pos, 0, sizeof(unsigned), c->stream));
+    CU(cudaMemcpyAsync(F.steady_stop, &stop, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    const int cur0 = c->cur, prev0 = c->P.have_prev, phase0 = c->phase;
+    int cur = cur0, hp = prev0;
+    if (c->P.sweep_fp32 && !c->shadow_valid) {   // float state copies for the first FP32 sweep
+      launch_shadow(c->P, F, cur0, prev0, c->stream);
+      c->launches += 1;
+      c->shadow_valid = true;
+    }
+    for (long q = 0; q < batch; ++q) {
+      cudaGraphExec_t& ge = c->graph[phase0][cur][hp];
+      if (!ge) {
+        const int save_cur = c->cur, save_hp = c->P.have_prev;
+        c->cur = cur;
+        c->P.have_prev = hp;
+        hosc_status st = capture_step(c, &ge);
+        c->cur = save_cur;
+        c->P.have_prev = save_hp;
+        if (st) {
+          c->graphs_ok = false;
+          return st;
+        }
+      }
+      CU(cudaGraphLaunch(ge, c->stream));
+      cur ^= 1;
+      hp = c->prm.use_history ? 1 : 0;
+    }
+    unsigned n = 0;
+    CU(cudaMemcpyAsync(&n, F.ring_pos, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (n > (unsigned)batch) n = (unsigned)batch;
+    CU(cudaMemcpyAsync(c->h_ring, F.ring, n * sizeof(StepRecord), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CU(cudaMemcpyAsync(c->h_rec, F.rec, sizeof(StepRecord), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    // the state advanced by the n steps that ran
+    c->cur = cur0 ^ (int)(n & 1u);
+    if (n > 0) c->P.have_prev = c->prm.use_history ? 1 : 0;
+    done += n;
+    bool st_steady = false;
+    hosc_status st = fold_records(c, n, info, &st_steady);
+    if (steady) *steady = *steady || st_steady;
+    if (st) return st;
+    if (stop_steady && st_steady) return HOSC_OK;
+    if (n < (unsigned)batch) return HOSC_OK;   // halted without failure (steady stop)
+    if (c->phase != phase0) continue;          // a stall switched the phase: next batch uses it
+  }
+  return HOSC_OK;
+}
+
 hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** out) {
   if (!out) return HOSC_EINVAL;
   *out = nullptr;
@@ -414,6 +592,9 @@ hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** ou
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_ks, 4 * sizeof(KrylovScalars));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_rec, sizeof(StepRecord));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_scal, 8 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_ring, kRing * sizeof(StepRecord));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap[0], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap[1], cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     snprintf(g_detail, sizeof(g_detail), "create: %s", cudaGetErrorString(e));
     hosc_destroy(c);
@@ -470,7 +651,9 @@ size_t workspace_layout(int N, Fields* f, char* base) {
   }
   F.div = fld();
   F.eloc = (double*)take(3 * n3 * sizeof(double));
-  F.red = (double*)take((size_t)red_blocks((long)n3) * kRedSlots * sizeof(double));
+  // per-block partials: up to one row of blocks per system (the Krylov launches) or one per
+  // block of a whole-grid launch
+  F.red = (double*)take((size_t)4 * red_blocks((long)n3) * kRedSlots * sizeof(double));
   F.counter = (unsigned int*)take(sizeof(unsigned int));
   F.ks = (KrylovScalars*)take(4 * sizeof(KrylovScalars));
   F.rec = (StepRecord*)take(sizeof(StepRecord));
@@ -479,6 +662,10 @@ size_t workspace_layout(int N, Fields* f, char* base) {
   F.nu_cold = (double*)take((size_t)N * N * sizeof(double));
   F.nu_avg = (double*)take((size_t)N * sizeof(double));
   F.alg_bytes = (double*)take(HOSC_K_COUNT * sizeof(double));
+  F.halt = (int*)take(sizeof(int));
+  F.steady_stop = (int*)take(sizeof(int));
+  F.ring = (StepRecord*)take(kRing * sizeof(StepRecord));
+  F.ring_pos = (unsigned int*)take(sizeof(unsigned int));
   const size_t ff = n3 * sizeof(float);
   for (int b = 0; b < 2; ++b) {
     F.us[b] = (float*)take(ff);
@@ -542,6 +729,10 @@ void hosc_destroy(void* ctx) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  drop_graphs(c);
+  for (cudaStream_t q : c->cap)
+    if (q) cudaStreamDestroy(q);
+  if (c->h_ring) cudaFreeHost(c->h_ring);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (c->h_ks) cudaFreeHost(c->h_ks);
@@ -564,6 +755,11 @@ hosc_status hosc_step(void* ctx, int nsteps, hosc_info* out) {
   hosc_info info;
   memset(&info, 0, sizeof(info));
   hosc_status st = HOSC_OK;
+  if (graphs_usable(c)) {
+    st = graph_steps(c, nsteps, false, &info, nullptr);
+    if (out) *out = info;
+    return st;
+  }
   for (int s = 0; s < nsteps; ++s) {
     st = one_step(c, &info);
     if (st) break;
@@ -580,6 +776,13 @@ hosc_status hosc_solve_steady(void* ctx, long max_steps, hosc_info* out) {
   hosc_info info;
   memset(&info, 0, sizeof(info));
   hosc_status st = HOSC_ESTEPLIMIT;
+  if (graphs_usable(c)) {
+    bool steady = false;
+    st = graph_steps(c, max_steps, true, &info, &steady);
+    if (out) *out = info;
+    if (st) return st;
+    return steady ? HOSC_OK : HOSC_ESTEPLIMIT;
+  }
   for (long s = 0; s < max_steps; ++s) {
     hosc_status q = one_step(c, &info);
     if (q) {

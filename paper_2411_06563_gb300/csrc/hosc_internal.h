@@ -21,7 +21,11 @@ struct DevParams {
   int krylov_fp32;   // right-hand sides, operator weights and Krylov vectors in float
   double h, h2;      // grid spacing (h = k = l) and its square
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
+  double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (and div below tol_div)
+                       // is steady (tol_steady * dt)
 };
+
+constexpr int kRing = 256;   // step records kept on the device between host reads
 
 // BiCGSTAB scalars of one system, resident in device memory.
 struct KrylovScalars {
@@ -71,6 +75,12 @@ struct Fields {
   double* nu_avg;          // [N]
   double* eloc;            // [3 N^3] E_HT, E_FF, E_local (diagnostics)
   double* alg_bytes;       // [HOSC_K_COUNT] algorithmic bytes moved by each kernel class
+  // device-side control of a sequence of steps enqueued without host synchronisation
+  int* halt;              // 0: run; 1: a step failed; 2: steady (when *steady_stop); later
+                          // kernels of the sequence return at once
+  int* steady_stop;       // stop the sequence at the first steady step
+  StepRecord* ring;       // [kRing] records of the steps of the sequence
+  unsigned int* ring_pos; // records appended so far
   // float copies of the state for the FP32 sweeps of mixed precision (rounded once per step)
   float* us[2];
   float* vs[2];
@@ -93,6 +103,8 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s);
 void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
+// Body of the BiCGSTAB loop of a captured step: end of the loop when every system is done.
+void launch_loop_cond(const Fields& F, unsigned long long handle, cudaStream_t s);
 // S6-S8: increments, theta walls, div V, pressure correction and walls, step record.
 void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s);
 // Mixed precision: round u, v, w (level cur, and level 1-cur when both), theta and p to float.

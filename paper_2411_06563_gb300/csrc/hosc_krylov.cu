@@ -35,6 +35,7 @@ __device__ __forceinline__ const T* const* ops(double* const* p) {
 }
 
 // Thread t -> interior node (1 + t % ni, ...) in 32-bit arithmetic (N^3 < 2^31 for N <= 1025).
+// Thread t -> interior node (1 + t % ni, ...) in 32-bit arithmetic (N^3 < 2^31 for N <= 1025).
 __device__ __forceinline__ bool interior_index(const DevParams& P, unsigned t, int& c) {
   const unsigned N = P.N, ni = N - 2;
   if (t >= ni * ni * ni) return false;
@@ -54,19 +55,74 @@ __device__ __forceinline__ double launch_bytes(const DevParams& P, const int don
   return word_bytes * ni * ni * ni * words;
 }
 
-// Per-thread terms of the dot products are formed in T; for float vectors the warp stage of the
-// block reduction runs in float and everything above it in double, for double vectors all in
-// double.
+// Float-float ("double-float") numbers: an unevaluated sum hi + lo of two floats. Knuth's TwoSum
+// and an FMA-based exact product give sums with about 44 significant bits using float
+// instructions only, which GB300 issues at 64x the rate of double instructions.
+struct FF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_prod(float a, float b) {
+  FF r;
+  r.hi = a * b;
+  r.lo = fmaf(a, b, -r.hi);   // exact rounding error of the product
+  return r;
+}
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float err = (a.hi - (s - bb)) + (b.hi - bb);   // TwoSum: s + err == a.hi + b.hi exactly
+  const float lo = err + a.lo + b.lo;
+  FF r;
+  r.hi = s + lo;
+  r.lo = lo - (r.hi - s);
+  return r;
+}
+
+__device__ __forceinline__ FF ff_shfl_down(FF a, int off) {
+  FF r;
+  r.hi = __shfl_down_sync(0xffffffffu, a.hi, off);
+  r.lo = __shfl_down_sync(0xffffffffu, a.lo, off);
+  return r;
+}
+
+// Block partial of M dot-product terms a[m] * b[m]. For float vectors the products and the warp
+// and cross-warp sums are float-float (no double instruction per thread) and thread 0 widens the
+// block total to double; for double vectors every stage is double. The grid stage in the last
+// block adds the block totals in double. The result is valid in thread 0.
 template <class T, int M>
-__device__ __forceinline__ void block_dots(const T (&acc)[M], double (&out)[M], double* smem) {
+__device__ __forceinline__ void block_partial(const T (&a)[M], const T (&b)[M], double (&out)[M],
+                                              double* smem) {
   if constexpr (sizeof(T) == sizeof(float)) {
-    float f[M];
+    FF* fs = reinterpret_cast<FF*>(smem);
+    FF w[M];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
 #pragma unroll
-    for (int m = 0; m < M; ++m) f[m] = (float)acc[m];
-    block_sum_f32<M>(f, out, smem);
+    for (int m = 0; m < M; ++m) {
+      w[m] = ff_prod(a[m], b[m]);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) w[m] = ff_add(w[m], ff_shfl_down(w[m], off));
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) fs[wid * M + m] = w[m];
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int m = 0; m < M; ++m) {
+        FF x = (lane < nw) ? fs[lane * M + m] : FF{0.0f, 0.0f};
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x = ff_add(x, ff_shfl_down(x, off));
+        if (lane == 0) out[m] = (double)x.hi + (double)x.lo;
+      }
+    }
+    __syncthreads();
   } else {
 #pragma unroll
-    for (int m = 0; m < M; ++m) out[m] = (double)acc[m];
+    for (int m = 0; m < M; ++m) out[m] = (double)a[m] * (double)b[m];
     block_reduce<M, false>(out, smem);
   }
 }
@@ -77,7 +133,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_init(DevParams P, Fields F, i
   __shared__ double smem[32 * 4];
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   int c;
-  T acc[4] = {T(0), T(0), T(0), T(0)};
+  T da[4] = {T(0), T(0), T(0), T(0)}, db[4] = {T(0), T(0), T(0), T(0)};
   if (interior_index(P, t, c)) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -88,11 +144,12 @@ __global__ void __launch_bounds__(kThreads) k_bicg_init(DevParams P, Fields F, i
       vec<T>(F.pk[1][s])[c] = T(0);
       vec<T>(F.vk[0][s])[c] = T(0);
       vec<T>(F.vk[1][s])[c] = T(0);
-      acc[s] = r * r;
+      da[s] = r;
+      db[s] = r;
     }
   }
   double part[4];
-  block_dots<T, 4>(acc, part, smem);
+  block_partial<T, 4>(da, db, part, smem);
   if (publish_is_last<4>(part, F.red, F.counter)) {
     double tot[4];
     reduce_partials<4, false>(tot, F.red, nblocks, F.counter, smem);
@@ -107,9 +164,18 @@ __global__ void __launch_bounds__(kThreads) k_bicg_init(DevParams P, Fields F, i
         k.beta = 0.0;
         k.iters = 0;
         k.status = 0;
-        k.done = (k.r0norm == 0.0) ? 1 : 0;
+        k.done = (k.r0norm == 0.0 || *F.halt) ? 1 : 0;
       }
     }
+  }
+}
+
+// End of one pass of the captured BiCGSTAB loop body: continue while a system is iterating.
+// Bounded: k_bicg_xr marks a system done at max_lin_iter at the latest.
+__global__ void k_loop_cond(const KrylovScalars* ks, cudaGraphConditionalHandle handle) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    const unsigned more = !(ks[0].done && ks[1].done && ks[2].done && ks[3].done);
+    cudaGraphSetConditional(handle, more);
   }
 }
 
@@ -130,7 +196,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_pv(DevParams P, Fields F, int
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const int sy = P.N, sz = P.N * P.N;
   int c;
-  T acc[4] = {T(0), T(0), T(0), T(0)};
+  T da[4] = {T(0), T(0), T(0), T(0)}, db[4] = {T(0), T(0), T(0), T(0)};
   if (interior_index(P, t, c)) {
 #pragma unroll 1
     for (int s = 0; s < 4; ++s) {
@@ -147,11 +213,12 @@ __global__ void __launch_bounds__(kThreads) k_bicg_pv(DevParams P, Fields F, int
       const T vn = apply7<T>(A, c, pn[0], pn[1], pn[2], pn[3], pn[4], pn[5], pn[6]);
       vec<T>(F.pk[1 - pp][s])[c] = pn[0];
       vec<T>(F.vk[1 - pp][s])[c] = vn;
-      acc[s] = vec<T>(F.rhs[s])[c] * vn;
+      da[s] = vec<T>(F.rhs[s])[c];
+      db[s] = vn;
     }
   }
   double part[4];
-  block_dots<T, 4>(acc, part, smem);
+  block_partial<T, 4>(da, db, part, smem);
   if (publish_is_last<4>(part, F.red, F.counter)) {
     double tot[4];
     reduce_partials<4, false>(tot, F.red, nblocks, F.counter, smem);
@@ -188,7 +255,8 @@ __global__ void __launch_bounds__(kThreads) k_bicg_st(DevParams P, Fields F, int
   const int sy = P.N, sz = P.N * P.N;
   const int np = 1 - pp;   // buffers written by k_bicg_pv of this iteration
   int c;
-  T acc[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  T da[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  T db[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   if (interior_index(P, t, c)) {
 #pragma unroll 1
     for (int s = 0; s < 4; ++s) {
@@ -203,12 +271,14 @@ __global__ void __launch_bounds__(kThreads) k_bicg_st(DevParams P, Fields F, int
       const T* const* A = (s < 3) ? ops<T>(F.Am) : ops<T>(F.Ae);
       const T tv = apply7<T>(A, c, sv[0], sv[1], sv[2], sv[3], sv[4], sv[5], sv[6]);
       vec<T>(F.t[s])[c] = tv;
-      acc[2 * s] = tv * sv[0];
-      acc[2 * s + 1] = tv * tv;
+      da[2 * s] = tv;
+      db[2 * s] = sv[0];
+      da[2 * s + 1] = tv;
+      db[2 * s + 1] = tv;
     }
   }
   double part[8];
-  block_dots<T, 8>(acc, part, smem);
+  block_partial<T, 8>(da, db, part, smem);
   if (publish_is_last<8>(part, F.red, F.counter)) {
     double tot[8];
     reduce_partials<8, false>(tot, F.red, nblocks, F.counter, smem);
@@ -240,7 +310,8 @@ __global__ void __launch_bounds__(kThreads) k_bicg_xr(DevParams P, Fields F, int
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const int np = 1 - pp;
   int c;
-  T acc[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  T da[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  T db[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
   if (interior_index(P, t, c)) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -252,12 +323,14 @@ __global__ void __launch_bounds__(kThreads) k_bicg_xr(DevParams P, Fields F, int
       x[c] = x[c] + a * vec<T>(F.pk[np][s])[c] + om * sv;
       const T rn = sv - om * vec<T>(F.t[s])[c];
       r[c] = rn;
-      acc[2 * s] = vec<T>(F.rhs[s])[c] * rn;
-      acc[2 * s + 1] = rn * rn;
+      da[2 * s] = vec<T>(F.rhs[s])[c];
+      db[2 * s] = rn;
+      da[2 * s + 1] = rn;
+      db[2 * s + 1] = rn;
     }
   }
   double part[8];
-  block_dots<T, 8>(acc, part, smem);
+  block_partial<T, 8>(da, db, part, smem);
   if (publish_is_last<8>(part, F.red, F.counter)) {
     double tot[8];
     reduce_partials<8, false>(tot, F.red, nblocks, F.counter, smem);
@@ -291,6 +364,10 @@ int interior_blocks(const DevParams& P) {
 }
 
 }  // namespace
+
+void launch_loop_cond(const Fields& F, unsigned long long handle, cudaStream_t s) {
+  k_loop_cond<<<1, 32, 0, s>>>(F.ks, (cudaGraphConditionalHandle)handle);
+}
 
 void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
   const int b = interior_blocks(P);

@@ -75,10 +75,11 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const T* __restrict__ u,
                                                         const T* __restrict__ v,
                                                         const T* __restrict__ w,
-                                                        T* __restrict__ eta, T* __restrict__ L) {
+                                                        T* __restrict__ eta, T* __restrict__ L,
+                                                        const int* __restrict__ halt) {
   const unsigned N = P.N;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= N * N * N) return;
+  if (t >= N * N * N || *halt) return;
   const unsigned q = t / N;
   int i = (int)(t - q * N), j = (int)(q % N), k = (int)(q / N);
   T e = T(1);
@@ -113,10 +114,11 @@ __global__ void __launch_bounds__(kThreads) k_sources(DevParams P, const T* __re
                                                      const T* __restrict__ p,
                                                      const T* __restrict__ eta,
                                                      T* __restrict__ Eu, T* __restrict__ Ev,
-                                                     T* __restrict__ Ew) {
+                                                     T* __restrict__ Ew,
+                                                     const int* __restrict__ halt) {
   const int N = P.N;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (unsigned)N * N * N) return;
+  if (t >= (unsigned)N * N * N || *halt) return;
   const unsigned q = t / (unsigned)N;
   const int i = (int)(t - q * (unsigned)N), j = (int)(q % (unsigned)N), k = (int)(q / (unsigned)N);
   const T inv2h = (T)(0.5 / P.h);
@@ -280,7 +282,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs(
   const int N = P.N;
   const unsigned ni = N - 2;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= ni * ni * ni) return;
+  if (t >= ni * ni * ni || *F.halt) return;
   const unsigned q = t / ni;
   const int i = 1 + (int)(t - q * ni), j = 1 + (int)(q % ni), k = 1 + (int)(q / ni);
   const long sy = N, sz = (long)N * N;
@@ -375,6 +377,7 @@ template <class Ts>
 __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Fields F, int cur,
                                                               int nblocks) {
   __shared__ double smem[32];
+  if (*F.halt) return;
   const int N = P.N;
   const long n3 = (long)N * N * N;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -424,6 +427,7 @@ __device__ __forceinline__ int wall_weights(int a, int N, int idx[2], double wt[
 // walls keep theta = 1 and theta = 0. Max |change| joins the step record.
 __global__ void __launch_bounds__(kThreads) k_theta_walls(DevParams P, Fields F, int nblocks) {
   __shared__ double smem[32];
+  if (*F.halt) return;
   const int N = P.N;
   const long cnt = (long)(N - 2) * N * N;   // x interior, all y, z
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -459,6 +463,7 @@ __global__ void __launch_bounds__(kThreads) k_theta_walls(DevParams P, Fields F,
 __global__ void __launch_bounds__(kThreads) k_divergence(DevParams P, Fields F, int nxt,
                                                          int nblocks) {
   __shared__ double smem[32];
+  if (*F.halt) return;
   const int N = P.N, ni = N - 2;
   const long cnt = (long)ni * ni * ni;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -487,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure_correct(DevParams P, Fiel
   const int N = P.N, ni = N - 2;
   const long cnt = (long)ni * ni * ni;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= cnt) return;
+  if (t >= cnt || *F.halt) return;
   if (!(F.rec->div_max > P.tol_div)) return;
   const int i = 1 + (int)(t % ni), j = 1 + (int)((t / ni) % ni), k = 1 + (int)(t / ((long)ni * ni));
   const long c = node(i, j, k, N);
@@ -500,7 +505,7 @@ __global__ void __launch_bounds__(kThreads) k_pressure_walls(DevParams P, Fields
   const int N = P.N;
   const long n3 = (long)N * N * N;
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n3) return;
+  if (t >= n3 || *F.halt) return;
   if (!(F.rec->div_max > P.tol_div)) return;
   const int i = (int)(t % N), j = (int)((t / N) % N), k = (int)(t / ((long)N * N));
   if (!(on_wall(i, N) | on_wall(j, N) | on_wall(k, N))) return;
@@ -521,9 +526,11 @@ __global__ void __launch_bounds__(kThreads) k_pressure_walls(DevParams P, Fields
   F.p[t] = s;
 }
 
-// Step record: Krylov outcomes and the overall status.
-__global__ void k_finish_record(Fields F) {
+// Step record: Krylov outcomes and the overall status; appended to the ring. A failed step (or,
+// when asked, a steady one) halts the rest of the enqueued sequence.
+__global__ void k_finish_record(DevParams P, Fields F) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (*F.halt) return;
   StepRecord* r = F.rec;
   int st = HOSC_OK;
   double lres = 0.0;
@@ -537,6 +544,11 @@ __global__ void k_finish_record(Fields F) {
   r->lin_res = lres;
   if (!isfinite(r->res) || !isfinite(r->div_max) || !isfinite(lres)) st = HOSC_EDIVERGED;
   r->status = st;
+  const unsigned pos = *F.ring_pos;
+  F.ring[pos % kRing] = *r;
+  *F.ring_pos = pos + 1;
+  if (st != HOSC_OK) *F.halt = 1;
+  else if (*F.steady_stop && r->res < P.steady_res && r->div_max < P.tol_div) *F.halt = 2;
 }
 
 }  // namespace
@@ -553,9 +565,10 @@ __global__ void __launch_bounds__(kThreads) k_shadow(int n3, const double* __res
                                                      float* __restrict__ us, float* __restrict__ vs,
                                                      float* __restrict__ ws,
                                                      float* __restrict__ ths,
-                                                     float* __restrict__ ps) {
+                                                     float* __restrict__ ps,
+                                                     const int* __restrict__ halt) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n3) return;
+  if (t >= n3 || *halt) return;
   us[t] = (float)u[t];
   vs[t] = (float)v[t];
   ws[t] = (float)w[t];
@@ -569,11 +582,12 @@ __global__ void __launch_bounds__(kThreads) k_shadow(int n3, const double* __res
 void launch_shadow(const DevParams& P, const Fields& F, int cur, int both, cudaStream_t s) {
   const int n3 = P.N * P.N * P.N;
   k_shadow<<<red_blocks(n3), kThreads, 0, s>>>(n3, F.u[cur], F.v[cur], F.w[cur], F.th, F.p,
-                                               F.us[cur], F.vs[cur], F.ws[cur], F.ths, F.ps);
+                                               F.us[cur], F.vs[cur], F.ws[cur], F.ths, F.ps, F.halt);
   if (both) {
     const int o = 1 - cur;
     k_shadow<<<red_blocks(n3), kThreads, 0, s>>>(n3, F.u[o], F.v[o], F.w[o], nullptr, nullptr,
-                                                 F.us[o], F.vs[o], F.ws[o], nullptr, nullptr);
+                                                 F.us[o], F.vs[o], F.ws[o], nullptr, nullptr,
+                                                 F.halt);
   }
 }
 
@@ -582,10 +596,10 @@ void launch_viscosity(const DevParams& P, const Fields& F, int cur, cudaStream_t
   if (P.sweep_fp32)
     k_viscosity<float><<<red_blocks(n3), kThreads, 0, s>>>(
         P, F.us[cur], F.vs[cur], F.ws[cur], reinterpret_cast<float*>(F.eta),
-        reinterpret_cast<float*>(F.L[cur]));
+        reinterpret_cast<float*>(F.L[cur]), F.halt);
   else
     k_viscosity<double><<<red_blocks(n3), kThreads, 0, s>>>(P, F.u[cur], F.v[cur], F.w[cur],
-                                                            F.eta, F.L[cur]);
+                                                            F.eta, F.L[cur], F.halt);
 }
 
 void launch_sources(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
@@ -594,11 +608,11 @@ void launch_sources(const DevParams& P, const Fields& F, int cur, cudaStream_t s
     k_sources<float><<<red_blocks(n3), kThreads, 0, s>>>(
         P, F.us[cur], F.vs[cur], F.ws[cur], F.ths, F.ps, reinterpret_cast<const float*>(F.eta),
         reinterpret_cast<float*>(F.Eu[cur]), reinterpret_cast<float*>(F.Ev[cur]),
-        reinterpret_cast<float*>(F.Ew[cur]));
+        reinterpret_cast<float*>(F.Ew[cur]), F.halt);
   else
     k_sources<double><<<red_blocks(n3), kThreads, 0, s>>>(P, F.u[cur], F.v[cur], F.w[cur], F.th,
                                                           F.p, F.eta, F.Eu[cur], F.Ev[cur],
-                                                          F.Ew[cur]);
+                                                          F.Ew[cur], F.halt);
 }
 
 template <class Tc, class Ts>
@@ -644,7 +658,7 @@ void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s)
   k_divergence<<<b_int, kThreads, 0, s>>>(P, F, 1 - cur, b_int);
   k_pressure_correct<<<b_int, kThreads, 0, s>>>(P, F);
   k_pressure_walls<<<b_all, kThreads, 0, s>>>(P, F);
-  k_finish_record<<<1, 32, 0, s>>>(F);
+  k_finish_record<<<1, 32, 0, s>>>(P, F);
 }
 
 }  // namespace hosc

@@ -264,3 +264,45 @@ def test_small_and_even_grids():
         o = O.diagnostics(st, op)
         assert d["Nu_hot_mean"] == pytest.approx(o["Nu_hot_mean"], rel=1e-12)
         assert d["Be"] == pytest.approx(o["Be"], rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_captured_steps_match_stage_by_stage(precision):
+    """hosc_step enqueues captured steps (BiCGSTAB as a device-side loop, no host round trip);
+    with per-launch timing on, the same steps run stage by stage from the host. Same kernels in
+    the same order: the fields must agree bit for bit, and so must the step records."""
+    N = 17
+    st = inputs.cavity_state(N, 1e4, seed=9)
+    outs = []
+    for timed in (False, True):
+        p = _params(N, 1e4, 0.8, dt=0.002, precision=precision, tol_lin=1e-10)
+        with H.Cavity(p) as cav:
+            for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
+                                ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
+                cav.set(which, st[name])
+            H.hosc_profile_enable(cav.h, 1 if timed else 0)
+            info = cav.step(5)
+            outs.append((info, [cav.get(w) for w in (H.HOSC_U, H.HOSC_V, H.HOSC_W, H.HOSC_THETA,
+                                                      H.HOSC_P)]))
+    (ia, fa), (ib, fb) = outs
+    assert ia["steps"] == ib["steps"] == 5 and ia["lin_iters"] == ib["lin_iters"]
+    assert ia["res"] == ib["res"] and ia["div_max"] == ib["div_max"]
+    for a, b in zip(fa, fb):
+        assert np.array_equal(a, b)
+
+
+def test_captured_steady_stop_is_exact():
+    """solve_steady with captured steps stops on the device at the first steady step: the same
+    step count and fields as the stage-by-stage solve."""
+    N = 11
+    res = []
+    for timed in (False, True):
+        p = _params(N, 1e3, 1.0, dt=0.02, tol_lin=1e-10, tol_steady=1e-4, tol_div=1e-3,
+                    lambda_=0.1)
+        with H.Cavity(p) as cav:
+            H.hosc_profile_enable(cav.h, 1 if timed else 0)
+            info = cav.solve_steady(5000)
+            res.append((info, cav.get(H.HOSC_V)))
+    (ia, va), (ib, vb) = res
+    assert ia["call_status"] == ib["call_status"] == 0
+    assert ia["steps"] == ib["steps"] and np.array_equal(va, vb)
