@@ -217,6 +217,32 @@ int hosc_get_phase(void* ctx);
 /* Number of kernel launches the library has made since the context was created. */
 long hosc_kernel_launches(void* ctx);
 
+/* Allocation-free BiCGSTAB solve of the four level-(n+1) systems of one step, for callers that
+ * cannot call cudaMalloc: code that runs while a stream is being captured into a CUDA graph (where
+ * cudaMalloc is not permitted), loops with a fixed memory budget that must not synchronise the
+ * device (cudaMalloc may), and hosts whose own allocator already owns the device memory. The
+ * paper has no counterpart; this is an interface of this library.
+ *
+ * Solves A_mom x_s = rhs_s for s = u, v, w and A_ene x_theta = rhs_theta with the same kernels as
+ * hosc_step (FP64 BiCGSTAB from x = 0, stop when ||r|| <= tol ||r_0||), on the interior nodes of
+ * an N^3 grid. weights: host array of 14 device pointers, N^3 doubles each, in the order
+ * centre, x+, x-, y+, y-, z+, z- of the momentum operator then of the energy operator (the
+ * layout of HOSC_A_MOM / HOSC_A_ENE); rhs: host array of 4 device pointers (N^3 doubles, interior
+ * nodes read); x: host array of 4 device pointers (N^3 doubles; interior nodes written, walls
+ * untouched). iters_out: host int[4] or NULL. stream: cudaStream_t or NULL.
+ * The caller owns every input and output. Scratch (Krylov vectors, partial sums, solver scalars)
+ * is one file-scope device array of 13.3 MB sized for N <= HOSC_NOALLOC_MAX_N, which every GPU
+ * that loads the library holds until the process exits; larger N returns HOSC_EINVAL. The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current: make that first call before any stream capture. All calls share the array and it keeps
+ * the last call's contents (each call clears what must start at zero), so calls that overlap on
+ * the GPU race: serialise them (one stream, or wait between calls). Returns HOSC_ENOCONV if a
+ * system did not converge within max_iter, HOSC_ECUDA on a CUDA error. */
+#define HOSC_NOALLOC_MAX_N 41
+hosc_status hosc_bicgstab_noalloc(int N, const double* const* weights, const double* const* rhs,
+                                  double* const* x, double tol, int max_iter, int* iters_out,
+                                  void* stream);
+
 const char* hosc_strerror(int status);
 
 /* Text of the last CUDA failure seen by this host thread (for HOSC_ECUDA / HOSC_ENOMEM). */

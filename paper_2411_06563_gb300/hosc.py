@@ -113,6 +113,10 @@ def lib():
                                              _DP]),
         "hosc_kernel_launches": (ctypes.c_long, [_P]),
         "hosc_set_phase": (ctypes.c_int, [_P, ctypes.c_int]),
+        "hosc_bicgstab_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P),
+                                                 ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                                 ctypes.c_double, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int), _P]),
         "hosc_get_phase": (ctypes.c_int, [_P]),
         "hosc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "hosc_last_error_detail": (ctypes.c_char_p, []),
@@ -240,6 +244,21 @@ def hosc_profile_read(h, kernel_id):
 
 def hosc_kernel_launches(h):
     return int(lib().hosc_kernel_launches(h))
+
+
+HOSC_NOALLOC_MAX_N = 41
+
+
+def hosc_bicgstab_noalloc(N, weights, rhs, x, tol, max_iter, stream=None):
+    """Allocation-free solve (see include/hosc.h): weights, rhs, x are sequences of device
+    addresses (ints) of N^3 double arrays (14, 4 and 4 of them). Returns (status, iters[4])."""
+    W = (_P * 14)(*[_P(a) for a in weights])
+    R = (_P * 4)(*[_P(a) for a in rhs])
+    X = (_P * 4)(*[_P(a) for a in x])
+    its = (ctypes.c_int * 4)()
+    st = lib().hosc_bicgstab_noalloc(int(N), W, R, X, float(tol), int(max_iter), its,
+                                     _P(stream) if stream else None)
+    return st, list(its)
 
 
 def hosc_set_phase(h, phase):
