@@ -174,6 +174,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shape of the mixed-precision solve")
     ap.add_argument("--spinup", type=int, default=None,
                     help="untimed steps from rest before the warm-up (default: per workload)")
     args = ap.parse_args()
@@ -205,9 +207,13 @@ def main():
         p.auto_defect = 0   # time the FP32 sweeps; the FP64 defect phase is for the last digits
         p.cuda_stream = stream.cuda_stream
         cav = H.Cavity(p, workspace="torch")
-        # spin-up from rest (untimed), then warm-up steps
+        # spin-up from rest (untimed), then the launch-shape autotuner (mixed precision), then
+        # warm-up steps
         info = cav.step(spinup)
         assert info["call_status"] == 0, info
+        if precision == "mixed" and not args.no_autotune:
+            rc, kb, kz, _ = H.hosc_autotune(cav.h, 5)
+            assert rc == 0, rc
         cav.step(args.warmup)
         torch.cuda.synchronize()
         return p, cav
@@ -263,6 +269,15 @@ def main():
         _, kms, kl, kb = H.hosc_profile_read(cav.h, kid)
         kern[name] = dict(ms=kms, launches=kl, bytes=kb)
     H.hosc_profile_enable(cav.h, 0)
+    # each class alone, launched back to back on the current buffers (no host gaps), inside an
+    # NVTX range that a profiler can select
+    iso = {}
+    torch.cuda.nvtx.range_push("kernels_alone")
+    for kid, name in enumerate(names[:6]):
+        rc, kms, kb = H.hosc_time_kernel(cav.h, kid, 20)
+        if rc == 0:
+            iso[name] = {"us_per_launch": kms * 1e3, "GBps": kb / (kms * 1e-3) / 1e9}
+    torch.cuda.nvtx.range_pop()
     dom = max(kern, key=lambda k: kern[k]["ms"])
     peak, peak_kind = _peaks()
     d = kern[dom]
@@ -312,6 +327,8 @@ def main():
                        "spinup_steps": spinup, "tol_lin": p.tol_lin,
                        "use_history": wl["history"], "lambda": p.lambda_,
                        "bicgstab_iters_per_step": lin_iters / (4.0 * args.steps),
+                       "krylov_tiles": (dict(zip(("block", "kz"), H.hosc_get_tiles(cav.h)[1:]))
+                                        if args.precision == "mixed" else None),
                        "l2": "no flush: device working set %.0f MB > 129 MB L2"
                              % (H.hosc_workspace_bytes(p) / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single"},
@@ -320,6 +337,7 @@ def main():
                          "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                          "peak_kind": peak_kind,
                          "share": d["ms"] / total_ms if total_ms else None},
+            "kernels_alone": iso,
             "kernels": {k: {"ms_per_step": v["ms"] / prof_steps, "launches": v["launches"],
                             "GBps": (v["bytes"] / (v["ms"] * 1e-3) / 1e9) if v["ms"] else 0.0}
                         for k, v in kern.items()},

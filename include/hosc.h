@@ -204,7 +204,35 @@ hosc_status hosc_profile_enable(void* ctx, int on);
 hosc_status hosc_profile_read(void* ctx, int kernel_id, double* total_ms, long* launches,
                               double* alg_bytes);
 
-/* Kernel classes for hosc_profile_read. */
+/* Time one kernel class in isolation (kernel_id HOSC_K_VISC .. HOSC_K_BICG_XR): between steps,
+ * launch that kernel reps times back to back on the context's stream between two CUDA events,
+ * on the current state (the BiCGSTAB kernels on the buffers of the last solve, with all four
+ * systems marked as iterating; the marking kernel's time is measured apart and subtracted).
+ * Returns the mean milliseconds per launch and the algorithmic bytes of one launch. The fields
+ * u, v, w, theta, p and the history keep their values; the derived arrays and the Krylov
+ * buffers are overwritten and recomputed by the next step. HOSC_EINVAL for another id or
+ * reps < 1, HOSC_ESTATE in the middle of a stage-by-stage step. */
+hosc_status hosc_time_kernel(void* ctx, int kernel_id, int reps, double* ms_per_launch,
+                             double* bytes_per_launch);
+
+/* Launch shape of the mixed-precision BiCGSTAB kernels, which store the four systems interleaved
+ * (one float4 per node) and give each thread one interior (i, j) column over kz consecutive
+ * planes: kblock threads per block (a multiple of 32, 64..512), kz in 1..N-2, and at most
+ * 4 * ceil(N^3/256) blocks per launch. The default is chosen from N at creation. Changing it
+ * drops the captured steps (they are captured again at the next step). HOSC_EINVAL for a shape
+ * outside these limits, HOSC_ESTATE in the middle of a stage-by-stage step. The FP64 solve has
+ * one thread per node and ignores the setting. */
+hosc_status hosc_set_tiles(void* ctx, int kblock, int kz);
+hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz);
+
+/* Autotuner for the launch shape above: after at least one completed step, time the three
+ * BiCGSTAB kernels (hosc_time_kernel, reps launches each) for every valid kblock in
+ * {64, 128, 256, 512} and kz in {1, 2, 4, 8, 16, 32}, keep the shape with the least total
+ * time and report it (any output pointer may be NULL; ms_out = the three kernels' summed mean
+ * milliseconds). Mixed precision only (HOSC_EINVAL for FP64). The fields keep their values. */
+hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, double* ms_out);
+
+/* Kernel classes for hosc_profile_read and hosc_time_kernel. */
 enum { HOSC_K_VISC = 0, HOSC_K_SOURCES = 1, HOSC_K_RHS = 2, HOSC_K_BICG_PV = 3,
        HOSC_K_BICG_ST = 4, HOSC_K_BICG_XR = 5, HOSC_K_UPDATE = 6, HOSC_K_COUNT = 7 };
 
@@ -242,6 +270,60 @@ long hosc_kernel_launches(void* ctx);
 hosc_status hosc_bicgstab_noalloc(int N, const double* const* weights, const double* const* rhs,
                                   double* const* x, double tol, int max_iter, int* iters_out,
                                   void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Pools: many cavity solves advancing together on one GPU (batching and serving). Not in the
+ * paper, which solves one cavity at a time; each member runs the same step as hosc_step.
+ *
+ * Members are contexts admitted against a device-memory budget (the sum of their
+ * hosc_workspace_bytes). hosc_pool_run advances every active member by rounds of
+ * steps_per_round captured steps; each member stops on the device at its first steady step
+ * (the hosc_solve_steady criterion). After each round the host folds the step records and
+ * completes a member that is steady (status HOSC_OK), failed (its step status) or has taken at
+ * least max_steps steps (HOSC_ESTEPLIMIT; the last round may overrun max_steps by fewer than
+ * steps_per_round steps). Diagnostics are computed at completion. A completed member keeps its
+ * device memory (its fields can be read through the context that hosc_pool_result returns)
+ * until hosc_pool_retire.
+ *
+ * mode HOSC_POOL_STREAMS: each member launches its captured steps on its own stream.
+ * mode HOSC_POOL_GRAPH: a whole round of every active member is one captured graph with one
+ *   branch per member (steps_per_round must be even); it is captured again when membership,
+ *   or a member's level parity, history, phase or launch shape, changes.
+ * autotune != 0: after the first round of the first mixed-precision member of each N, the pool
+ *   runs hosc_autotune on it and gives later members of that N the same launch shape.
+ * The pool's calls are single-threaded; members use their own streams and the pool's stream. */
+enum { HOSC_POOL_STREAMS = 0, HOSC_POOL_GRAPH = 1 };
+
+typedef struct {
+  int active;          /* members still advancing */
+  int completed;       /* members completed and not yet retired */
+  int tuned_sizes;     /* grid sizes N with a tuned launch shape */
+  size_t bytes_used;   /* device bytes held by members */
+  size_t budget;
+  long rounds;         /* rounds run */
+  long captures;       /* round graphs captured (HOSC_POOL_GRAPH) */
+  double capture_ms;   /* host milliseconds spent capturing and instantiating them */
+} hosc_pool_info;
+
+/* budget_bytes > 0; 1 <= steps_per_round <= 256. */
+hosc_status hosc_pool_create(size_t budget_bytes, int steps_per_round, int mode, int autotune,
+                             void** pool);
+void hosc_pool_destroy(void* pool);  /* destroys every member */
+/* Create a member for *params (its cuda_stream is ignored: each member has its own stream).
+ * HOSC_ENOMEM when it does not fit the budget now (it may after retirements), HOSC_EINVAL when
+ * it can never fit or the parameters are invalid. *slot: the member's index. */
+hosc_status hosc_pool_admit(void* pool, const hosc_params* params, long max_steps, int* slot);
+/* Run up to `rounds` rounds, returning after the first round in which a member completed. The
+ * completed slots go to done_slots[0 .. min(*ndone, cap)). HOSC_ECUDA stops the pool. */
+hosc_status hosc_pool_run(void* pool, int rounds, int* done_slots, int cap, int* ndone);
+/* Result of a member: status (HOSC_ESTATE while active), steps and iterations over its whole
+ * solve, diagnostics (after completion), and its context (for hosc_get_field, until retire).
+ * Any output pointer may be NULL. */
+hosc_status hosc_pool_result(void* pool, int slot, hosc_status* status, hosc_info* info,
+                             hosc_diag* diag, void** ctx);
+/* Free a member's context and device memory (active or completed). */
+hosc_status hosc_pool_retire(void* pool, int slot);
+hosc_status hosc_pool_stats(void* pool, hosc_pool_info* out);
 
 const char* hosc_strerror(int status);
 

@@ -66,6 +66,13 @@ struct Ctx {
   double prof_ms[HOSC_K_COUNT] = {0};
   long prof_launches[HOSC_K_COUNT] = {0};
   double host_bytes[HOSC_K_COUNT] = {0};   // algorithmic bytes of the fixed-work kernels
+  int kblock = 128, kz = 1;                // tiles of the interleaved Krylov kernels
+  // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
+  // asynchronously into h_ring / h_ring_pos, completion marked by round_ev
+  int round_cur0 = 0, round_prev0 = 0;
+  long round_n = 0;
+  unsigned* h_ring_pos = nullptr;
+  cudaEvent_t round_ev = nullptr;
 };
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -84,6 +91,33 @@ hosc_status validate(const hosc_params* p) {
   if (p->auto_defect != 0 && p->auto_defect != 1) return HOSC_EINVAL;
   if (p->precision != HOSC_FP64 && p->precision != HOSC_MIXED) return HOSC_EINVAL;
   return HOSC_OK;
+}
+
+// Algorithmic bytes of one launch of a kernel class: every array element it must touch, once.
+double kernel_bytes(const DevParams& P, int kid) {
+  const double N = P.N, n3 = N * N * N, ni3 = (N - 2) * (N - 2) * (N - 2);
+  const double sb = P.sweep_fp32 ? 4.0 : 8.0;   // bytes of a sweep-array element
+  const bool f4 = P.krylov_fp32 != 0;           // interleaved float Krylov storage
+  switch (kid) {
+    case HOSC_K_VISC: return n3 * 5 * sb;                        // u, v, w -> eta, L
+    case HOSC_K_SOURCES: return n3 * 9 * sb;                     // u, v, w, th, p, eta -> E* x3
+    case HOSC_K_RHS:   // L, u, v, w, theta, E* x3 (+ 7 history arrays) -> rhs x4, 14 weights
+      return ni3 * ((8 + (P.have_prev ? 7 : 0)) * sb + (f4 ? 16.0 * (1 + 4) : 8.0 * 18));
+    case HOSC_K_BICG_PV: return ni3 * (f4 ? 16.0 * (6 + 4) : 8.0 * (4 * 6 + 14));
+    case HOSC_K_BICG_ST: return ni3 * (f4 ? 16.0 * (3 + 4) : 8.0 * (4 * 3 + 14));
+    case HOSC_K_BICG_XR: return ni3 * (f4 ? 16.0 * 8 : 8.0 * 4 * 8);
+    default: return 0.0;
+  }
+}
+
+bool tiles_valid(const Ctx* c, int kblock, int kz) {
+  if (kblock < 64 || kblock > 512 || kblock % 32 != 0) return false;
+  if (kz < 1 || kz > c->prm.N - 2) return false;
+  DevParams P = c->P;
+  P.kblock = kblock;
+  P.kz = kz;
+  const long n3 = (long)c->prm.N * c->prm.N * c->prm.N;
+  return krylov4_blocks(P) <= 4L * red_blocks(n3);   // rows of the partials buffer
 }
 
 // FP32 Krylov vectors cannot resolve relative residuals far below their rounding.
@@ -167,6 +201,12 @@ bool float_field(Ctx* c, int which) {
   }
 }
 
+// Fields held in the interleaved float arrays when the Krylov solve is FP32.
+bool interleaved_field(int which) {
+  return (which >= HOSC_RHS_U && which <= HOSC_DX_THETA) ||
+         (which >= HOSC_A_MOM && which < HOSC_A_ENE + 7);
+}
+
 bool settable(int which) {
   return (which >= HOSC_U && which <= HOSC_P) || (which >= HOSC_PREV_L && which <= HOSC_PREV_EW);
 }
@@ -222,6 +262,8 @@ hosc_status set_initial_state(Ctx* c) {
   c->best_res = INFINITY;
   c->since_best = 0;
   c->P = device_params(c->prm, 0, 0);
+  c->P.kblock = c->kblock;
+  c->P.kz = c->kz;
   return HOSC_OK;
 }
 
@@ -284,22 +326,21 @@ hosc_status run_stage(Ctx* c, int stage) {
       launch_viscosity(c->P, F, c->cur, c->stream);
       prof_end(c, HOSC_K_VISC);
       c->launches += 1;
-      c->host_bytes[HOSC_K_VISC] += 8.0 * n3 * 5;          // u, v, w -> eta, L
+      c->host_bytes[HOSC_K_VISC] += kernel_bytes(c->P, HOSC_K_VISC);
       break;
     case HOSC_STAGE_SOURCES:
       prof_begin(c, HOSC_K_SOURCES);
       launch_sources(c->P, F, c->cur, c->stream);
       prof_end(c, HOSC_K_SOURCES);
       c->launches += 1;
-      c->host_bytes[HOSC_K_SOURCES] += 8.0 * n3 * 9;       // u, v, w, theta, p, eta -> E*x3
+      c->host_bytes[HOSC_K_SOURCES] += kernel_bytes(c->P, HOSC_K_SOURCES);
       break;
     case HOSC_STAGE_RHS:
       prof_begin(c, HOSC_K_RHS);
       launch_rhs(c->P, F, c->cur, c->stream);
       prof_end(c, HOSC_K_RHS);
       c->launches += 1;
-      // reads L, u, v, w, theta, E*x3 (+ 7 history arrays), writes rhs x4 and 14 weights
-      c->host_bytes[HOSC_K_RHS] += 8.0 * ni3 * (8 + (c->P.have_prev ? 7 : 0) + 18);
+      c->host_bytes[HOSC_K_RHS] += kernel_bytes(c->P, HOSC_K_RHS);
       break;
     case HOSC_STAGE_SOLVE:
       st = solve(c);
@@ -334,6 +375,50 @@ hosc_status run_stage(Ctx* c, int stage) {
   return HOSC_OK;
 }
 
+// Mean milliseconds of one launch of a kernel class, run reps times back to back between
+// steps on the current buffers (see hosc_time_kernel).
+hosc_status time_class(Ctx* c, int kid, int reps, double* ms_out) {
+  const DevParams& P = c->P;
+  const Fields& F = c->F;
+  const bool krylov = kid >= HOSC_K_BICG_PV;
+  CU(cudaMemsetAsync(F.halt, 0, sizeof(int), c->stream));
+  cudaEvent_t ev[4];
+  for (int q = 0; q < 4; ++q) CU(cudaEventCreate(&ev[q]));
+  // Window 1: one untimed launch, then reps launches (each Krylov launch preceded by the tiny
+  // kernel that marks the four systems as iterating, so that no launch exits early on a
+  // converged system). Window 2: the marking kernel alone reps times, subtracted.
+  for (int r = -1; r < reps; ++r) {
+    if (r == 0) CU(cudaEventRecord(ev[0], c->stream));
+    switch (kid) {
+      case HOSC_K_VISC: launch_viscosity(P, F, c->cur, c->stream); break;
+      case HOSC_K_SOURCES: launch_sources(P, F, c->cur, c->stream); break;
+      case HOSC_K_RHS: launch_rhs(P, F, c->cur, c->stream); break;
+      default:
+        launch_krylov_activate(F, c->stream);
+        if (kid == HOSC_K_BICG_PV) launch_bicg_pv(P, F, 0, c->stream);
+        if (kid == HOSC_K_BICG_ST) launch_bicg_st(P, F, 0, c->stream);
+        if (kid == HOSC_K_BICG_XR) launch_bicg_xr(P, F, 0, c->stream);
+        break;
+    }
+  }
+  CU(cudaEventRecord(ev[1], c->stream));
+  if (krylov) {
+    CU(cudaEventRecord(ev[2], c->stream));
+    for (int r = 0; r < reps; ++r) launch_krylov_activate(F, c->stream);
+    CU(cudaEventRecord(ev[3], c->stream));
+  }
+  CU(cudaEventSynchronize(ev[krylov ? 3 : 1]));
+  float ms = 0.f, ms_mark = 0.f;
+  CU(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+  if (krylov) CU(cudaEventElapsedTime(&ms_mark, ev[2], ev[3]));
+  for (int q = 0; q < 4; ++q) cudaEventDestroy(ev[q]);
+  hosc_status st = check_launch();
+  if (st) return st;
+  *ms_out = (ms - ms_mark) / reps;
+  c->launches += (krylov ? 3L * reps + 2 : reps + 1);
+  return HOSC_OK;
+}
+
 hosc_status read_record(Ctx* c, hosc_info* info) {
   CU(cudaMemcpyAsync(c->h_rec, c->F.rec, sizeof(StepRecord), cudaMemcpyDeviceToHost, c->stream));
   CU(cudaStreamSynchronize(c->stream));
@@ -355,6 +440,8 @@ void set_phase(Ctx* c, int phase) {
   if (c->prm.precision != HOSC_MIXED || phase == c->phase) return;
   c->phase = phase;
   c->P = device_params(c->prm, 0, phase);
+  c->P.kblock = c->kblock;
+  c->P.kz = c->kz;
 }
 
 void watch_stall(Ctx* c, double res) {
@@ -384,40 +471,34 @@ hosc_status one_step(Ctx* c, hosc_info* info) {
 
 // ------------------------------------------------------------------ captured steps (CUDA graphs)
 
-// Capture one whole step: S1-S4 kernels, then a conditional WHILE node whose body runs two
-// BiCGSTAB iterations (the ping-pong buffers return to their parity) and sets the condition on
-// the device, then the update kernels (and the float state copy in mixed precision). Nothing in
-// the step waits on the host.
-hosc_status capture_step(Ctx* c, cudaGraphExec_t* out) {
-  const DevParams& P = c->P;
+// Append one whole step to the capture in progress on s0: S1-S4 kernels, then a conditional
+// WHILE node whose body (captured on s1) runs two BiCGSTAB iterations (the ping-pong buffers
+// return to their parity) and sets the condition on the device, then the update kernels (and the
+// float state copy in mixed precision). Nothing in the step waits on the host. cur and have_prev
+// are those of the step's level n.
+cudaError_t append_step(Ctx* c, cudaStream_t s0, cudaStream_t s1, int cur, int have_prev) {
+  DevParams P = c->P;
+  P.have_prev = have_prev;
   const Fields& F = c->F;
-  cudaStream_t s0 = c->cap[0], s1 = c->cap[1];
-  cudaGraph_t g = nullptr;
-  CU(cudaGraphCreate(&g, 0));
-  cudaError_t e = cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal);
-  if (e != cudaSuccess) {
-    cudaGraphDestroy(g);
-    CU(e);
-  }
-  launch_viscosity(P, F, c->cur, s0);
-  launch_sources(P, F, c->cur, s0);
-  launch_rhs(P, F, c->cur, s0);
+  launch_viscosity(P, F, cur, s0);
+  launch_sources(P, F, cur, s0);
+  launch_rhs(P, F, cur, s0);
   launch_bicg_init(P, F, s0);
   cudaStreamCaptureStatus cs;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
   cudaGraph_t cg = nullptr;
-  e = cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, &deps, nullptr, &nd);
+  cudaError_t e = cudaStreamGetCaptureInfo(s0, &cs, nullptr, &cg, &deps, nullptr, &nd);
+  if (e == cudaSuccess && cs != cudaStreamCaptureStatusActive) e = cudaErrorStreamCaptureInvalidated;
   cudaGraphConditionalHandle h = 0;
-  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 1, cudaGraphCondAssignDefault);
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = h;
   cp.conditional.type = cudaGraphCondTypeWhile;
   cp.conditional.size = 1;
   cudaGraphNode_t cn = nullptr;
-  if (e == cudaSuccess) e = cudaGraphAddNode(&cn, g, deps, nullptr, nd, &cp);
+  if (e == cudaSuccess) e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &cp);
   if (e == cudaSuccess)
     e = cudaStreamUpdateCaptureDependencies(s0, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
   if (e == cudaSuccess) {
@@ -435,8 +516,23 @@ hosc_status capture_step(Ctx* c, cudaGraphExec_t* out) {
       e = cudaStreamEndCapture(s1, &bo);
     }
   }
-  launch_update(P, F, c->cur, s0);
-  if (P.krylov_fp32) launch_shadow(P, F, 1 - c->cur, 0, s0);
+  launch_update(P, F, cur, s0);
+  if (P.krylov_fp32) launch_shadow(P, F, 1 - cur, 0, s0);
+  return e;
+}
+
+// Capture one step at the context's current level into an executable graph.
+hosc_status capture_step(Ctx* c, cudaGraphExec_t* out) {
+  cudaStream_t s0 = c->cap[0], s1 = c->cap[1];
+  cudaGraph_t g = nullptr;
+  CU(cudaGraphCreate(&g, 0));
+  cudaError_t e = cudaStreamBeginCaptureToGraph(s0, g, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    CU(e);
+  }
+  e = append_step(c, s0, s1, c->cur, c->P.have_prev);
   cudaGraph_t go = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(s0, &go);
   if (e == cudaSuccess) e = e2;
@@ -593,6 +689,8 @@ hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** ou
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_rec, sizeof(StepRecord));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_scal, 8 * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_ring, kRing * sizeof(StepRecord));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_ring_pos, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->round_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap[0], cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap[1], cudaStreamNonBlocking);
   if (e != cudaSuccess) {
@@ -600,6 +698,7 @@ hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** ou
     hosc_destroy(c);
     return HOSC_ECUDA;
   }
+  default_tiles(p->N, &c->kblock, &c->kz);
   st = set_initial_state(c);
   if (st) {
     hosc_destroy(c);
@@ -612,6 +711,113 @@ hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** ou
 }  // namespace
 
 namespace hosc {
+
+// ------------------------------------------------------------- rounds of steps for a pool
+
+char* detail_buffer() { return g_detail; }
+
+size_t ctx_workspace(void* ctx) { return ((Ctx*)ctx)->ws_bytes; }
+int ctx_N(void* ctx) { return ((Ctx*)ctx)->prm.N; }
+cudaStream_t ctx_branch_stream(void* ctx) { return ((Ctx*)ctx)->cap[0]; }
+
+// What a captured round assumes about the context: level parity, history, phase, launch shape.
+long ctx_signature(void* ctx) {
+  const Ctx* c = (const Ctx*)ctx;
+  return (long)c->cur | ((long)c->P.have_prev << 1) | ((long)c->phase << 2) |
+         ((long)c->kblock << 3) | ((long)c->kz << 13);
+}
+
+// Start of a round of n steps from the current level (read back by ctx_collect_round).
+void ctx_begin_round(void* ctx, long n) {
+  Ctx* c = (Ctx*)ctx;
+  c->round_cur0 = c->cur;
+  c->round_prev0 = c->P.have_prev;
+  c->round_n = n;
+}
+
+// Enqueue a round on the context's own stream: re-arm the device halt flag (stop at the first
+// steady step), n captured steps, and the asynchronous read-back of their records. Returns
+// without waiting.
+hosc_status ctx_enqueue_round(void* ctx, int n) {
+  Ctx* c = (Ctx*)ctx;
+  if (!graphs_usable(c) || n < 1 || n > kRing) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  const Fields& F = c->F;
+  ctx_begin_round(c, n);
+  launch_arm(F, 1, c->stream);
+  if (c->P.sweep_fp32 && !c->shadow_valid) {
+    launch_shadow(c->P, F, c->cur, c->P.have_prev, c->stream);
+    c->launches += 1;
+    c->shadow_valid = true;
+  }
+  int cur = c->cur, hp = c->P.have_prev;
+  for (int q = 0; q < n; ++q) {
+    cudaGraphExec_t& ge = c->graph[c->phase][cur][hp];
+    if (!ge) {
+      const int save_cur = c->cur, save_hp = c->P.have_prev;
+      c->cur = cur;
+      c->P.have_prev = hp;
+      hosc_status st = capture_step(c, &ge);
+      c->cur = save_cur;
+      c->P.have_prev = save_hp;
+      if (st) return st;
+    }
+    CU(cudaGraphLaunch(ge, c->stream));
+    cur ^= 1;
+    hp = c->prm.use_history ? 1 : 0;
+  }
+  CU(cudaMemcpyAsync(c->h_ring_pos, F.ring_pos, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CU(cudaMemcpyAsync(c->h_ring, F.ring, n * sizeof(StepRecord), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CU(cudaEventRecord(c->round_ev, c->stream));
+  return HOSC_OK;
+}
+
+// Append the same round to the capture in progress on the context's branch stream (forked from
+// the pool's capture). The float state copies are refreshed at the start of every round.
+hosc_status ctx_append_round(void* ctx, int n) {
+  Ctx* c = (Ctx*)ctx;
+  if (c->stage != 0 || n < 1 || n > kRing) return HOSC_ESTATE;
+  const Fields& F = c->F;
+  cudaStream_t s0 = c->cap[0], s1 = c->cap[1];
+  launch_arm(F, 1, s0);
+  if (c->P.sweep_fp32) launch_shadow(c->P, F, c->cur, c->P.have_prev, s0);
+  int cur = c->cur, hp = c->P.have_prev;
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < n && e == cudaSuccess; ++q) {
+    e = append_step(c, s0, s1, cur, hp);
+    cur ^= 1;
+    hp = c->prm.use_history ? 1 : 0;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_ring_pos, F.ring_pos, sizeof(unsigned), cudaMemcpyDeviceToHost, s0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->h_ring, F.ring, n * sizeof(StepRecord), cudaMemcpyDeviceToHost, s0);
+  if (e != cudaSuccess) {
+    snprintf(g_detail, sizeof(g_detail), "round capture: %s", cudaGetErrorString(e));
+    return HOSC_ECUDA;
+  }
+  return HOSC_OK;
+}
+
+// Fold the records of the last round (waiting for its event first when wait): the context
+// advances by the steps that ran; steady is set when one of them was steady.
+hosc_status ctx_collect_round(void* ctx, bool wait, hosc_info* info, bool* steady) {
+  Ctx* c = (Ctx*)ctx;
+  if (wait) CU(cudaEventSynchronize(c->round_ev));
+  unsigned n = *c->h_ring_pos;
+  if (n > (unsigned)c->round_n) n = (unsigned)c->round_n;
+  c->cur = c->round_cur0 ^ (int)(n & 1u);
+  if (n > 0) {
+    c->P.have_prev = c->prm.use_history ? 1 : 0;
+    c->shadow_valid = true;
+  }
+  bool st_steady = false;
+  hosc_status st = fold_records(c, n, info, &st_steady);
+  if (steady) *steady = st_steady;
+  return st;
+}
 
 size_t workspace_layout(int N, Fields* f, char* base) {
   const size_t n3 = (size_t)N * N * N;
@@ -648,6 +854,20 @@ size_t workspace_layout(int N, Fields* f, char* base) {
       F.pk[b][s] = fld();
       F.vk[b][s] = fld();
     }
+  }
+  // The interleaved float solve of mixed precision reuses the 46 planar Krylov arrays above
+  // (contiguous from Am[0]): weights 64 bytes per node, then eight float4 vectors.
+  {
+    char* kb = (char*)F.Am[0];
+    const size_t v4 = align_up(n3 * sizeof(float4));
+    F.kw = (float4*)kb;
+    kb += align_up(4 * n3 * sizeof(float4));
+    float4** vecs[8] = {&F.kr0, &F.kx, &F.kr, &F.kt, &F.kp[0], &F.kp[1], &F.kv[0], &F.kv[1]};
+    for (float4** v : vecs) {
+      *v = (float4*)kb;
+      kb += v4;
+    }
+    static_assert(4 * 16 + 8 * 16 <= 46 * 8, "interleaved solve must fit the planar arrays");
   }
   F.div = fld();
   F.eloc = (double*)take(3 * n3 * sizeof(double));
@@ -733,6 +953,8 @@ void hosc_destroy(void* ctx) {
   for (cudaStream_t q : c->cap)
     if (q) cudaStreamDestroy(q);
   if (c->h_ring) cudaFreeHost(c->h_ring);
+  if (c->h_ring_pos) cudaFreeHost(c->h_ring_pos);
+  if (c->round_ev) cudaEventDestroy(c->round_ev);
   if (c->own_ws && c->ws) cudaFree(c->ws);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   if (c->h_ks) cudaFreeHost(c->h_ks);
@@ -863,6 +1085,27 @@ hosc_status hosc_get_field(void* ctx, int which, double* host_out) {
   if (!d) return HOSC_EINVAL;
   CU(cudaSetDevice(c->device));
   const size_t n3 = (size_t)c->prm.N * c->prm.N * c->prm.N;
+  if (c->P.krylov_fp32 && interleaved_field(which)) {   // one component of a float4 array
+    const float4* base = nullptr;
+    int stride = 4, comp = 0;
+    if (which >= HOSC_RHS_U && which <= HOSC_RHS_THETA) {
+      base = c->F.kr0;
+      comp = which - HOSC_RHS_U;
+    } else if (which >= HOSC_DX_U && which <= HOSC_DX_THETA) {
+      base = c->F.kx;
+      comp = which - HOSC_DX_U;
+    } else {
+      base = c->F.kw;
+      stride = 16;
+      comp = (which >= HOSC_A_ENE) ? 7 + (which - HOSC_A_ENE) : which - HOSC_A_MOM;
+    }
+    std::vector<float> tmp(n3 * stride);
+    CU(cudaMemcpyAsync(tmp.data(), base, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    for (size_t q = 0; q < n3; ++q) host_out[q] = tmp[q * stride + comp];
+    return HOSC_OK;
+  }
   if (float_field(c, which)) {
     std::vector<float> tmp(n3);
     CU(cudaMemcpyAsync(tmp.data(), d, n3 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
@@ -989,6 +1232,85 @@ hosc_status hosc_set_phase(void* ctx, int phase) {
 int hosc_get_phase(void* ctx) {
   Ctx* c = (Ctx*)ctx;
   return c ? c->phase : -1;
+}
+
+hosc_status hosc_time_kernel(void* ctx, int kernel_id, int reps, double* ms_per_launch,
+                             double* bytes_per_launch) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || reps < 1 || kernel_id < 0 || kernel_id > HOSC_K_BICG_XR) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  double ms = 0.0;
+  hosc_status st = time_class(c, kernel_id, reps, &ms);
+  if (st) return st;
+  if (ms_per_launch) *ms_per_launch = ms;
+  if (bytes_per_launch) *bytes_per_launch = kernel_bytes(c->P, kernel_id);
+  return HOSC_OK;
+}
+
+hosc_status hosc_set_tiles(void* ctx, int kblock, int kz) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  if (!tiles_valid(c, kblock, kz)) return HOSC_EINVAL;
+  if (kblock != c->kblock || kz != c->kz) {
+    c->kblock = c->P.kblock = kblock;
+    c->kz = c->P.kz = kz;
+    drop_graphs(c);   // the captured steps hold the old launch shapes
+  }
+  return HOSC_OK;
+}
+
+hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  if (kblock) *kblock = c->kblock;
+  if (kz) *kz = c->kz;
+  return HOSC_OK;
+}
+
+hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, double* ms_out) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || reps < 1) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  if (!c->P.krylov_fp32) return HOSC_EINVAL;
+  CU(cudaSetDevice(c->device));
+  const int save_b = c->kblock, save_z = c->kz;
+  int best_b = save_b, best_z = save_z;
+  double best = INFINITY;
+  static const int blocks[] = {64, 128, 256, 512};
+  static const int zs[] = {1, 2, 4, 8, 16, 32};
+  for (int b : blocks) {
+    for (int z : zs) {
+      if (!tiles_valid(c, b, z)) continue;
+      c->P.kblock = b;
+      c->P.kz = z;
+      double tot = 0.0;
+      for (int kid = HOSC_K_BICG_PV; kid <= HOSC_K_BICG_XR; ++kid) {
+        double ms = 0.0;
+        hosc_status st = time_class(c, kid, reps, &ms);
+        if (st) {
+          c->P.kblock = save_b;
+          c->P.kz = save_z;
+          return st;
+        }
+        tot += ms;
+      }
+      if (tot < best) {
+        best = tot;
+        best_b = b;
+        best_z = z;
+      }
+    }
+  }
+  c->P.kblock = save_b;
+  c->P.kz = save_z;
+  hosc_status st = hosc_set_tiles(c, best_b, best_z);
+  if (st) return st;
+  if (kblock_out) *kblock_out = best_b;
+  if (kz_out) *kz_out = best_z;
+  if (ms_out) *ms_out = best;
+  return HOSC_OK;
 }
 
 long hosc_kernel_launches(void* ctx) {

@@ -115,23 +115,30 @@ __device__ __forceinline__ void block_sum_f32(const float (&vf)[M], double (&v)[
   __syncthreads();
 }
 
-// Publish this block's M partials (valid in thread 0) and report whether this block is the last
-// one of the grid to do so. No thread waits on another block: the last block to take a ticket
-// does the final reduction, every other block simply exits.
+// Publish the M partials of block b of nb (valid in thread 0) and report whether this block is
+// the last one to do so. No thread waits on another block: the last block to take a ticket does
+// the final reduction, every other block simply exits.
 template <int M>
 __device__ __forceinline__ bool publish_is_last(const double (&v)[M], double* red,
-                                                unsigned int* counter) {
+                                                unsigned int* counter, unsigned int b,
+                                                unsigned int nb) {
   __shared__ int s_last;
   if (threadIdx.x == 0) {
-    const unsigned int b = blockIdx.x;
 #pragma unroll
     for (int m = 0; m < M; ++m) red[(long)b * kRedSlots + m] = v[m];
     __threadfence();
     const unsigned int ticket = atomicAdd(counter, 1u);
-    s_last = (ticket == gridDim.x - 1);
+    s_last = (ticket == nb - 1);
   }
   __syncthreads();
   return s_last != 0;
+}
+
+// The same for a one-dimensional grid.
+template <int M>
+__device__ __forceinline__ bool publish_is_last(const double (&v)[M], double* red,
+                                                unsigned int* counter) {
+  return publish_is_last<M>(v, red, counter, blockIdx.x, gridDim.x);
 }
 
 // In the last block: reduce the partials of all blocks in a fixed order (valid in thread 0) and

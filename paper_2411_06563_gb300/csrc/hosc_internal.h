@@ -18,7 +18,10 @@ struct DevParams {
   int have_prev;     // level n-1 history present (else delta_t^- = 0)
   int max_lin_iter;
   int sweep_fp32;    // S1-S3 arithmetic (and eta, L, E* storage) in float
-  int krylov_fp32;   // right-hand sides, operator weights and Krylov vectors in float
+  int krylov_fp32;   // right-hand sides, operator weights and Krylov vectors in float,
+                     // interleaved (one float4 per node for the four systems)
+  int kblock;        // interleaved Krylov kernels: threads per block (multiple of 32, 64..512)
+  int kz;            // interleaved Krylov kernels: planes marched by one thread (1..N-2)
   double h, h2;      // grid spacing (h = k = l) and its square
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
   double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (and div below tol_div)
@@ -81,6 +84,15 @@ struct Fields {
   int* steady_stop;       // stop the sequence at the first steady step
   StepRecord* ring;       // [kRing] records of the steps of the sequence
   unsigned int* ring_pos; // records appended so far
+  // Mixed precision solve, interleaved over the four systems (u, v, w, theta components of one
+  // float4 per node). These alias the planar Krylov arrays above, which only the FP64 solve uses.
+  float4* kw;        // [4 N^3] weights: (Am0 Am1 Am2 Am3)(Am4 Am5 Am6 Ae0)(Ae1 Ae2 Ae3 Ae4)(Ae5 Ae6 0 0)
+  float4* kr0;       // right-hand sides dt (R - B chi^n) = r_0, the shadow residual
+  float4* kx;        // iterate (the increments)
+  float4* kr;        // residual
+  float4* kt;        // A s
+  float4* kp[2];     // search direction, ping-pong
+  float4* kv[2];     // A p, ping-pong
   // float copies of the state for the FP32 sweeps of mixed precision (rounded once per step)
   float* us[2];
   float* vs[2];
@@ -91,6 +103,11 @@ struct Fields {
 
 size_t workspace_layout(int N, Fields* f, char* base);   // returns bytes; fills f when base != 0
 int red_blocks(long count);
+// Blocks of one interleaved Krylov launch (the partials buffer holds 4 red_blocks(N^3) rows).
+long krylov4_blocks(const DevParams& P);
+// Threads per block and planes per thread of the interleaved Krylov kernels when none are set:
+// the longest z-segment that still gives four blocks per SM on a 152-SM GPU.
+void default_tiles(int N, int* kblock, int* kz);
 
 // S1: eta and L at every node.
 void launch_viscosity(const DevParams& P, const Fields& F, int cur, cudaStream_t s);
@@ -103,14 +120,31 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s);
 void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
+// Mark all four systems as iterating (for timing the Krylov kernels in isolation).
+void launch_krylov_activate(const Fields& F, cudaStream_t s);
 // Body of the BiCGSTAB loop of a captured step: end of the loop when every system is done.
 void launch_loop_cond(const Fields& F, unsigned long long handle, cudaStream_t s);
 // S6-S8: increments, theta walls, div V, pressure correction and walls, step record.
 void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s);
+// Re-arm the device control of a sequence of steps: run (halt = 0), no records yet, and stop at
+// the first steady step when stop_steady.
+void launch_arm(const Fields& F, int stop_steady, cudaStream_t s);
 // Mixed precision: round u, v, w (level cur, and level 1-cur when both), theta and p to float.
 void launch_shadow(const DevParams& P, const Fields& F, int cur, int both, cudaStream_t s);
 // Diagnostics.
 void launch_diagnostics(const DevParams& P, const Fields& F, int cur, int want_fields,
                         cudaStream_t s);
+
+// Rounds of captured steps of one context, driven by a pool (hosc_pool.cu); defined with the
+// context in hosc_api.cu. ctx is a context made by hosc_create.
+char* detail_buffer();                       // text returned by hosc_last_error_detail
+size_t ctx_workspace(void* ctx);             // device bytes the context holds
+int ctx_N(void* ctx);
+cudaStream_t ctx_branch_stream(void* ctx);   // stream on which ctx_append_round captures
+long ctx_signature(void* ctx);               // changes when a captured round no longer applies
+void ctx_begin_round(void* ctx, long n);
+hosc_status ctx_enqueue_round(void* ctx, int n);
+hosc_status ctx_append_round(void* ctx, int n);
+hosc_status ctx_collect_round(void* ctx, bool wait, hosc_info* info, bool* steady);
 
 }  // namespace hosc

@@ -10,6 +10,12 @@
 //
 // One iteration = three kernels; each ends with a last-block reduction that finalises the scalar
 // the next kernel needs (alpha, omega, beta / convergence). No kernel waits on another block.
+//
+// Two storage forms. FP64 (planar): one array per system and per weight, one thread per interior
+// node. Mixed precision (interleaved, float): one float4 per node holds the four systems, the
+// fourteen weights sit in four float4 per node, and a thread owns one interior (i, j) column over
+// a segment of kz planes, keeping the z-neighbours in registers as it marches; its dot-product
+// terms accumulate in float-float over the segment before the block reduction.
 
 #include <math.h>
 
@@ -87,44 +93,41 @@ __device__ __forceinline__ FF ff_shfl_down(FF a, int off) {
   return r;
 }
 
-// Block partial of M dot-product terms a[m] * b[m]. For float vectors the products and the warp
-// and cross-warp sums are float-float (no double instruction per thread) and thread 0 widens the
-// block total to double; for double vectors every stage is double. The grid stage in the last
-// block adds the block totals in double. The result is valid in thread 0.
-template <class T, int M>
-__device__ __forceinline__ void block_partial(const T (&a)[M], const T (&b)[M], double (&out)[M],
-                                              double* smem) {
-  if constexpr (sizeof(T) == sizeof(float)) {
-    FF* fs = reinterpret_cast<FF*>(smem);
-    FF w[M];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nw = (blockDim.x + 31) >> 5;
+// Block partial of M dot-product terms a[m] * b[m] in double (valid in thread 0).
+template <int M>
+__device__ __forceinline__ void block_partial(const double (&a)[M], const double (&b)[M],
+                                              double (&out)[M], double* smem) {
+#pragma unroll
+  for (int m = 0; m < M; ++m) out[m] = a[m] * b[m];
+  block_reduce<M, false>(out, smem);
+}
+
+// Block sum of M per-thread float-float accumulators; thread 0 receives the totals in double.
+template <int M>
+__device__ __forceinline__ void block_ff(FF (&acc)[M], double (&out)[M], double* smem) {
+  FF* fs = reinterpret_cast<FF*>(smem);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc[m] = ff_add(acc[m], ff_shfl_down(acc[m], off));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) fs[wid * M + m] = acc[m];
+  }
+  __syncthreads();
+  if (wid == 0) {
 #pragma unroll
     for (int m = 0; m < M; ++m) {
-      w[m] = ff_prod(a[m], b[m]);
+      FF x = (lane < nw) ? fs[lane * M + m] : FF{0.0f, 0.0f};
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) w[m] = ff_add(w[m], ff_shfl_down(w[m], off));
+      for (int off = 16; off > 0; off >>= 1) x = ff_add(x, ff_shfl_down(x, off));
+      out[m] = (double)x.hi + (double)x.lo;
     }
-    if (lane == 0) {
-#pragma unroll
-      for (int m = 0; m < M; ++m) fs[wid * M + m] = w[m];
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-      for (int m = 0; m < M; ++m) {
-        FF x = (lane < nw) ? fs[lane * M + m] : FF{0.0f, 0.0f};
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x = ff_add(x, ff_shfl_down(x, off));
-        if (lane == 0) out[m] = (double)x.hi + (double)x.lo;
-      }
-    }
-    __syncthreads();
-  } else {
-#pragma unroll
-    for (int m = 0; m < M; ++m) out[m] = (double)a[m] * (double)b[m];
-    block_reduce<M, false>(out, smem);
   }
+  __syncthreads();
 }
 
 // r = r_0 = rhs, x = 0, p = v = 0; ||r_0||^2 per system.
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_init(DevParams P, Fields F, i
     }
   }
   double part[4];
-  block_partial<T, 4>(da, db, part, smem);
+  block_partial<4>(da, db, part, smem);
   if (publish_is_last<4>(part, F.red, F.counter)) {
     double tot[4];
     reduce_partials<4, false>(tot, F.red, nblocks, F.counter, smem);
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_pv(DevParams P, Fields F, int
     }
   }
   double part[4];
-  block_partial<T, 4>(da, db, part, smem);
+  block_partial<4>(da, db, part, smem);
   if (publish_is_last<4>(part, F.red, F.counter)) {
     double tot[4];
     reduce_partials<4, false>(tot, F.red, nblocks, F.counter, smem);
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_st(DevParams P, Fields F, int
     }
   }
   double part[8];
-  block_partial<T, 8>(da, db, part, smem);
+  block_partial<8>(da, db, part, smem);
   if (publish_is_last<8>(part, F.red, F.counter)) {
     double tot[8];
     reduce_partials<8, false>(tot, F.red, nblocks, F.counter, smem);
@@ -330,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_xr(DevParams P, Fields F, int
     }
   }
   double part[8];
-  block_partial<T, 8>(da, db, part, smem);
+  block_partial<8>(da, db, part, smem);
   if (publish_is_last<8>(part, F.red, F.counter)) {
     double tot[8];
     reduce_partials<8, false>(tot, F.red, nblocks, F.counter, smem);
@@ -358,6 +361,306 @@ __global__ void __launch_bounds__(kThreads) k_bicg_xr(DevParams P, Fields F, int
   }
 }
 
+// ------------------------------------------------------------------ interleaved FP32 solve
+
+__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
+
+// a + b * c per component
+__device__ __forceinline__ float4 fma4(float4 b, float4 c, float4 a) {
+  return make_float4(fmaf(b.x, c.x, a.x), fmaf(b.y, c.y, a.y), fmaf(b.z, c.z, a.z),
+                     fmaf(b.w, c.w, a.w));
+}
+__device__ __forceinline__ float4 sub4(float4 a, float4 b) {
+  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+__device__ __forceinline__ float4 neg4(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
+
+// acc[m0 + s] += a_s * b_s for the four systems s
+__device__ __forceinline__ void ff_dot4(FF* acc, float4 a, float4 b) {
+  acc[0] = ff_add(acc[0], ff_prod(a.x, b.x));
+  acc[1] = ff_add(acc[1], ff_prod(a.y, b.y));
+  acc[2] = ff_add(acc[2], ff_prod(a.z, b.z));
+  acc[3] = ff_add(acc[3], ff_prod(a.w, b.w));
+}
+
+// The seven-point operators of the four systems at node c: momentum weights for u, v, w, energy
+// weights for theta. Arguments: the operand at c, x+, x-, y+, y-, z+, z-.
+__device__ __forceinline__ float4 apply7x4(const float4* __restrict__ W, int c, float4 o,
+                                           float4 xp, float4 xm, float4 yp, float4 ym, float4 zp,
+                                           float4 zm) {
+  const float4* w = W + 4 * (size_t)c;
+  const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3);
+  float4 y;
+  y.x = w0.x * o.x + w0.y * xp.x + w0.z * xm.x + w0.w * yp.x + w1.x * ym.x + w1.y * zp.x +
+        w1.z * zm.x;
+  y.y = w0.x * o.y + w0.y * xp.y + w0.z * xm.y + w0.w * yp.y + w1.x * ym.y + w1.y * zp.y +
+        w1.z * zm.y;
+  y.z = w0.x * o.z + w0.y * xp.z + w0.z * xm.z + w0.w * yp.z + w1.x * ym.z + w1.y * zp.z +
+        w1.z * zm.z;
+  y.w = w1.w * o.w + w2.x * xp.w + w2.y * xm.w + w2.z * yp.w + w2.w * ym.w + w3.x * zp.w +
+        w3.y * zm.w;
+  return y;
+}
+
+// Thread -> interior column (i, j) and its segment [k0, k1) of planes. False for the threads
+// past the last column of the plane (they still take part in the block reduction).
+struct Column {
+  int cb;      // node index of (i, j, 0)
+  int k0, k1;  // planes of the segment
+};
+__device__ __forceinline__ bool column(const DevParams& P, Column& col) {
+  const int N = P.N, ni = N - 2;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ni * ni) return false;
+  const int j = q / ni, i = q - j * ni;
+  col.cb = (i + 1) + N * (j + 1);
+  col.k0 = 1 + (int)blockIdx.y * P.kz;
+  col.k1 = min(col.k0 + P.kz, N - 1);
+  return true;
+}
+
+__device__ __forceinline__ unsigned block_id() { return blockIdx.x + gridDim.x * blockIdx.y; }
+__device__ __forceinline__ unsigned block_count() { return gridDim.x * gridDim.y; }
+
+// Per-system scalars of the interleaved kernels, zero for a finished system so that its vectors
+// stay as they are (x += 0, r = r - 0).
+struct Scal4 {
+  float4 a, b, om;
+  int done[4];
+  int all_done;
+};
+
+__device__ __forceinline__ void load_scalars(const KrylovScalars* ks, Scal4& sc) {
+  if (threadIdx.x == 0) {
+    float a[4], b[4], om[4];
+    int all = 1;
+    for (int s = 0; s < 4; ++s) {
+      const int d = ks[s].done;
+      sc.done[s] = d;
+      all &= d;
+      a[s] = d ? 0.f : (float)ks[s].alpha;
+      b[s] = d ? 0.f : (float)ks[s].beta;
+      om[s] = d ? 0.f : (float)ks[s].omega;
+    }
+    sc.a = make_float4(a[0], a[1], a[2], a[3]);
+    sc.b = make_float4(b[0], b[1], b[2], b[3]);
+    sc.om = make_float4(om[0], om[1], om[2], om[3]);
+    sc.all_done = all;
+  }
+  __syncthreads();
+}
+
+// Algorithmic bytes of one interleaved launch: words (float4 per interior node) moved.
+__device__ __forceinline__ double bytes4(const DevParams& P, double float4_words) {
+  const double ni = (double)(P.N - 2);
+  return 16.0 * float4_words * ni * ni * ni;
+}
+
+// r = r_0, x = 0, p = v = 0 at interior nodes, every vector zero on the walls; ||r_0||^2.
+__global__ void __launch_bounds__(kThreads) k4_init(DevParams P, Fields F) {
+  __shared__ double smem[32 * 4];
+  const int N = P.N;
+  const int n3 = N * N * N;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  FF acc[4] = {};
+  if (c < n3) {
+    const int i = c % N, j = (c / N) % N, k = c / (N * N);
+    const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
+    const float4 z = f4(0.f);
+    const float4 r = inner ? F.kr0[c] : z;
+    F.kr[c] = r;
+    F.kx[c] = z;
+    F.kt[c] = z;
+    F.kp[0][c] = z;
+    F.kp[1][c] = z;
+    F.kv[0][c] = z;
+    F.kv[1][c] = z;
+    ff_dot4(acc, r, r);
+  }
+  double part[4];
+  block_ff<4>(acc, part, smem);
+  if (publish_is_last<4>(part, F.red, F.counter)) {
+    double tot[4];
+    reduce_partials<4, false>(tot, F.red, gridDim.x, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        k.r0norm = sqrt(tot[s]);
+        k.rnorm = k.r0norm;
+        k.rho = tot[s];
+        k.alpha = 1.0;
+        k.omega = 1.0;
+        k.beta = 0.0;
+        k.iters = 0;
+        k.status = 0;
+        k.done = (k.r0norm == 0.0 || *F.halt) ? 1 : 0;
+      }
+    }
+  }
+}
+
+// p_new = r + beta (p_old - omega v_old) at the seven stencil nodes, v_new = A p_new, partial
+// r_0 . v_new; last block: alpha = rho / (r_0 . v_new).
+__global__ void __launch_bounds__(512) k4_pv(DevParams P, Fields F, int pp) {
+  __shared__ double smem[32 * 4];
+  __shared__ Scal4 sc;
+  load_scalars(F.ks, sc);
+  if (sc.all_done) return;   // uniform over the grid
+  const int N = P.N, N2 = N * N;
+  const float4 b = sc.b, mom = neg4(sc.om);
+  const float4* __restrict__ R = F.kr;
+  const float4* __restrict__ Po = F.kp[pp];
+  const float4* __restrict__ Vo = F.kv[pp];
+  float4* __restrict__ Pn = F.kp[1 - pp];
+  float4* __restrict__ Vn = F.kv[1 - pp];
+  auto pnew = [&](int c) {
+    const float4 r = __ldg(R + c), p = __ldg(Po + c), v = __ldg(Vo + c);
+    return fma4(b, fma4(mom, v, p), r);
+  };
+  FF acc[4] = {};
+  Column col;
+  if (column(P, col)) {
+    float4 pm = pnew(col.cb + N2 * (col.k0 - 1));
+    float4 pc = pnew(col.cb + N2 * col.k0);
+    for (int k = col.k0; k < col.k1; ++k) {
+      const int c = col.cb + N2 * k;
+      const float4 pz = pnew(c + N2);
+      const float4 vn = apply7x4(F.kw, c, pc, pnew(c + 1), pnew(c - 1), pnew(c + N),
+                                 pnew(c - N), pz, pm);
+      Pn[c] = pc;
+      Vn[c] = vn;
+      ff_dot4(acc, __ldg(F.kr0 + c), vn);
+      pm = pc;
+      pc = pz;
+    }
+  }
+  double part[4];
+  block_ff<4>(acc, part, smem);
+  if (publish_is_last<4>(part, F.red, F.counter, block_id(), block_count())) {
+    double tot[4];
+    reduce_partials<4, false>(tot, F.red, block_count(), F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        if (tot[s] == 0.0 || !isfinite(tot[s])) {
+          k.done = 1;
+          k.status = HOSC_ENOCONV;
+          continue;
+        }
+        k.alpha = k.rho / tot[s];
+      }
+      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 6.0 + 4.0);   // r p v r0 in, p v out, 4 weights
+    }
+  }
+}
+
+// s = r - alpha v at the seven stencil nodes, t = A s, partials (t . s, t . t); last block:
+// omega = (t . s) / (t . t) (0 when t = 0).
+__global__ void __launch_bounds__(512) k4_st(DevParams P, Fields F, int pp) {
+  __shared__ double smem[32 * 8];
+  __shared__ Scal4 sc;
+  load_scalars(F.ks, sc);
+  if (sc.all_done) return;
+  const int N = P.N, N2 = N * N;
+  const int np = 1 - pp;   // written by k4_pv of this iteration
+  const float4 ma = neg4(sc.a);
+  const float4* __restrict__ R = F.kr;
+  const float4* __restrict__ V = F.kv[np];
+  float4* __restrict__ T = F.kt;
+  auto sval = [&](int c) { return fma4(ma, __ldg(V + c), __ldg(R + c)); };
+  FF acc[8] = {};
+  Column col;
+  if (column(P, col)) {
+    float4 sm = sval(col.cb + N2 * (col.k0 - 1));
+    float4 sc0 = sval(col.cb + N2 * col.k0);
+    for (int k = col.k0; k < col.k1; ++k) {
+      const int c = col.cb + N2 * k;
+      const float4 sz = sval(c + N2);
+      const float4 tv = apply7x4(F.kw, c, sc0, sval(c + 1), sval(c - 1), sval(c + N),
+                                 sval(c - N), sz, sm);
+      T[c] = tv;
+      ff_dot4(acc, tv, sc0);
+      ff_dot4(acc + 4, tv, tv);
+      sm = sc0;
+      sc0 = sz;
+    }
+  }
+  double part[8];
+  block_ff<8>(acc, part, smem);
+  if (publish_is_last<8>(part, F.red, F.counter, block_id(), block_count())) {
+    double tot[8];
+    reduce_partials<8, false>(tot, F.red, block_count(), F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        k.omega = tot[4 + s] > 0.0 ? tot[s] / tot[4 + s] : 0.0;
+      }
+      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 3.0 + 4.0);   // r v in, t out, 4 weights
+    }
+  }
+}
+
+// s = r - alpha v; x += alpha p + omega s; r = s - omega t; partials (r_0 . r, r . r); last block:
+// convergence and breakdown tests, beta and rho of the next iteration.
+__global__ void __launch_bounds__(512) k4_xr(DevParams P, Fields F, int pp) {
+  __shared__ double smem[32 * 8];
+  __shared__ Scal4 sc;
+  load_scalars(F.ks, sc);
+  if (sc.all_done) return;
+  const int N2 = P.N * P.N;
+  const int np = 1 - pp;
+  const float4 a = sc.a, om = sc.om, ma = neg4(sc.a), mom = neg4(sc.om);
+  FF acc[8] = {};
+  Column col;
+  if (column(P, col)) {
+    for (int k = col.k0; k < col.k1; ++k) {
+      const int c = col.cb + N2 * k;
+      const float4 r = F.kr[c], v = __ldg(F.kv[np] + c), p = __ldg(F.kp[np] + c);
+      const float4 t = __ldg(F.kt + c), r0 = __ldg(F.kr0 + c);
+      const float4 sv = fma4(ma, v, r);
+      F.kx[c] = fma4(om, sv, fma4(a, p, F.kx[c]));
+      const float4 rn = fma4(mom, t, sv);
+      F.kr[c] = rn;
+      ff_dot4(acc, r0, rn);
+      ff_dot4(acc + 4, rn, rn);
+    }
+  }
+  double part[8];
+  block_ff<8>(acc, part, smem);
+  if (publish_is_last<8>(part, F.red, F.counter, block_id(), block_count())) {
+    double tot[8];
+    reduce_partials<8, false>(tot, F.red, block_count(), F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        const double rho_new = tot[s];
+        k.rnorm = sqrt(tot[4 + s]);
+        k.iters += 1;
+        if (k.rnorm <= P.tol_lin * k.r0norm) {
+          k.done = 1;
+          k.status = 0;
+        } else if (!isfinite(k.rnorm) || k.iters >= P.max_lin_iter || rho_new == 0.0 ||
+                   k.omega == 0.0) {
+          k.done = 1;
+          k.status = HOSC_ENOCONV;
+        } else {
+          k.beta = (rho_new / k.rho) * (k.alpha / k.omega);
+          k.rho = rho_new;
+        }
+      }
+      F.alg_bytes[HOSC_K_BICG_XR] += bytes4(P, 8.0);   // r v p x t r0 in, x r out
+    }
+  }
+}
+
+dim3 grid4(const DevParams& P) {
+  const int ni = P.N - 2;
+  return dim3((unsigned)((ni * ni + P.kblock - 1) / P.kblock), (unsigned)((ni + P.kz - 1) / P.kz));
+}
+
 int interior_blocks(const DevParams& P) {
   const long ni = P.N - 2;
   return red_blocks(ni * ni * ni);
@@ -365,32 +668,74 @@ int interior_blocks(const DevParams& P) {
 
 }  // namespace
 
+namespace {
+__global__ void k_krylov_activate(KrylovScalars* ks) {
+  if (threadIdx.x < 4) {
+    ks[threadIdx.x].done = 0;
+    ks[threadIdx.x].iters = 0;
+    ks[threadIdx.x].status = 0;
+  }
+}
+}  // namespace
+
+void launch_krylov_activate(const Fields& F, cudaStream_t s) {
+  k_krylov_activate<<<1, 32, 0, s>>>(F.ks);
+}
+
 void launch_loop_cond(const Fields& F, unsigned long long handle, cudaStream_t s) {
   k_loop_cond<<<1, 32, 0, s>>>(F.ks, (cudaGraphConditionalHandle)handle);
 }
 
 void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
+  if (P.krylov_fp32) {
+    const long n3 = (long)P.N * P.N * P.N;
+    k4_init<<<red_blocks(n3), kThreads, 0, s>>>(P, F);
+    return;
+  }
   const int b = interior_blocks(P);
-  if (P.krylov_fp32) k_bicg_init<float><<<b, kThreads, 0, s>>>(P, F, b);
-  else k_bicg_init<double><<<b, kThreads, 0, s>>>(P, F, b);
+  k_bicg_init<double><<<b, kThreads, 0, s>>>(P, F, b);
 }
 
 void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  if (P.krylov_fp32) {
+    k4_pv<<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    return;
+  }
   const int b = interior_blocks(P);
-  if (P.krylov_fp32) k_bicg_pv<float><<<b, kThreads, 0, s>>>(P, F, pp, b);
-  else k_bicg_pv<double><<<b, kThreads, 0, s>>>(P, F, pp, b);
+  k_bicg_pv<double><<<b, kThreads, 0, s>>>(P, F, pp, b);
 }
 
 void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  if (P.krylov_fp32) {
+    k4_st<<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    return;
+  }
   const int b = interior_blocks(P);
-  if (P.krylov_fp32) k_bicg_st<float><<<b, kThreads, 0, s>>>(P, F, pp, b);
-  else k_bicg_st<double><<<b, kThreads, 0, s>>>(P, F, pp, b);
+  k_bicg_st<double><<<b, kThreads, 0, s>>>(P, F, pp, b);
 }
 
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  if (P.krylov_fp32) {
+    k4_xr<<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    return;
+  }
   const int b = interior_blocks(P);
-  if (P.krylov_fp32) k_bicg_xr<float><<<b, kThreads, 0, s>>>(P, F, pp, b);
-  else k_bicg_xr<double><<<b, kThreads, 0, s>>>(P, F, pp, b);
+  k_bicg_xr<double><<<b, kThreads, 0, s>>>(P, F, pp, b);
+}
+
+long krylov4_blocks(const DevParams& P) {
+  const dim3 g = grid4(P);
+  return (long)g.x * g.y;
+}
+
+void default_tiles(int N, int* kblock, int* kz) {
+  const long ni = N - 2;
+  const long gx = (ni * ni + 127) / 128;
+  int z = 1;
+  for (int cand = 2; cand <= 16; cand *= 2)
+    if (gx * ((ni + cand - 1) / cand) >= 4L * 152) z = cand;
+  *kblock = 128;
+  *kz = z;
 }
 
 }  // namespace hosc

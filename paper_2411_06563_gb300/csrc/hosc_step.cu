@@ -289,9 +289,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs(
   const long c = node(i, j, k, N);
   const double h = P.h, h2 = P.h2, inv2h = 0.5 / h, invh2 = 1.0 / h2;
   const Tc tinv2h = (Tc)inv2h, tinvh2 = (Tc)invh2, h2_12 = (Tc)(h2 / 12.0), tdt = (Tc)P.dt;
-  Ts* const* rhs = reinterpret_cast<Ts* const*>(F.rhs);
-  Ts* const* Am = reinterpret_cast<Ts* const*>(F.Am);
-  Ts* const* Ae = reinterpret_cast<Ts* const*>(F.Ae);
+  Tc rv[4], Am[7], Ae[7];   // right-hand sides and weights, stored at the end
 
   Tc L7[7], u7[7], v7[7], w7[7];
   load7<Tc, Tc>(L, c, sy, sz, L7);
@@ -325,7 +323,7 @@ __global__ void __launch_bounds__(kThreads) k_rhs(
       const Tc Epc = P.have_prev ? Ep[s][c] : E7[0];
       const Tc R = bracket<Tc>(diffs7<Tc>(E7, tinv2h, tinvh2), E7[0], Epc, cm, h2_12);
       load19<Tc>(X[s], c, sy, sz, f19);
-      rhs[s][c] = (Ts)(tdt * (R - applyB<Tc>(cm, f19, h, tinv2h, tinvh2)));
+      rv[s] = tdt * (R - applyB<Tc>(cm, f19, h, tinv2h, tinvh2));
     }
     // level-(n+1) weights (Eq. 6): Mx = -dt/(2L) + h^2/12, M15 = (h^2/(6L)) dx L, ...
     const D7<Tc> dL = diffs7<Tc>(L7, tinv2h, tinvh2);
@@ -340,32 +338,48 @@ __global__ void __launch_bounds__(kThreads) k_rhs(
                          ? pseudo_time_mass<Tc>(cm.G, cm.H, cm.I, Lc, tdt, tinvh2, (Tc)P.a_boost)
                          : Tc(0);
     const Tc a2 = M * tinvh2;
-    Am[0][c] = (Ts)(Lc * (Tc(1) - Tc(6) * a2) + M18 + sig_m);
-    Am[1][c] = (Ts)(Lc * (a2 - M * cm.G * tinv2h + m15 * tinv2h));
-    Am[2][c] = (Ts)(Lc * (a2 + M * cm.G * tinv2h - m15 * tinv2h));
-    Am[3][c] = (Ts)(Lc * (a2 - M * cm.H * tinv2h + m16 * tinv2h));
-    Am[4][c] = (Ts)(Lc * (a2 + M * cm.H * tinv2h - m16 * tinv2h));
-    Am[5][c] = (Ts)(Lc * (a2 - M * cm.I * tinv2h + m17 * tinv2h));
-    Am[6][c] = (Ts)(Lc * (a2 + M * cm.I * tinv2h - m17 * tinv2h));
+    Am[0] = Lc * (Tc(1) - Tc(6) * a2) + M18 + sig_m;
+    Am[1] = Lc * (a2 - M * cm.G * tinv2h + m15 * tinv2h);
+    Am[2] = Lc * (a2 + M * cm.G * tinv2h - m15 * tinv2h);
+    Am[3] = Lc * (a2 - M * cm.H * tinv2h + m16 * tinv2h);
+    Am[4] = Lc * (a2 + M * cm.H * tinv2h - m16 * tinv2h);
+    Am[5] = Lc * (a2 - M * cm.I * tinv2h + m17 * tinv2h);
+    Am[6] = Lc * (a2 + M * cm.I * tinv2h - m17 * tinv2h);
   }
   // ---------------- energy: L = 1, G* = u, H* = v, I* = w, K* = E* = 0
   {
     const Eq5<Tc> ce = eq5_coefficients<Tc>(u7, v7, w7, upc, vpc, wpc, tinv2h, tinvh2, h2_12);
     Tc f19[19];
     load19<Tc>(th, c, sy, sz, f19);
-    rhs[3][c] = (Ts)(-tdt * applyB<Tc>(ce, f19, h, tinv2h, tinvh2));
+    rv[3] = -tdt * applyB<Tc>(ce, f19, h, tinv2h, tinvh2);
     const Tc M = Tc(-0.5) * tdt + h2_12;
     const Tc a2 = M * tinvh2;
     const Tc sig_e = P.a_boost > 0.0
                          ? pseudo_time_mass<Tc>(ce.G, ce.H, ce.I, Tc(1), tdt, tinvh2, (Tc)P.a_boost)
                          : Tc(0);
-    Ae[0][c] = (Ts)(Tc(1) - Tc(6) * a2 + sig_e);
-    Ae[1][c] = (Ts)(a2 - M * ce.G * tinv2h);
-    Ae[2][c] = (Ts)(a2 + M * ce.G * tinv2h);
-    Ae[3][c] = (Ts)(a2 - M * ce.H * tinv2h);
-    Ae[4][c] = (Ts)(a2 + M * ce.H * tinv2h);
-    Ae[5][c] = (Ts)(a2 - M * ce.I * tinv2h);
-    Ae[6][c] = (Ts)(a2 + M * ce.I * tinv2h);
+    Ae[0] = Tc(1) - Tc(6) * a2 + sig_e;
+    Ae[1] = a2 - M * ce.G * tinv2h;
+    Ae[2] = a2 + M * ce.G * tinv2h;
+    Ae[3] = a2 - M * ce.H * tinv2h;
+    Ae[4] = a2 + M * ce.H * tinv2h;
+    Ae[5] = a2 - M * ce.I * tinv2h;
+    Ae[6] = a2 + M * ce.I * tinv2h;
+  }
+  if constexpr (sizeof(Ts) == sizeof(float)) {   // interleaved float storage
+    F.kr0[c] = make_float4((float)rv[0], (float)rv[1], (float)rv[2], (float)rv[3]);
+    float4* W = F.kw + 4 * (size_t)c;
+    W[0] = make_float4((float)Am[0], (float)Am[1], (float)Am[2], (float)Am[3]);
+    W[1] = make_float4((float)Am[4], (float)Am[5], (float)Am[6], (float)Ae[0]);
+    W[2] = make_float4((float)Ae[1], (float)Ae[2], (float)Ae[3], (float)Ae[4]);
+    W[3] = make_float4((float)Ae[5], (float)Ae[6], 0.f, 0.f);
+  } else {                                         // planar double storage
+#pragma unroll
+    for (int s = 0; s < 4; ++s) F.rhs[s][c] = (double)rv[s];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      F.Am[q][c] = (double)Am[q];
+      F.Ae[q][c] = (double)Ae[q];
+    }
   }
 }
 
@@ -386,8 +400,19 @@ __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Field
     const int i = (int)(t % N), j = (int)((t / N) % N), k = (int)(t / ((long)N * N));
     const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
     if (inner) {
-      const double xu = (double)as<Ts>(F.x[0])[t], xv = (double)as<Ts>(F.x[1])[t],
-                   xw = (double)as<Ts>(F.x[2])[t], xt = (double)as<Ts>(F.x[3])[t];
+      double xu, xv, xw, xt;
+      if constexpr (sizeof(Ts) == sizeof(float)) {   // interleaved float increments
+        const float4 x4 = F.kx[t];
+        xu = x4.x;
+        xv = x4.y;
+        xw = x4.z;
+        xt = x4.w;
+      } else {
+        xu = F.x[0][t];
+        xv = F.x[1][t];
+        xw = F.x[2][t];
+        xt = F.x[3][t];
+      }
       F.u[1 - cur][t] = F.u[cur][t] + xu;
       F.v[1 - cur][t] = F.v[cur][t] + xv;
       F.w[1 - cur][t] = F.w[cur][t] + xw;
@@ -551,7 +576,19 @@ __global__ void k_finish_record(DevParams P, Fields F) {
   else if (*F.steady_stop && r->res < P.steady_res && r->div_max < P.tol_div) *F.halt = 2;
 }
 
+__global__ void k_arm(int* halt, unsigned int* ring_pos, int* steady_stop, int stop) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *halt = 0;
+    *ring_pos = 0u;
+    *steady_stop = stop;
+  }
+}
+
 }  // namespace
+
+void launch_arm(const Fields& F, int stop_steady, cudaStream_t s) {
+  k_arm<<<1, 32, 0, s>>>(F.halt, F.ring_pos, F.steady_stop, stop_steady);
+}
 
 int red_blocks(long count) { return (int)((count + kThreads - 1) / kThreads); }
 

@@ -65,6 +65,19 @@ class hosc_diag(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hosc_pool_info(ctypes.Structure):
+    _fields_ = [("active", ctypes.c_int), ("completed", ctypes.c_int),
+                ("tuned_sizes", ctypes.c_int), ("bytes_used", ctypes.c_size_t),
+                ("budget", ctypes.c_size_t), ("rounds", ctypes.c_long),
+                ("captures", ctypes.c_long), ("capture_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+HOSC_POOL_STREAMS, HOSC_POOL_GRAPH = 0, 1
+
+
 class HoscError(RuntimeError):
     def __init__(self, status, where=""):
         self.status = status
@@ -112,12 +125,30 @@ def lib():
         "hosc_profile_read": (ctypes.c_int, [_P, ctypes.c_int, _DP, ctypes.POINTER(ctypes.c_long),
                                              _DP]),
         "hosc_kernel_launches": (ctypes.c_long, [_P]),
+        "hosc_time_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _DP, _DP]),
+        "hosc_set_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+        "hosc_get_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int)]),
+        "hosc_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), _DP]),
         "hosc_set_phase": (ctypes.c_int, [_P, ctypes.c_int]),
         "hosc_bicgstab_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P),
                                                  ctypes.POINTER(_P), ctypes.POINTER(_P),
                                                  ctypes.c_double, ctypes.c_int,
                                                  ctypes.POINTER(ctypes.c_int), _P]),
         "hosc_get_phase": (ctypes.c_int, [_P]),
+        "hosc_pool_create": (ctypes.c_int, [ctypes.c_size_t, ctypes.c_int, ctypes.c_int,
+                                            ctypes.c_int, ctypes.POINTER(_P)]),
+        "hosc_pool_destroy": (None, [_P]),
+        "hosc_pool_admit": (ctypes.c_int, [_P, ctypes.POINTER(hosc_params), ctypes.c_long,
+                                           ctypes.POINTER(ctypes.c_int)]),
+        "hosc_pool_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.c_int, ctypes.POINTER(ctypes.c_int)]),
+        "hosc_pool_result": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(hosc_info), ctypes.POINTER(hosc_diag),
+                                            ctypes.POINTER(_P)]),
+        "hosc_pool_retire": (ctypes.c_int, [_P, ctypes.c_int]),
+        "hosc_pool_stats": (ctypes.c_int, [_P, ctypes.POINTER(hosc_pool_info)]),
         "hosc_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "hosc_last_error_detail": (ctypes.c_char_p, []),
     }
@@ -240,6 +271,76 @@ def hosc_profile_read(h, kernel_id):
     st = lib().hosc_profile_read(h, int(kernel_id), ctypes.byref(ms), ctypes.byref(n),
                                  ctypes.byref(b))
     return st, ms.value, n.value, b.value
+
+
+def hosc_time_kernel(h, kernel_id, reps):
+    ms = ctypes.c_double()
+    b = ctypes.c_double()
+    st = lib().hosc_time_kernel(h, int(kernel_id), int(reps), ctypes.byref(ms), ctypes.byref(b))
+    return st, ms.value, b.value
+
+
+def hosc_set_tiles(h, kblock, kz):
+    return lib().hosc_set_tiles(h, int(kblock), int(kz))
+
+
+def hosc_get_tiles(h):
+    b = ctypes.c_int()
+    z = ctypes.c_int()
+    st = lib().hosc_get_tiles(h, ctypes.byref(b), ctypes.byref(z))
+    return st, b.value, z.value
+
+
+def hosc_autotune(h, reps=5):
+    b = ctypes.c_int()
+    z = ctypes.c_int()
+    ms = ctypes.c_double()
+    st = lib().hosc_autotune(h, int(reps), ctypes.byref(b), ctypes.byref(z), ctypes.byref(ms))
+    return st, b.value, z.value, ms.value
+
+
+def hosc_pool_create(budget_bytes, steps_per_round=8, mode=HOSC_POOL_GRAPH, autotune=1):
+    h = _P()
+    st = lib().hosc_pool_create(int(budget_bytes), int(steps_per_round), int(mode),
+                                int(autotune), ctypes.byref(h))
+    return st, h
+
+
+def hosc_pool_destroy(pool):
+    lib().hosc_pool_destroy(pool)
+
+
+def hosc_pool_admit(pool, params, max_steps):
+    slot = ctypes.c_int(-1)
+    st = lib().hosc_pool_admit(pool, ctypes.byref(params), int(max_steps), ctypes.byref(slot))
+    return st, slot.value
+
+
+def hosc_pool_run(pool, rounds, cap=256):
+    done = (ctypes.c_int * max(cap, 1))()
+    nd = ctypes.c_int(0)
+    st = lib().hosc_pool_run(pool, int(rounds), done, int(cap), ctypes.byref(nd))
+    return st, [done[q] for q in range(min(nd.value, cap))]
+
+
+def hosc_pool_result(pool, slot):
+    status = ctypes.c_int()
+    info = hosc_info()
+    diag = hosc_diag()
+    ctx = _P()
+    st = lib().hosc_pool_result(pool, int(slot), ctypes.byref(status), ctypes.byref(info),
+                                ctypes.byref(diag), ctypes.byref(ctx))
+    return st, status.value, info, diag, ctx
+
+
+def hosc_pool_retire(pool, slot):
+    return lib().hosc_pool_retire(pool, int(slot))
+
+
+def hosc_pool_stats(pool):
+    out = hosc_pool_info()
+    st = lib().hosc_pool_stats(pool, ctypes.byref(out))
+    return st, out
 
 
 def hosc_kernel_launches(h):

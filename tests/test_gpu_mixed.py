@@ -95,3 +95,76 @@ def test_phase_api():
     with H.Cavity(p) as cav:
         assert H.hosc_set_phase(cav.h, 1) == H.HOSC_EINVAL
         assert H.hosc_set_phase(cav.h, 0) == 0
+
+
+def _one_mixed_step(N, Ra, n, dt, seed, tiles=None):
+    p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-12)
+    st = inputs.cavity_state(N, Ra, seed=seed)
+    with H.Cavity(p) as cav:
+        if tiles is not None:
+            assert H.hosc_set_tiles(cav.h, *tiles) == 0
+            assert H.hosc_get_tiles(cav.h) == (0,) + tuple(tiles)
+        for name, which in FIELDS:
+            cav.set(which, st[name])
+        info = cav.step(1)
+        assert info["call_status"] == 0
+        return p, st, {name: cav.get(which) - st[name] for name, which in FIELDS}
+
+
+@pytest.mark.parametrize("tiles", [(64, 1), (128, 3), (512, 17), (96, 7), (256, 16)])
+def test_one_step_any_launch_shape(tiles):
+    """The launch shape of the interleaved FP32 solve (threads per block, planes per thread)
+    changes only the grouping of the float-float dot-product sums: the increment equals the
+    default shape's within the FP32 solve tolerance (relative residual 3e-6), for segments that
+    do not divide the interior, blocks that overhang the plane and a single segment. A missed or
+    doubled plane or column would differ at O(1)."""
+    N, Ra, n, dt = 19, 1e4, 0.75, 0.002
+    _, _, ref = _one_mixed_step(N, Ra, n, dt, 219)
+    _, _, got = _one_mixed_step(N, Ra, n, dt, 219, tiles)
+    for name in ref:
+        scale = max(np.max(np.abs(ref[name])), 1e-12)
+        assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, tiles)
+
+
+def test_tiles_limits_and_autotune():
+    N = 21
+    p = _params(N, 1e4, 0.75, 0.002, H.HOSC_MIXED)
+    with H.Cavity(p) as cav:
+        for bad in ((32, 1), (100, 1), (1024, 1), (128, 0), (128, N - 1)):
+            assert H.hosc_set_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
+        cav.step(2)
+        u0 = cav.get(H.HOSC_U)
+        rc, b, z, ms = H.hosc_autotune(cav.h, 2)
+        assert rc == 0 and b in (64, 128, 256, 512) and 1 <= z <= N - 2 and ms > 0
+        assert H.hosc_get_tiles(cav.h) == (0, b, z)
+        assert np.array_equal(cav.get(H.HOSC_U), u0)   # tuning leaves the state alone
+        info = cav.step(3)
+        assert info["call_status"] == 0
+    p64 = _params(N, 1e4, 0.75, 0.002, H.HOSC_FP64)
+    with H.Cavity(p64) as cav:
+        cav.step(1)
+        assert H.hosc_autotune(cav.h, 1)[0] == H.HOSC_EINVAL
+
+
+def test_interleaved_fields_read_back():
+    """In mixed precision the right-hand sides and weights live in interleaved float arrays;
+    hosc_get_field returns each component as its own N^3 array. With FP64 sweeps (phase 1) they
+    are the FP64 path's values rounded once to float: within 2^-24 of each value."""
+    N = 13
+    st = inputs.cavity_state(N, 1e4, seed=31)
+    got = {}
+    for prec in (H.HOSC_FP64, H.HOSC_MIXED):
+        p = _params(N, 1e4, 0.75, 0.002, prec)
+        with H.Cavity(p) as cav:
+            if prec == H.HOSC_MIXED:
+                assert H.hosc_set_phase(cav.h, 1) == 0
+            for name, which in FIELDS:
+                cav.set(which, st[name])
+            for stage in range(3):
+                cav.run_stage(stage)
+            got[prec] = {w: cav.get(w) for w in
+                         [H.HOSC_RHS_U + s for s in range(4)] +
+                         [H.HOSC_A_MOM + q for q in range(7)] +
+                         [H.HOSC_A_ENE + q for q in range(7)]}
+    for w, ref in got[H.HOSC_FP64].items():
+        assert np.all(np.abs(got[H.HOSC_MIXED][w] - ref) <= 2.0 ** -24 * np.abs(ref) + 1e-37), w

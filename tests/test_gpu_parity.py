@@ -306,3 +306,30 @@ def test_captured_steady_stop_is_exact():
     (ia, va), (ib, vb) = res
     assert ia["call_status"] == ib["call_status"] == 0
     assert ia["steps"] == ib["steps"] and np.array_equal(va, vb)
+
+
+def test_isolated_kernel_timing_leaves_the_state():
+    """hosc_time_kernel re-runs one kernel class on the last step's buffers: positive times and
+    bytes for every class, unchanged fields, and a following step equal to one taken without the
+    timing (the Krylov buffers are re-initialised by every step)."""
+    N = 15
+    outs = []
+    for timed in (False, True):
+        p = _params(N, 1e4, 0.75, dt=0.002, tol_lin=1e-10)
+        with H.Cavity(p) as cav:
+            st = inputs.cavity_state(N, 1e4, seed=77)
+            for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
+                                ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
+                cav.set(which, st[name])
+            cav.step(1)
+            before = cav.get(H.HOSC_U)
+            if timed:
+                for kid in range(H.HOSC_K_BICG_XR + 1):
+                    rc, ms, b = H.hosc_time_kernel(cav.h, kid, 5)
+                    assert rc == 0 and ms > 0 and b > 0, (kid, rc, ms, b)
+                assert np.array_equal(cav.get(H.HOSC_U), before)
+                assert H.hosc_time_kernel(cav.h, H.HOSC_K_UPDATE, 5)[0] == H.HOSC_EINVAL
+                assert H.hosc_time_kernel(cav.h, 0, 0)[0] == H.HOSC_EINVAL
+            cav.step(1)
+            outs.append(cav.get(H.HOSC_U))
+    assert np.array_equal(outs[0], outs[1])

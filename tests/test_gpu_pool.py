@@ -1,0 +1,111 @@
+"""The native pool (batching and serving): members advance together and give the same result
+alone, in a mix, in either launch mode, and as a plain single-cavity solve; admission follows the
+device-memory budget."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+H = pytest.importorskip("paper_2411_06563_gb300.hosc")
+from paper_2411_06563_gb300 import serve as S  # noqa: E402
+
+FIELDS = (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W), ("th", H.HOSC_THETA), ("p", H.HOSC_P))
+
+# (N, Ra, n): the cavity followed by the tests, then the others of the mix
+TARGET = (15, 2e3, 0.9)
+OTHERS = [(11, 5e2, 1.2), (21, 1e3, 1.0), (13, 3e3, 0.8), (17, 1e3, 1.1), (9, 1e2, 1.0)]
+
+
+def _params(N, Ra, n, precision=H.HOSC_MIXED):
+    """Loose steady tolerances and a fixed dt = 0.01 (inside the stability bound at these Ra)
+    keep the solves to a few thousand steps; FP32 sweeps throughout (no phase switch, whose step
+    depends on when the host reads the records)."""
+    p = S.request_params(N, Ra, n, precision=precision, tol_steady=1e-2, tol_div=1e-3)
+    p.dt = 0.01
+    p.lambda_ = 0.1
+    p.auto_defect = 0
+    return p
+
+
+def _solve(members, mode=H.HOSC_POOL_GRAPH, autotune=False, G=8, max_steps=4000):
+    """Run members to completion in one pool; results of all members, in order."""
+    budget = sum(H.hosc_workspace_bytes(_params(*m)) for m in members) + 1
+    with S.Pool(budget, G, mode, autotune) as pool:
+        slots = [pool.admit(_params(*m), max_steps) for m in members]
+        assert None not in slots
+        out = {}
+        while len(out) < len(members):
+            for slot in pool.run(50):
+                out[slot] = pool.result(slot, FIELDS)
+        stats = pool.stats()
+    return [out[s] for s in slots], stats
+
+
+def test_same_alone_and_in_the_mix():
+    alone, _ = _solve([TARGET])
+    mixed, stats = _solve([TARGET] + OTHERS)
+    a, b = alone[0], mixed[0]
+    assert a["status"] == b["status"] == 0
+    assert a["info"]["steps"] == b["info"]["steps"]
+    for name, _ in FIELDS:
+        assert np.array_equal(a[name], b[name]), name
+    assert a["diag"] == b["diag"]
+    assert all(r["status"] == 0 for r in mixed), [r["status"] for r in mixed]
+    assert stats["captures"] >= 2   # captured again as members completed
+
+
+def test_graph_and_stream_modes_agree():
+    g, _ = _solve([TARGET] + OTHERS[:2], mode=H.HOSC_POOL_GRAPH)
+    s, stats = _solve([TARGET] + OTHERS[:2], mode=H.HOSC_POOL_STREAMS)
+    assert stats["captures"] == 0
+    for a, b in zip(g, s):
+        assert a["status"] == b["status"] and a["info"]["steps"] == b["info"]["steps"]
+        for name, _ in FIELDS:
+            assert np.array_equal(a[name], b[name]), name
+
+
+def test_pool_member_equals_plain_solve():
+    """A member stops at the same first steady step as hosc_solve_steady on its own context."""
+    res, _ = _solve([TARGET], G=6)
+    with H.Cavity(_params(*TARGET)) as cav:
+        info = cav.solve_steady(4000)
+        assert info["call_status"] == 0
+        assert info["steps"] == res[0]["info"]["steps"]
+        for name, which in FIELDS:
+            assert np.array_equal(cav.get(which), res[0][name]), name
+
+
+def test_autotuned_mix_within_tolerance():
+    """With the launch shape tuned per grid size the dot products group differently; the steady
+    fields stay within the mixed-precision target (1e-5 max-abs) of the untuned run."""
+    a, _ = _solve([TARGET] + OTHERS[:3], autotune=False)
+    b, stats = _solve([TARGET] + OTHERS[:3], autotune=True)
+    assert stats["tuned_sizes"] >= 1
+    for x, y in zip(a, b):
+        assert x["status"] == y["status"] == 0
+        for name, _ in FIELDS[:4]:
+            assert np.max(np.abs(x[name] - y[name])) <= 1e-5, name
+
+
+def test_admission_by_budget():
+    p = _params(13, 1e3, 1.0)
+    need = H.hosc_workspace_bytes(p)
+    with S.Pool(2 * need + 10, 4, H.HOSC_POOL_GRAPH, False) as pool:
+        s0 = pool.admit(p, 10)
+        s1 = pool.admit(p, 10)
+        assert s0 is not None and s1 is not None and s0 != s1
+        assert pool.admit(p, 10) is None          # no room now
+        with pytest.raises(H.HoscError):
+            pool.admit(_params(41, 1e3, 1.0), 10)  # never fits
+        st = pool.stats()
+        assert st["active"] == 2 and st["bytes_used"] <= st["budget"]
+        done = pool.run(3)                         # 4 steps per round: 12 >= 10 steps
+        assert sorted(done) == sorted([s0, s1])
+        for s in done:
+            r = pool.result(s)
+            assert r["status"] == H.HOSC_ESTEPLIMIT and r["info"]["steps"] == 12
+        pool.retire(s0)
+        assert pool.admit(p, 10) is not None       # room again
+    assert H.hosc_pool_create(0, 4, 0, 0)[0] == H.HOSC_EINVAL
+    assert H.hosc_pool_create(1 << 20, 3, H.HOSC_POOL_GRAPH, 0)[0] == H.HOSC_EINVAL
