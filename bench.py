@@ -32,9 +32,6 @@ WORKLOADS = {
     "cavity41": dict(N=41, Ra=1e4, Pr=1.0, n=0.75, dt=2e-4, spinup=300, history=0,
                      desc="cavity 41^3, n=0.75, Ra=1e4, Pr=1, mixed precision"),
 }
-ALG_WORDS = {  # algorithmic 8-byte words per interior node of one launch, all four systems active
-    "k_bicg_pv": 38, "k_bicg_st": 26, "k_bicg_xr": 32,
-}
 
 
 def _peaks():
@@ -142,6 +139,122 @@ def run_reference(args, wl):
     return 0
 
 
+def _one_at_a_time(H, S, cavs, precision, steps, warmup):
+    """Plain single-cavity solves, one after the other: GPUPS over the set (each cavity warmed
+    up, then `steps` steps timed; device-synchronised host clock)."""
+    import torch
+    tot_pts, tot_s = 0.0, 0.0
+    for c in cavs:
+        p = S.request_params(c["N"], c["Ra"], c["n"], c["Pr"], precision=precision)
+        with H.Cavity(p) as cav:
+            cav.step(warmup)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = cav.step(steps)
+            torch.cuda.synchronize()
+            tot_s += time.perf_counter() - t0
+            tot_pts += (c["N"] - 2) ** 3 * info["steps"]
+    return tot_pts / tot_s
+
+
+def run_batch(args):
+    """Batched configuration: 64 uneven cavities (N in {21, 31, 41, 61}, log-uniform Ra in
+    [1e2, 1e5], n uniform in [0.75, 1.25], Pr = 1, seed 20241106) advancing together in a pool,
+    one captured graph launch per round of G steps for all cavities, launch shapes autotuned per
+    N. value = aggregate GPUPS over the timed rounds; compared with the same cavities solved one
+    at a time (mixed and plain FP64, GPUPS over a fixed step count each)."""
+    import torch
+    from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
+    cavs = inputs.batch_mix()
+    G = args.round_steps
+    mode = H.HOSC_POOL_GRAPH if args.pool_mode == "graph" else H.HOSC_POOL_STREAMS
+    budget = sum(H.hosc_workspace_bytes(S.request_params(c["N"], c["Ra"], c["n"], c["Pr"]))
+                 for c in cavs) + (1 << 20)
+    rounds = max(1, args.steps // G)
+    warm_rounds = max(3, args.warmup)
+    with S.Pool(budget, G, mode, True) as pool:
+        slots = [pool.admit(S.request_params(c["N"], c["Ra"], c["n"], c["Pr"]),
+                            (warm_rounds + rounds) * G + G) for c in cavs]
+        assert None not in slots
+        for _ in range(warm_rounds):   # captures, per-N autotuning, first rounds
+            assert not pool.run(1)
+        torch.cuda.synchronize()
+        steps0 = [pool.result(s)["info"]["steps"] for s in slots]
+        t0 = time.perf_counter()
+        for _ in range(rounds):
+            pool.run(1)   # a cavity that completes stays in the pool, idle
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        st1 = pool.stats()
+        res = [pool.result(s)["info"] for s in slots]
+    pts = sum((c["N"] - 2) ** 3 * (r["steps"] - s0) for c, r, s0 in zip(cavs, res, steps0))
+    iters = sum(r["lin_iters"] for r in res)
+    value = pts / el
+    sub = cavs[:args.baseline_cavities]
+    one_mixed = _one_at_a_time(H, S, sub, H.HOSC_MIXED, args.baseline_steps, 5)
+    one_fp64 = _one_at_a_time(H, S, sub, H.HOSC_FP64, args.baseline_steps, 5)
+    out = {"metric": "grid-point updates/s (batched)", "value": value, "unit": "GPUPS",
+           "n_gpus": 1, "steps": rounds * G, "warmup": warm_rounds * G,
+           "ms_per_step": 1e3 * el / (rounds * G), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "batch of 64 cavities, N in {21,31,41,61}, Ra log-uniform "
+                                  "[1e2,1e5], n uniform [0.75,1.25], Pr=1, seed 20241106, mixed",
+                      "pool_mode": args.pool_mode, "steps_per_round": G,
+                      "graph_launches_timed": rounds if mode == H.HOSC_POOL_GRAPH else None,
+                      "captures": st1["captures"], "capture_ms": st1["capture_ms"],
+                      "tuned_sizes": st1["tuned_sizes"],
+                      "bicgstab_iters_per_cavity_step":
+                          iters / (4.0 * max(1, sum(r["steps"] for r in res))),
+                      "dt": "per cavity from the stability bound (serve.pseudo_time_step)"},
+           "one_at_a_time": {"cavities": len(sub), "steps_each": args.baseline_steps,
+                             "mixed_GPUPS": one_mixed, "fp64_GPUPS": one_fp64,
+                             "batched_over_fp64": value / one_fp64,
+                             "batched_over_mixed": value / one_mixed}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_serve(args):
+    """Serving configuration: a seeded Poisson stream (seed 20241107) of cavity solves, N in
+    {21, 31, ..., 101}, log-uniform Ra in [1e2, 1e5], n in {0.75, 1.0, 1.25}, Pr = 1, admitted
+    against a device-memory budget, each solved to steady state (or a step cap) in a pool.
+    First the saturated rate (all requests present at t = 0), then the stream at rho times that
+    rate; p50 / p99 arrival-to-completion times."""
+    from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
+    mode = H.HOSC_POOL_GRAPH if args.pool_mode == "graph" else H.HOSC_POOL_STREAMS
+    budget = int(args.budget_gb * (1 << 30))
+
+    def make(r):
+        return S.request_params(r["N"], r["Ra"], r["n"], r["Pr"], tol_steady=args.tol_steady,
+                                tol_div=1e-4)
+
+    base = inputs.request_stream(args.requests, rate=1.0)
+    sat_reqs = [dict(r, t=0.0) for r in base[:args.saturation_requests]]
+    with S.Pool(budget, args.round_steps, mode, True) as pool:
+        _, sat = S.serve(sat_reqs, pool, make, args.max_steps)
+    rate = args.rho * sat["solves_per_s"]
+    stream = inputs.request_stream(args.requests, rate=rate)
+    with S.Pool(budget, args.round_steps, mode, True) as pool:
+        res, summ = S.serve(stream, pool, make, args.max_steps)
+        pst = pool.stats()
+    out = {"metric": "served cavity solves/s", "value": summ["solves_per_s"], "unit": "solves/s",
+           "n_gpus": 1, "steps": args.requests, "warmup": 0,
+           "ms_per_step": 1e3 / summ["solves_per_s"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
+           "config": {"workload": "Poisson stream of %d cavity solves, N in {21..101} step 10, "
+                                  "Ra log-uniform [1e2,1e5], n in {0.75,1,1.25}, Pr=1, seed "
+                                  "20241107" % args.requests,
+                      "rho": args.rho, "saturated_solves_per_s": sat["solves_per_s"],
+                      "saturation_requests": len(sat_reqs), "budget_GB": args.budget_gb,
+                      "max_steps": args.max_steps, "tol_steady": args.tol_steady,
+                      "pool_mode": args.pool_mode, "steps_per_round": args.round_steps,
+                      "completed": summ["completed"], "steady": summ["steady"],
+                      "captures": pst["captures"], "capture_ms": pst["capture_ms"]}}
+    print(json.dumps(out))
+    return 0
+
+
 def cpu_baseline(cav, H, wl):
     """One oracle step of the same 101^3 workload from the GPU's current state (with history)."""
     import numpy as np
@@ -178,8 +291,25 @@ def main():
                     help="keep the default launch shape of the mixed-precision solve")
     ap.add_argument("--spinup", type=int, default=None,
                     help="untimed steps from rest before the warm-up (default: per workload)")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+                    help="step: the single-cavity headline; batch: 64 cavities in a pool; "
+                         "serve: a Poisson request stream on a pool")
+    ap.add_argument("--pool-mode", default="graph", choices=["graph", "streams"])
+    ap.add_argument("--round-steps", type=int, default=8)
+    ap.add_argument("--baseline-cavities", type=int, default=16)
+    ap.add_argument("--baseline-steps", type=int, default=40)
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--saturation-requests", type=int, default=32)
+    ap.add_argument("--rho", type=float, default=0.8)
+    ap.add_argument("--max-steps", type=int, default=1000)
+    ap.add_argument("--tol-steady", type=float, default=1e-4)
+    ap.add_argument("--budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
+    if args.impl == "ours" and args.mode == "batch":
+        return run_batch(args)
+    if args.impl == "ours" and args.mode == "serve":
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -244,10 +374,12 @@ def main():
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_steps")
         e0.record(stream)
         info = cav.step(args.steps)
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         barrier()
     ms = e0.elapsed_time(e1)
     launches = cav.kernel_launches() - l0

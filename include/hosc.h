@@ -226,8 +226,10 @@ hosc_status hosc_set_tiles(void* ctx, int kblock, int kz);
 hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz);
 
 /* Autotuner for the launch shape above: after at least one completed step, time the three
- * BiCGSTAB kernels (hosc_time_kernel, reps launches each) for every valid kblock in
- * {64, 128, 256, 512} and kz in {1, 2, 4, 8, 16, 32}, keep the shape with the least total
+ * BiCGSTAB kernels (hosc_time_kernel, reps launches each) for the valid shapes with kblock in
+ * {64, 96, 128, 160, 192, 256, 320, 384, 512} and kz in 1..33 whose modelled cost (waves of
+ * resident blocks on this GPU, from the kernels' occupancy, times kz + 2 planes streamed per
+ * block) is within 1.5x of the least, keep the shape with the least total
  * time and report it (any output pointer may be NULL; ms_out = the three kernels' summed mean
  * milliseconds). Mixed precision only (HOSC_EINVAL for FP64). The fields keep their values. */
 hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, double* ms_out);

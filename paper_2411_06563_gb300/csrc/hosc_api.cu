@@ -1278,11 +1278,20 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   const int save_b = c->kblock, save_z = c->kz;
   int best_b = save_b, best_z = save_z;
   double best = INFINITY;
-  static const int blocks[] = {64, 128, 256, 512};
-  static const int zs[] = {1, 2, 4, 8, 16, 32};
+  static const int blocks[] = {64, 96, 128, 160, 192, 256, 320, 384, 512};
+  // time every shape whose modelled cost is within 1.5x of the best model cost
+  const int sms = device_sms();
+  double best_model = 1e300;
+  for (int b : blocks)
+    for (int z = 1; z <= 33; ++z)
+      if (tiles_valid(c, b, z)) {
+        const double m = krylov4_wave_cost(c->prm.N, b, z, sms);
+        if (m < best_model) best_model = m;
+      }
   for (int b : blocks) {
-    for (int z : zs) {
+    for (int z = 1; z <= 33; ++z) {
       if (!tiles_valid(c, b, z)) continue;
+      if (krylov4_wave_cost(c->prm.N, b, z, sms) > 1.5 * best_model) continue;
       c->P.kblock = b;
       c->P.kz = z;
       double tot = 0.0;

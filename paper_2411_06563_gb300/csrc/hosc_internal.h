@@ -106,8 +106,12 @@ int red_blocks(long count);
 // Blocks of one interleaved Krylov launch (the partials buffer holds 4 red_blocks(N^3) rows).
 long krylov4_blocks(const DevParams& P);
 // Threads per block and planes per thread of the interleaved Krylov kernels when none are set:
-// the longest z-segment that still gives four blocks per SM on a 152-SM GPU.
+// 128 threads and the z-segment with the least wave cost below.
 void default_tiles(int N, int* kblock, int* kz);
+// Waves of resident blocks a launch shape needs on this GPU times the planes each block streams
+// (kz + 2): a model of the launch's duration when it is latency-bound.
+double krylov4_wave_cost(int N, int kblock, int kz, int sms);
+int device_sms();
 
 // S1: eta and L at every node.
 void launch_viscosity(const DevParams& P, const Fields& F, int cur, cudaStream_t s);

@@ -728,14 +728,48 @@ long krylov4_blocks(const DevParams& P) {
   return (long)g.x * g.y;
 }
 
-void default_tiles(int N, int* kblock, int* kz) {
+int krylov4_occupancy(int kblock) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_pv, kblock, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return occ > 0 ? occ : 1;
+}
+
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 152;
+  }
+  return sms > 0 ? sms : 152;
+}
+
+double krylov4_wave_cost(int N, int kblock, int kz, int sms) {
   const long ni = N - 2;
-  const long gx = (ni * ni + 127) / 128;
-  int z = 1;
-  for (int cand = 2; cand <= 16; cand *= 2)
-    if (gx * ((ni + cand - 1) / cand) >= 4L * 152) z = cand;
-  *kblock = 128;
-  *kz = z;
+  const long items = ((ni * ni + kblock - 1) / kblock) * ((ni + kz - 1) / kz);
+  const long slots = (long)krylov4_occupancy(kblock) * sms;
+  const long waves = (items + slots - 1) / slots;
+  // every resident block streams kz planes plus the two it reads around its segment
+  return (double)waves * (kz + 2);
+}
+
+void default_tiles(int N, int* kblock, int* kz) {
+  const int sms = device_sms();
+  const int ni = N - 2;
+  double best = 1e300;
+  int bb = 128, bz = 1;
+  for (int z = 1; z <= (ni < 16 ? ni : 16); ++z) {
+    const double c = krylov4_wave_cost(N, 128, z, sms);
+    if (c < best) {
+      best = c;
+      bz = z;
+    }
+  }
+  *kblock = bb;
+  *kz = bz;
 }
 
 }  // namespace hosc
