@@ -214,6 +214,73 @@ def run_batch(args):
     return 0
 
 
+def run_equal(args):
+    """Steady solves at equal accuracy: a seeded set of small cavities (N in {17, 21}, Ra
+    log-uniform in [1e2, 1e3], n uniform in [0.9, 1.1], Pr = 1, dt = 0.02, lambda = 0.1,
+    tol_steady = tol_div = 1e-6), each solved to steady state by the plain FP64 path one at a
+    time, then all together in a mixed-precision pool (FP32 sweeps, FP64 defect sweeps once the
+    step change stalls). value = pool solves/s; the line carries the FP64 solves/s and the
+    largest field and Nu differences between the two."""
+    import numpy as np
+    import torch
+    from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
+    cavs = inputs.steady_mix(args.equal_cavities)
+    fields = (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W), ("th", H.HOSC_THETA))
+
+    def params(c, precision):
+        p = S.request_params(c["N"], c["Ra"], c["n"], c["Pr"], precision=precision,
+                             tol_steady=1e-6, tol_div=1e-6)
+        p.dt = 0.02
+        p.lambda_ = 0.1
+        return p
+
+    ref = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in cavs:
+        with H.Cavity(params(c, H.HOSC_FP64)) as cav:
+            info = cav.solve_steady(args.equal_max_steps)
+            ref.append(dict(info=info, diag=cav.diagnostics(),
+                            **{k: cav.get(w) for k, w in fields}))
+    t64 = time.perf_counter() - t0
+    budget = sum(H.hosc_workspace_bytes(params(c, H.HOSC_MIXED)) for c in cavs) + (1 << 20)
+    mode = H.HOSC_POOL_GRAPH if args.pool_mode == "graph" else H.HOSC_POOL_STREAMS
+    got = {}
+    t0 = time.perf_counter()
+    with S.Pool(budget, args.round_steps, mode, True) as pool:
+        slots = [pool.admit(params(c, H.HOSC_MIXED), args.equal_max_steps) for c in cavs]
+        while len(got) < len(cavs):
+            for s_ in pool.run(64):
+                got[s_] = pool.result(s_, fields)
+        tmx = time.perf_counter() - t0
+        pst = pool.stats()
+    mix = [got[s_] for s_ in slots]
+    steady64 = sum(1 for r in ref if r["info"]["call_status"] == 0)
+    steadymx = sum(1 for r in mix if r["status"] == 0)
+    dfield = max(float(np.max(np.abs(a[k] - b[k]))) for a, b in zip(mix, ref) for k, _ in fields)
+    dnu = max(abs(a["diag"]["Nu_hot_mean"] - b["diag"]["Nu_hot_mean"]) / abs(b["diag"]["Nu_hot_mean"])
+              for a, b in zip(mix, ref))
+    out = {"metric": "steady cavity solves/s at equal accuracy", "value": len(cavs) / tmx,
+           "unit": "solves/s", "n_gpus": 1, "steps": len(cavs), "warmup": 0,
+           "ms_per_step": 1e3 * tmx / len(cavs), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+           "config": {"workload": "%d cavities N in {17,21}, Ra log-uniform [1e2,1e3], n uniform "
+                                  "[0.9,1.1], Pr=1, dt=0.02, lambda=0.1, tol_steady=tol_div=1e-6, "
+                                  "seed 20241108" % len(cavs),
+                      "pool_mode": args.pool_mode, "steps_per_round": args.round_steps,
+                      "captures": pst["captures"]},
+           "fp64_one_at_a_time": {"solves_per_s": len(cavs) / t64, "seconds": t64,
+                                  "steady": steady64,
+                                  "steps": [r["info"]["steps"] for r in ref]},
+           "mixed_pool": {"seconds": tmx, "steady": steadymx,
+                          "steps": [r["info"]["steps"] for r in mix]},
+           "speedup_over_fp64": t64 / tmx,
+           "accuracy": {"max_abs_field_diff": dfield, "max_rel_Nu_diff": dnu,
+                        "targets": {"field": 1e-5, "Nu": 1e-4}}}
+    print(json.dumps(out))
+    return 0
+
+
 def run_serve(args):
     """Serving configuration: a seeded Poisson stream (seed 20241107) of cavity solves, N in
     {21, 31, ..., 101}, log-uniform Ra in [1e2, 1e5], n in {0.75, 1.0, 1.25}, Pr = 1, admitted
@@ -291,9 +358,12 @@ def main():
                     help="keep the default launch shape of the mixed-precision solve")
     ap.add_argument("--spinup", type=int, default=None,
                     help="untimed steps from rest before the warm-up (default: per workload)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "equal"],
                     help="step: the single-cavity headline; batch: 64 cavities in a pool; "
-                         "serve: a Poisson request stream on a pool")
+                         "serve: a Poisson request stream on a pool; equal: steady solves of "
+                         "the pool against one-at-a-time FP64 at equal accuracy")
+    ap.add_argument("--equal-cavities", type=int, default=8)
+    ap.add_argument("--equal-max-steps", type=int, default=20000)
     ap.add_argument("--pool-mode", default="graph", choices=["graph", "streams"])
     ap.add_argument("--round-steps", type=int, default=8)
     ap.add_argument("--baseline-cavities", type=int, default=16)
@@ -310,6 +380,8 @@ def main():
         return run_batch(args)
     if args.impl == "ours" and args.mode == "serve":
         return run_serve(args)
+    if args.impl == "ours" and args.mode == "equal":
+        return run_equal(args)
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -394,7 +466,9 @@ def main():
     # ------------------------------------------------------------- kernel breakdown (events)
     H.hosc_profile_enable(cav.h, 1)
     prof_steps = max(5, min(args.steps, 50))
+    torch.cuda.nvtx.range_push("profiled_steps")   # uncaptured steps: one launch per kernel
     cav.step(prof_steps)
+    torch.cuda.nvtx.range_pop()
     names = ["k_viscosity", "k_sources", "k_rhs", "k_bicg_pv", "k_bicg_st", "k_bicg_xr", "update"]
     kern = {}
     for kid, name in enumerate(names):
@@ -459,8 +533,12 @@ def main():
                        "spinup_steps": spinup, "tol_lin": p.tol_lin,
                        "use_history": wl["history"], "lambda": p.lambda_,
                        "bicgstab_iters_per_step": lin_iters / (4.0 * args.steps),
-                       "krylov_tiles": (dict(zip(("block", "kz"), H.hosc_get_tiles(cav.h)[1:]))
+                       "krylov_tiles": (dict(zip(("block", "kz", "narrow"),
+                                                 H.hosc_get_tiles(cav.h)[1:]))
                                         if args.precision == "mixed" else None),
+                       "stencil_tiles": (dict(zip(("sx", "sy", "skz"),
+                                                  H.hosc_get_stencil_tiles(cav.h)[1:]))
+                                         if args.precision == "mixed" else None),
                        "l2": "no flush: device working set %.0f MB > 129 MB L2"
                              % (H.hosc_workspace_bytes(p) / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single"},

@@ -217,21 +217,37 @@ hosc_status hosc_time_kernel(void* ctx, int kernel_id, int reps, double* ms_per_
 
 /* Launch shape of the mixed-precision BiCGSTAB kernels, which store the four systems interleaved
  * (one float4 per node) and give each thread one interior (i, j) column over kz consecutive
- * planes: kblock threads per block (a multiple of 32, 64..512), kz in 1..N-2, and at most
- * 4 * ceil(N^3/256) blocks per launch. The default is chosen from N at creation. Changing it
+ * planes: kblock threads per block (a multiple of 32, 64..384), kz in 1..N-2, and at most
+ * N^3/16 + 1024 blocks per launch; narrow = 1 selects the kernels compiled for at most 64
+ * registers per thread (more resident blocks; kblock <= 256), 0 those with up to 80. The
+ * default (128 threads, wide, kz from the wave model below) is chosen from N at creation. Changing it
  * drops the captured steps (they are captured again at the next step). HOSC_EINVAL for a shape
  * outside these limits, HOSC_ESTATE in the middle of a stage-by-stage step. The FP64 solve has
  * one thread per node and ignores the setting. */
-hosc_status hosc_set_tiles(void* ctx, int kblock, int kz);
-hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz);
+hosc_status hosc_set_tiles(void* ctx, int kblock, int kz, int narrow);
+hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz, int* narrow);
+
+/* Staged stencil kernels of the mixed-precision solve (the p/v and s/t kernels with their reads
+ * staged through shared memory by cp.async, several planes ahead): a block owns sx * sy interior
+ * columns (one thread each; sx * sy a multiple of 32 in 32..256) and skz consecutive planes
+ * (1..N-2). sx == 0
+ * selects the register kernels of hosc_set_tiles for p/v and s/t (the default). HOSC_EINVAL for
+ * a shape that does not fit (shared memory above 200 KB per block, too many blocks),
+ * HOSC_ESTATE in the middle of a stage-by-stage step. Changing it drops the captured steps. */
+hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz);
+hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz);
 
 /* Autotuner for the launch shape above: after at least one completed step, time the three
  * BiCGSTAB kernels (hosc_time_kernel, reps launches each) for the valid shapes with kblock in
- * {64, 96, 128, 160, 192, 256, 320, 384, 512} and kz in 1..33 whose modelled cost (waves of
+ * {64, 96, 128, 160, 192, 256, 320, 384} and kz in 1..33 whose modelled cost (waves of
  * resident blocks on this GPU, from the kernels' occupancy, times kz + 2 planes streamed per
- * block) is within 1.5x of the least, keep the shape with the least total
- * time and report it (any output pointer may be NULL; ms_out = the three kernels' summed mean
- * milliseconds). Mixed precision only (HOSC_EINVAL for FP64). The fields keep their values. */
+ * block) is within 1.5x of the least, for both register budgets (narrow 0 and 1), keep the
+ * shape with the least total time; then time the
+ * staged p/v and s/t kernels (hosc_set_stencil_tiles) for tiles sx in {8, 16, ..., 64},
+ * sy in {4, 8} and skz in 1..33 within 1.5x of their least modelled cost, and keep them when
+ * they beat the register kernels. Reports the register shape (any output pointer may be NULL;
+ * ms_out = the three kernels' summed mean milliseconds with the chosen kernels). Mixed precision
+ * only (HOSC_EINVAL for FP64). The fields keep their values. */
 hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, double* ms_out);
 
 /* Kernel classes for hosc_profile_read and hosc_time_kernel. */

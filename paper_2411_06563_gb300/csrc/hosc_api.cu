@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "hosc.h"
@@ -66,7 +67,8 @@ struct Ctx {
   double prof_ms[HOSC_K_COUNT] = {0};
   long prof_launches[HOSC_K_COUNT] = {0};
   double host_bytes[HOSC_K_COUNT] = {0};   // algorithmic bytes of the fixed-work kernels
-  int kblock = 128, kz = 1;                // tiles of the interleaved Krylov kernels
+  int kblock = 128, kz = 1, narrow = 0;    // tiles of the interleaved Krylov kernels
+  int sx = 0, sy = 0, skz = 0;             // staged stencil kernels (sx == 0: not used)
   // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
   // asynchronously into h_ring / h_ring_pos, completion marked by round_ev
   int round_cur0 = 0, round_prev0 = 0;
@@ -110,14 +112,38 @@ double kernel_bytes(const DevParams& P, int kid) {
   }
 }
 
-bool tiles_valid(const Ctx* c, int kblock, int kz) {
-  if (kblock < 64 || kblock > 512 || kblock % 32 != 0) return false;
+void apply_tiles(Ctx* c) {
+  c->P.kblock = c->kblock;
+  c->P.kz = c->kz;
+  c->P.narrow = c->narrow;
+  c->P.sx = c->sx;
+  c->P.sy = c->sy;
+  c->P.skz = c->skz;
+}
+
+bool stencil_tiles_valid(const Ctx* c, int sx, int sy, int skz) {
+  if (sx == 0) return true;   // register kernels
+  if (sx < 1 || sy < 1 || sx * sy < 32 || sx * sy > 256 || (sx * sy) % 32 != 0) return false;
+  if (skz < 1 || skz > c->prm.N - 2) return false;
+  if (staged_smem_bytes(sx, sy, true) > 200 * 1024) return false;
+  DevParams P = c->P;
+  P.sx = sx;
+  P.sy = sy;
+  P.skz = skz;
+  const long n3 = (long)c->prm.N * c->prm.N * c->prm.N;
+  return krylov4_blocks(P) <= red_rows(n3) &&
+         staged_wave_cost(c->prm.N, sx, sy, skz, device_sms()) < 1e299;
+}
+
+bool tiles_valid(const Ctx* c, int kblock, int kz, int narrow) {
+  if (kblock < 64 || kblock > (narrow ? 256 : 384) || kblock % 32 != 0) return false;
+  if (narrow != 0 && narrow != 1) return false;
   if (kz < 1 || kz > c->prm.N - 2) return false;
   DevParams P = c->P;
   P.kblock = kblock;
   P.kz = kz;
   const long n3 = (long)c->prm.N * c->prm.N * c->prm.N;
-  return krylov4_blocks(P) <= 4L * red_blocks(n3);   // rows of the partials buffer
+  return krylov4_blocks(P) <= red_rows(n3);   // rows of the partials buffer
 }
 
 // FP32 Krylov vectors cannot resolve relative residuals far below their rounding.
@@ -262,8 +288,7 @@ hosc_status set_initial_state(Ctx* c) {
   c->best_res = INFINITY;
   c->since_best = 0;
   c->P = device_params(c->prm, 0, 0);
-  c->P.kblock = c->kblock;
-  c->P.kz = c->kz;
+  apply_tiles(c);
   return HOSC_OK;
 }
 
@@ -440,8 +465,7 @@ void set_phase(Ctx* c, int phase) {
   if (c->prm.precision != HOSC_MIXED || phase == c->phase) return;
   c->phase = phase;
   c->P = device_params(c->prm, 0, phase);
-  c->P.kblock = c->kblock;
-  c->P.kz = c->kz;
+  apply_tiles(c);
 }
 
 void watch_stall(Ctx* c, double res) {
@@ -724,7 +748,8 @@ cudaStream_t ctx_branch_stream(void* ctx) { return ((Ctx*)ctx)->cap[0]; }
 long ctx_signature(void* ctx) {
   const Ctx* c = (const Ctx*)ctx;
   return (long)c->cur | ((long)c->P.have_prev << 1) | ((long)c->phase << 2) |
-         ((long)c->kblock << 3) | ((long)c->kz << 13);
+         ((long)c->kblock << 3) | ((long)c->kz << 13) | ((long)c->narrow << 23) | ((long)c->sx << 24) |
+         ((long)c->sy << 32) | ((long)c->skz << 42);
 }
 
 // Start of a round of n steps from the current level (read back by ctx_collect_round).
@@ -871,9 +896,8 @@ size_t workspace_layout(int N, Fields* f, char* base) {
   }
   F.div = fld();
   F.eloc = (double*)take(3 * n3 * sizeof(double));
-  // per-block partials: up to one row of blocks per system (the Krylov launches) or one per
-  // block of a whole-grid launch
-  F.red = (double*)take((size_t)4 * red_blocks((long)n3) * kRedSlots * sizeof(double));
+  // per-block partials: one row per block of any accepted launch shape
+  F.red = (double*)take((size_t)red_rows((long)n3) * kRedSlots * sizeof(double));
   F.counter = (unsigned int*)take(sizeof(unsigned int));
   F.ks = (KrylovScalars*)take(4 * sizeof(KrylovScalars));
   F.rec = (StepRecord*)take(sizeof(StepRecord));
@@ -1248,24 +1272,52 @@ hosc_status hosc_time_kernel(void* ctx, int kernel_id, int reps, double* ms_per_
   return HOSC_OK;
 }
 
-hosc_status hosc_set_tiles(void* ctx, int kblock, int kz) {
+hosc_status hosc_set_tiles(void* ctx, int kblock, int kz, int narrow) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
   if (c->stage != 0) return HOSC_ESTATE;
-  if (!tiles_valid(c, kblock, kz)) return HOSC_EINVAL;
-  if (kblock != c->kblock || kz != c->kz) {
+  if (!tiles_valid(c, kblock, kz, narrow)) return HOSC_EINVAL;
+  if (kblock != c->kblock || kz != c->kz || narrow != c->narrow) {
     c->kblock = c->P.kblock = kblock;
     c->kz = c->P.kz = kz;
+    c->narrow = c->P.narrow = narrow;
     drop_graphs(c);   // the captured steps hold the old launch shapes
   }
   return HOSC_OK;
 }
 
-hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz) {
+hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  if (!stencil_tiles_valid(c, sx, sy, skz)) return HOSC_EINVAL;
+  if (sx == 0) sy = skz = 0;
+  if (sx != c->sx || sy != c->sy || skz != c->skz) {
+    c->sx = sx;
+    c->sy = sy;
+    c->skz = skz;
+    apply_tiles(c);
+    drop_graphs(c);
+  }
+  return HOSC_OK;
+}
+
+hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  if (sx) *sx = c->sx;
+  if (sy) *sy = c->sy;
+  if (skz) *skz = c->skz;
+  return HOSC_OK;
+}
+
+hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz, int* narrow) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
   if (kblock) *kblock = c->kblock;
   if (kz) *kz = c->kz;
+  if (narrow) *narrow = c->narrow;
   return HOSC_OK;
 }
 
@@ -1275,46 +1327,106 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   if (c->stage != 0) return HOSC_ESTATE;
   if (!c->P.krylov_fp32) return HOSC_EINVAL;
   CU(cudaSetDevice(c->device));
-  const int save_b = c->kblock, save_z = c->kz;
-  int best_b = save_b, best_z = save_z;
+  c->P.sx = 0;   // the register kernels first
+  int best_b = c->kblock, best_z = c->kz, best_n = c->narrow;
   double best = INFINITY;
-  static const int blocks[] = {64, 96, 128, 160, 192, 256, 320, 384, 512};
+  static const int blocks[] = {64, 96, 128, 160, 192, 256, 320, 384};
   // time every shape whose modelled cost is within 1.5x of the best model cost
   const int sms = device_sms();
   double best_model = 1e300;
-  for (int b : blocks)
-    for (int z = 1; z <= 33; ++z)
-      if (tiles_valid(c, b, z)) {
-        const double m = krylov4_wave_cost(c->prm.N, b, z, sms);
-        if (m < best_model) best_model = m;
-      }
-  for (int b : blocks) {
-    for (int z = 1; z <= 33; ++z) {
-      if (!tiles_valid(c, b, z)) continue;
-      if (krylov4_wave_cost(c->prm.N, b, z, sms) > 1.5 * best_model) continue;
-      c->P.kblock = b;
-      c->P.kz = z;
-      double tot = 0.0;
-      for (int kid = HOSC_K_BICG_PV; kid <= HOSC_K_BICG_XR; ++kid) {
-        double ms = 0.0;
-        hosc_status st = time_class(c, kid, reps, &ms);
-        if (st) {
-          c->P.kblock = save_b;
-          c->P.kz = save_z;
-          return st;
+  for (int nr = 0; nr <= 1; ++nr)
+    for (int b : blocks)
+      for (int z = 1; z <= 33; ++z)
+        if (tiles_valid(c, b, z, nr))
+          best_model = fmin(best_model, krylov4_wave_cost(c->prm.N, b, z, nr, sms));
+  hosc_status st = HOSC_OK;
+  for (int nr = 0; nr <= 1 && !st; ++nr) {
+    for (int b : blocks) {
+      for (int z = 1; z <= 33 && !st; ++z) {
+        if (!tiles_valid(c, b, z, nr)) continue;
+        if (krylov4_wave_cost(c->prm.N, b, z, nr, sms) > 1.5 * best_model) continue;
+        c->P.kblock = b;
+        c->P.kz = z;
+        c->P.narrow = nr;
+        double tot = 0.0;
+        for (int kid = HOSC_K_BICG_PV; kid <= HOSC_K_BICG_XR && !st; ++kid) {
+          double ms = 0.0;
+          st = time_class(c, kid, reps, &ms);
+          tot += ms;
         }
-        tot += ms;
-      }
-      if (tot < best) {
-        best = tot;
-        best_b = b;
-        best_z = z;
+        if (!st && tot < best) {
+          best = tot;
+          best_b = b;
+          best_z = z;
+          best_n = nr;
+        }
       }
     }
   }
-  c->P.kblock = save_b;
-  c->P.kz = save_z;
-  hosc_status st = hosc_set_tiles(c, best_b, best_z);
+  apply_tiles(c);
+  if (st) return st;
+  st = hosc_set_tiles(c, best_b, best_z, best_n);
+  if (st) return st;
+  // Staged stencil kernels for p/v and s/t: against the register kernels at the shape found.
+  double reg_pvst = 0.0;
+  {
+    const int ssx = c->sx, ssy = c->sy, sskz = c->skz;
+    c->P.sx = 0;
+    for (int kid = HOSC_K_BICG_PV; kid <= HOSC_K_BICG_ST && !st; ++kid) {
+      double ms = 0.0;
+      st = time_class(c, kid, reps, &ms);
+      reg_pvst += ms;
+    }
+    c->P.sx = ssx;
+    c->P.sy = ssy;
+    c->P.skz = sskz;
+    if (st) return st;
+  }
+  std::vector<std::pair<int, int>> shapes;
+  for (int sxc = 8; sxc <= 64; sxc += 8)
+    for (int syc : {4, 8})
+      if (sxc * syc >= 32 && sxc * syc <= 256) shapes.emplace_back(sxc, syc);
+  double best_smodel = 1e300;
+  for (auto& sh : shapes)
+    for (int z = 1; z <= 33; ++z)
+      if (stencil_tiles_valid(c, sh.first, sh.second, z))
+        best_smodel = fmin(best_smodel, staged_wave_cost(c->prm.N, sh.first, sh.second, z, sms));
+  double best_staged = INFINITY;
+  int bsx = 0, bsy = 0, bskz = 0;
+  const int ssx = c->sx, ssy = c->sy, sskz = c->skz;
+  for (auto& sh : shapes) {
+    for (int z = 1; z <= 33; ++z) {
+      if (!stencil_tiles_valid(c, sh.first, sh.second, z)) continue;
+      if (staged_wave_cost(c->prm.N, sh.first, sh.second, z, sms) > 1.5 * best_smodel) continue;
+      c->P.sx = sh.first;
+      c->P.sy = sh.second;
+      c->P.skz = z;
+      double tot = 0.0;
+      for (int kid = HOSC_K_BICG_PV; kid <= HOSC_K_BICG_ST && !st; ++kid) {
+        double ms = 0.0;
+        st = time_class(c, kid, reps, &ms);
+        tot += ms;
+      }
+      if (st) break;
+      if (tot < best_staged) {
+        best_staged = tot;
+        bsx = sh.first;
+        bsy = sh.second;
+        bskz = z;
+      }
+    }
+    if (st) break;
+  }
+  c->P.sx = ssx;
+  c->P.sy = ssy;
+  c->P.skz = sskz;
+  if (st) return st;
+  if (best_staged < reg_pvst) {
+    st = hosc_set_stencil_tiles(c, bsx, bsy, bskz);
+    best += best_staged - reg_pvst;
+  } else {
+    st = hosc_set_stencil_tiles(c, 0, 0, 0);
+  }
   if (st) return st;
   if (kblock_out) *kblock_out = best_b;
   if (kz_out) *kz_out = best_z;

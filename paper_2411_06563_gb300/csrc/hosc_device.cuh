@@ -142,22 +142,43 @@ __device__ __forceinline__ bool publish_is_last(const double (&v)[M], double* re
 }
 
 // In the last block: reduce the partials of all blocks in a fixed order (valid in thread 0) and
-// re-arm the ticket counter for the next kernel.
+// re-arm the ticket counter for the next kernel. Thread t reads slot t % M of rows t / M,
+// t / M + blockDim/M, ... (consecutive threads read consecutive doubles; four rows' loads in
+// flight at a time), then the threads of each slot combine through shuffles and shared memory.
+// blockDim.x must be a multiple of 32; smem: >= 32*M doubles.
 template <int M, bool IsMax>
 __device__ __forceinline__ void reduce_partials(double (&tot)[M], const double* red, int nblocks,
                                                 unsigned int* counter, double* smem) {
+  static_assert(M == 1 || M == 2 || M == 4 || M == 8, "slots per row must divide the warp");
   __threadfence();
-#pragma unroll
-  for (int m = 0; m < M; ++m) tot[m] = 0.0;
-  for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-      const double x = __ldcg(red + (long)b * kRedSlots + m);
-      tot[m] = IsMax ? fmax(tot[m], x) : tot[m] + x;
-    }
+  const int t = threadIdx.x, bd = blockDim.x;
+  const int m = t % M, rstep = bd / M;
+  auto op = [](double a, double b) { return IsMax ? fmax(a, b) : a + b; };
+  double acc = 0.0;
+  int r = t / M;
+  for (; r + 3 * rstep < nblocks; r += 4 * rstep) {
+    const double a0 = __ldcg(red + (long)r * kRedSlots + m);
+    const double a1 = __ldcg(red + (long)(r + rstep) * kRedSlots + m);
+    const double a2 = __ldcg(red + (long)(r + 2 * rstep) * kRedSlots + m);
+    const double a3 = __ldcg(red + (long)(r + 3 * rstep) * kRedSlots + m);
+    acc = op(op(op(op(acc, a0), a1), a2), a3);
   }
-  block_reduce<M, IsMax>(tot, smem);
-  if (threadIdx.x == 0) *counter = 0u;
+  for (; r < nblocks; r += rstep) acc = op(acc, __ldcg(red + (long)r * kRedSlots + m));
+#pragma unroll
+  for (int off = 16; off >= M; off >>= 1) acc = op(acc, __shfl_down_sync(0xffffffffu, acc, off));
+  const int lane = t & 31, wid = t >> 5, nw = bd >> 5;
+  if (lane < M) smem[wid * M + lane] = acc;
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int q = 0; q < M; ++q) {
+      double v = 0.0;
+      for (int w = 0; w < nw; ++w) v = op(v, smem[w * M + q]);
+      tot[q] = v;
+    }
+    *counter = 0u;
+  }
+  __syncthreads();
 }
 
 }  // namespace hosc

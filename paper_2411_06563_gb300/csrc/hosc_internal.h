@@ -20,8 +20,12 @@ struct DevParams {
   int sweep_fp32;    // S1-S3 arithmetic (and eta, L, E* storage) in float
   int krylov_fp32;   // right-hand sides, operator weights and Krylov vectors in float,
                      // interleaved (one float4 per node for the four systems)
-  int kblock;        // interleaved Krylov kernels: threads per block (multiple of 32, 64..512)
+  int kblock;        // interleaved Krylov kernels: threads per block (multiple of 32, 64..384)
   int kz;            // interleaved Krylov kernels: planes marched by one thread (1..N-2)
+  int narrow;        // interleaved Krylov kernels compiled for 64 registers (kblock <= 256);
+                     // otherwise for 80 (kblock <= 384)
+  int sx, sy, skz;   // staged stencil kernels (p/v and s/t): tile of sx * sy interior columns,
+                     // skz planes per block; sx == 0 selects the register kernels instead
   double h, h2;      // grid spacing (h = k = l) and its square
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
   double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (and div below tol_div)
@@ -103,6 +107,9 @@ struct Fields {
 
 size_t workspace_layout(int N, Fields* f, char* base);   // returns bytes; fills f when base != 0
 int red_blocks(long count);
+// Rows of the per-block partials buffer of an N^3 context: enough for any launch shape the
+// validation accepts (at least 32 threads per block, one plane per thread).
+inline long red_rows(long n3) { return n3 / 16 + 1024; }
 // Blocks of one interleaved Krylov launch (the partials buffer holds 4 red_blocks(N^3) rows).
 long krylov4_blocks(const DevParams& P);
 // Threads per block and planes per thread of the interleaved Krylov kernels when none are set:
@@ -110,7 +117,12 @@ long krylov4_blocks(const DevParams& P);
 void default_tiles(int N, int* kblock, int* kz);
 // Waves of resident blocks a launch shape needs on this GPU times the planes each block streams
 // (kz + 2): a model of the launch's duration when it is latency-bound.
-double krylov4_wave_cost(int N, int kblock, int kz, int sms);
+double krylov4_wave_cost(int N, int kblock, int kz, int narrow, int sms);
+// The same model for the staged stencil kernels with tile sx * sy and skz planes per block
+// (occupancy from their shared memory and registers); infinite for a shape that cannot launch.
+double staged_wave_cost(int N, int sx, int sy, int skz, int sms);
+// Dynamic shared memory of a staged launch (bytes), for tile sx * sy.
+size_t staged_smem_bytes(int sx, int sy, bool pv);
 int device_sms();
 
 // S1: eta and L at every node.

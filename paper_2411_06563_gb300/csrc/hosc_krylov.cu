@@ -501,7 +501,9 @@ __global__ void __launch_bounds__(kThreads) k4_init(DevParams P, Fields F) {
 
 // p_new = r + beta (p_old - omega v_old) at the seven stencil nodes, v_new = A p_new, partial
 // r_0 . v_new; last block: alpha = rho / (r_0 . v_new).
-__global__ void __launch_bounds__(512) k4_pv(DevParams P, Fields F, int pp) {
+template <int MinB>
+__global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
+    k4_pv(DevParams P, Fields F, int pp) {
   __shared__ double smem[32 * 4];
   __shared__ Scal4 sc;
   load_scalars(F.ks, sc);
@@ -557,7 +559,9 @@ __global__ void __launch_bounds__(512) k4_pv(DevParams P, Fields F, int pp) {
 
 // s = r - alpha v at the seven stencil nodes, t = A s, partials (t . s, t . t); last block:
 // omega = (t . s) / (t . t) (0 when t = 0).
-__global__ void __launch_bounds__(512) k4_st(DevParams P, Fields F, int pp) {
+template <int MinB>
+__global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
+    k4_st(DevParams P, Fields F, int pp) {
   __shared__ double smem[32 * 8];
   __shared__ Scal4 sc;
   load_scalars(F.ks, sc);
@@ -604,7 +608,9 @@ __global__ void __launch_bounds__(512) k4_st(DevParams P, Fields F, int pp) {
 
 // s = r - alpha v; x += alpha p + omega s; r = s - omega t; partials (r_0 . r, r . r); last block:
 // convergence and breakdown tests, beta and rho of the next iteration.
-__global__ void __launch_bounds__(512) k4_xr(DevParams P, Fields F, int pp) {
+template <int MinB>
+__global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
+    k4_xr(DevParams P, Fields F, int pp) {
   __shared__ double smem[32 * 8];
   __shared__ Scal4 sc;
   load_scalars(F.ks, sc);
@@ -656,6 +662,235 @@ __global__ void __launch_bounds__(512) k4_xr(DevParams P, Fields F, int pp) {
   }
 }
 
+// ------------------------------------------------------- staged stencil kernels (cp.async)
+//
+// The p/v and s/t kernels again, with their reads staged through shared memory. A block owns a
+// tile of sx * sy interior columns (one thread each) and a segment of skz planes. The planes it
+// needs (the haloed tile of each stencil vector, and the weights and r_0 at the tile's nodes)
+// stream through a ring of kStages shared-memory stages with cp.async: 16-byte copies from global
+// to shared memory that hold no registers while in flight. While plane k is computed (from the
+// stages of planes k and k+1; plane k-1 is held in registers), planes k+2 and k+3 are in flight.
+// The stencil reads shared memory only.
+
+constexpr int kStages = 4;
+
+__device__ __forceinline__ void cp_async16(float4* smem_dst, const float4* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int n = valid ? 16 : 0;   // 0: write zeros, read nothing
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_two() {   // all but the two newest groups have landed
+  asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+}
+
+// Shared-memory layout of one stage, in float4: NV haloed vectors ((sx+2)(sy+2) each), then the
+// weights of the tile's nodes part-major (4 x sx*sy), then (p/v only) r_0 of the tile.
+struct StageLayout {
+  int hx, halo, tile, nv, per_stage;
+  __host__ __device__ StageLayout(int sx, int sy, int nvec, bool with_r0) {
+    hx = sx + 2;
+    halo = (sx + 2) * (sy + 2);
+    tile = sx * sy;
+    nv = nvec;
+    per_stage = nv * halo + 4 * tile + (with_r0 ? tile : 0);
+  }
+};
+
+// Copy plane q (if it exists for this block) into stage buffer st: the haloed tile of each
+// stencil vector, then the weights (and r_0) at the tile's interior nodes. Positions outside the
+// grid are zero-filled without a read; the data of this plane form one commit group.
+template <int NV, bool R0>
+__device__ __forceinline__ void stage_plane(float4* st, const StageLayout& L, int N, int i0,
+                                            int j0, int q, bool live,
+                                            const float4* const (&vecs)[NV],
+                                            const float4* W, const float4* r0, int sx) {
+  if (live) {
+    const int nthr = blockDim.x;
+    for (int idx = threadIdx.x; idx < L.halo; idx += nthr) {
+      const int hy = idx / L.hx, hx = idx - hy * L.hx;
+      const int gi = i0 - 1 + hx, gj = j0 - 1 + hy;
+      const bool ok = gi <= N - 1 && gj <= N - 1;
+      const int off = ok ? gi + N * (gj + N * q) : 0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) cp_async16(st + v * L.halo + idx, vecs[v] + off, ok);
+    }
+    const bool inner_plane = q >= 1 && q <= N - 2;
+    for (int e = threadIdx.x; e < 4 * L.tile; e += nthr) {   // weights: node-major in global
+      const int node = e >> 2, part = e & 3;
+      const int ty = node / sx, tx = node - ty * sx;
+      const int gi = i0 + tx, gj = j0 + ty;
+      const bool ok = inner_plane && gi <= N - 2 && gj <= N - 2;
+      const float4* src = W + (ok ? 4 * (size_t)(gi + N * (gj + N * q)) + part : 0);
+      cp_async16(st + NV * L.halo + part * L.tile + node, src, ok);
+    }
+    if (R0) {
+      for (int e = threadIdx.x; e < L.tile; e += nthr) {
+        const int ty = e / sx, tx = e - ty * sx;
+        const int gi = i0 + tx, gj = j0 + ty;
+        const bool ok = inner_plane && gi <= N - 2 && gj <= N - 2;
+        const float4* src = r0 + (ok ? gi + N * (gj + N * q) : 0);
+        cp_async16(st + NV * L.halo + 4 * L.tile + e, src, ok);
+      }
+    }
+  }
+  cp_commit();   // one group per plane, empty past the segment
+}
+
+__device__ __forceinline__ float4 apply7s(const float4* sw, int tile, int t, float4 o, float4 xp,
+                                          float4 xm, float4 yp, float4 ym, float4 zp, float4 zm) {
+  const float4 w0 = sw[t], w1 = sw[tile + t], w2 = sw[2 * tile + t], w3 = sw[3 * tile + t];
+  float4 y;
+  y.x = w0.x * o.x + w0.y * xp.x + w0.z * xm.x + w0.w * yp.x + w1.x * ym.x + w1.y * zp.x +
+        w1.z * zm.x;
+  y.y = w0.x * o.y + w0.y * xp.y + w0.z * xm.y + w0.w * yp.y + w1.x * ym.y + w1.y * zp.y +
+        w1.z * zm.y;
+  y.z = w0.x * o.z + w0.y * xp.z + w0.z * xm.z + w0.w * yp.z + w1.x * ym.z + w1.y * zp.z +
+        w1.z * zm.z;
+  y.w = w1.w * o.w + w2.x * xp.w + w2.y * xm.w + w2.z * yp.w + w2.w * ym.w + w3.x * zp.w +
+        w3.y * zm.w;
+  return y;
+}
+
+// Staged p/v kernel (same arithmetic as k4_pv).
+__global__ void __launch_bounds__(256) k5_pv(DevParams P, Fields F, int pp) {
+  extern __shared__ float4 ring[];
+  __shared__ double smem[32 * 4];
+  __shared__ Scal4 sc;
+  load_scalars(F.ks, sc);
+  if (sc.all_done) return;
+  const int N = P.N, N2 = N * N, sx = P.sx;
+  const StageLayout L(sx, P.sy, 3, true);
+  const int i0 = 1 + blockIdx.x * sx, j0 = 1 + blockIdx.y * P.sy;
+  const int k0 = 1 + blockIdx.z * P.skz, k1 = min(k0 + P.skz, N - 1);
+  const int t = threadIdx.x, ty = t / sx, tx = t - ty * sx;
+  const bool mine = ty < P.sy && i0 + tx <= N - 2 && j0 + ty <= N - 2;
+  const int h = (ty + 1) * L.hx + (tx + 1);
+  const float4 b = sc.b, mom = neg4(sc.om);
+  const float4* const vecs[3] = {F.kr, F.kp[pp], F.kv[pp]};
+  auto stage_of = [&](int q) { return ring + ((q - (k0 - 1)) % kStages) * L.per_stage; };
+  auto pnew = [&](const float4* st, int idx) {
+    return fma4(b, fma4(mom, st[2 * L.halo + idx], st[L.halo + idx]), st[idx]);
+  };
+  // planes k0-1 .. k0+2 in flight; wait for the first two
+  for (int q = k0 - 1; q <= k0 + 2; ++q)
+    stage_plane<3, true>(stage_of(q), L, N, i0, j0, q, q <= k1, vecs, F.kw, F.kr0, sx);
+  cp_wait_two();
+  __syncthreads();
+  float4 pm = pnew(stage_of(k0 - 1), h), pc = pnew(stage_of(k0), h);
+  __syncthreads();   // the stage of plane k0-1 is free for plane k0+3
+  FF acc[4] = {};
+  for (int k = k0; k < k1; ++k) {
+    stage_plane<3, true>(stage_of(k + 3), L, N, i0, j0, k + 3, k + 3 <= k1, vecs, F.kw, F.kr0,
+                         sx);
+    cp_wait_two();   // plane k+1 has landed
+    __syncthreads();
+    const float4* sq = stage_of(k);
+    const float4 pz = pnew(stage_of(k + 1), h);
+    if (mine) {
+      const float4 vn = apply7s(sq + 3 * L.halo, L.tile, t, pc, pnew(sq, h + 1), pnew(sq, h - 1),
+                                pnew(sq, h + L.hx), pnew(sq, h - L.hx), pz, pm);
+      const int c = (i0 + tx) + N * (j0 + ty) + N2 * k;
+      F.kp[1 - pp][c] = pc;
+      F.kv[1 - pp][c] = vn;
+      ff_dot4(acc, sq[3 * L.halo + 4 * L.tile + t], vn);
+    }
+    pm = pc;
+    pc = pz;
+    __syncthreads();   // the stage of plane k is free for plane k+4
+  }
+  double part[4];
+  block_ff<4>(acc, part, smem);
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+  if (publish_is_last<4>(part, F.red, F.counter, bid, nb)) {
+    double tot[4];
+    reduce_partials<4, false>(tot, F.red, nb, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        if (tot[s] == 0.0 || !isfinite(tot[s])) {
+          k.done = 1;
+          k.status = HOSC_ENOCONV;
+          continue;
+        }
+        k.alpha = k.rho / tot[s];
+      }
+      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 6.0 + 4.0);
+    }
+  }
+}
+
+// Staged s/t kernel (same arithmetic as k4_st).
+__global__ void __launch_bounds__(256) k5_st(DevParams P, Fields F, int pp) {
+  extern __shared__ float4 ring[];
+  __shared__ double smem[32 * 8];
+  __shared__ Scal4 sc;
+  load_scalars(F.ks, sc);
+  if (sc.all_done) return;
+  const int N = P.N, N2 = N * N, sx = P.sx;
+  const StageLayout L(sx, P.sy, 2, false);
+  const int i0 = 1 + blockIdx.x * sx, j0 = 1 + blockIdx.y * P.sy;
+  const int k0 = 1 + blockIdx.z * P.skz, k1 = min(k0 + P.skz, N - 1);
+  const int t = threadIdx.x, ty = t / sx, tx = t - ty * sx;
+  const bool mine = ty < P.sy && i0 + tx <= N - 2 && j0 + ty <= N - 2;
+  const int h = (ty + 1) * L.hx + (tx + 1);
+  const float4 ma = neg4(sc.a);
+  const float4* const vecs[2] = {F.kr, F.kv[1 - pp]};
+  auto stage_of = [&](int q) { return ring + ((q - (k0 - 1)) % kStages) * L.per_stage; };
+  auto sval = [&](const float4* st, int idx) { return fma4(ma, st[L.halo + idx], st[idx]); };
+  for (int q = k0 - 1; q <= k0 + 2; ++q)
+    stage_plane<2, false>(stage_of(q), L, N, i0, j0, q, q <= k1, vecs, F.kw, nullptr, sx);
+  cp_wait_two();
+  __syncthreads();
+  float4 sm = sval(stage_of(k0 - 1), h), sc0 = sval(stage_of(k0), h);
+  __syncthreads();
+  FF acc[8] = {};
+  for (int k = k0; k < k1; ++k) {
+    stage_plane<2, false>(stage_of(k + 3), L, N, i0, j0, k + 3, k + 3 <= k1, vecs, F.kw,
+                          nullptr, sx);
+    cp_wait_two();
+    __syncthreads();
+    const float4* sq = stage_of(k);
+    const float4 sz = sval(stage_of(k + 1), h);
+    if (mine) {
+      const float4 tv = apply7s(sq + 2 * L.halo, L.tile, t, sc0, sval(sq, h + 1), sval(sq, h - 1),
+                                sval(sq, h + L.hx), sval(sq, h - L.hx), sz, sm);
+      const int c = (i0 + tx) + N * (j0 + ty) + N2 * k;
+      F.kt[c] = tv;
+      ff_dot4(acc, tv, sc0);
+      ff_dot4(acc + 4, tv, tv);
+    }
+    sm = sc0;
+    sc0 = sz;
+    __syncthreads();
+  }
+  double part[8];
+  block_ff<8>(acc, part, smem);
+  const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+  const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+  if (publish_is_last<8>(part, F.red, F.counter, bid, nb)) {
+    double tot[8];
+    reduce_partials<8, false>(tot, F.red, nb, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        k.omega = tot[4 + s] > 0.0 ? tot[s] / tot[4 + s] : 0.0;
+      }
+      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 3.0 + 4.0);
+    }
+  }
+}
+
+dim3 grid5(const DevParams& P) {
+  const int ni = P.N - 2;
+  return dim3((unsigned)((ni + P.sx - 1) / P.sx), (unsigned)((ni + P.sy - 1) / P.sy),
+              (unsigned)((ni + P.skz - 1) / P.skz));
+}
+
 dim3 grid4(const DevParams& P) {
   const int ni = P.N - 2;
   return dim3((unsigned)((ni * ni + P.kblock - 1) / P.kblock), (unsigned)((ni + P.kz - 1) / P.kz));
@@ -697,8 +932,13 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
 }
 
 void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  if (P.krylov_fp32 && P.sx > 0) {
+    k5_pv<<<grid5(P), P.sx * P.sy, staged_smem_bytes(P.sx, P.sy, true), s>>>(P, F, pp);
+    return;
+  }
   if (P.krylov_fp32) {
-    k4_pv<<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    if (P.narrow) k4_pv<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    else k4_pv<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
     return;
   }
   const int b = interior_blocks(P);
@@ -706,8 +946,13 @@ void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
 }
 
 void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  if (P.krylov_fp32 && P.sx > 0) {
+    k5_st<<<grid5(P), P.sx * P.sy, staged_smem_bytes(P.sx, P.sy, false), s>>>(P, F, pp);
+    return;
+  }
   if (P.krylov_fp32) {
-    k4_st<<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    if (P.narrow) k4_st<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    else k4_st<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
     return;
   }
   const int b = interior_blocks(P);
@@ -716,7 +961,8 @@ void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
 
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
   if (P.krylov_fp32) {
-    k4_xr<<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    if (P.narrow) k4_xr<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    else k4_xr<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
     return;
   }
   const int b = interior_blocks(P);
@@ -725,12 +971,62 @@ void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
 
 long krylov4_blocks(const DevParams& P) {
   const dim3 g = grid4(P);
-  return (long)g.x * g.y;
+  long nb = (long)g.x * g.y;
+  if (P.sx > 0) {
+    const dim3 g5 = grid5(P);
+    const long n5 = (long)g5.x * g5.y * g5.z;
+    nb = n5 > nb ? n5 : nb;
+  }
+  return nb;
 }
 
-int krylov4_occupancy(int kblock) {
+size_t staged_smem_bytes(int sx, int sy, bool pv) {
+  const StageLayout L(sx, sy, pv ? 3 : 2, pv);
+  return (size_t)kStages * L.per_stage * sizeof(float4);
+}
+
+// Opt the staged kernels in to large dynamic shared memory (once per device and process).
+bool staged_smem_ready() {
+  static int done[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  if (!done[dev]) {
+    const int cap = 200 * 1024;
+    if (cudaFuncSetAttribute(k5_pv, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k5_st, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    done[dev] = 1;
+  }
+  return true;
+}
+
+double staged_wave_cost(int N, int sx, int sy, int skz, int sms) {
+  if (!staged_smem_ready()) return 1e300;
+  const size_t smem = staged_smem_bytes(sx, sy, true);
+  if (smem > 200 * 1024) return 1e300;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_pv, kblock, 0) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k5_pv, sx * sy, smem) != cudaSuccess ||
+      occ < 1) {
+    cudaGetLastError();
+    return 1e300;
+  }
+  const long ni = N - 2;
+  const long items = ((ni + sx - 1) / sx) * ((ni + sy - 1) / sy) * ((ni + skz - 1) / skz);
+  const long slots = (long)occ * sms;
+  const long waves = (items + slots - 1) / slots;
+  return (double)waves * (skz + 2);
+}
+
+int krylov4_occupancy(int kblock, int narrow) {
+  int occ = 0;
+  const cudaError_t e =
+      narrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_pv<4>, kblock, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_pv<2>, kblock, 0);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
   }
@@ -747,10 +1043,10 @@ int device_sms() {
   return sms > 0 ? sms : 152;
 }
 
-double krylov4_wave_cost(int N, int kblock, int kz, int sms) {
+double krylov4_wave_cost(int N, int kblock, int kz, int narrow, int sms) {
   const long ni = N - 2;
   const long items = ((ni * ni + kblock - 1) / kblock) * ((ni + kz - 1) / kz);
-  const long slots = (long)krylov4_occupancy(kblock) * sms;
+  const long slots = (long)krylov4_occupancy(kblock, narrow) * sms;
   const long waves = (items + slots - 1) / slots;
   // every resident block streams kz planes plus the two it reads around its segment
   return (double)waves * (kz + 2);
@@ -762,7 +1058,7 @@ void default_tiles(int N, int* kblock, int* kz) {
   double best = 1e300;
   int bb = 128, bz = 1;
   for (int z = 1; z <= (ni < 16 ? ni : 16); ++z) {
-    const double c = krylov4_wave_cost(N, 128, z, sms);
+    const double c = krylov4_wave_cost(N, 128, z, 0, sms);
     if (c < best) {
       best = c;
       bz = z;

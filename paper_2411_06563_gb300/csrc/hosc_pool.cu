@@ -18,10 +18,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <array>
 #include <chrono>
 #include <map>
 #include <new>
-#include <utility>
 #include <vector>
 
 #include "hosc.h"
@@ -66,7 +66,8 @@ struct Pool {
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t exec = nullptr;
   bool dirty = true;                          // membership changed since the capture
-  std::map<int, std::pair<int, int>> tiles;   // tuned launch shape per N
+  // tuned launch shapes per N: kblock, kz, narrow, sx, sy, skz
+  std::map<int, std::array<int, 6>> tiles;
   long rounds = 0, captures = 0;
   double capture_ms = 0.0;
 };
@@ -120,6 +121,12 @@ bool needs_capture(const Pool* P) {
   return false;
 }
 
+hosc_status apply_shape(void* ctx, const std::array<int, 6>& t) {
+  hosc_status st = hosc_set_tiles(ctx, t[0], t[1], t[2]);
+  if (!st) st = hosc_set_stencil_tiles(ctx, t[3], t[4], t[5]);
+  return st;
+}
+
 // After a member's round: complete it (steady, failed, out of steps) or tune its launch shape.
 hosc_status settle(Pool* P, int slot, hosc_status st, bool steady, const hosc_info& ri,
                    int* done, int cap, int* ndone) {
@@ -161,12 +168,14 @@ hosc_status settle(Pool* P, int slot, hosc_status st, bool steady, const hosc_in
     if (hosc_get_params(q.ctx, &prm) == HOSC_OK && prm.precision == HOSC_MIXED) {
       auto it = P->tiles.find(q.N);
       if (it == P->tiles.end()) {
-        int kb = 0, kz = 0;
-        hosc_status ts = hosc_autotune(q.ctx, 3, &kb, &kz, nullptr);
+        hosc_status ts = hosc_autotune(q.ctx, 3, nullptr, nullptr, nullptr);
+        std::array<int, 6> t = {};
+        if (!ts) ts = hosc_get_tiles(q.ctx, &t[0], &t[1], &t[2]);
+        if (!ts) ts = hosc_get_stencil_tiles(q.ctx, &t[3], &t[4], &t[5]);
         if (ts) return ts;
-        P->tiles[q.N] = std::make_pair(kb, kz);
+        P->tiles[q.N] = t;
       } else {
-        hosc_status ts = hosc_set_tiles(q.ctx, it->second.first, it->second.second);
+        hosc_status ts = apply_shape(q.ctx, it->second);
         if (ts) return ts;
       }
     }
@@ -260,7 +269,7 @@ hosc_status hosc_pool_admit(void* pool, const hosc_params* params, long max_step
   P->dirty = true;
   if (p.precision == HOSC_MIXED) {
     auto it = P->tiles.find(p.N);
-    if (it != P->tiles.end()) hosc_set_tiles(ctx, it->second.first, it->second.second);
+    if (it != P->tiles.end()) apply_shape(ctx, it->second);
   }
   *slot = s;
   return HOSC_OK;

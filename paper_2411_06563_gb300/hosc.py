@@ -126,9 +126,14 @@ def lib():
                                              _DP]),
         "hosc_kernel_launches": (ctypes.c_long, [_P]),
         "hosc_time_kernel": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _DP, _DP]),
-        "hosc_set_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+        "hosc_set_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "hosc_get_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
+        "hosc_set_stencil_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "hosc_get_stencil_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                                  ctypes.POINTER(ctypes.c_int),
+                                                  ctypes.POINTER(ctypes.c_int)]),
         "hosc_autotune": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), _DP]),
         "hosc_set_phase": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -280,15 +285,27 @@ def hosc_time_kernel(h, kernel_id, reps):
     return st, ms.value, b.value
 
 
-def hosc_set_tiles(h, kblock, kz):
-    return lib().hosc_set_tiles(h, int(kblock), int(kz))
+def hosc_set_tiles(h, kblock, kz, narrow=0):
+    return lib().hosc_set_tiles(h, int(kblock), int(kz), int(narrow))
 
 
 def hosc_get_tiles(h):
+    """(status, kblock, kz, narrow)"""
     b = ctypes.c_int()
     z = ctypes.c_int()
-    st = lib().hosc_get_tiles(h, ctypes.byref(b), ctypes.byref(z))
-    return st, b.value, z.value
+    n = ctypes.c_int()
+    st = lib().hosc_get_tiles(h, ctypes.byref(b), ctypes.byref(z), ctypes.byref(n))
+    return st, b.value, z.value, n.value
+
+
+def hosc_set_stencil_tiles(h, sx, sy, skz):
+    return lib().hosc_set_stencil_tiles(h, int(sx), int(sy), int(skz))
+
+
+def hosc_get_stencil_tiles(h):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    st = lib().hosc_get_stencil_tiles(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return st, a.value, b.value, c.value
 
 
 def hosc_autotune(h, reps=5):

@@ -85,6 +85,15 @@ def batch_mix(count=64, seed=20241106, sizes=(21, 31, 41, 61)):
     return out
 
 
+def steady_mix(count=8, seed=20241108, sizes=(17, 21)):
+    """Small cavities that reach steady state in a few thousand steps at dt = 0.02 (for the
+    equal-accuracy comparison): list of dicts (N, Ra, n, Pr), Ra log-uniform in [1e2, 1e3],
+    n uniform in [0.9, 1.1]."""
+    rng = np.random.default_rng(seed)
+    return [dict(N=int(rng.choice(sizes)), Ra=float(10.0 ** rng.uniform(2.0, 3.0)),
+                 n=float(rng.uniform(0.9, 1.1)), Pr=1.0) for _ in range(count)]
+
+
 def request_stream(count=2000, rate=1.0, seed=20241107, sizes=tuple(range(21, 102, 10)),
                    indices=(0.75, 1.0, 1.25)):
     """Poisson request stream: list of dicts (t_arrival, N, Ra, n, Pr) sorted by arrival."""

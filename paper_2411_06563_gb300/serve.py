@@ -19,20 +19,23 @@ import numpy as np
 from . import hosc as H
 
 
-def pseudo_time_step(N, Ra, n, Pr=1.0):
+def pseudo_time_step(N, Ra, n, Pr=1.0, I2_eps=1e-10):
     """Pseudo-time step for a cavity (N, Ra, n, Pr), from the stability bound of the scheme as
     printed in Eq. (5): the explicit compact term bounds dt * G*^2 / L <= 4 with G* = u L,
     L = 1 / (Pr eta) (frozen-coefficient von Neumann analysis of the highest mode). The velocity
     scale is taken as 1.5 c(n) sqrt(Ra) with c = 0.12 * 2^(4 (1 - n)) (about 1.5x the peak
-    speeds of the steady cavities), the shear rate of the boundary layers as u Ra^(1/4), so
-    eta ~ (u^2 Ra^(1/2))^((n-1)/2) where that makes the fluid thinner. dt keeps dt u^2 L <= 1
-    (a factor 4 inside the bound) and is at most the paper's 0.02."""
+    speeds of the steady cavities). For n < 1 the thinnest fluid is in the boundary layers, shear
+    rate u Ra^(1/4), so eta ~ (u^2 Ra^(1/2))^((n-1)/2); for n > 1 it is where the shear vanishes,
+    eta = I2_eps^((n-1)/2) (the regularised viscosity at rest). dt keeps dt u^2 L <= 1 (a factor
+    4 inside the bound) and is at most the paper's 0.02."""
     c = 0.12 * 2.0 ** (4.0 * (1.0 - n))
     u = max(1.0, 1.5 * c * math.sqrt(max(Ra, 0.0)))
     eta = 1.0
     if n < 1.0:
         i2 = u * u * math.sqrt(max(Ra, 1.0))
         eta = min(1.0, i2 ** ((n - 1.0) / 2.0))
+    elif n > 1.0:
+        eta = I2_eps ** ((n - 1.0) / 2.0)
     L = 1.0 / (Pr * eta)
     return min(0.02, 1.0 / (u * u * L))
 

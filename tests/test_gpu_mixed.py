@@ -97,13 +97,16 @@ def test_phase_api():
         assert H.hosc_set_phase(cav.h, 0) == 0
 
 
-def _one_mixed_step(N, Ra, n, dt, seed, tiles=None):
+def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None):
     p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-12)
     st = inputs.cavity_state(N, Ra, seed=seed)
     with H.Cavity(p) as cav:
         if tiles is not None:
             assert H.hosc_set_tiles(cav.h, *tiles) == 0
-            assert H.hosc_get_tiles(cav.h) == (0,) + tuple(tiles)
+            assert H.hosc_get_tiles(cav.h)[:3] == (0,) + tuple(tiles[:2])
+        if stencil is not None:
+            assert H.hosc_set_stencil_tiles(cav.h, *stencil) == 0
+            assert H.hosc_get_stencil_tiles(cav.h) == (0,) + tuple(stencil)
         for name, which in FIELDS:
             cav.set(which, st[name])
         info = cav.step(1)
@@ -111,7 +114,8 @@ def _one_mixed_step(N, Ra, n, dt, seed, tiles=None):
         return p, st, {name: cav.get(which) - st[name] for name, which in FIELDS}
 
 
-@pytest.mark.parametrize("tiles", [(64, 1), (128, 3), (512, 17), (96, 7), (256, 16)])
+@pytest.mark.parametrize("tiles", [(64, 1), (128, 3), (384, 17), (96, 7), (256, 16),
+                                   (128, 5, 1), (256, 9, 1)])
 def test_one_step_any_launch_shape(tiles):
     """The launch shape of the interleaved FP32 solve (threads per block, planes per thread)
     changes only the grouping of the float-float dot-product sums: the increment equals the
@@ -126,17 +130,34 @@ def test_one_step_any_launch_shape(tiles):
         assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, tiles)
 
 
+@pytest.mark.parametrize("stencil", [(32, 4, 9), (16, 2, 1), (8, 8, 17), (64, 4, 5), (24, 4, 3)])
+def test_staged_stencil_kernels(stencil):
+    """The staged (cp.async) p/v and s/t kernels compute what the register kernels compute: the
+    increment equals the default's within the FP32 solve tolerance, for tiles that overhang the
+    interior in x and y, single-plane and whole-column segments."""
+    N, Ra, n, dt = 19, 1e4, 0.75, 0.002
+    _, _, ref = _one_mixed_step(N, Ra, n, dt, 219)
+    _, _, got = _one_mixed_step(N, Ra, n, dt, 219, stencil=stencil)
+    for name in ref:
+        scale = max(np.max(np.abs(ref[name])), 1e-12)
+        assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, stencil)
+
+
 def test_tiles_limits_and_autotune():
     N = 21
     p = _params(N, 1e4, 0.75, 0.002, H.HOSC_MIXED)
     with H.Cavity(p) as cav:
-        for bad in ((32, 1), (100, 1), (1024, 1), (128, 0), (128, N - 1)):
+        for bad in ((32, 1), (100, 1), (512, 1), (128, 0), (128, N - 1), (384, 1, 1),
+                    (128, 1, 2)):
             assert H.hosc_set_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
+        for bad in ((4, 4, 1), (32, 16, 1), (32, 4, 0), (32, 4, N - 1), (64, 8, 1), (17, 2, 1)):
+            assert H.hosc_set_stencil_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
+        assert H.hosc_set_stencil_tiles(cav.h, 0, 0, 0) == 0
         cav.step(2)
         u0 = cav.get(H.HOSC_U)
         rc, b, z, ms = H.hosc_autotune(cav.h, 2)
-        assert rc == 0 and b in (64, 96, 128, 192, 256, 384, 512) and 1 <= z <= N - 2 and ms > 0
-        assert H.hosc_get_tiles(cav.h) == (0, b, z)
+        assert rc == 0 and b in (64, 96, 128, 160, 192, 256, 320, 384) and 1 <= z <= N - 2 and ms > 0
+        assert H.hosc_get_tiles(cav.h)[:3] == (0, b, z)
         assert np.array_equal(cav.get(H.HOSC_U), u0)   # tuning leaves the state alone
         info = cav.step(3)
         assert info["call_status"] == 0
