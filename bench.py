@@ -31,6 +31,10 @@ WORKLOADS = {
                            "mixed precision"),
     "cavity41": dict(N=41, Ra=1e4, Pr=1.0, n=0.75, dt=2e-4, spinup=300, history=0,
                      desc="cavity 41^3, n=0.75, Ra=1e4, Pr=1, mixed precision"),
+    # out-of-L2 probe: the Krylov working set (2 GB) is 15x the L2
+    "cavity257": dict(N=257, Ra=1e5, Pr=1.0, n=0.75, dt=2e-5, spinup=50, history=0,
+                      desc="single cavity 257^3, n=0.75, Ra=1e5, Pr=1, mixed precision "
+                           "(out-of-L2 roofline probe)"),
 }
 
 
@@ -290,31 +294,48 @@ def run_serve(args):
     from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
     mode = H.HOSC_POOL_GRAPH if args.pool_mode == "graph" else H.HOSC_POOL_STREAMS
     budget = int(args.budget_gb * (1 << 30))
+    steady_set = args.stream == "steady"
+    # "config": the stream of the serving configuration (most requests end at the step cap);
+    # "steady": small, slow cavities that reach steady state (time-to-steady is meaningful)
+    kw = (dict(sizes=(17, 21), indices=(0.9, 1.0, 1.1), ra_log10=(2.0, 3.0)) if steady_set
+          else {})
 
     def make(r):
+        if steady_set:
+            p = S.request_params(r["N"], r["Ra"], r["n"], r["Pr"], tol_steady=1e-6,
+                                 tol_div=1e-6)
+            p.dt = 0.02
+            p.lambda_ = 0.1
+            return p
         return S.request_params(r["N"], r["Ra"], r["n"], r["Pr"], tol_steady=args.tol_steady,
                                 tol_div=1e-4)
 
-    base = inputs.request_stream(args.requests, rate=1.0)
+    max_steps = max(args.max_steps, 20000) if steady_set else args.max_steps
+    base = inputs.request_stream(args.requests, rate=1.0, **kw)
     sat_reqs = [dict(r, t=0.0) for r in base[:args.saturation_requests]]
     with S.Pool(budget, args.round_steps, mode, True) as pool:
-        _, sat = S.serve(sat_reqs, pool, make, args.max_steps)
+        _, sat = S.serve(sat_reqs, pool, make, max_steps)
     rate = args.rho * sat["solves_per_s"]
-    stream = inputs.request_stream(args.requests, rate=rate)
+    stream = inputs.request_stream(args.requests, rate=rate, **kw)
     with S.Pool(budget, args.round_steps, mode, True) as pool:
-        res, summ = S.serve(stream, pool, make, args.max_steps)
+        res, summ = S.serve(stream, pool, make, max_steps)
         pst = pool.stats()
     out = {"metric": "served cavity solves/s", "value": summ["solves_per_s"], "unit": "solves/s",
            "n_gpus": 1, "steps": args.requests, "warmup": 0,
            "ms_per_step": 1e3 / summ["solves_per_s"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
-           "config": {"workload": "Poisson stream of %d cavity solves, N in {21..101} step 10, "
-                                  "Ra log-uniform [1e2,1e5], n in {0.75,1,1.25}, Pr=1, seed "
-                                  "20241107" % args.requests,
+           "config": {"workload": ("Poisson stream of %d cavity solves, N in {17,21}, Ra "
+                                   "log-uniform [1e2,1e3], n in {0.9,1,1.1}, Pr=1, dt=0.02, "
+                                   "lambda=0.1, tol 1e-6, seed 20241107" if steady_set else
+                                   "Poisson stream of %d cavity solves, N in {21..101} step 10, "
+                                   "Ra log-uniform [1e2,1e5], n in {0.75,1,1.25}, Pr=1, seed "
+                                   "20241107") % args.requests,
+                      "stream": args.stream,
                       "rho": args.rho, "saturated_solves_per_s": sat["solves_per_s"],
                       "saturation_requests": len(sat_reqs), "budget_GB": args.budget_gb,
-                      "max_steps": args.max_steps, "tol_steady": args.tol_steady,
+                      "max_steps": max_steps,
+                      "tol_steady": 1e-6 if steady_set else args.tol_steady,
                       "pool_mode": args.pool_mode, "steps_per_round": args.round_steps,
                       "completed": summ["completed"], "steady": summ["steady"],
                       "captures": pst["captures"], "capture_ms": pst["capture_ms"]}}
@@ -371,6 +392,7 @@ def main():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--saturation-requests", type=int, default=32)
     ap.add_argument("--rho", type=float, default=0.8)
+    ap.add_argument("--stream", default="config", choices=["config", "steady"])
     ap.add_argument("--max-steps", type=int, default=1000)
     ap.add_argument("--tol-steady", type=float, default=1e-4)
     ap.add_argument("--budget-gb", type=float, default=64.0)
@@ -482,7 +504,8 @@ def main():
     for kid, name in enumerate(names[:6]):
         rc, kms, kb = H.hosc_time_kernel(cav.h, kid, 20)
         if rc == 0:
-            iso[name] = {"us_per_launch": kms * 1e3, "GBps": kb / (kms * 1e-3) / 1e9}
+            iso[name] = {"us_per_launch": kms * 1e3,
+                         "GBps": kb / (kms * 1e-3) / 1e9 if kb > 0 and kms > 0 else 0.0}
     torch.cuda.nvtx.range_pop()
     dom = max(kern, key=lambda k: kern[k]["ms"])
     peak, peak_kind = _peaks()
@@ -539,6 +562,10 @@ def main():
                        "stencil_tiles": (dict(zip(("sx", "sy", "skz"),
                                                   H.hosc_get_stencil_tiles(cav.h)[1:]))
                                          if args.precision == "mixed" else None),
+                       "krylov_form": (("merged: 2 kernels per iteration"
+                                        if H.hosc_get_krylov_merged(cav.h) else
+                                        "3 kernels per iteration")
+                                       if args.precision == "mixed" else None),
                        "l2": "no flush: device working set %.0f MB > 129 MB L2"
                              % (H.hosc_workspace_bytes(p) / 1e6),
                        "parallelism": "replicas" if ws > 1 else "single"},

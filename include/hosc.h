@@ -217,11 +217,12 @@ hosc_status hosc_time_kernel(void* ctx, int kernel_id, int reps, double* ms_per_
 
 /* Launch shape of the mixed-precision BiCGSTAB kernels, which store the four systems interleaved
  * (one float4 per node) and give each thread one interior (i, j) column over kz consecutive
- * planes: kblock threads per block (a multiple of 32, 64..384), kz in 1..N-2, and at most
- * N^3/16 + 1024 blocks per launch; narrow = 1 selects the kernels compiled for at most 64
- * registers per thread (more resident blocks; kblock <= 256), 0 those with up to 80. The
- * default (128 threads, wide, kz from the wave model below) is chosen from N at creation. Changing it
- * drops the captured steps (they are captured again at the next step). HOSC_EINVAL for a shape
+ * planes: kblock threads per block (a multiple of 32, 64..384; at most 256 with narrow = 1 or
+ * the merged iteration form), kz in 1..N-2, and at most N^3/16 + 1024 blocks per launch;
+ * narrow = 1 selects the kernels compiled for at most 64 registers per thread (more resident
+ * blocks), 0 those with more (80 for the three-kernel form, 128 for the merged form). The
+ * default (128 threads, wide, kz from the wave model below) is chosen from N at creation.
+ * Changing it drops the captured steps (captured again at the next step). HOSC_EINVAL for a shape
  * outside these limits, HOSC_ESTATE in the middle of a stage-by-stage step. The FP64 solve has
  * one thread per node and ignores the setting. */
 hosc_status hosc_set_tiles(void* ctx, int kblock, int kz, int narrow);
@@ -237,12 +238,24 @@ hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz, int* narrow);
 hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz);
 hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz);
 
+/* Form of the mixed-precision BiCGSTAB iteration: merged = 1 runs two kernels per iteration,
+ * folding the x, r update of iteration i-1 into the p, v kernel of iteration i and obtaining
+ * r_0.r_{i+1} for beta from r_0.s and r_0.t of the s, t kernel (the same method; the
+ * convergence test sees the true residual one kernel later); 0 (the default) runs the three
+ * kernels p/v, s/t, x/r. HOSC_EINVAL for another value or when the current launch shape does not suit the form,
+ * HOSC_ESTATE mid-step. Drops the captured steps. hosc_get_krylov_merged returns the current
+ * form (-1 for a NULL context). */
+hosc_status hosc_set_krylov_merged(void* ctx, int merged);
+int hosc_get_krylov_merged(void* ctx);
+
 /* Autotuner for the launch shape above: after at least one completed step, time the three
  * BiCGSTAB kernels (hosc_time_kernel, reps launches each) for the valid shapes with kblock in
  * {64, 96, 128, 160, 192, 256, 320, 384} and kz in 1..33 whose modelled cost (waves of
  * resident blocks on this GPU, from the kernels' occupancy, times kz + 2 planes streamed per
- * block) is within 1.5x of the least, for both register budgets (narrow 0 and 1), keep the
- * shape with the least total time; then time the
+ * block) is within 1.5x of the least, for both register budgets (narrow 0 and 1), time the
+ * four fastest again with 4 reps launches each and keep the fastest; then time the other
+ * iteration form (hosc_set_krylov_merged)
+ * at that shape and keep the faster; with the three-kernel form, then time the
  * staged p/v and s/t kernels (hosc_set_stencil_tiles) for tiles sx in {8, 16, ..., 64},
  * sy in {4, 8} and skz in 1..33 within 1.5x of their least modelled cost, and keep them when
  * they beat the register kernels. Reports the register shape (any output pointer may be NULL;

@@ -8,6 +8,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <utility>
 #include <vector>
@@ -68,6 +69,7 @@ struct Ctx {
   long prof_launches[HOSC_K_COUNT] = {0};
   double host_bytes[HOSC_K_COUNT] = {0};   // algorithmic bytes of the fixed-work kernels
   int kblock = 128, kz = 1, narrow = 0;    // tiles of the interleaved Krylov kernels
+  int merged = 0;                          // two-kernel BiCGSTAB iteration (mixed precision)
   int sx = 0, sy = 0, skz = 0;             // staged stencil kernels (sx == 0: not used)
   // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
   // asynchronously into h_ring / h_ring_pos, completion marked by round_ev
@@ -105,14 +107,17 @@ double kernel_bytes(const DevParams& P, int kid) {
     case HOSC_K_SOURCES: return n3 * 9 * sb;                     // u, v, w, th, p, eta -> E* x3
     case HOSC_K_RHS:   // L, u, v, w, theta, E* x3 (+ 7 history arrays) -> rhs x4, 14 weights
       return ni3 * ((8 + (P.have_prev ? 7 : 0)) * sb + (f4 ? 16.0 * (1 + 4) : 8.0 * 18));
-    case HOSC_K_BICG_PV: return ni3 * (f4 ? 16.0 * (6 + 4) : 8.0 * (4 * 6 + 14));
-    case HOSC_K_BICG_ST: return ni3 * (f4 ? 16.0 * (3 + 4) : 8.0 * (4 * 3 + 14));
-    case HOSC_K_BICG_XR: return ni3 * (f4 ? 16.0 * 8 : 8.0 * 4 * 8);
+    case HOSC_K_BICG_PV:   // merged form: the x, r update folded in
+      return ni3 * (f4 ? 16.0 * ((P.merged ? 10 : 6) + 4) : 8.0 * (4 * 6 + 14));
+    case HOSC_K_BICG_ST:
+      return ni3 * (f4 ? 16.0 * ((P.merged ? 4 : 3) + 4) : 8.0 * (4 * 3 + 14));
+    case HOSC_K_BICG_XR: return ni3 * (f4 ? (P.merged ? 0.0 : 16.0 * 8) : 8.0 * 4 * 8);
     default: return 0.0;
   }
 }
 
 void apply_tiles(Ctx* c) {
+  c->P.merged = c->merged;
   c->P.kblock = c->kblock;
   c->P.kz = c->kz;
   c->P.narrow = c->narrow;
@@ -131,19 +136,21 @@ bool stencil_tiles_valid(const Ctx* c, int sx, int sy, int skz) {
   P.sy = sy;
   P.skz = skz;
   const long n3 = (long)c->prm.N * c->prm.N * c->prm.N;
-  return krylov4_blocks(P) <= red_rows(n3) &&
+  return krylov4_blocks(P) * (P.merged ? 2 : 1) <= red_rows(n3) &&
          staged_wave_cost(c->prm.N, sx, sy, skz, device_sms()) < 1e299;
 }
 
 bool tiles_valid(const Ctx* c, int kblock, int kz, int narrow) {
-  if (kblock < 64 || kblock > (narrow ? 256 : 384) || kblock % 32 != 0) return false;
+  if (kblock < 64 || kblock > ((narrow || c->P.merged) ? 256 : 384) || kblock % 32 != 0)
+    return false;
   if (narrow != 0 && narrow != 1) return false;
   if (kz < 1 || kz > c->prm.N - 2) return false;
   DevParams P = c->P;
   P.kblock = kblock;
   P.kz = kz;
   const long n3 = (long)c->prm.N * c->prm.N * c->prm.N;
-  return krylov4_blocks(P) <= red_rows(n3);   // rows of the partials buffer
+  // rows of the partials buffer (two per block for the merged form's 12 and 16 values)
+  return krylov4_blocks(P) * (P.merged ? 2 : 1) <= red_rows(n3);
 }
 
 // FP32 Krylov vectors cannot resolve relative residuals far below their rounding.
@@ -322,7 +329,7 @@ hosc_status solve(Ctx* c) {
       prof_end(c, HOSC_K_BICG_XR);
       pp ^= 1;
     }
-    c->launches += 3L * chunk;
+    c->launches += (P.krylov_fp32 && P.merged ? 2L : 3L) * chunk;
     it += chunk;
     hosc_status st = check_launch();
     if (st) return st;
@@ -602,7 +609,9 @@ hosc_status fold_records(Ctx* c, unsigned n, hosc_info* info, bool* steady) {
     }
     int most = 0;
     for (int s = 0; s < 4; ++s) most = r.iters[s] > most ? r.iters[s] : most;
-    c->launches += 4 + 6 + (c->P.krylov_fp32 ? 1 : 0) + 7L * ((most + 1) / 2 > 0 ? (most + 1) / 2 : 1);
+    const long body = (c->P.krylov_fp32 && c->P.merged) ? 5 : 7;   // kernels per loop pass
+    const long passes = (most + 1) / 2 > 0 ? (most + 1) / 2 : 1;
+    c->launches += 4 + 6 + (c->P.krylov_fp32 ? 1 : 0) + body * passes;
     if (r.status != HOSC_OK) {
       st = (hosc_status)r.status;
       break;
@@ -749,7 +758,7 @@ long ctx_signature(void* ctx) {
   const Ctx* c = (const Ctx*)ctx;
   return (long)c->cur | ((long)c->P.have_prev << 1) | ((long)c->phase << 2) |
          ((long)c->kblock << 3) | ((long)c->kz << 13) | ((long)c->narrow << 23) | ((long)c->sx << 24) |
-         ((long)c->sy << 32) | ((long)c->skz << 42);
+         ((long)c->sy << 32) | ((long)c->skz << 42) | ((long)c->merged << 52);
 }
 
 // Start of a round of n steps from the current level (read back by ctx_collect_round).
@@ -881,18 +890,19 @@ size_t workspace_layout(int N, Fields* f, char* base) {
     }
   }
   // The interleaved float solve of mixed precision reuses the 46 planar Krylov arrays above
-  // (contiguous from Am[0]): weights 64 bytes per node, then eight float4 vectors.
+  // (contiguous from Am[0]): weights 64 bytes per node, then nine float4 vectors.
   {
     char* kb = (char*)F.Am[0];
     const size_t v4 = align_up(n3 * sizeof(float4));
     F.kw = (float4*)kb;
     kb += align_up(4 * n3 * sizeof(float4));
-    float4** vecs[8] = {&F.kr0, &F.kx, &F.kr, &F.kt, &F.kp[0], &F.kp[1], &F.kv[0], &F.kv[1]};
+    float4** vecs[9] = {&F.kr0, &F.kx, &F.kr, &F.kr1, &F.kt,
+                        &F.kp[0], &F.kp[1], &F.kv[0], &F.kv[1]};
     for (float4** v : vecs) {
       *v = (float4*)kb;
       kb += v4;
     }
-    static_assert(4 * 16 + 8 * 16 <= 46 * 8, "interleaved solve must fit the planar arrays");
+    static_assert(4 * 16 + 9 * 16 <= 46 * 8, "interleaved solve must fit the planar arrays");
   }
   F.div = fld();
   F.eloc = (double*)take(3 * n3 * sizeof(double));
@@ -1303,6 +1313,29 @@ hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
   return HOSC_OK;
 }
 
+hosc_status hosc_set_krylov_merged(void* ctx, int merged) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || (merged != 0 && merged != 1)) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  if (merged != c->merged) {
+    const int save = c->merged;
+    c->merged = merged;
+    apply_tiles(c);
+    if (!tiles_valid(c, c->kblock, c->kz, c->narrow)) {
+      c->merged = save;
+      apply_tiles(c);
+      return HOSC_EINVAL;
+    }
+    drop_graphs(c);
+  }
+  return HOSC_OK;
+}
+
+int hosc_get_krylov_merged(void* ctx) {
+  Ctx* c = (Ctx*)ctx;
+  return c ? c->merged : -1;
+}
+
 hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
@@ -1338,13 +1371,20 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
     for (int b : blocks)
       for (int z = 1; z <= 33; ++z)
         if (tiles_valid(c, b, z, nr))
-          best_model = fmin(best_model, krylov4_wave_cost(c->prm.N, b, z, nr, sms));
+          best_model =
+              fmin(best_model, krylov4_wave_cost(c->prm.N, b, z, nr, c->P.merged, sms));
   hosc_status st = HOSC_OK;
+  struct Cand {
+    double ms;
+    int b, z, nr;
+  };
+  std::vector<Cand> cands;
   for (int nr = 0; nr <= 1 && !st; ++nr) {
     for (int b : blocks) {
       for (int z = 1; z <= 33 && !st; ++z) {
         if (!tiles_valid(c, b, z, nr)) continue;
-        if (krylov4_wave_cost(c->prm.N, b, z, nr, sms) > 1.5 * best_model) continue;
+        if (krylov4_wave_cost(c->prm.N, b, z, nr, c->P.merged, sms) > 1.5 * best_model)
+          continue;
         c->P.kblock = b;
         c->P.kz = z;
         c->P.narrow = nr;
@@ -1354,19 +1394,64 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
           st = time_class(c, kid, reps, &ms);
           tot += ms;
         }
-        if (!st && tot < best) {
-          best = tot;
-          best_b = b;
-          best_z = z;
-          best_n = nr;
-        }
+        if (!st) cands.push_back({tot, b, z, nr});
       }
+    }
+  }
+  // the four fastest again, with four times the launches: the screening times are noisy
+  std::sort(cands.begin(), cands.end(),
+            [](const Cand& x, const Cand& y) { return x.ms < y.ms; });
+  for (size_t q = 0; q < cands.size() && q < 4 && !st; ++q) {
+    c->P.kblock = cands[q].b;
+    c->P.kz = cands[q].z;
+    c->P.narrow = cands[q].nr;
+    double tot = 0.0;
+    for (int kid = HOSC_K_BICG_PV; kid <= HOSC_K_BICG_XR && !st; ++kid) {
+      double ms = 0.0;
+      st = time_class(c, kid, 4 * reps, &ms);
+      tot += ms;
+    }
+    if (!st && tot < best) {
+      best = tot;
+      best_b = cands[q].b;
+      best_z = cands[q].z;
+      best_n = cands[q].nr;
     }
   }
   apply_tiles(c);
   if (st) return st;
   st = hosc_set_tiles(c, best_b, best_z, best_n);
   if (st) return st;
+  // The other iteration form (two or three kernels) at the shape found.
+  {
+    const int other = 1 - c->merged;
+    c->merged = other;
+    apply_tiles(c);
+    c->P.sx = 0;
+    const bool ok = tiles_valid(c, best_b, best_z, best_n);
+    double tot = 0.0;
+    for (int kid = HOSC_K_BICG_PV; ok && kid <= HOSC_K_BICG_XR && !st; ++kid) {
+      double ms = 0.0;
+      st = time_class(c, kid, 4 * reps, &ms);
+      tot += ms;
+    }
+    c->merged = 1 - other;
+    apply_tiles(c);
+    if (st) return st;
+    if (ok && tot < best) {
+      st = hosc_set_krylov_merged(c, other);
+      if (st) return st;
+      best = tot;
+    }
+  }
+  if (c->merged) {   // the staged kernels implement the three-kernel form only
+    st = hosc_set_stencil_tiles(c, 0, 0, 0);
+    if (st) return st;
+    if (kblock_out) *kblock_out = best_b;
+    if (kz_out) *kz_out = best_z;
+    if (ms_out) *ms_out = best;
+    return HOSC_OK;
+  }
   // Staged stencil kernels for p/v and s/t: against the register kernels at the shape found.
   double reg_pvst = 0.0;
   {

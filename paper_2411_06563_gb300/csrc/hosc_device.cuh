@@ -115,6 +115,11 @@ __device__ __forceinline__ void block_sum_f32(const float (&vf)[M], double (&v)[
   __syncthreads();
 }
 
+// Doubles per row of the partials buffer for M values per block: kRedSlots, or 2 kRedSlots for
+// 8 < M <= 16 (then one row spans two rows of kRedSlots).
+template <int M>
+__host__ __device__ constexpr int row_stride() { return M > kRedSlots ? 2 * kRedSlots : kRedSlots; }
+
 // Publish the M partials of block b of nb (valid in thread 0) and report whether this block is
 // the last one to do so. No thread waits on another block: the last block to take a ticket does
 // the final reduction, every other block simply exits.
@@ -125,7 +130,7 @@ __device__ __forceinline__ bool publish_is_last(const double (&v)[M], double* re
   __shared__ int s_last;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int m = 0; m < M; ++m) red[(long)b * kRedSlots + m] = v[m];
+    for (int m = 0; m < M; ++m) red[(long)b * row_stride<M>() + m] = v[m];
     __threadfence();
     const unsigned int ticket = atomicAdd(counter, 1u);
     s_last = (ticket == nb - 1);
@@ -142,30 +147,33 @@ __device__ __forceinline__ bool publish_is_last(const double (&v)[M], double* re
 }
 
 // In the last block: reduce the partials of all blocks in a fixed order (valid in thread 0) and
-// re-arm the ticket counter for the next kernel. Thread t reads slot t % M of rows t / M,
-// t / M + blockDim/M, ... (consecutive threads read consecutive doubles; four rows' loads in
-// flight at a time), then the threads of each slot combine through shuffles and shared memory.
-// blockDim.x must be a multiple of 32; smem: >= 32*M doubles.
+// re-arm the ticket counter for the next kernel. With Mp the power of two >= M, thread t reads
+// slot t % Mp (if below M) of rows t / Mp, t / Mp + blockDim/Mp, ... (consecutive threads read
+// consecutive doubles; four rows' loads in flight at a time), then the threads of each slot
+// combine through shuffles and shared memory.
+// blockDim.x must be a multiple of 32 (and at least Mp); smem: >= 16*M doubles.
 template <int M, bool IsMax>
 __device__ __forceinline__ void reduce_partials(double (&tot)[M], const double* red, int nblocks,
                                                 unsigned int* counter, double* smem) {
-  static_assert(M == 1 || M == 2 || M == 4 || M == 8, "slots per row must divide the warp");
+  static_assert(M >= 1 && M <= 16, "at most 16 values per block");
+  constexpr int Mp = M <= 1 ? 1 : M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : 16;   // lanes per row
+  constexpr long S = row_stride<M>();
   __threadfence();
   const int t = threadIdx.x, bd = blockDim.x;
-  const int m = t % M, rstep = bd / M;
+  const int m = t % Mp, rstep = bd / Mp;
   auto op = [](double a, double b) { return IsMax ? fmax(a, b) : a + b; };
   double acc = 0.0;
-  int r = t / M;
+  int r = m < M ? t / Mp : nblocks;   // lanes past the M values read nothing
   for (; r + 3 * rstep < nblocks; r += 4 * rstep) {
-    const double a0 = __ldcg(red + (long)r * kRedSlots + m);
-    const double a1 = __ldcg(red + (long)(r + rstep) * kRedSlots + m);
-    const double a2 = __ldcg(red + (long)(r + 2 * rstep) * kRedSlots + m);
-    const double a3 = __ldcg(red + (long)(r + 3 * rstep) * kRedSlots + m);
+    const double a0 = __ldcg(red + r * S + m);
+    const double a1 = __ldcg(red + (r + rstep) * S + m);
+    const double a2 = __ldcg(red + (r + 2 * rstep) * S + m);
+    const double a3 = __ldcg(red + (r + 3 * rstep) * S + m);
     acc = op(op(op(op(acc, a0), a1), a2), a3);
   }
-  for (; r < nblocks; r += rstep) acc = op(acc, __ldcg(red + (long)r * kRedSlots + m));
+  for (; r < nblocks; r += rstep) acc = op(acc, __ldcg(red + r * S + m));
 #pragma unroll
-  for (int off = 16; off >= M; off >>= 1) acc = op(acc, __shfl_down_sync(0xffffffffu, acc, off));
+  for (int off = 16; off >= Mp; off >>= 1) acc = op(acc, __shfl_down_sync(0xffffffffu, acc, off));
   const int lane = t & 31, wid = t >> 5, nw = bd >> 5;
   if (lane < M) smem[wid * M + lane] = acc;
   __syncthreads();

@@ -23,7 +23,10 @@ struct DevParams {
   int kblock;        // interleaved Krylov kernels: threads per block (multiple of 32, 64..384)
   int kz;            // interleaved Krylov kernels: planes marched by one thread (1..N-2)
   int narrow;        // interleaved Krylov kernels compiled for 64 registers (kblock <= 256);
-                     // otherwise for 80 (kblock <= 384)
+                     // otherwise for 80 (three-kernel form, kblock <= 384) or 128 (merged
+                     // form, kblock <= 256)
+  int merged;        // interleaved solve: two kernels per BiCGSTAB iteration (the x, r update
+                     // folded into the next p, v kernel) instead of three
   int sx, sy, skz;   // staged stencil kernels (p/v and s/t): tile of sx * sy interior columns,
                      // skz planes per block; sx == 0 selects the register kernels instead
   double h, h2;      // grid spacing (h = k = l) and its square
@@ -93,7 +96,8 @@ struct Fields {
   float4* kw;        // [4 N^3] weights: (Am0 Am1 Am2 Am3)(Am4 Am5 Am6 Ae0)(Ae1 Ae2 Ae3 Ae4)(Ae5 Ae6 0 0)
   float4* kr0;       // right-hand sides dt (R - B chi^n) = r_0, the shadow residual
   float4* kx;        // iterate (the increments)
-  float4* kr;        // residual
+  float4* kr;        // residual (the merged iteration ping-pongs it with kr1)
+  float4* kr1;
   float4* kt;        // A s
   float4* kp[2];     // search direction, ping-pong
   float4* kv[2];     // A p, ping-pong
@@ -110,14 +114,14 @@ int red_blocks(long count);
 // Rows of the per-block partials buffer of an N^3 context: enough for any launch shape the
 // validation accepts (at least 32 threads per block, one plane per thread).
 inline long red_rows(long n3) { return n3 / 16 + 1024; }
-// Blocks of one interleaved Krylov launch (the partials buffer holds 4 red_blocks(N^3) rows).
+// Blocks of one interleaved Krylov launch (the partials buffer holds red_rows(N^3) rows).
 long krylov4_blocks(const DevParams& P);
 // Threads per block and planes per thread of the interleaved Krylov kernels when none are set:
-// 128 threads and the z-segment with the least wave cost below.
+// 128 threads (wide three-kernel form) and the z-segment with the least wave cost below.
 void default_tiles(int N, int* kblock, int* kz);
 // Waves of resident blocks a launch shape needs on this GPU times the planes each block streams
 // (kz + 2): a model of the launch's duration when it is latency-bound.
-double krylov4_wave_cost(int N, int kblock, int kz, int narrow, int sms);
+double krylov4_wave_cost(int N, int kblock, int kz, int narrow, int merged, int sms);
 // The same model for the staged stencil kernels with tile sx * sy and skz planes per block
 // (occupancy from their shared memory and registers); infinite for a shape that cannot launch.
 double staged_wave_cost(int N, int sx, int sy, int skz, int sms);

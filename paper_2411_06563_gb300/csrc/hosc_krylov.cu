@@ -662,6 +662,194 @@ __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
   }
 }
 
+// ------------------------------------------------------------- merged iteration (two kernels)
+//
+// The same BiCGSTAB with two kernels per iteration i. k6_a applies the end of iteration i-1
+// (s = r - alpha v, x += alpha p + omega s, r_i = s - omega t) and the start of iteration i
+// (p_i = r_i + beta (p - omega v), v_i = A p_i) in one pass, recomputing r_i and p_i at the
+// stencil's nodes; its partials give rho_i = r_0 . r_i, alpha_i = rho_i / (r_0 . v_i) and the
+// true ||r_i|| (the convergence test, one kernel later than in the three-kernel form). k6_b
+// computes s, t = A s and the dot products t.s, t.t, r_0.s, r_0.t, from which
+// omega_i = t.s / t.t and r_0 . r_{i+1} = r_0.s - omega_i r_0.t follow without another pass;
+// then beta_{i+1} = (r_0 . r_{i+1} / rho_i)(alpha_i / omega_i). The residual ping-pongs
+// (kr, kr1) since k6_a reads it at the neighbours while writing it.
+
+__global__ void __launch_bounds__(kThreads) k6_init(DevParams P, Fields F) {
+  __shared__ double smem[32 * 4];
+  const int N = P.N;
+  const int n3 = N * N * N;
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  FF acc[4] = {};
+  if (c < n3) {
+    const int i = c % N, j = (c / N) % N, k = c / (N * N);
+    const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
+    const float4 z = f4(0.f);
+    const float4 r = inner ? F.kr0[c] : z;
+    F.kr[c] = r;
+    F.kr1[c] = z;
+    F.kx[c] = z;
+    F.kt[c] = z;
+    F.kp[0][c] = z;
+    F.kp[1][c] = z;
+    F.kv[0][c] = z;
+    F.kv[1][c] = z;
+    ff_dot4(acc, r, r);
+  }
+  double part[4];
+  block_ff<4>(acc, part, smem);
+  if (publish_is_last<4>(part, F.red, F.counter)) {
+    double tot[4];
+    reduce_partials<4, false>(tot, F.red, gridDim.x, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        k.r0norm = sqrt(tot[s]);
+        k.rnorm = k.r0norm;
+        k.rho = tot[s];
+        k.alpha = 0.0;   // the first k6_a then leaves x = 0, r = r_0 and sets p = r_0
+        k.omega = 0.0;
+        k.beta = 0.0;
+        k.iters = 0;
+        k.pad = 0;       // no x, r update applied yet
+        k.status = 0;
+        k.done = (k.r0norm == 0.0 || *F.halt) ? 1 : 0;
+      }
+    }
+  }
+}
+
+template <int MinB>
+__global__ void __launch_bounds__(256, MinB) k6_a(DevParams P, Fields F, int pp) {
+  __shared__ double smem[32 * 8];
+  __shared__ Scal4 sc;
+  load_scalars(F.ks, sc);
+  if (sc.all_done) return;   // uniform over the grid
+  const int N = P.N, N2 = N * N;
+  const float4 a = sc.a, ma = neg4(sc.a), om = sc.om, mom = neg4(sc.om), b = sc.b;
+  const float4* __restrict__ Ro = pp ? F.kr1 : F.kr;
+  float4* __restrict__ Rn = pp ? F.kr : F.kr1;
+  const float4* __restrict__ Vo = F.kv[pp];
+  const float4* __restrict__ Po = F.kp[pp];
+  const float4* __restrict__ T = F.kt;
+  auto pnew = [&](int c) {
+    const float4 v = __ldg(Vo + c);
+    const float4 rn = fma4(mom, __ldg(T + c), fma4(ma, v, __ldg(Ro + c)));
+    return fma4(b, fma4(mom, v, __ldg(Po + c)), rn);
+  };
+  FF acc[12] = {};
+  Column col;
+  if (column(P, col)) {
+    float4 pm = pnew(col.cb + N2 * (col.k0 - 1));
+    float4 pc = pnew(col.cb + N2 * col.k0);
+    for (int k = col.k0; k < col.k1; ++k) {
+      const int c = col.cb + N2 * k;
+      const float4 pz = pnew(c + N2);
+      const float4 vn = apply7x4(F.kw, c, pc, pnew(c + 1), pnew(c - 1), pnew(c + N),
+                                 pnew(c - N), pz, pm);
+      const float4 r = __ldg(Ro + c), v = __ldg(Vo + c), p = __ldg(Po + c);
+      const float4 sv = fma4(ma, v, r);
+      const float4 rn = fma4(mom, __ldg(T + c), sv);
+      F.kx[c] = fma4(om, sv, fma4(a, p, F.kx[c]));
+      Rn[c] = rn;
+      F.kp[1 - pp][c] = pc;
+      F.kv[1 - pp][c] = vn;
+      const float4 r0 = __ldg(F.kr0 + c);
+      ff_dot4(acc, r0, vn);
+      ff_dot4(acc + 4, rn, rn);
+      ff_dot4(acc + 8, r0, rn);
+      pm = pc;
+      pc = pz;
+    }
+  }
+  double part[12];
+  block_ff<12>(acc, part, smem);
+  if (publish_is_last<12>(part, F.red, F.counter, block_id(), block_count())) {
+    double tot[12];
+    reduce_partials<12, false>(tot, F.red, block_count(), F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        k.rnorm = sqrt(tot[4 + s]);
+        if (k.pad) k.iters += 1;
+        k.pad = 1;
+        if (k.rnorm <= P.tol_lin * k.r0norm) {
+          k.done = 1;
+          k.status = 0;
+          continue;
+        }
+        if (!isfinite(k.rnorm) || k.iters >= P.max_lin_iter || tot[s] == 0.0 ||
+            !isfinite(tot[s])) {
+          k.done = 1;
+          k.status = HOSC_ENOCONV;
+          continue;
+        }
+        k.rho = tot[8 + s];   // rho_i = r_0 . r_i from the stored r_i
+        k.alpha = k.rho / tot[s];
+      }
+      // r p v t x r0 in, x r p v out, 4 weight float4
+      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 10.0 + 4.0);
+    }
+  }
+}
+
+template <int MinB>
+__global__ void __launch_bounds__(256, MinB) k6_b(DevParams P, Fields F, int pp) {
+  __shared__ double smem[32 * 8];
+  __shared__ Scal4 sc;
+  load_scalars(F.ks, sc);
+  if (sc.all_done) return;
+  const int N = P.N, N2 = N * N;
+  const float4 ma = neg4(sc.a);
+  const float4* __restrict__ R = pp ? F.kr : F.kr1;   // r_i, written by k6_a
+  const float4* __restrict__ V = F.kv[1 - pp];
+  auto sval = [&](int c) { return fma4(ma, __ldg(V + c), __ldg(R + c)); };
+  FF acc[16] = {};
+  Column col;
+  if (column(P, col)) {
+    float4 sm = sval(col.cb + N2 * (col.k0 - 1));
+    float4 sc0 = sval(col.cb + N2 * col.k0);
+    for (int k = col.k0; k < col.k1; ++k) {
+      const int c = col.cb + N2 * k;
+      const float4 sz = sval(c + N2);
+      const float4 tv = apply7x4(F.kw, c, sc0, sval(c + 1), sval(c - 1), sval(c + N),
+                                 sval(c - N), sz, sm);
+      F.kt[c] = tv;
+      const float4 r0 = __ldg(F.kr0 + c);
+      ff_dot4(acc, tv, sc0);
+      ff_dot4(acc + 4, tv, tv);
+      ff_dot4(acc + 8, r0, sc0);
+      ff_dot4(acc + 12, r0, tv);
+      sm = sc0;
+      sc0 = sz;
+    }
+  }
+  double part[16];
+  block_ff<16>(acc, part, smem);
+  if (publish_is_last<16>(part, F.red, F.counter, block_id(), block_count())) {
+    double tot[16];
+    reduce_partials<16, false>(tot, F.red, block_count(), F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        const double ts = tot[s], tt = tot[4 + s], r0s = tot[8 + s], r0t = tot[12 + s];
+        const double om = tt > 0.0 ? ts / tt : 0.0;
+        const double rho_next = r0s - om * r0t;   // r_0 . (s - omega t) = r_0 . r_{i+1}
+        if (om == 0.0 || rho_next == 0.0 || !isfinite(rho_next)) {
+          k.done = 1;
+          k.status = HOSC_ENOCONV;
+          continue;
+        }
+        // k6_a recomputes rho_{i+1} from the stored r_{i+1}; this value only sets beta
+        k.beta = (rho_next / k.rho) * (k.alpha / om);
+        k.omega = om;
+      }
+      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 4.0 + 4.0);   // r v r0 in, t out, 4 weights
+    }
+  }
+}
+
 // ------------------------------------------------------- staged stencil kernels (cp.async)
 //
 // The p/v and s/t kernels again, with their reads staged through shared memory. A block owns a
@@ -922,6 +1110,11 @@ void launch_loop_cond(const Fields& F, unsigned long long handle, cudaStream_t s
 }
 
 void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
+  if (P.krylov_fp32 && P.merged) {
+    const long n3 = (long)P.N * P.N * P.N;
+    k6_init<<<red_blocks(n3), kThreads, 0, s>>>(P, F);
+    return;
+  }
   if (P.krylov_fp32) {
     const long n3 = (long)P.N * P.N * P.N;
     k4_init<<<red_blocks(n3), kThreads, 0, s>>>(P, F);
@@ -932,6 +1125,11 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
 }
 
 void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  if (P.krylov_fp32 && P.merged) {   // x, r update of the previous iteration, then p, v
+    if (P.narrow) k6_a<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    else k6_a<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    return;
+  }
   if (P.krylov_fp32 && P.sx > 0) {
     k5_pv<<<grid5(P), P.sx * P.sy, staged_smem_bytes(P.sx, P.sy, true), s>>>(P, F, pp);
     return;
@@ -946,6 +1144,11 @@ void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
 }
 
 void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  if (P.krylov_fp32 && P.merged) {
+    if (P.narrow) k6_b<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    else k6_b<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    return;
+  }
   if (P.krylov_fp32 && P.sx > 0) {
     k5_st<<<grid5(P), P.sx * P.sy, staged_smem_bytes(P.sx, P.sy, false), s>>>(P, F, pp);
     return;
@@ -960,6 +1163,7 @@ void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
 }
 
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  if (P.krylov_fp32 && P.merged) return;   // folded into the next k6_a
   if (P.krylov_fp32) {
     if (P.narrow) k4_xr<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
     else k4_xr<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
@@ -1021,11 +1225,15 @@ double staged_wave_cost(int N, int sx, int sy, int skz, int sms) {
   return (double)waves * (skz + 2);
 }
 
-int krylov4_occupancy(int kblock, int narrow) {
+int krylov4_occupancy(int kblock, int narrow, int merged) {
   int occ = 0;
-  const cudaError_t e =
-      narrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_pv<4>, kblock, 0)
-             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_pv<2>, kblock, 0);
+  cudaError_t e;
+  if (merged)
+    e = narrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k6_a<4>, kblock, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k6_a<2>, kblock, 0);
+  else
+    e = narrow ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_pv<4>, kblock, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_pv<2>, kblock, 0);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 1;
@@ -1043,10 +1251,10 @@ int device_sms() {
   return sms > 0 ? sms : 152;
 }
 
-double krylov4_wave_cost(int N, int kblock, int kz, int narrow, int sms) {
+double krylov4_wave_cost(int N, int kblock, int kz, int narrow, int merged, int sms) {
   const long ni = N - 2;
   const long items = ((ni * ni + kblock - 1) / kblock) * ((ni + kz - 1) / kz);
-  const long slots = (long)krylov4_occupancy(kblock, narrow) * sms;
+  const long slots = (long)krylov4_occupancy(kblock, narrow, merged) * sms;
   const long waves = (items + slots - 1) / slots;
   // every resident block streams kz planes plus the two it reads around its segment
   return (double)waves * (kz + 2);
@@ -1058,7 +1266,7 @@ void default_tiles(int N, int* kblock, int* kz) {
   double best = 1e300;
   int bb = 128, bz = 1;
   for (int z = 1; z <= (ni < 16 ? ni : 16); ++z) {
-    const double c = krylov4_wave_cost(N, 128, z, 0, sms);
+    const double c = krylov4_wave_cost(N, 128, z, 0, 0, sms);
     if (c < best) {
       best = c;
       bz = z;

@@ -272,7 +272,9 @@ __device__ __forceinline__ T pseudo_time_mass(T G, T H, T I, T L, T dt, T invh2,
 // for u, v, w, theta at interior nodes, and the seven level-(n+1) weights L1..L7 of the momentum
 // and energy systems. Tc: arithmetic and the type of L, E*; Ts: type of the outputs.
 template <class Tc, class Ts>
-__global__ void __launch_bounds__(kThreads) k_rhs(
+// The float build is bounded to 80 registers (three 256-thread blocks per SM); the double builds
+// keep the compiler's choice.
+__global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0) k_rhs(
     DevParams P, const Tc* __restrict__ u, const Tc* __restrict__ v,
     const Tc* __restrict__ w, const Tc* __restrict__ th, const Tc* __restrict__ L,
     const Tc* __restrict__ Eu, const Tc* __restrict__ Ev, const Tc* __restrict__ Ew,
@@ -313,18 +315,19 @@ __global__ void __launch_bounds__(kThreads) k_rhs(
     }
     const Eq5<Tc> cm = eq5_coefficients<Tc>(G7, H7, I7, upc * Lpc, vpc * Lpc, wpc * Lpc, tinv2h,
                                             tinvh2, h2_12);
-    const Tc* E[3] = {Eu, Ev, Ew};
-    const Tc* Ep[3] = {Eup, Evp, Ewp};
-    const Tc* X[3] = {u, v, w};
-#pragma unroll 1
-    for (int s = 0; s < 3; ++s) {
+    // one momentum system: source E (level n, and n-1 when kept) and the field X
+    auto system = [&](const Tc* __restrict__ E, const Tc* __restrict__ Ep,
+                      const Tc* __restrict__ X) {
       Tc E7[7], f19[19];
-      load7<Tc, Tc>(E[s], c, sy, sz, E7);
-      const Tc Epc = P.have_prev ? Ep[s][c] : E7[0];
+      load7<Tc, Tc>(E, c, sy, sz, E7);
+      const Tc Epc = P.have_prev ? Ep[c] : E7[0];
       const Tc R = bracket<Tc>(diffs7<Tc>(E7, tinv2h, tinvh2), E7[0], Epc, cm, h2_12);
-      load19<Tc>(X[s], c, sy, sz, f19);
-      rv[s] = tdt * (R - applyB<Tc>(cm, f19, h, tinv2h, tinvh2));
-    }
+      load19<Tc>(X, c, sy, sz, f19);
+      return tdt * (R - applyB<Tc>(cm, f19, h, tinv2h, tinvh2));
+    };
+    rv[0] = system(Eu, Eup, u);
+    rv[1] = system(Ev, Evp, v);
+    rv[2] = system(Ew, Ewp, w);
     // level-(n+1) weights (Eq. 6): Mx = -dt/(2L) + h^2/12, M15 = (h^2/(6L)) dx L, ...
     const D7<Tc> dL = diffs7<Tc>(L7, tinv2h, tinvh2);
     const Tc M = -tdt / (Tc(2) * Lc) + h2_12;
@@ -392,12 +395,13 @@ __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Field
                                                               int nblocks) {
   __shared__ double smem[32];
   if (*F.halt) return;
-  const int N = P.N;
-  const long n3 = (long)N * N * N;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned N = P.N;
+  const unsigned n3 = N * N * N;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   double m[1] = {0.0};
   if (t < n3) {
-    const int i = (int)(t % N), j = (int)((t / N) % N), k = (int)(t / ((long)N * N));
+    const unsigned q = t / N;
+    const unsigned i = t - q * N, j = q % N, k = q / N;
     const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
     if (inner) {
       double xu, xv, xw, xt;
@@ -432,6 +436,43 @@ __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Field
   }
 }
 
+__device__ __forceinline__ int node32(int i, int j, int k, int N) { return i + N * (j + N * k); }
+
+// Node number t of the y faces (x interior, all z), then of the z faces (x, y interior):
+// 0 <= t < 2 (N-2) N + 2 (N-2)^2, x fastest.
+__device__ __forceinline__ void boundary_yz(int t, int N, int& i, int& j, int& k) {
+  const int ni = N - 2;
+  if (t < 2 * ni * N) {
+    const int side = t / (ni * N), r = t - side * ni * N;
+    const int q = r / ni;
+    i = 1 + (r - q * ni);
+    k = q;
+    j = side ? N - 1 : 0;
+  } else {
+    const int u = t - 2 * ni * N;
+    const int side = u / (ni * ni), r = u - side * ni * ni;
+    const int q = r / ni;
+    i = 1 + (r - q * ni);
+    j = 1 + q;
+    k = side ? N - 1 : 0;
+  }
+}
+
+// Node number t of the cube's boundary, 0 <= t < N^3 - (N-2)^3: the x faces, then the y and z
+// faces as in boundary_yz.
+__device__ __forceinline__ void boundary_node(int t, int N, int& i, int& j, int& k) {
+  const int N2 = N * N;
+  if (t < 2 * N2) {
+    const int side = t / N2, r = t - side * N2;
+    const int q = r / N;
+    j = r - q * N;
+    k = q;
+    i = side ? N - 1 : 0;
+  } else {
+    boundary_yz(t - 2 * N2, N, i, j, k);
+  }
+}
+
 // Extrapolation weights along one axis for a wall condition of zero normal derivative:
 // (4 f_1 - f_2)/3 at the first wall, mirrored at the second; identity inside.
 __device__ __forceinline__ int wall_weights(int a, int N, int idx[2], double wt[2]) {
@@ -453,28 +494,24 @@ __device__ __forceinline__ int wall_weights(int a, int N, int idx[2], double wt[
 __global__ void __launch_bounds__(kThreads) k_theta_walls(DevParams P, Fields F, int nblocks) {
   __shared__ double smem[32];
   if (*F.halt) return;
-  const int N = P.N;
-  const long cnt = (long)(N - 2) * N * N;   // x interior, all y, z
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int N = P.N, ni = N - 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double m[1] = {0.0};
-  if (t < cnt) {
-    const int i = 1 + (int)(t % (N - 2));
-    const long r = t / (N - 2);
-    const int j = (int)(r % N), k = (int)(r / N);
-    if (on_wall(j, N) | on_wall(k, N)) {
-      int jy[2], kz[2];
-      double wy[2], wz[2];
-      const int ny = wall_weights(j, N, jy, wy), nz = wall_weights(k, N, kz, wz);
-      double s = 0.0;
-      for (int b = 0; b < nz; ++b) {
-        double sb = 0.0;
-        for (int a = 0; a < ny; ++a) sb += wy[a] * F.th[node(i, jy[a], kz[b], N)];
-        s += wz[b] * sb;
-      }
-      const long c = node(i, j, k, N);
-      m[0] = absfin(s - F.th[c]);
-      F.th[c] = s;
+  int i, j, k;
+  if (t < 2 * ni * N + 2 * ni * ni) {   // the y faces, then the z faces (x interior)
+    boundary_yz(t, N, i, j, k);
+    int jy[2], kz[2];
+    double wy[2], wz[2];
+    const int ny = wall_weights(j, N, jy, wy), nz = wall_weights(k, N, kz, wz);
+    double s = 0.0;
+    for (int b = 0; b < nz; ++b) {
+      double sb = 0.0;
+      for (int a = 0; a < ny; ++a) sb += wy[a] * F.th[node32(i, jy[a], kz[b], N)];
+      s += wz[b] * sb;
     }
+    const int c = node32(i, j, k, N);
+    m[0] = absfin(s - F.th[c]);
+    F.th[c] = s;
   }
   block_reduce<1, true>(m, smem);
   if (publish_is_last<1>(m, F.red, F.counter)) {
@@ -490,12 +527,12 @@ __global__ void __launch_bounds__(kThreads) k_divergence(DevParams P, Fields F, 
   __shared__ double smem[32];
   if (*F.halt) return;
   const int N = P.N, ni = N - 2;
-  const long cnt = (long)ni * ni * ni;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int cnt = ni * ni * ni;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   double m[1] = {0.0};
   if (t < cnt) {
-    const int i = 1 + (int)(t % ni), j = 1 + (int)((t / ni) % ni), k = 1 + (int)(t / ((long)ni * ni));
-    const long c = node(i, j, k, N), sy = N, sz = (long)N * N;
+    const int q = t / ni, i = 1 + (t - q * ni), j = 1 + q % ni, k = 1 + q / ni;
+    const int c = node32(i, j, k, N), sy = N, sz = N * N;
     const double* u = F.u[nxt];
     const double* v = F.v[nxt];
     const double* w = F.w[nxt];
@@ -515,25 +552,24 @@ __global__ void __launch_bounds__(kThreads) k_divergence(DevParams P, Fields F, 
 // p <- p - lambda div V at interior nodes when max|div V| > tol_div (Sec. 2.2).
 __global__ void __launch_bounds__(kThreads) k_pressure_correct(DevParams P, Fields F) {
   const int N = P.N, ni = N - 2;
-  const long cnt = (long)ni * ni * ni;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int cnt = ni * ni * ni;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= cnt || *F.halt) return;
   if (!(F.rec->div_max > P.tol_div)) return;
-  const int i = 1 + (int)(t % ni), j = 1 + (int)((t / ni) % ni), k = 1 + (int)(t / ((long)ni * ni));
-  const long c = node(i, j, k, N);
+  const int q = t / ni, i = 1 + (t - q * ni), j = 1 + q % ni, k = 1 + q / ni;
+  const int c = node32(i, j, k, N);
   F.p[c] -= P.lambda * F.div[c];
 }
 
 // Zero normal pressure gradient on every wall: p_b = (4 p_1 - p_2)/3 along each wall normal the
 // node lies on (products on edges and corners); applied after a correction.
 __global__ void __launch_bounds__(kThreads) k_pressure_walls(DevParams P, Fields F) {
-  const int N = P.N;
-  const long n3 = (long)N * N * N;
-  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n3 || *F.halt) return;
+  const int N = P.N, ni = N - 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * N * N - ni * ni * ni || *F.halt) return;
   if (!(F.rec->div_max > P.tol_div)) return;
-  const int i = (int)(t % N), j = (int)((t / N) % N), k = (int)(t / ((long)N * N));
-  if (!(on_wall(i, N) | on_wall(j, N) | on_wall(k, N))) return;
+  int i, j, k;
+  boundary_node(t, N, i, j, k);
   int ix[2], jy[2], kz[2];
   double wx[2], wy[2], wz[2];
   const int nx = wall_weights(i, N, ix, wx), ny = wall_weights(j, N, jy, wy),
@@ -543,12 +579,12 @@ __global__ void __launch_bounds__(kThreads) k_pressure_walls(DevParams P, Fields
     double s2 = 0.0;
     for (int b = 0; b < ny; ++b) {
       double s1 = 0.0;
-      for (int a = 0; a < nx; ++a) s1 += wx[a] * F.p[node(ix[a], jy[b], kz[c3], N)];
+      for (int a = 0; a < nx; ++a) s1 += wx[a] * F.p[node32(ix[a], jy[b], kz[c3], N)];
       s2 += wy[b] * s1;
     }
     s += wz[c3] * s2;
   }
-  F.p[t] = s;
+  F.p[node32(i, j, k, N)] = s;
 }
 
 // Step record: Krylov outcomes and the overall status; appended to the ring. A failed step (or,
@@ -689,12 +725,12 @@ void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s)
     k_apply_increment<float><<<b_all, kThreads, 0, s>>>(P, F, cur, b_all);
   else
     k_apply_increment<double><<<b_all, kThreads, 0, s>>>(P, F, cur, b_all);
-  const int b_walls = red_blocks((N - 2) * N * N);
+  const int b_walls = red_blocks(2 * ni * N + 2 * ni * ni);
   k_theta_walls<<<b_walls, kThreads, 0, s>>>(P, F, b_walls);
   const int b_int = red_blocks(ni * ni * ni);
   k_divergence<<<b_int, kThreads, 0, s>>>(P, F, 1 - cur, b_int);
   k_pressure_correct<<<b_int, kThreads, 0, s>>>(P, F);
-  k_pressure_walls<<<b_all, kThreads, 0, s>>>(P, F);
+  k_pressure_walls<<<red_blocks(n3 - ni * ni * ni), kThreads, 0, s>>>(P, F);
   k_finish_record<<<1, 32, 0, s>>>(P, F);
 }
 

@@ -131,6 +131,8 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
         "hosc_set_stencil_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "hosc_set_krylov_merged": (ctypes.c_int, [_P, ctypes.c_int]),
+        "hosc_get_krylov_merged": (ctypes.c_int, [_P]),
         "hosc_get_stencil_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                                   ctypes.POINTER(ctypes.c_int),
                                                   ctypes.POINTER(ctypes.c_int)]),
@@ -300,6 +302,14 @@ def hosc_get_tiles(h):
 
 def hosc_set_stencil_tiles(h, sx, sy, skz):
     return lib().hosc_set_stencil_tiles(h, int(sx), int(sy), int(skz))
+
+
+def hosc_set_krylov_merged(h, merged):
+    return lib().hosc_set_krylov_merged(h, int(merged))
+
+
+def hosc_get_krylov_merged(h):
+    return int(lib().hosc_get_krylov_merged(h))
 
 
 def hosc_get_stencil_tiles(h):

@@ -95,13 +95,13 @@ def steady_mix(count=8, seed=20241108, sizes=(17, 21)):
 
 
 def request_stream(count=2000, rate=1.0, seed=20241107, sizes=tuple(range(21, 102, 10)),
-                   indices=(0.75, 1.0, 1.25)):
+                   indices=(0.75, 1.0, 1.25), ra_log10=(2.0, 5.0)):
     """Poisson request stream: list of dicts (t_arrival, N, Ra, n, Pr) sorted by arrival."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=count))
     out = []
     for q in range(count):
         out.append(dict(t=float(t[q]), N=int(rng.choice(sizes)),
-                        Ra=float(10.0 ** rng.uniform(2.0, 5.0)), n=float(rng.choice(indices)),
+                        Ra=float(10.0 ** rng.uniform(*ra_log10)), n=float(rng.choice(indices)),
                         Pr=1.0))
     return out

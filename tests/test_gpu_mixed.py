@@ -97,10 +97,13 @@ def test_phase_api():
         assert H.hosc_set_phase(cav.h, 0) == 0
 
 
-def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None):
+def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None, merged=None):
     p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-12)
     st = inputs.cavity_state(N, Ra, seed=seed)
     with H.Cavity(p) as cav:
+        if merged is not None:
+            assert H.hosc_set_krylov_merged(cav.h, merged) == 0
+            assert H.hosc_get_krylov_merged(cav.h) == merged
         if tiles is not None:
             assert H.hosc_set_tiles(cav.h, *tiles) == 0
             assert H.hosc_get_tiles(cav.h)[:3] == (0,) + tuple(tiles[:2])
@@ -114,17 +117,19 @@ def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None):
         return p, st, {name: cav.get(which) - st[name] for name, which in FIELDS}
 
 
-@pytest.mark.parametrize("tiles", [(64, 1), (128, 3), (384, 17), (96, 7), (256, 16),
-                                   (128, 5, 1), (256, 9, 1)])
-def test_one_step_any_launch_shape(tiles):
-    """The launch shape of the interleaved FP32 solve (threads per block, planes per thread)
-    changes only the grouping of the float-float dot-product sums: the increment equals the
-    default shape's within the FP32 solve tolerance (relative residual 3e-6), for segments that
-    do not divide the interior, blocks that overhang the plane and a single segment. A missed or
-    doubled plane or column would differ at O(1)."""
+@pytest.mark.parametrize("tiles,merged", [((64, 1), 1), ((128, 3), 1), ((256, 17), 1),
+                                          ((96, 7, 1), 1), ((256, 16, 1), 1), ((384, 17), 0),
+                                          ((128, 5, 1), 0), ((160, 9), 0)])
+def test_one_step_any_launch_shape(tiles, merged):
+    """The launch shape of the interleaved FP32 solve (threads per block, planes per thread,
+    register budget) and its form (two merged kernels per BiCGSTAB iteration, or three) change
+    only the grouping of the float-float dot-product sums and the rounding of the recurrences:
+    the increment equals the default's within the FP32 solve tolerance (relative residual
+    3e-6), for segments that do not divide the interior, blocks that overhang the plane and a
+    single segment. A missed or doubled plane or column would differ at O(1)."""
     N, Ra, n, dt = 19, 1e4, 0.75, 0.002
     _, _, ref = _one_mixed_step(N, Ra, n, dt, 219)
-    _, _, got = _one_mixed_step(N, Ra, n, dt, 219, tiles)
+    _, _, got = _one_mixed_step(N, Ra, n, dt, 219, tiles, merged=merged)
     for name in ref:
         scale = max(np.max(np.abs(ref[name])), 1e-12)
         assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, tiles)
@@ -137,7 +142,7 @@ def test_staged_stencil_kernels(stencil):
     interior in x and y, single-plane and whole-column segments."""
     N, Ra, n, dt = 19, 1e4, 0.75, 0.002
     _, _, ref = _one_mixed_step(N, Ra, n, dt, 219)
-    _, _, got = _one_mixed_step(N, Ra, n, dt, 219, stencil=stencil)
+    _, _, got = _one_mixed_step(N, Ra, n, dt, 219, stencil=stencil, merged=0)
     for name in ref:
         scale = max(np.max(np.abs(ref[name])), 1e-12)
         assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, stencil)
@@ -153,6 +158,13 @@ def test_tiles_limits_and_autotune():
         for bad in ((4, 4, 1), (32, 16, 1), (32, 4, 0), (32, 4, N - 1), (64, 8, 1), (17, 2, 1)):
             assert H.hosc_set_stencil_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
         assert H.hosc_set_stencil_tiles(cav.h, 0, 0, 0) == 0
+        assert H.hosc_get_krylov_merged(cav.h) == 0   # the default form: three kernels
+        assert H.hosc_set_krylov_merged(cav.h, 2) == H.HOSC_EINVAL
+        assert H.hosc_set_tiles(cav.h, 384, 1) == 0
+        assert H.hosc_set_krylov_merged(cav.h, 1) == H.HOSC_EINVAL   # 384 threads
+        assert H.hosc_set_tiles(cav.h, 128, 1) == 0 and H.hosc_set_krylov_merged(cav.h, 1) == 0
+        assert H.hosc_set_tiles(cav.h, 320, 1) == H.HOSC_EINVAL      # merged: at most 256
+        assert H.hosc_set_krylov_merged(cav.h, 0) == 0
         cav.step(2)
         u0 = cav.get(H.HOSC_U)
         rc, b, z, ms = H.hosc_autotune(cav.h, 2)
