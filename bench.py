@@ -556,6 +556,8 @@ def main():
                        "spinup_steps": spinup, "tol_lin": p.tol_lin,
                        "use_history": wl["history"], "lambda": p.lambda_,
                        "bicgstab_iters_per_step": lin_iters / (4.0 * args.steps),
+                       # interior nodes x systems x BiCGSTAB iterations per second
+                       "sweep_rate_per_s": (N - 2) ** 3 * lin_iters * ws / (ms * 1e-3),
                        "krylov_tiles": (dict(zip(("block", "kz", "narrow"),
                                                  H.hosc_get_tiles(cav.h)[1:]))
                                         if args.precision == "mixed" else None),
