@@ -101,17 +101,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def _dist():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def run_reference(args, wl):
     """The oracle (plain FP64 CPU implementation) timed on the host cores: each step is one
     pseudo-time step of a 51^3 cavity with the workload's physics (a bounded sample)."""
-    ws, rank, _ = _dist()
+    from paper_2411_06563_gb300 import replicas as R
+    ws, rank, _ = R.world()
     if rank != 0:
         return 0
     import numpy as np
@@ -409,11 +403,12 @@ def main():
 
     import numpy as np
     import torch
-    ws, rank, local = _dist()
+    from paper_2411_06563_gb300 import replicas as R
+    ws, rank, local = R.world()
+    torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
     from paper_2411_06563_gb300 import hosc as H
 
     N = wl["N"]
@@ -442,9 +437,7 @@ def main():
         torch.cuda.synchronize()
         return p, cav
 
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
+    barrier = R.barrier
 
     fp64_compare = None
     if args.precision == "mixed" and not args.no_fp64_compare:
@@ -477,10 +470,7 @@ def main():
         barrier()
     ms = e0.elapsed_time(e1)
     launches = cav.kernel_launches() - l0
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = R.max_over_ranks(ms)   # replicas: each rank ran its own cavity
     units = (N - 2) ** 3 * args.steps * ws
     value = units / (ms * 1e-3)
     lin_iters = info["lin_iters"]
@@ -531,10 +521,7 @@ def main():
             H.hosc_get_field(cav.h, w_, a)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = R.max_over_ranks(e2e_s)
     e2e_val = (N - 2) ** 3 * e2e_steps * ws / e2e_s
 
     cpu = None
