@@ -252,7 +252,7 @@ void prof_begin(Ctx* c, int kid) {
   c->ev_kid[c->ev_used / 2] = kid;
   cudaEventRecord(c->ev[c->ev_used], c->stream);
 }
-void prof_end(Ctx* c, int kid) {
+void prof_end(Ctx* c, int /*kid: recorded by prof_begin*/) {
   if (!c->prof_on) return;
   cudaEventRecord(c->ev[c->ev_used + 1], c->stream);
   c->ev_used += 2;

@@ -370,9 +370,6 @@ __device__ __forceinline__ float4 fma4(float4 b, float4 c, float4 a) {
   return make_float4(fmaf(b.x, c.x, a.x), fmaf(b.y, c.y, a.y), fmaf(b.z, c.z, a.z),
                      fmaf(b.w, c.w, a.w));
 }
-__device__ __forceinline__ float4 sub4(float4 a, float4 b) {
-  return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-}
 __device__ __forceinline__ float4 neg4(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
 
 // acc[m0 + s] += a_s * b_s for the four systems s

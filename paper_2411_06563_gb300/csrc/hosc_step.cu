@@ -27,10 +27,6 @@ template <class T> __device__ __forceinline__ T tpow(T x, T y);
 template <> __device__ __forceinline__ double tpow<double>(double x, double y) { return pow(x, y); }
 template <> __device__ __forceinline__ float tpow<float>(float x, float y) { return powf(x, y); }
 
-template <class T> __device__ __forceinline__ T* as(double* p) { return reinterpret_cast<T*>(p); }
-template <class T> __device__ __forceinline__ const T* as(const double* p) {
-  return reinterpret_cast<const T*>(p);
-}
 
 template <class T, class S>
 __device__ __forceinline__ T grad_axis_t(const S* __restrict__ f, long c, int a, int N, long st,
