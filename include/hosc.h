@@ -118,6 +118,11 @@ typedef struct {
   int auto_defect;    /* HOSC_MIXED: 1 switches from FP32 to FP64 defect sweeps by itself when the
                          step change stalls (200 steps without a 5 % improvement); 0 keeps the
                          phase chosen with hosc_set_phase */
+  int precond;        /* 0: BiCGSTAB on the systems as assembled (the paper's unpreconditioned
+                         solver, the default); 1: Jacobi row scaling, each row of the level-(n+1)
+                         system and its right-hand side divided by the row's diagonal before the
+                         solve (same solution; the stopping test then measures the scaled
+                         residual). Not in the paper. */
 } hosc_params;
 
 typedef struct {

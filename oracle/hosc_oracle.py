@@ -85,7 +85,7 @@ class Params:
 
     def __init__(self, N, Ra, Pr=1.0, n=1.0, dt=0.02, lam=None, theta_ref=0.5, I2_eps=1e-10,
                  phi=1e-4, tol_div=1e-6, tol_lin=1e-12, max_lin_iter=2000, theta_init=0.5,
-                 a_limit=0.25, a_boost=1.0, use_history=1):
+                 a_limit=0.25, a_boost=1.0, use_history=1, precond=0):
         self.N = int(N)
         self.Ra = float(Ra)
         self.Pr = float(Pr)
@@ -103,6 +103,9 @@ class Params:
         self.a_boost = float(a_boost)
         # 1: delta_t^- from the level n-1 history (Eq. 5); 0: delta_t^- = 0 every step (R20).
         self.use_history = int(use_history)
+        # 1: Jacobi row scaling of each level-(n+1) system before BiCGSTAB (not in the paper;
+        # the solution is the same, only the Krylov iteration changes)
+        self.precond = int(precond)
         self.theta_ref = float(theta_ref)
         self.theta_init = float(theta_init)
         self.I2_eps = float(I2_eps)
@@ -332,11 +335,14 @@ def solve_bicgstab(A, b, x0, tol, max_iter):
     return x, max_iter, 4
 
 
-def solve_system(g, dt, c, A, chi, tol, max_iter, direct=False, chi_wall_new=None):
+def solve_system(g, dt, c, A, chi, tol, max_iter, direct=False, chi_wall_new=None,
+                 precond=0):
     """One implicit HOSC solve, Eq. (6): A chi^{n+1} = Q chi^n + dt R with Q = A - dt B.
 
     Unknowns are the interior nodes. Wall values of chi^{n+1} are ``chi_wall_new`` when given
     (a field whose wall nodes hold level-(n+1) values), else the level-n wall values (reading R6).
+    With precond = 1 every row of the interior system and its right-hand side are divided by the
+    row's diagonal entry before BiCGSTAB (Jacobi row scaling; the solution does not change).
     Returns (chi_new, iterations, status).
     """
     chi_f = chi.ravel()
@@ -347,6 +353,11 @@ def solve_system(g, dt, c, A, chi, tol, max_iter, direct=False, chi_wall_new=Non
     A_II = A_rows[:, ii].tocsr()
     A_IB = A_rows[:, bb]
     rhs = b_full[ii] - A_IB @ wall[bb]
+    if precond:
+        d = A_II.diagonal()
+        d = np.where(d != 0.0, d, 1.0)
+        A_II = (sp.diags(1.0 / d) @ A_II).tocsr()
+        rhs = rhs / d
     if direct:
         import scipy.sparse.linalg as spla
         x, its, st = spla.spsolve(A_II.tocsc(), rhs), 0, 0
@@ -527,7 +538,8 @@ def step(state, prm, g=None, direct=False):
     for name in ("u", "v", "w", "th"):
         A = A_e if name == "th" else A_m
         new[name], iters[name], st = solve_system(g, prm.dt, coefs[name], A, state[name],
-                                                  prm.tol_lin, prm.max_lin_iter, direct=direct)
+                                                  prm.tol_lin, prm.max_lin_iter, direct=direct,
+                                                  precond=prm.precond)
         status = status or st
     new["th"] = apply_theta_bc(new["th"])
     h = g.h

@@ -93,6 +93,7 @@ hosc_status validate(const hosc_params* p) {
   if (!(p->a_boost >= 0.0) || !isfinite(p->a_boost)) return HOSC_EINVAL;
   if (p->use_history != 0 && p->use_history != 1) return HOSC_EINVAL;
   if (p->auto_defect != 0 && p->auto_defect != 1) return HOSC_EINVAL;
+  if (p->precond != 0 && p->precond != 1) return HOSC_EINVAL;
   if (p->precision != HOSC_FP64 && p->precision != HOSC_MIXED) return HOSC_EINVAL;
   return HOSC_OK;
 }
@@ -181,6 +182,7 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   d.tol_lin = d.krylov_fp32 ? fmax(p.tol_lin, kFp32TolFloor) : p.tol_lin;
   d.a_limit = p.a_limit;
   d.a_boost = p.a_boost;
+  d.precond = p.precond;
   d.steady_res = p.tol_steady * p.dt;
   return d;
 }

@@ -31,6 +31,7 @@ struct DevParams {
                      // skz planes per block; sx == 0 selects the register kernels instead
   double h, h2;      // grid spacing (h = k = l) and its square
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
+  int precond;         // Jacobi row scaling of the level-(n+1) systems
   double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (and div below tol_div)
                        // is steady (tol_steady * dt)
 };

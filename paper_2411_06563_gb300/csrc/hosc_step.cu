@@ -364,6 +364,17 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0)
     Ae[5] = a2 - M * ce.I * tinv2h;
     Ae[6] = a2 + M * ce.I * tinv2h;
   }
+  if (P.precond) {   // Jacobi row scaling: each row and its right-hand side over its diagonal
+    const Tc dm = Am[0] != Tc(0) ? Am[0] : Tc(1), de = Ae[0] != Tc(0) ? Ae[0] : Tc(1);
+#pragma unroll
+    for (int s = 0; s < 3; ++s) rv[s] /= dm;
+    rv[3] /= de;
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      Am[q] /= dm;
+      Ae[q] /= de;
+    }
+  }
   if constexpr (sizeof(Ts) == sizeof(float)) {   // interleaved float storage
     F.kr0[c] = make_float4((float)rv[0], (float)rv[1], (float)rv[2], (float)rv[3]);
     float4* W = F.kw + 4 * (size_t)c;

@@ -41,7 +41,8 @@ class hosc_params(ctypes.Structure):
                 ("tol_lin", ctypes.c_double), ("max_lin_iter", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("a_limit", ctypes.c_double), ("a_boost", ctypes.c_double),
-                ("use_history", ctypes.c_int), ("auto_defect", ctypes.c_int)]
+                ("use_history", ctypes.c_int), ("auto_defect", ctypes.c_int),
+                ("precond", ctypes.c_int)]
 
 
 class hosc_info(ctypes.Structure):

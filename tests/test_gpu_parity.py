@@ -45,7 +45,8 @@ def _oracle_params(p):
     return O.Params(N=p.N, Ra=p.Ra, Pr=p.Pr, n=p.n, dt=p.dt, lam=p.lambda_,
                     theta_ref=p.theta_ref, I2_eps=p.I2_eps, phi=p.phi, tol_div=p.tol_div,
                     tol_lin=p.tol_lin, max_lin_iter=p.max_lin_iter, theta_init=p.theta_init,
-                    a_limit=p.a_limit, a_boost=p.a_boost, use_history=p.use_history)
+                    a_limit=p.a_limit, a_boost=p.a_boost, use_history=p.use_history,
+                    precond=p.precond)
 
 
 def _setup(N, Ra, n, seed, history, **kw):
@@ -333,3 +334,32 @@ def test_isolated_kernel_timing_leaves_the_state():
             cav.step(1)
             outs.append(cav.get(H.HOSC_U))
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("precision", [H.HOSC_FP64, H.HOSC_MIXED])
+def test_jacobi_row_scaling_one_step(precision):
+    """With Jacobi row scaling (not in the paper) a step still gives the oracle's step: to 1e-10
+    in FP64 (both solved to 1e-13 relative residual), and the increment to FP32 accuracy (2e-5
+    of its size) in mixed precision."""
+    N, Ra, n = 15, 1e4, 0.75
+    p = _params(N, Ra, n, dt=0.002, precond=1, precision=precision)
+    if precision == H.HOSC_MIXED:
+        p.lambda_ = min(p.lambda_, 0.1)
+    op = _oracle_params(p)
+    st = inputs.cavity_state(N, Ra, seed=315)
+    new, _ = O.step(dict(st, prev=None, steps=0), op, O.Grid(N))
+    with H.Cavity(p) as cav:
+        for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
+                            ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
+            cav.set(which, st[name])
+        info = cav.step(1)
+        assert info["call_status"] == 0
+        for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
+                            ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
+            got = cav.get(which)
+            if precision == H.HOSC_FP64:
+                assert _rel(got, new[name]) <= 1e-10, name
+            else:
+                inc = new[name] - st[name]
+                scale = max(np.max(np.abs(inc)), 1e-12)
+                assert np.max(np.abs((got - st[name]) - inc)) <= 2e-5 * scale + 1e-12, name

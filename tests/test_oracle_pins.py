@@ -274,6 +274,26 @@ def test_bicgstab_matches_direct_solve():
         np.testing.assert_allclose(a[key], b[key], rtol=0, atol=1e-10 * max(1.0, np.abs(b[key]).max()))
 
 
+def test_row_scaled_bicgstab_matches_direct_solve():
+    """Jacobi row scaling (each row and right-hand side over the row's diagonal) changes the
+    Krylov iteration, not the solution: the scaled BiCGSTAB step equals the unscaled direct
+    solve, on a state where the momentum diagonal varies from node to node (n = 0.7)."""
+    prm = O.Params(N=7, Ra=5e3, n=0.7, tol_lin=1e-13, precond=1)
+    g = O.Grid(7)
+    rng = np.random.default_rng(4)
+    st = O.initial_state(prm)
+    for key in ("u", "v", "w"):
+        f = np.zeros((7, 7, 7))
+        f[1:-1, 1:-1, 1:-1] = 3.0 * rng.standard_normal((5, 5, 5))
+        st[key] = f
+    st["th"] = O.apply_theta_bc(rng.random((7, 7, 7)))
+    a, info = O.step(st, prm, g)
+    b, _ = O.step(st, O.Params(N=7, Ra=5e3, n=0.7, tol_lin=1e-13), g, direct=True)
+    assert info["status"] == 0
+    for key in ("u", "v", "w", "th", "p"):
+        np.testing.assert_allclose(a[key], b[key], rtol=0, atol=1e-10 * max(1.0, np.abs(b[key]).max()))
+
+
 # ------------------------------------------------------------------ coupled-system invariants
 
 def test_conduction_fixed_point_ra0():
