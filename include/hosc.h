@@ -123,6 +123,12 @@ typedef struct {
                          system and its right-hand side divided by the row's diagonal before the
                          solve (same solution; the stopping test then measures the scaled
                          residual). Not in the paper. */
+  int inner_max;      /* 0 (default): one pressure correction per step. >= 1: while max|div V| >
+                         tol_div after the correction, up to inner_max inner pressure passes: E*
+                         again with the corrected pressure (level-n velocities and viscosity, the
+                         new temperature), u, v, w solved again from level n, div V, correction
+                         (Sec. 2.2's "previous pressure iteration"; theta is not solved again).
+                         Such steps are issued from the host (not captured); pools reject it. */
 } hosc_params;
 
 typedef struct {
@@ -133,6 +139,7 @@ typedef struct {
   double div_max;     /* max|div V^{n+1}| at interior nodes of the last step */
   double lin_res;     /* largest ||r_k|| / ||r_0|| of the last step's four solves */
   int status;         /* hosc_status of the last step */
+  long inner_passes;  /* inner pressure passes summed over the steps of this call */
 } hosc_info;
 
 typedef struct {

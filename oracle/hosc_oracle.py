@@ -85,7 +85,7 @@ class Params:
 
     def __init__(self, N, Ra, Pr=1.0, n=1.0, dt=0.02, lam=None, theta_ref=0.5, I2_eps=1e-10,
                  phi=1e-4, tol_div=1e-6, tol_lin=1e-12, max_lin_iter=2000, theta_init=0.5,
-                 a_limit=0.25, a_boost=1.0, use_history=1, precond=0):
+                 a_limit=0.25, a_boost=1.0, use_history=1, precond=0, inner_max=0):
         self.N = int(N)
         self.Ra = float(Ra)
         self.Pr = float(Pr)
@@ -106,6 +106,9 @@ class Params:
         # 1: Jacobi row scaling of each level-(n+1) system before BiCGSTAB (not in the paper;
         # the solution is the same, only the Krylov iteration changes)
         self.precond = int(precond)
+        # >= 1: up to this many inner pressure iterations per step (see step); 0: one pressure
+        # correction per step
+        self.inner_max = int(inner_max)
         self.theta_ref = float(theta_ref)
         self.theta_init = float(theta_init)
         self.I2_eps = float(I2_eps)
@@ -548,6 +551,26 @@ def step(state, prm, g=None, direct=False):
     p = state["p"].copy()
     if d_max > prm.tol_div:
         p = apply_pressure_bc(p - prm.lam * D)
+    # Inner pressure iterations (Sec. 2.2: the divergence is checked after the momentum equations
+    # are solved, and while it exceeds the tolerance the pressure of the previous pressure
+    # iteration is corrected; reading: the momentum systems are then solved again). Each pass
+    # recomputes E* from the level-n velocities and viscosity with the corrected pressure and the
+    # new temperature, solves u, v, w again from level n with the level-n operator, and corrects
+    # the pressure; theta is not solved again (its system does not involve the pressure).
+    inner = 0
+    while prm.inner_max and d_max > prm.tol_div and inner < prm.inner_max:
+        inner += 1
+        lev = level_coefficients(dict(state, th=new["th"], p=p), prm)
+        coefs = _system_coefficients(g, prm, lev, state["prev"] if prm.use_history else None)
+        for name in ("u", "v", "w"):
+            new[name], iters[name], st = solve_system(g, prm.dt, coefs[name], A_m, state[name],
+                                                      prm.tol_lin, prm.max_lin_iter,
+                                                      direct=direct, precond=prm.precond)
+            status = status or st
+        D = divergence(new["u"], new["v"], new["w"], h)
+        d_max = float(np.max(np.abs(D)))
+        if d_max > prm.tol_div:
+            p = apply_pressure_bc(p - prm.lam * D)
     res = max(float(np.max(np.abs(new[k] - state[k]))) for k in ("u", "v", "w", "th"))
     out = dict(u=new["u"], v=new["v"], w=new["w"], th=new["th"], p=p,
                prev=dict(L=lev["L"], u=state["u"], v=state["v"], w=state["w"], Eu=lev["Eu"],
@@ -555,7 +578,7 @@ def step(state, prm, g=None, direct=False):
                steps=state["steps"] + 1)
     if not all(np.all(np.isfinite(out[k])) for k in ("u", "v", "w", "th", "p")):
         status = 5
-    info = dict(res=res, div_max=d_max, iters=iters, status=status)
+    info = dict(res=res, div_max=d_max, iters=iters, status=status, inner=inner)
     return out, info
 
 

@@ -70,6 +70,7 @@ struct Ctx {
   double host_bytes[HOSC_K_COUNT] = {0};   // algorithmic bytes of the fixed-work kernels
   int kblock = 128, kz = 1, narrow = 0;    // tiles of the interleaved Krylov kernels
   int merged = 0;                          // two-kernel BiCGSTAB iteration (mixed precision)
+  int inner_last = 0;                      // inner pressure passes of the last step
   int sx = 0, sy = 0, skz = 0;             // staged stencil kernels (sx == 0: not used)
   // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
   // asynchronously into h_ring / h_ring_pos, completion marked by round_ev
@@ -94,6 +95,7 @@ hosc_status validate(const hosc_params* p) {
   if (p->use_history != 0 && p->use_history != 1) return HOSC_EINVAL;
   if (p->auto_defect != 0 && p->auto_defect != 1) return HOSC_EINVAL;
   if (p->precond != 0 && p->precond != 1) return HOSC_EINVAL;
+  if (p->inner_max < 0 || p->inner_max > 100000) return HOSC_EINVAL;
   if (p->precision != HOSC_FP64 && p->precision != HOSC_MIXED) return HOSC_EINVAL;
   return HOSC_OK;
 }
@@ -311,8 +313,7 @@ hosc_status check_launch() {
 }
 
 // BiCGSTAB on the four systems; the host checks the done flags every few iterations.
-hosc_status solve(Ctx* c) {
-  const DevParams& P = c->P;
+hosc_status solve_with(Ctx* c, const DevParams& P) {
   const Fields& F = c->F;
   launch_bicg_init(P, F, c->stream);
   c->launches += 1;
@@ -340,6 +341,43 @@ hosc_status solve(Ctx* c) {
     if (c->h_ks[0].done && c->h_ks[1].done && c->h_ks[2].done && c->h_ks[3].done) break;
     if (check < 16) check *= 2;
   }
+  return HOSC_OK;
+}
+
+hosc_status solve(Ctx* c) { return solve_with(c, c->P); }
+
+// S6-S8 with inner pressure passes: after the first correction, while max|div V| > tol_div
+// and fewer than inner_max passes ran, E* again with the corrected pressure, the momentum
+// systems solved again from level n (theta's system skipped), increments, div V, correction.
+hosc_status update_with_inner(Ctx* c) {
+  const Fields& F = c->F;
+  launch_update_fields(c->P, F, c->cur, c->stream);
+  c->launches += 5;
+  int k = 0;
+  for (;;) {
+    hosc_status st = check_launch();
+    if (st) return st;
+    CU(cudaMemcpyAsync(c->h_rec, F.rec, sizeof(StepRecord), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (!(c->h_rec->div_max > c->P.tol_div) || k >= c->prm.inner_max) break;
+    ++k;
+    DevParams Q = c->P;
+    Q.inner_pass = 1;
+    if (Q.sweep_fp32) {   // float copies of the new temperature and the corrected pressure
+      launch_shadow(Q, F, c->cur, 0, c->stream);
+      c->launches += 1;
+    }
+    launch_sources(Q, F, c->cur, c->stream);
+    launch_rhs(Q, F, c->cur, c->stream);
+    c->launches += 2;
+    st = solve_with(c, Q);
+    if (st) return st;
+    launch_update_fields(Q, F, c->cur, c->stream);
+    c->launches += 5;
+  }
+  launch_finish(c->P, F, c->stream);
+  c->launches += 1;
+  c->inner_last = k;
   return HOSC_OK;
 }
 
@@ -381,9 +419,15 @@ hosc_status run_stage(Ctx* c, int stage) {
       break;
     case HOSC_STAGE_UPDATE:
       prof_begin(c, HOSC_K_UPDATE);
-      launch_update(c->P, F, c->cur, c->stream);
+      c->inner_last = 0;
+      if (c->prm.inner_max > 0) {
+        st = update_with_inner(c);
+      } else {
+        launch_update(c->P, F, c->cur, c->stream);
+        c->launches += 6;
+      }
       prof_end(c, HOSC_K_UPDATE);
-      c->launches += 6;
+      if (st) return st;
       if (c->P.krylov_fp32) {   // mixed precision: float copies of the new level
         launch_shadow(c->P, F, 1 - c->cur, 0, c->stream);
         c->launches += 1;
@@ -497,6 +541,7 @@ hosc_status one_step(Ctx* c, hosc_info* info) {
   watch_stall(c, c->h_rec->res);
   if (info) {
     info->steps += 1;
+    info->inner_passes += c->inner_last;
     for (int s = 0; s < 4; ++s) info->lin_iters += c->h_rec->iters[s];
   }
   return (hosc_status)c->h_rec->status;
@@ -579,7 +624,9 @@ hosc_status capture_step(Ctx* c, cudaGraphExec_t* out) {
   return HOSC_OK;
 }
 
-bool graphs_usable(Ctx* c) { return c->graphs_ok && !c->prof_on && c->stage == 0; }
+bool graphs_usable(Ctx* c) {
+  return c->graphs_ok && !c->prof_on && c->stage == 0 && c->prm.inner_max == 0;
+}
 
 void drop_graphs(Ctx* c) {
   for (auto& a : c->graph)

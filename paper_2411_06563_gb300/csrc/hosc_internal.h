@@ -32,6 +32,7 @@ struct DevParams {
   double h, h2;      // grid spacing (h = k = l) and its square
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
   int precond;         // Jacobi row scaling of the level-(n+1) systems
+  int inner_pass;      // an inner pressure pass: momentum only (theta kept, its system skipped)
   double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (and div below tol_div)
                        // is steady (tol_steady * dt)
 };
@@ -53,6 +54,7 @@ struct StepRecord {
   int lin_status[4];
   int status;
   int pad;
+  double res_theta;  // max |theta^{n+1} - theta^n| (walls included), kept for inner passes
 };
 
 // Device arrays of one context. All N^3 doubles unless noted.
@@ -147,6 +149,9 @@ void launch_krylov_activate(const Fields& F, cudaStream_t s);
 void launch_loop_cond(const Fields& F, unsigned long long handle, cudaStream_t s);
 // S6-S8: increments, theta walls, div V, pressure correction and walls, step record.
 void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s);
+// The same without the step record (an inner pressure pass follows), and the record alone.
+void launch_update_fields(const DevParams& P, const Fields& F, int cur, cudaStream_t s);
+void launch_finish(const DevParams& P, const Fields& F, cudaStream_t s);
 // Re-arm the device control of a sequence of steps: run (halt = 0), no records yet, and stop at
 // the first steady step when stop_steady.
 void launch_arm(const Fields& F, int stop_steady, cudaStream_t s);

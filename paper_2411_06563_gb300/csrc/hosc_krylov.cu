@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kThreads) k_bicg_init(DevParams P, Fields F, i
         k.beta = 0.0;
         k.iters = 0;
         k.status = 0;
-        k.done = (k.r0norm == 0.0 || *F.halt) ? 1 : 0;
+        // an inner pressure pass solves the momentum systems only
+        k.done = (k.r0norm == 0.0 || *F.halt || (s == 3 && P.inner_pass)) ? 1 : 0;
       }
     }
   }
@@ -490,7 +491,8 @@ __global__ void __launch_bounds__(kThreads) k4_init(DevParams P, Fields F) {
         k.beta = 0.0;
         k.iters = 0;
         k.status = 0;
-        k.done = (k.r0norm == 0.0 || *F.halt) ? 1 : 0;
+        // an inner pressure pass solves the momentum systems only
+        k.done = (k.r0norm == 0.0 || *F.halt || (s == 3 && P.inner_pass)) ? 1 : 0;
       }
     }
   }
@@ -709,7 +711,8 @@ __global__ void __launch_bounds__(kThreads) k6_init(DevParams P, Fields F) {
         k.iters = 0;
         k.pad = 0;       // no x, r update applied yet
         k.status = 0;
-        k.done = (k.r0norm == 0.0 || *F.halt) ? 1 : 0;
+        // an inner pressure pass solves the momentum systems only
+        k.done = (k.r0norm == 0.0 || *F.halt || (s == 3 && P.inner_pass)) ? 1 : 0;
       }
     }
   }

@@ -234,6 +234,7 @@ hosc_status hosc_pool_admit(void* pool, const hosc_params* params, long max_step
   const size_t need = hosc_workspace_bytes(params);
   if (need == 0) return HOSC_EINVAL;
   if (need > P->budget) return HOSC_EINVAL;            // can never fit
+  if (params->inner_max != 0) return HOSC_EINVAL;      // members run captured steps only
   if (P->used + need > P->budget) return HOSC_ENOMEM;  // fits once others retire
   PCU(cudaSetDevice(P->device));
   hosc_params p = *params;

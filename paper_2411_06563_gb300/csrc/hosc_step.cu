@@ -400,12 +400,12 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0)
 template <class Ts>
 __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Fields F, int cur,
                                                               int nblocks) {
-  __shared__ double smem[32];
+  __shared__ double smem[64];
   if (*F.halt) return;
   const unsigned N = P.N;
   const unsigned n3 = N * N * N;
   const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
-  double m[1] = {0.0};
+  double m[2] = {0.0, 0.0};   // max |x| of u, v, w and of theta
   if (t < n3) {
     const unsigned q = t / N;
     const unsigned i = t - q * N, j = q % N, k = q / N;
@@ -428,18 +428,23 @@ __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Field
       F.v[1 - cur][t] = F.v[cur][t] + xv;
       F.w[1 - cur][t] = F.w[cur][t] + xw;
       F.th[t] += xt;
-      m[0] = fmax(fmax(absfin(xu), absfin(xv)), fmax(absfin(xw), absfin(xt)));
+      m[0] = fmax(fmax(absfin(xu), absfin(xv)), absfin(xw));
+      m[1] = absfin(xt);
     } else {
       F.u[1 - cur][t] = F.u[cur][t];
       F.v[1 - cur][t] = F.v[cur][t];
       F.w[1 - cur][t] = F.w[cur][t];
     }
   }
-  block_reduce<1, true>(m, smem);
-  if (publish_is_last<1>(m, F.red, F.counter)) {
-    double tot[1];
-    reduce_partials<1, true>(tot, F.red, nblocks, F.counter, smem);
-    if (threadIdx.x == 0) F.rec->res = tot[0];
+  block_reduce<2, true>(m, smem);
+  if (publish_is_last<2>(m, F.red, F.counter)) {
+    double tot[2];
+    reduce_partials<2, true>(tot, F.red, nblocks, F.counter, smem);
+    if (threadIdx.x == 0) {
+      // an inner pressure pass changes u, v, w only: theta's change stays that of the first pass
+      if (!P.inner_pass) F.rec->res_theta = tot[1];
+      F.rec->res = fmax(tot[0], F.rec->res_theta);
+    }
   }
 }
 
@@ -524,7 +529,10 @@ __global__ void __launch_bounds__(kThreads) k_theta_walls(DevParams P, Fields F,
   if (publish_is_last<1>(m, F.red, F.counter)) {
     double tot[1];
     reduce_partials<1, true>(tot, F.red, nblocks, F.counter, smem);
-    if (threadIdx.x == 0) F.rec->res = fmax(F.rec->res, tot[0]);
+    if (threadIdx.x == 0) {
+      F.rec->res = fmax(F.rec->res, tot[0]);
+      if (!P.inner_pass) F.rec->res_theta = fmax(F.rec->res_theta, tot[0]);
+    }
   }
 }
 
@@ -726,6 +734,15 @@ void launch_rhs(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
 }
 
 void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
+  launch_update_fields(P, F, cur, s);
+  launch_finish(P, F, s);
+}
+
+void launch_finish(const DevParams& P, const Fields& F, cudaStream_t s) {
+  k_finish_record<<<1, 32, 0, s>>>(P, F);
+}
+
+void launch_update_fields(const DevParams& P, const Fields& F, int cur, cudaStream_t s) {
   const long N = P.N, n3 = N * N * N, ni = N - 2;
   const int b_all = red_blocks(n3);
   if (P.krylov_fp32)
@@ -738,7 +755,6 @@ void launch_update(const DevParams& P, const Fields& F, int cur, cudaStream_t s)
   k_divergence<<<b_int, kThreads, 0, s>>>(P, F, 1 - cur, b_int);
   k_pressure_correct<<<b_int, kThreads, 0, s>>>(P, F);
   k_pressure_walls<<<red_blocks(n3 - ni * ni * ni), kThreads, 0, s>>>(P, F);
-  k_finish_record<<<1, 32, 0, s>>>(P, F);
 }
 
 }  // namespace hosc

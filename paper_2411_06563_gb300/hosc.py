@@ -42,19 +42,19 @@ class hosc_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("a_limit", ctypes.c_double), ("a_boost", ctypes.c_double),
                 ("use_history", ctypes.c_int), ("auto_defect", ctypes.c_int),
-                ("precond", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("inner_max", ctypes.c_int)]
 
 
 class hosc_info(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_long), ("lin_iters", ctypes.c_long),
                 ("last_iters", ctypes.c_int * 4), ("res_steady", ctypes.c_double),
                 ("div_max", ctypes.c_double), ("lin_res", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("inner_passes", ctypes.c_long)]
 
     def as_dict(self):
         return dict(steps=self.steps, lin_iters=self.lin_iters, last_iters=list(self.last_iters),
                     res=self.res_steady, div_max=self.div_max, lin_res=self.lin_res,
-                    status=self.status)
+                    status=self.status, inner_passes=self.inner_passes)
 
 
 class hosc_diag(ctypes.Structure):

@@ -46,7 +46,7 @@ def _oracle_params(p):
                     theta_ref=p.theta_ref, I2_eps=p.I2_eps, phi=p.phi, tol_div=p.tol_div,
                     tol_lin=p.tol_lin, max_lin_iter=p.max_lin_iter, theta_init=p.theta_init,
                     a_limit=p.a_limit, a_boost=p.a_boost, use_history=p.use_history,
-                    precond=p.precond)
+                    precond=p.precond, inner_max=p.inner_max)
 
 
 def _setup(N, Ra, n, seed, history, **kw):
@@ -363,3 +363,38 @@ def test_jacobi_row_scaling_one_step(precision):
                 inc = new[name] - st[name]
                 scale = max(np.max(np.abs(inc)), 1e-12)
                 assert np.max(np.abs((got - st[name]) - inc)) <= 2e-5 * scale + 1e-12, name
+
+
+def test_inner_pressure_passes_match_the_oracle():
+    """Inner pressure passes (Sec. 2.2's "previous pressure iteration": E* again with the
+    corrected pressure, u, v, w solved again, div V, correction) reproduce the oracle's step
+    in FP64 to 1e-10, with the same number of passes; the mixed path runs the same passes and
+    stays within 1e-4 of the FP64 step (relative to each field's change)."""
+    N, Ra, n = 13, 1e4, 0.75
+    st = inputs.cavity_state(N, Ra, seed=413)
+    names = (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W), ("th", H.HOSC_THETA),
+             ("p", H.HOSC_P))
+    out = {}
+    for precision in (H.HOSC_FP64, H.HOSC_MIXED):
+        p = _params(N, Ra, n, dt=0.002, inner_max=12, precision=precision)
+        p.lambda_ = min(p.lambda_, 0.1)
+        with H.Cavity(p) as cav:
+            for name, which in names:
+                cav.set(which, st[name])
+            info = cav.step(1)
+            assert info["call_status"] == 0
+            out[precision] = (info, {name: cav.get(which) for name, which in names})
+    op = _oracle_params(_params(N, Ra, n, dt=0.002, inner_max=12))
+    op.lam = min(op.lam, 0.1)
+    ref, rinfo = O.step(dict(st, prev=None, steps=0), op, O.Grid(N))
+    info64, f64 = out[H.HOSC_FP64]
+    assert info64["inner_passes"] == rinfo["inner"] > 0
+    for name, _ in names:
+        assert _rel(f64[name], ref[name]) <= 1e-10, name
+    infomx, fmx = out[H.HOSC_MIXED]
+    assert infomx["inner_passes"] == rinfo["inner"]
+    for name, _ in names:
+        scale = max(np.max(np.abs(f64[name] - st[name])), 1e-12)
+        assert np.max(np.abs(fmx[name] - f64[name])) <= 1e-4 * scale, name
+    with pytest.raises(H.HoscError):
+        H.Cavity(_params(N, Ra, n, inner_max=-1))
