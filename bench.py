@@ -38,6 +38,14 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum)
+# from an ncu capture of the same kernel build, workload and launch shape, summarised in
+# profiles/k4_pv_cavity101_mixed.md (isolated p/v launches: 137.8 MB read + 16.2 MB written).
+# Keyed by (workload, kernel class, threads per block, planes per thread, narrow); any other
+# configuration reports null.
+NCU_TRAFFIC = {("cavity101", "k_bicg_pv", 128, 9, 0): 154.0e6}
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -373,6 +381,9 @@ def main():
                     help="skip the timing of the solver variant outside the paper's method")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shape of the mixed-precision solve")
+    ap.add_argument("--tiles", default=None,
+                    help="launch shape of the mixed-precision solve as BLOCK,KZ,NARROW "
+                         "(instead of the autotuner)")
     ap.add_argument("--spinup", type=int, default=None,
                     help="untimed steps from rest before the warm-up (default: per workload)")
     ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "equal"],
@@ -433,7 +444,11 @@ def main():
         # warm-up steps
         info = cav.step(spinup)
         assert info["call_status"] == 0, info
-        if precision == "mixed" and not args.no_autotune:
+        if precision == "mixed" and args.tiles:
+            kb, kz, nr = (int(x) for x in args.tiles.split(","))
+            rc = H.hosc_set_tiles(cav.h, kb, kz, nr)
+            assert rc == 0, ("launch shape", args.tiles, rc)
+        elif precision == "mixed" and not args.no_autotune:
             rc, kb, kz, _ = H.hosc_autotune(cav.h, 5)
             assert rc == 0, rc
         cav.step(args.warmup)
@@ -534,6 +549,10 @@ def main():
              if mixed else None,
              "form": (("merged: 2 kernels per iteration" if H.hosc_get_krylov_merged(cav.h)
                        else "3 kernels per iteration") if mixed else None)}
+    traffic = None
+    if mixed:
+        t = shape["tiles"]
+        traffic = NCU_TRAFFIC.get((args.workload, dom, t["block"], t["kz"], t["narrow"]))
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cav, H, wl)
@@ -584,7 +603,7 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "single"},
             "gpu_launches": launches,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                         "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": peak_kind,
                          "share": d["ms"] / total_ms if total_ms else None},
             "kernels_alone": iso,

@@ -7,7 +7,8 @@
 * BiCGSTAB against a direct sparse LU solve;
 * the exact conduction fixed point at Ra = 0 (Nu = 1, E_total = 1, Be = 1);
 * centro- and z-mirror symmetry of the coupled step, hot/cold Nusselt balance and the sign and
-  range of the entropy quantities (Sec. 4.3).
+  range of the entropy quantities (Sec. 4.3);
+* the Newtonian Nusselt numbers printed in Table 2 (Sec. 3.2; fixture under tests/golden/).
 """
 
 import math
@@ -15,6 +16,7 @@ import math
 import numpy as np
 import pytest
 
+from golden_values import table
 from oracle import hosc_oracle as O
 
 
@@ -418,6 +420,12 @@ def test_steady_state_balance_entropy_and_certificate():
         assert np.all(d[key] >= 0.0)
     assert 0.0 < d["Be"] < 1.0
     assert np.all((d["Be_local"] >= 0.0) & (d["Be_local"] <= 1.0))
+    # The steady energy equation times theta, integrated over the cavity: the convective term
+    # integrates to zero (div V = 0, V = 0 on the walls) and the diffusive one to the wall flux
+    # weighted by theta, which only the hot wall (theta = 1) carries. So the integral of the
+    # heat-transfer entropy term |grad theta|^2 (Sec. 4.3) equals the hot-wall mean Nusselt
+    # number, up to the discretisation error (0.5 % here).
+    assert abs(d["Be"] * d["E_total"] - d["Nu_hot_mean"]) < 2e-2 * d["Nu_hot_mean"]
     assert np.max(np.abs(st["th"] + _mirror_all(st["th"]) - 1.0)) < 1e-10
     # the steady state does not depend on the pseudo-time step
     prm2 = O.Params(N=9, Ra=1e3, n=0.75, dt=0.005, lam=0.25 / 64 / 0.005, tol_lin=1e-11,
@@ -425,6 +433,9 @@ def test_steady_state_balance_entropy_and_certificate():
     st2, info2 = O.solve_steady(prm2, 8000, tol_steady=1e-9, g=g)
     for key in ("u", "v", "w", "th"):
         assert np.max(np.abs(st2[key] - st[key])) < 1e-5 * max(1.0, np.abs(st[key]).max())
+
+
+TABLE2 = {Ra: nu for Ra, nu in table("table2_newtonian_nu_max.txt")}
 
 
 def test_newtonian_limit_table2_ra1e3_coarse():
@@ -436,7 +447,7 @@ def test_newtonian_limit_table2_ra1e3_coarse():
     st, info = O.solve_steady(prm, 3000, tol_steady=1e-6, div_stop=np.inf)
     assert info["status"] == 0 and info["res"] < 1e-6
     d = O.diagnostics(st, prm)
-    assert d["Nu_hot_max"] == pytest.approx(1.098, rel=1e-2)
+    assert d["Nu_hot_max"] == pytest.approx(TABLE2[1e3], rel=1e-2)
     assert 1.0 < d["Nu_hot_mean"] < d["Nu_hot_max"]
     # steady heat balance: the flux through the mid-plane x = 1/2 matches the wall Nusselt number
     flux = _midplane_heat_flux(st, 1.0 / (N - 1))
@@ -445,9 +456,8 @@ def test_newtonian_limit_table2_ra1e3_coarse():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("Ra,expect,dt", [(1e3, 1.098, 0.02), (1e4, 2.256, 0.004),
-                                          (1e5, 4.638, 5e-4)])
-def test_newtonian_limit_table2_51(Ra, expect, dt):
+@pytest.mark.parametrize("Ra,dt", [(1e3, 0.02), (1e4, 0.004), (1e5, 5e-4)])
+def test_newtonian_limit_table2_51(Ra, dt):
     """Table 2 on its own grid (51^3, n = 1, Pr = 0.71): within 1.5 % of the printed values
     (the paper's own gap to the two cited benchmarks is up to 0.99 %)."""
     N = 51
@@ -456,4 +466,4 @@ def test_newtonian_limit_table2_51(Ra, expect, dt):
     st, info = O.solve_steady(prm, 200000, tol_steady=1e-6 * dt / 0.02, div_stop=np.inf)
     assert info["status"] == 0
     d = O.diagnostics(st, prm)
-    assert d["Nu_hot_max"] == pytest.approx(expect, rel=1.5e-2)
+    assert d["Nu_hot_max"] == pytest.approx(TABLE2[Ra], rel=1.5e-2)
