@@ -38,12 +38,13 @@ WORKLOADS = {
 }
 
 
-# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum)
-# from an ncu capture of the same kernel build, workload and launch shape, summarised in
-# profiles/k4_pv_cavity101_mixed.md (isolated p/v launches: 137.8 MB read + 16.2 MB written).
-# Keyed by (workload, kernel class, threads per block, planes per thread, narrow); any other
-# configuration reports null.
-NCU_TRAFFIC = {("cavity101", "k_bicg_pv", 128, 9, 0): 154.0e6}
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum,
+# mean of the captured launches) from ncu captures of the same kernel build, workload and launch
+# shape, summarised in profiles/k4_pv_cavity101_mixed.md. Keyed by (workload, kernel class,
+# threads per block, planes per thread, narrow); any other configuration reports null.
+NCU_TRAFFIC = {("cavity101", "k_bicg_pv", 128, 9, 0): 154.0e6,
+               ("cavity101", "k_bicg_pv", 256, 9, 0): 151.9e6,
+               ("cavity101", "k_bicg_pv", 384, 9, 0): 151.7e6}
 
 
 def _peaks():
