@@ -85,17 +85,23 @@ class Params:
 
     def __init__(self, N, Ra, Pr=1.0, n=1.0, dt=0.02, lam=None, theta_ref=0.5, I2_eps=1e-10,
                  phi=1e-4, tol_div=1e-6, tol_lin=1e-12, max_lin_iter=2000, theta_init=0.5,
-                 a_limit=0.25, a_boost=1.0, use_history=1, precond=0, inner_max=0):
+                 a_limit=0.25, a_boost=1.0, use_history=1, precond=0, inner_max=0, Ly=1.0,
+                 Lz=1.0):
         self.N = int(N)
+        # Box 1 x Ly x Lz (lengths in units of the hot-cold wall distance) on N nodes per side:
+        # spacings h = 1/(N-1), k = Ly/(N-1), l = Lz/(N-1) (the scheme of Sec. 2.2 is written
+        # for unequal spacings; the paper's cavity is the cube, Ly = Lz = 1)
+        self.Ly = float(Ly)
+        self.Lz = float(Lz)
         self.Ra = float(Ra)
         self.Pr = float(Pr)
         self.n = float(n)
         self.dt = float(dt)
-        h = 1.0 / (self.N - 1)
+        h = min(self.spacings())
         # Relaxation of the artificial-compressibility update (not given in the paper): the
-        # smaller of h^2/(4 dt) and Pr/10. Above h^2/dt the highest grid mode of the coupled
-        # update grows even at constant viscosity; at small dt the pressure mode needs lam below
-        # about twice the smallest Pr*eta.
+        # smaller of h^2/(4 dt) and Pr/10 (h the smallest spacing). Above h^2/dt the highest
+        # grid mode of the coupled update grows even at constant viscosity; at small dt the
+        # pressure mode needs lam below about twice the smallest Pr*eta.
         self.lam = float(min(0.25 * h * h / self.dt, 0.1 * self.Pr) if lam is None else lam)
         # Lower limit of M18 in units of L (reading R18); 0 disables the limiter.
         self.a_limit = float(a_limit)
@@ -116,6 +122,11 @@ class Params:
         self.tol_div = float(tol_div)
         self.tol_lin = float(tol_lin)
         self.max_lin_iter = int(max_lin_iter)
+
+    def spacings(self):
+        """(h, k, l): node spacings along x, y, z."""
+        m = self.N - 1
+        return 1.0 / m, self.Ly / m, self.Lz / m
 
 
 # --------------------------------------------------------------------------------- operators
@@ -140,16 +151,17 @@ def _d2(n, dx):
 
 
 class Grid:
-    """Uniform N^3 node grid of the unit cube and the central-difference operators of Eq. (2).
+    """Uniform N^3 node grid of the box 1 x Ly x Lz (spacings h, k, l along x, y, z; the unit
+    cube by default) and the central-difference operators of Eq. (2).
 
     Each 3D operator is an N^3 x N^3 sparse matrix acting on flattened fields. The row of a node
     is filled only where the node is interior along that operator's direction, so products such
     as delta_x^2 delta_y^2 are exact tensor-product stencils at every interior node.
     """
 
-    def __init__(self, N):
+    def __init__(self, N, Ly=1.0, Lz=1.0):
         self.N = N = int(N)
-        self.h = self.k = self.l = 1.0 / (N - 1)
+        self.h, self.k, self.l = 1.0 / (N - 1), Ly / (N - 1), Lz / (N - 1)
         eye = sp.identity(N, format="csr")
         kr = lambda a, b, c: sp.kron(a, sp.kron(b, c, format="csr"), format="csr")
         # flattened index = x + N*y + N*N*z  ->  kron(z-factor, y-factor, x-factor)
@@ -178,9 +190,16 @@ class Grid:
         self.int_idx = np.flatnonzero(interior.ravel())
         self.bnd_idx = np.flatnonzero(~interior.ravel())
         self.x = np.linspace(0.0, 1.0, N)
+        self.y = np.linspace(0.0, Ly, N)
+        self.z = np.linspace(0.0, Lz, N)
+
+    @classmethod
+    def of(cls, prm):
+        """The grid of a parameter set."""
+        return cls(prm.N, prm.Ly, prm.Lz)
 
     def coords(self):
-        z, y, x = np.meshgrid(self.x, self.x, self.x, indexing="ij")
+        z, y, x = np.meshgrid(self.z, self.y, self.x, indexing="ij")
         return x, y, z
 
 
@@ -228,13 +247,16 @@ def pseudo_time_mass(g, dt, c, kappa):
 
     The level-n operator B carries the compact correction (h^2/12)|G*|^2 delta^2 explicitly
     (inside alpha, beta, gamma); for the grid mode that alternates in all three directions the
-    level-(n+1) operator reduces to 6 dt/h^2 (its compact mass cancels), so that mode grows once
-    |G*|^2 h^2 > 24, and the mode alternating in one direction grows once dt |G*|^2 > 4 L.
-    sigma = kappa * max(0, dt (|G*|^2/6 - 1/h^2), dt |G*|^2/6 - 2 L/3) keeps both damped. It is
-    zero for well-resolved flows; A only sets the pseudo-time path, never the steady state.
+    level-(n+1) operator reduces to 2 dt S with S = 1/h^2 + 1/k^2 + 1/l^2 (its compact mass
+    cancels whatever the spacings), so that mode grows once |G*|^2 > 8 S (|G*|^2 h^2 > 24 on a
+    cubic grid), and the mode alternating in one direction grows once dt |G*|^2 > 4 L.
+    sigma = kappa * max(0, dt (|G*|^2/6 - S/3), dt |G*|^2/6 - 2 L/3) keeps both damped (S/3 =
+    1/h^2 on a cubic grid). It is zero for well-resolved flows; A only sets the pseudo-time
+    path, never the steady state.
     """
     G2 = c["G"] ** 2 + c["H"] ** 2 + c["I"] ** 2
-    sig = np.maximum(0.0, np.maximum(dt * (G2 / 6.0 - 1.0 / g.h ** 2), dt * G2 / 6.0 - 2.0 * c["L"] / 3.0))
+    S = 1.0 / g.h ** 2 + 1.0 / g.k ** 2 + 1.0 / g.l ** 2
+    sig = np.maximum(0.0, np.maximum(dt * (G2 / 6.0 - S / 3.0), dt * G2 / 6.0 - 2.0 * c["L"] / 3.0))
     return kappa * sig
 
 
@@ -384,13 +406,16 @@ def grad_full(f, axis, dx):
     return np.moveaxis(d, 0, axis)
 
 
-def strain_gradients(u, v, w, h):
-    """All nine velocity gradients at every node (keys 'ux', 'uy', ... ; reading R7)."""
+def strain_gradients(u, v, w, h, k=None, l=None):
+    """All nine velocity gradients at every node (keys 'ux', 'uy', ... ; reading R7); spacings
+    h, k, l along x, y, z (k = l = h when not given)."""
+    k = h if k is None else k
+    l = h if l is None else l
     out = {}
     for name, f in (("u", u), ("v", v), ("w", w)):
         out[name + "x"] = grad_full(f, 2, h)
-        out[name + "y"] = grad_full(f, 1, h)
-        out[name + "z"] = grad_full(f, 0, h)
+        out[name + "y"] = grad_full(f, 1, k)
+        out[name + "z"] = grad_full(f, 0, l)
     return out
 
 
@@ -402,8 +427,7 @@ def second_invariant(gr):
 
 def viscosity(u, v, w, prm):
     """Apparent viscosity eta = I2^((n-1)/2) (Eqs. 7-8) at every node, regularised (reading R1)."""
-    h = 1.0 / (prm.N - 1)
-    gr = strain_gradients(u, v, w, h)
+    gr = strain_gradients(u, v, w, *prm.spacings())
     I2 = second_invariant(gr)
     if prm.n == 1.0:
         eta = np.ones_like(I2)
@@ -431,9 +455,9 @@ def edge_from_diagonal(f):
 
 def momentum_sources(u, v, w, th, p, eta, gr, prm):
     """E* of the three momentum equations at every node (Sec. 2.2 coefficient list, reading R2)."""
-    h = 1.0 / (prm.N - 1)
-    ex, ey, ez = grad_full(eta, 2, h), grad_full(eta, 1, h), grad_full(eta, 0, h)
-    px, py, pz = grad_full(p, 2, h), grad_full(p, 1, h), grad_full(p, 0, h)
+    h, k, l = prm.spacings()
+    ex, ey, ez = grad_full(eta, 2, h), grad_full(eta, 1, k), grad_full(eta, 0, l)
+    px, py, pz = grad_full(p, 2, h), grad_full(p, 1, k), grad_full(p, 0, l)
     exx, eyy, ezz = gr["ux"], gr["vy"], gr["wz"]
     exy = 0.5 * (gr["uy"] + gr["vx"])
     exz = 0.5 * (gr["uz"] + gr["wx"])
@@ -472,12 +496,15 @@ def apply_pressure_bc(p):
     return p
 
 
-def divergence(u, v, w, h):
-    """Central div V at interior nodes (zero elsewhere)."""
+def divergence(u, v, w, h, k=None, l=None):
+    """Central div V at interior nodes (zero elsewhere); spacings h, k, l along x, y, z (k = l =
+    h when not given)."""
+    k = h if k is None else k
+    l = h if l is None else l
     D = np.zeros_like(u)
-    D[1:-1, 1:-1, 1:-1] = ((u[1:-1, 1:-1, 2:] - u[1:-1, 1:-1, :-2])
-                           + (v[1:-1, 2:, 1:-1] - v[1:-1, :-2, 1:-1])
-                           + (w[2:, 1:-1, 1:-1] - w[:-2, 1:-1, 1:-1])) / (2.0 * h)
+    D[1:-1, 1:-1, 1:-1] = ((u[1:-1, 1:-1, 2:] - u[1:-1, 1:-1, :-2]) / (2.0 * h)
+                           + (v[1:-1, 2:, 1:-1] - v[1:-1, :-2, 1:-1]) / (2.0 * k)
+                           + (w[2:, 1:-1, 1:-1] - w[:-2, 1:-1, 1:-1]) / (2.0 * l))
     return D
 
 
@@ -532,7 +559,7 @@ def step(state, prm, g=None, direct=False):
     3. theta wall update;  4. div V^{n+1}, artificial-compressibility pressure correction;
     5. steady-state change r_n = max over u, v, w, theta of |chi^{n+1} - chi^n|.
     """
-    g = g or Grid(prm.N)
+    g = g or Grid.of(prm)
     lev = level_coefficients(state, prm)
     coefs = _system_coefficients(g, prm, lev, state["prev"] if prm.use_history else None)
     A_m = assemble_A(g, prm.dt, coefs["u"], prm.a_limit, prm.a_boost)
@@ -545,8 +572,8 @@ def step(state, prm, g=None, direct=False):
                                                   precond=prm.precond)
         status = status or st
     new["th"] = apply_theta_bc(new["th"])
-    h = g.h
-    D = divergence(new["u"], new["v"], new["w"], h)
+    sp3 = (g.h, g.k, g.l)
+    D = divergence(new["u"], new["v"], new["w"], *sp3)
     d_max = float(np.max(np.abs(D)))
     p = state["p"].copy()
     if d_max > prm.tol_div:
@@ -567,7 +594,7 @@ def step(state, prm, g=None, direct=False):
                                                       prm.tol_lin, prm.max_lin_iter,
                                                       direct=direct, precond=prm.precond)
             status = status or st
-        D = divergence(new["u"], new["v"], new["w"], h)
+        D = divergence(new["u"], new["v"], new["w"], *sp3)
         d_max = float(np.max(np.abs(D)))
         if d_max > prm.tol_div:
             p = apply_pressure_bc(p - prm.lam * D)
@@ -586,7 +613,7 @@ def solve_steady(prm, max_steps, tol_steady=1e-6, state=None, g=None, callback=N
                  div_stop=None):
     """March to steady state: stop when r_n < tol_steady and max|div V| < div_stop
     (default tol_div)."""
-    g = g or Grid(prm.N)
+    g = g or Grid.of(prm)
     state = state or initial_state(prm)
     div_stop = prm.tol_div if div_stop is None else div_stop
     info = None
@@ -604,7 +631,7 @@ def solve_steady(prm, max_steps, tol_steady=1e-6, state=None, g=None, callback=N
 def steady_certificate(state, prm, g=None):
     """Steady residuals of a field set: max over the four systems of |B chi - R| at interior nodes
     (the dt-free fixed-point equation of Eq. 5) and max|div V|."""
-    g = g or Grid(prm.N)
+    g = g or Grid.of(prm)
     st = dict(state, prev=None)
     lev = level_coefficients(st, prm)
     coefs = _system_coefficients(g, prm, lev, None)
@@ -612,7 +639,7 @@ def steady_certificate(state, prm, g=None):
     for name in ("u", "v", "w", "th"):
         r = apply_B(g, coefs[name], state[name].ravel()) - coefs[name]["R"]
         worst = max(worst, float(np.max(np.abs(r[g.int_idx]))))
-    D = divergence(state["u"], state["v"], state["w"], g.h)
+    D = divergence(state["u"], state["v"], state["w"], g.h, g.k, g.l)
     return worst, float(np.max(np.abs(D)))
 
 
@@ -635,9 +662,12 @@ def diagnostics(state, prm):
     """Nusselt numbers (Sec. 4.2) and entropy generation / Bejan number (Sec. 4.3).
 
     Returns a dict: Nu_hot_local[z, y], Nu_avg_z[z], Nu_hot_max, Nu_hot_mean, Nu_cold_mean,
-    E_HT, E_FF, E_local (fields), E_total, E_HT_total, E_FF_total, Be, Be_local.
+    E_HT, E_FF, E_local (fields), E_total, E_HT_total, E_FF_total, Be, Be_local. On a box
+    1 x Ly x Lz the wall averages are over the wall (Nu_avg_z: mean over y; Nu_mean: over y and
+    z) and the entropy totals are integrals over the box volume.
     """
-    N, h = prm.N, 1.0 / (prm.N - 1)
+    N = prm.N
+    h, k, l = prm.spacings()
     th = state["th"]
     # fourth-order one-sided d theta/dx at x = 0 and x = 1 (reading R10)
     dth0 = (-25.0 * th[:, :, 0] + 48.0 * th[:, :, 1] - 36.0 * th[:, :, 2] + 16.0 * th[:, :, 3]
@@ -646,15 +676,17 @@ def diagnostics(state, prm):
             - 16.0 * th[:, :, -4] + 3.0 * th[:, :, -5]) / (12.0 * h)
     nu_hot = -dth0
     nu_cold = -dth1
-    wy = simpson_weights(N, h)
-    nu_avg_z = nu_hot @ wy
+    wx, wy, wz = simpson_weights(N, h), simpson_weights(N, k), simpson_weights(N, l)
+    area = prm.Ly * prm.Lz
+    nu_avg_z = nu_hot @ wy / prm.Ly
     out = dict(Nu_hot_local=nu_hot, Nu_avg_z=nu_avg_z, Nu_hot_max=float(np.max(nu_avg_z)),
-               Nu_hot_mean=float(wy @ nu_hot @ wy), Nu_cold_mean=float(wy @ nu_cold @ wy))
+               Nu_hot_mean=float(wz @ nu_hot @ wy) / area,
+               Nu_cold_mean=float(wz @ nu_cold @ wy) / area)
     eta, I2, _ = viscosity(state["u"], state["v"], state["w"], prm)
-    E_HT = grad_full(th, 2, h) ** 2 + grad_full(th, 1, h) ** 2 + grad_full(th, 0, h) ** 2
+    E_HT = grad_full(th, 2, h) ** 2 + grad_full(th, 1, k) ** 2 + grad_full(th, 0, l) ** 2
     E_FF = prm.phi * eta * I2
     E_loc = E_HT + E_FF
-    vol = lambda f: float(np.einsum("zyx,z,y,x->", f, wy, wy, wy))
+    vol = lambda f: float(np.einsum("zyx,z,y,x->", f, wz, wy, wx))
     t_ht, t_ff = vol(E_HT), vol(E_FF)
     be_loc = np.where(E_loc > 0.0, E_HT / np.where(E_loc > 0.0, E_loc, 1.0), 1.0)
     out.update(E_HT=E_HT, E_FF=E_FF, E_local=E_loc, E_HT_total=t_ht, E_FF_total=t_ff,

@@ -59,6 +59,42 @@ def test_mehrstellen_special_case():
     np.testing.assert_allclose(c["R"][ii], (E + h2 / 12.0 * lap)[ii], rtol=1e-13, atol=1e-12)
 
 
+def test_mehrstellen_unequal_spacings():
+    """The same special case with spacings h, k, l: the fourth-order compact 19-point Laplacian
+    for unequal mesh sizes. Centre (4/3)(1/h^2 + 1/k^2 + 1/l^2); x faces -1/h^2 + (h^2 + k^2)/
+    (6 h^2 k^2) + (h^2 + l^2)/(6 h^2 l^2) (and cyclically); xy edges -(h^2 + k^2)/(12 h^2 k^2)
+    (and cyclically); no corners. R = (1 + h^2/12 dx^2 + k^2/12 dy^2 + l^2/12 dz^2) E."""
+    N = 7
+    g = O.Grid(N, 0.6, 1.45)
+    h2, k2, l2 = g.h ** 2, g.k ** 2, g.l ** 2
+    one, zero = np.ones(N ** 3), np.zeros(N ** 3)
+    c = O.scalar_coefficients(g, 0.01, one, zero, zero, zero, zero, zero)
+    w = _stencil_of_B(g, c, (3, 3, 3))
+    sq = {0: h2, 1: k2, 2: l2}
+    expect = {(0, 0, 0): 4.0 / 3.0 * (1 / h2 + 1 / k2 + 1 / l2)}
+    for a in range(3):
+        b, c_ = (a + 1) % 3, (a + 2) % 3
+        face = -1 / sq[a] + (sq[a] + sq[b]) / (6 * sq[a] * sq[b]) + (sq[a] + sq[c_]) / (6 * sq[a] * sq[c_])
+        edge = -(sq[a] + sq[b]) / (12 * sq[a] * sq[b])
+        for s1 in (-1, 1):
+            off = [0, 0, 0]
+            off[a] = s1
+            expect[tuple(off)] = face
+            for s2 in (-1, 1):
+                off2 = [0, 0, 0]
+                off2[a], off2[b] = s1, s2
+                expect[tuple(off2)] = edge
+    scale = max(abs(v) for v in expect.values())
+    for off, val in w.items():
+        assert val == pytest.approx(expect.get(off, 0.0), abs=1e-12 * scale), off
+    rng = np.random.default_rng(2)
+    E = rng.standard_normal(N ** 3)
+    c = O.scalar_coefficients(g, 0.01, one, zero, zero, zero, zero, E)
+    corr = (h2 * (g.Dxx @ E) + k2 * (g.Dyy @ E) + l2 * (g.Dzz @ E)) / 12.0
+    ii = g.int_idx
+    np.testing.assert_allclose(c["R"][ii], (E + corr)[ii], rtol=1e-13, atol=1e-12)
+
+
 # ------------------------------------------------------------------ manufactured solution
 
 PI = math.pi
@@ -83,8 +119,8 @@ def _mms_fields(g, t, with_K=True):
     return chi, dict(L=L, G=G, H=H, I=I, K=K, E=E)
 
 
-def _mms_run(N, dt, T, with_K=True):
-    g = O.Grid(N)
+def _mms_run(N, dt, T, with_K=True, Ly=1.0, Lz=1.0):
+    g = O.Grid(N, Ly, Lz)
     steps = int(round(T / dt))
     chi, _ = _mms_fields(g, 0.0, with_K)
     chi = chi.reshape(N, N, N)
@@ -109,6 +145,16 @@ def test_mms_fourth_order_space(with_K):
     for N in (9, 17, 33):
         h = 1.0 / (N - 1)
         errs.append(_mms_run(N, 2.0 * h * h, 1.0 / 16.0, with_K))
+    order = math.log2(errs[1] / errs[2])
+    assert 3.6 < order < 4.6, (errs, order)
+
+
+def test_mms_fourth_order_space_unequal_spacings():
+    """The same on a box 1 x 0.8 x 1.25 (three different spacings): still fourth order."""
+    errs = []
+    for N in (9, 17, 33):
+        h = 1.0 / (N - 1)
+        errs.append(_mms_run(N, 2.0 * h * h, 1.0 / 16.0, True, 0.8, 1.25))
     order = math.log2(errs[1] / errs[2])
     assert 3.6 < order < 4.6, (errs, order)
 
@@ -142,12 +188,14 @@ def test_mms_second_order_time():
 
 # ------------------------------------------------------------------ printed weights of Eq. (6)
 
-def test_printed_stencil_weights_eq6():
+@pytest.mark.parametrize("Ly,Lz", [(1.0, 1.0), (0.7, 1.3)])
+def test_printed_stencil_weights_eq6(Ly, Lz):
     """Q = A - dt B from the operator composition must equal the expanded weights printed with
     Eq. (6) (readings: the operator missing in Q1/Q3 is a '+'; the N4, N5 terms change sign
-    between the +/- neighbours; '2l^h' is 2 l^2 h; h = k = l here)."""
+    between the +/- neighbours; '2l^h' is 2 l^2 h), on a cubic grid and with three different
+    spacings h, k, l (a box 1 x Ly x Lz)."""
     N, dt = 7, 0.013
-    g = O.Grid(N)
+    g = O.Grid(N, Ly, Lz)
     rng = np.random.default_rng(7)
     f = lambda s=1.0, o=0.0: o + s * rng.standard_normal(N ** 3)
     L, G, H, I, K, E = f(0.2, 1.3), f(), f(), f(), f(0.3), f()
@@ -164,7 +212,7 @@ def test_printed_stencil_weights_eq6():
     for off, b in wB.items():
         col = (i + off[0]) + N * ((j + off[1]) + N * (k + off[2]))
         Q[off] = Arow[col] - dt * b
-    h = k_ = l = g.h
+    h, k_, l = g.h, g.k, g.l
     at = lambda a: a[n0]
     Lc, Gc, Hc, Ic, Kc = at(L), at(G), at(H), at(I), at(K)
     Mx = -dt / (2 * Lc) + h * h / 12
@@ -323,12 +371,14 @@ def test_inner_pressure_iterations_reduce_the_divergence():
 
 # ------------------------------------------------------------------ coupled-system invariants
 
-def test_conduction_fixed_point_ra0():
+@pytest.mark.parametrize("Ly,Lz", [(1.0, 1.0), (0.5, 2.0)])
+def test_conduction_fixed_point_ra0(Ly, Lz):
     """Ra = 0: theta = 1 - x, V = 0, p = 0 is an exact discrete steady state; Nu = 1,
-    E_total = 1 and Be = 1 (Sec. 4.2-4.3 definitions applied to pure conduction)."""
+    E_total = the volume Ly Lz and Be = 1 (Sec. 4.2-4.3 definitions applied to pure
+    conduction), in the cube and in a box."""
     for n in (0.75, 1.0, 1.25):
-        prm = O.Params(N=9, Ra=0.0, n=n)
-        g = O.Grid(9)
+        prm = O.Params(N=9, Ra=0.0, n=n, Ly=Ly, Lz=Lz)
+        g = O.Grid.of(prm)
         st = O.initial_state(prm)
         x, _, _ = g.coords()
         st["th"] = 1.0 - x
@@ -339,8 +389,59 @@ def test_conduction_fixed_point_ra0():
         assert d["Nu_hot_max"] == pytest.approx(1.0, abs=1e-12)
         assert d["Nu_hot_mean"] == pytest.approx(1.0, abs=1e-12)
         assert d["Nu_cold_mean"] == pytest.approx(1.0, abs=1e-12)
-        assert d["E_total"] == pytest.approx(1.0, abs=1e-12)
+        assert d["E_total"] == pytest.approx(Ly * Lz, abs=1e-12)
         assert d["Be"] == pytest.approx(1.0, abs=1e-15)
+
+
+def test_box_gradients_sources_and_wall_averages():
+    """On a box 1 x Ly x Lz (spacings h, k, l) every difference formula of the coupled system
+    is exact on quadratics: the nine velocity gradients (central inside, one-sided at the walls),
+    div V, the pressure gradient in E* (n = 1: eta = 1, grad eta = 0), and the fourth-order
+    one-sided wall derivative of the Nusselt number. With theta = 1 - x + e y^2 z x (1 - x) the
+    wall averages have closed forms: Nu_local = 1 - e y^2 z on the hot wall, its mean over y is
+    1 - e z Ly^2/3 and over the wall 1 - e Ly^2 Lz/6 (cold wall: + instead of -); Simpson's rule
+    is exact on them. A spacing taken along the wrong axis fails here."""
+    N, Ly, Lz, e = 9, 0.6, 1.4, 0.3
+    prm = O.Params(N=N, Ra=7.0, Pr=0.8, n=1.0, Ly=Ly, Lz=Lz)
+    g = O.Grid.of(prm)
+    x, y, z = g.coords()
+    rng = np.random.default_rng(5)
+    def quad():
+        a = rng.standard_normal(10)
+        f = (a[0] + a[1] * x + a[2] * y + a[3] * z + a[4] * x * x + a[5] * y * y + a[6] * z * z
+             + a[7] * x * y + a[8] * y * z + a[9] * z * x)
+        fx = a[1] + 2 * a[4] * x + a[7] * y + a[9] * z
+        fy = a[2] + 2 * a[5] * y + a[7] * x + a[8] * z
+        fz = a[3] + 2 * a[6] * z + a[8] * y + a[9] * x
+        return f, fx, fy, fz
+    (u, ux, uy, uz), (v, vx, vy, vz), (w, wx, wy, wz) = quad(), quad(), quad()
+    gr = O.strain_gradients(u, v, w, g.h, g.k, g.l)
+    exact = dict(ux=ux, uy=uy, uz=uz, vx=vx, vy=vy, vz=vz, wx=wx, wy=wy, wz=wz)
+    for key, val in exact.items():
+        np.testing.assert_allclose(gr[key], val, rtol=0, atol=1e-11, err_msg=key)
+    D = O.divergence(u, v, w, g.h, g.k, g.l)
+    ii = g.interior
+    np.testing.assert_allclose(D[ii], (ux + vy + wz)[ii], rtol=0, atol=1e-11)
+    p, px, py, pz = quad()
+    th = rng.random((N, N, N))
+    eta, _, gr = O.viscosity(u, v, w, prm)
+    Eu, Ev, Ew = O.momentum_sources(u, v, w, th, p, eta, gr, prm)
+    np.testing.assert_allclose(Eu, -px / prm.Pr, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(Ev, -py / prm.Pr + prm.Ra * (th - prm.theta_ref), rtol=0, atol=1e-10)
+    np.testing.assert_allclose(Ew, -pz / prm.Pr, rtol=0, atol=1e-10)
+    th = 1.0 - x + e * y * y * z * x * (1.0 - x)
+    z0 = np.zeros((N, N, N))
+    d = O.diagnostics(dict(u=z0, v=z0, w=z0, th=th), prm)
+    zs = g.z
+    np.testing.assert_allclose(d["Nu_hot_local"], 1.0 - e * y[:, :, 0] ** 2 * z[:, :, 0], atol=1e-12)
+    np.testing.assert_allclose(d["Nu_avg_z"], 1.0 - e * zs * Ly ** 2 / 3.0, atol=1e-12)
+    assert d["Nu_hot_max"] == pytest.approx(1.0, abs=1e-12)
+    assert d["Nu_hot_mean"] == pytest.approx(1.0 - e * Ly ** 2 * Lz / 6.0, abs=1e-12)
+    assert d["Nu_cold_mean"] == pytest.approx(1.0 + e * Ly ** 2 * Lz / 6.0, abs=1e-12)
+    tx = -1.0 + e * y * y * z * (1.0 - 2.0 * x)
+    ty = 2.0 * e * y * z * x * (1.0 - x)
+    tz = e * y * y * x * (1.0 - x)
+    np.testing.assert_allclose(d["E_HT"], tx ** 2 + ty ** 2 + tz ** 2, rtol=0, atol=1e-11)
 
 
 def test_conduction_reached_from_rest_ra0():
@@ -355,14 +456,15 @@ def _mirror_all(f):
     return f[::-1, ::-1, ::-1]
 
 
-@pytest.mark.parametrize("n", [0.75, 1.0, 1.25])
-def test_centro_and_z_symmetry_of_the_step(n):
+@pytest.mark.parametrize("n,Ly,Lz", [(0.75, 1.0, 1.0), (1.0, 1.0, 1.0), (1.25, 1.0, 1.0),
+                                     (0.75, 0.7, 1.6)])
+def test_centro_and_z_symmetry_of_the_step(n, Ly, Lz):
     """With theta_ref = 1/2 the coupled step maps a centro-symmetric state (theta + theta' = 1,
     V = -V', p = p' about the cavity centre) to a centro-symmetric state, and a z-mirror-symmetric
-    state (w odd, the rest even in z) to a z-mirror-symmetric state."""
+    state (w odd, the rest even in z) to a z-mirror-symmetric state; in the cube and in a box."""
     N = 9
-    prm = O.Params(N=N, Ra=5e3, n=n)
-    g = O.Grid(N)
+    prm = O.Params(N=N, Ra=5e3, n=n, Ly=Ly, Lz=Lz)
+    g = O.Grid.of(prm)
     rng = np.random.default_rng(11)
     # build a state with both symmetries
     base = {}
