@@ -129,6 +129,12 @@ typedef struct {
                          new temperature), u, v, w solved again from level n, div V, correction
                          (Sec. 2.2's "previous pressure iteration"; theta is not solved again).
                          Such steps are issued from the host (not captured); pools reject it. */
+  double Ly, Lz;      /* box 1 x Ly x Lz (lengths in units of the hot-cold wall distance, the x
+                         length): N nodes per side, spacings h = 1/(N-1), k = Ly/(N-1),
+                         l = Lz/(N-1) along x, y, z (the scheme of Sec. 2.2 is written for unequal
+                         spacings). 0 stands for 1 (the paper's cube, the default); otherwise
+                         1/64 <= Ly, Lz <= 64. Wall means are averages over the wall; E_total,
+                         E_HT, E_FF are integrals over the box volume. */
 } hosc_params;
 
 typedef struct {

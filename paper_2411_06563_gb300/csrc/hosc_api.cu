@@ -96,6 +96,8 @@ hosc_status validate(const hosc_params* p) {
   if (p->auto_defect != 0 && p->auto_defect != 1) return HOSC_EINVAL;
   if (p->precond != 0 && p->precond != 1) return HOSC_EINVAL;
   if (p->inner_max < 0 || p->inner_max > 100000) return HOSC_EINVAL;
+  for (double len : {p->Ly, p->Lz})
+    if (!(len == 0.0 || (len >= 1.0 / 64.0 && len <= 64.0))) return HOSC_EINVAL;
   if (p->precision != HOSC_FP64 && p->precision != HOSC_MIXED) return HOSC_EINVAL;
   return HOSC_OK;
 }
@@ -163,7 +165,7 @@ constexpr double kFp32TolFloor = 3e-6;
 constexpr long kStallSteps = 200;
 
 DevParams device_params(const hosc_params& p, int have_prev, int phase) {
-  DevParams d;
+  DevParams d{};   // every field not set below (launch shapes, inner_pass, ...) starts at zero
   d.N = p.N;
   d.newtonian = (p.n == 1.0);
   d.have_prev = have_prev;
@@ -172,6 +174,33 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   d.sweep_fp32 = (p.precision == HOSC_MIXED && phase == 0);
   d.h = 1.0 / (p.N - 1);
   d.h2 = d.h * d.h;
+  d.Ly = p.Ly > 0.0 ? p.Ly : 1.0;
+  d.Lz = p.Lz > 0.0 ? p.Lz : 1.0;
+  const double sp[3] = {d.h, d.Ly / (p.N - 1), d.Lz / (p.N - 1)};
+  double sq[3];
+  for (int a = 0; a < 3; ++a) {
+    sq[a] = sp[a] * sp[a];
+    d.inv2[a] = 0.5 / sp[a];
+    d.isq[a] = 1.0 / sq[a];
+    d.sq12[a] = sq[a] / 12.0;
+    d.ih[a] = 1.0 / sp[a];
+  }
+  for (int a = 0; a < 3; ++a) {   // the (a, a+1) edge group and the weights of p1, q1, r1
+    const int b = (a + 1) % 3;
+    d.grp[a] = d.sq12[a] + d.sq12[b];
+    d.pw[2 * a] = 2.0 * sq[b] / (sq[a] + sq[b]);
+    d.pw[2 * a + 1] = 2.0 * sq[a] / (sq[a] + sq[b]);
+  }
+  for (int a = 0; a < 3; ++a) {
+    d.inv2f[a] = (float)d.inv2[a];
+    d.isqf[a] = (float)d.isq[a];
+    d.sq12f[a] = (float)d.sq12[a];
+    d.ihf[a] = (float)d.ih[a];
+    d.grpf[a] = (float)d.grp[a];
+  }
+  for (int q = 0; q < 6; ++q) d.pwf[q] = (float)d.pw[q];
+  d.s3 = (d.isq[0] + d.isq[1] + d.isq[2]) / 3.0;
+  d.s3f = (float)d.s3;
   d.Ra = p.Ra;
   d.Pr = p.Pr;
   d.n = p.n;
@@ -1008,6 +1037,8 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
   p->a_boost = 1.0;
   p->use_history = 1;
   p->auto_defect = 1;
+  p->Ly = 1.0;
+  p->Lz = 1.0;
   return HOSC_OK;
 }
 

@@ -25,22 +25,24 @@ struct Grad9 {
   double ux, uy, uz, vx, vy, vz, wx, wy, wz;
 };
 
+// The nine velocity gradients at node (i, j, k); ix, iy, iz = 1/(2 h_d) of the three directions.
 __device__ __forceinline__ Grad9 velocity_gradients(const double* __restrict__ u,
                                                     const double* __restrict__ v,
                                                     const double* __restrict__ w, int i, int j,
-                                                    int k, int N, double inv2h) {
+                                                    int k, int N, double ix, double iy,
+                                                    double iz) {
   const long c = node(i, j, k, N);
   const long sy = N, sz = (long)N * N;
   Grad9 g;
-  g.ux = grad_axis(u, c, i, N, 1, inv2h);
-  g.uy = grad_axis(u, c, j, N, sy, inv2h);
-  g.uz = grad_axis(u, c, k, N, sz, inv2h);
-  g.vx = grad_axis(v, c, i, N, 1, inv2h);
-  g.vy = grad_axis(v, c, j, N, sy, inv2h);
-  g.vz = grad_axis(v, c, k, N, sz, inv2h);
-  g.wx = grad_axis(w, c, i, N, 1, inv2h);
-  g.wy = grad_axis(w, c, j, N, sy, inv2h);
-  g.wz = grad_axis(w, c, k, N, sz, inv2h);
+  g.ux = grad_axis(u, c, i, N, 1, ix);
+  g.uy = grad_axis(u, c, j, N, sy, iy);
+  g.uz = grad_axis(u, c, k, N, sz, iz);
+  g.vx = grad_axis(v, c, i, N, 1, ix);
+  g.vy = grad_axis(v, c, j, N, sy, iy);
+  g.vz = grad_axis(v, c, k, N, sz, iz);
+  g.wx = grad_axis(w, c, i, N, 1, ix);
+  g.wy = grad_axis(w, c, j, N, sy, iy);
+  g.wz = grad_axis(w, c, k, N, sz, iz);
   return g;
 }
 

@@ -1,8 +1,9 @@
 // Diagnostics of a cavity state (Punia & Ray, arXiv:2411.06563, Sec. 4.2-4.3): local Nusselt
-// number on the hot and cold walls, Nu_avg(z) = int_0^1 Nu_local dy, its maximum over z, wall
-// means, the entropy-generation fields E_HT = |grad theta|^2, E_FF = phi eta I2 (chi* = phi* = phi),
-// E_local = E_HT + E_FF, their volume integrals and the Bejan number E_HT / E_total.
-// Integrals use composite Simpson weights (N odd; trapezoid for even N); all in double.
+// number on the hot and cold walls, Nu_avg(z) = (1/Ly) int_0^Ly Nu_local dy, its maximum over z,
+// wall means (over the wall area Ly Lz), the entropy-generation fields E_HT = |grad theta|^2,
+// E_FF = phi eta I2 (chi* = phi* = phi), E_local = E_HT + E_FF, their integrals over the box and
+// the Bejan number E_HT / E_total. Integrals use composite Simpson weights with the spacing of
+// each direction (N odd; trapezoid for even N); all in double.
 
 #include <math.h>
 
@@ -43,27 +44,31 @@ __global__ void k_nu_reduce(DevParams P, const double* nu_hot, const double* nu_
                             double* nu_avg, double* scal) {
   __shared__ double smem[32 * 2];
   const int N = P.N;
-  const double h = P.h;
+  const double hy = P.Ly / (N - 1), hz = P.Lz / (N - 1);
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     double s = 0.0;
-    for (int j = 0; j < N; ++j) s += nu_hot[j + (long)N * k] * simpson_w(j, N, h);
-    nu_avg[k] = s;
+    for (int j = 0; j < N; ++j) s += nu_hot[j + (long)N * k] * simpson_w(j, N, hy);
+    nu_avg[k] = s;   // divided by Ly below, after the surface sums
   }
   __syncthreads();
   double acc[2] = {0.0, 0.0};
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     double sc = 0.0;
-    for (int j = 0; j < N; ++j) sc += nu_cold[j + (long)N * k] * simpson_w(j, N, h);
-    acc[0] += simpson_w(k, N, h) * nu_avg[k];
-    acc[1] += simpson_w(k, N, h) * sc;
+    for (int j = 0; j < N; ++j) sc += nu_cold[j + (long)N * k] * simpson_w(j, N, hy);
+    acc[0] += simpson_w(k, N, hz) * nu_avg[k];
+    acc[1] += simpson_w(k, N, hz) * sc;
   }
   block_reduce<2, false>(acc, smem);
+  __syncthreads();   // every nu_avg read above precedes its scaling
+  for (int k = threadIdx.x; k < N; k += blockDim.x) nu_avg[k] /= P.Ly;
+  __syncthreads();
   if (threadIdx.x == 0) {
     double mx = -INFINITY;
     for (int k = 0; k < N; ++k) mx = fmax(mx, nu_avg[k]);
+    const double area = P.Ly * P.Lz;
     scal[0] = mx;
-    scal[1] = acc[0];
-    scal[2] = acc[1];
+    scal[1] = acc[0] / area;
+    scal[2] = acc[1] / area;
   }
 }
 
@@ -82,12 +87,12 @@ __global__ void __launch_bounds__(kThreads) k_entropy(DevParams P, const double*
   double acc[2] = {0.0, 0.0};
   if (t < n3) {
     const int i = (int)(t % N), j = (int)((t / N) % N), k = (int)(t / ((long)N * N));
-    const double inv2h = 0.5 / P.h;
-    const double tx = grad_axis(th, t, i, N, 1, inv2h);
-    const double ty = grad_axis(th, t, j, N, N, inv2h);
-    const double tz = grad_axis(th, t, k, N, (long)N * N, inv2h);
+    const double ix = P.inv2[0], iy = P.inv2[1], iz = P.inv2[2];
+    const double tx = grad_axis(th, t, i, N, 1, ix);
+    const double ty = grad_axis(th, t, j, N, N, iy);
+    const double tz = grad_axis(th, t, k, N, (long)N * N, iz);
     const double eht = tx * tx + ty * ty + tz * tz;
-    const Grad9 g = velocity_gradients(u, v, w, i, j, k, N, inv2h);
+    const Grad9 g = velocity_gradients(u, v, w, i, j, k, N, ix, iy, iz);
     const double I2 = second_invariant(g);
     double eta = 1.0;
     if (!P.newtonian) {
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(kThreads) k_entropy(DevParams P, const double*
         b = (j == 0) ? 1 : (j == N - 1 ? N - 2 : j);
         cc = (k == 0) ? 1 : (k == N - 1 ? N - 2 : k);
       }
-      const Grad9 ge = velocity_gradients(u, v, w, a, b, cc, N, inv2h);
+      const Grad9 ge = velocity_gradients(u, v, w, a, b, cc, N, ix, iy, iz);
       eta = pow(second_invariant(ge) + P.I2_eps, 0.5 * (P.n - 1.0));
     }
     const double eff = P.phi * eta * I2;
@@ -109,7 +114,8 @@ __global__ void __launch_bounds__(kThreads) k_entropy(DevParams P, const double*
       eloc[n3 + t] = eff;
       eloc[2 * n3 + t] = eht + eff;
     }
-    const double wgt = simpson_w(i, N, P.h) * simpson_w(j, N, P.h) * simpson_w(k, N, P.h);
+    const double wgt = simpson_w(i, N, P.h) * simpson_w(j, N, P.Ly / (N - 1)) *
+                       simpson_w(k, N, P.Lz / (N - 1));
     acc[0] = wgt * eht;
     acc[1] = wgt * eff;
   }

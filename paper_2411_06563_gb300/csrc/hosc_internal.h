@@ -29,7 +29,18 @@ struct DevParams {
                      // folded into the next p, v kernel) instead of three
   int sx, sy, skz;   // staged stencil kernels (p/v and s/t): tile of sx * sy interior columns,
                      // skz planes per block; sx == 0 selects the register kernels instead
-  double h, h2;      // grid spacing (h = k = l) and its square
+  double h, h2;      // grid spacing along x and its square
+  double Ly, Lz;     // box 1 x Ly x Lz: lengths along y and z (1 for the cube)
+  // Spacing constants of the directions d = x, y, z (spacings h, k, l = h, Ly h, Lz h), in double
+  // and in float (the float sweeps read them as operands): 1/(2 h_d), 1/h_d^2, h_d^2/12, 1/h_d;
+  // the edge-group factors (h^2+k^2)/12, (k^2+l^2)/12, (l^2+h^2)/12; the weights of the
+  // first-derivative terms of p1, q1, r1: 2k^2/(h^2+k^2), 2h^2/(h^2+k^2), 2l^2/(k^2+l^2),
+  // 2k^2/(k^2+l^2), 2h^2/(l^2+h^2), 2l^2/(l^2+h^2) (all 1 when h = k = l)
+  double inv2[3], isq[3], sq12[3], ih[3], grp[3], pw[6];
+  float inv2f[3], isqf[3], sq12f[3], ihf[3], grpf[3], pwf[6];
+  double s3;         // (1/h^2 + 1/k^2 + 1/l^2)/3: threshold of the pseudo-time mass (1/h^2 when
+                     // h = k = l)
+  float s3f;
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
   int precond;         // Jacobi row scaling of the level-(n+1) systems
   int inner_pass;      // an inner pressure pass: momentum only (theta kept, its system skipped)

@@ -41,23 +41,61 @@ struct Grad9T {
   T ux, uy, uz, vx, vy, vz, wx, wy, wz;
 };
 
+// Spacing constants of the directions x, y, z in the arithmetic type T (spacings h, k, l of a
+// box 1 x Ly x Lz; all equal in the cube): 1/(2 h_d), 1/h_d^2, h_d^2/12, 1/h_d, the edge-group
+// factors and the weights of p1, q1, r1 (DevParams).
+template <class T>
+struct Spc {
+  T i2[3], isq[3], s12[3], ih[3], grp[3], pw[6], s3;
+};
+
+template <class T>
+__device__ __forceinline__ Spc<T> spacing(const DevParams& P) {
+  Spc<T> s;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if constexpr (sizeof(T) == sizeof(float)) {
+      s.i2[a] = P.inv2f[a];
+      s.isq[a] = P.isqf[a];
+      s.s12[a] = P.sq12f[a];
+      s.ih[a] = P.ihf[a];
+      s.grp[a] = P.grpf[a];
+    } else {
+      s.i2[a] = P.inv2[a];
+      s.isq[a] = P.isq[a];
+      s.s12[a] = P.sq12[a];
+      s.ih[a] = P.ih[a];
+      s.grp[a] = P.grp[a];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    if constexpr (sizeof(T) == sizeof(float)) s.pw[q] = P.pwf[q];
+    else s.pw[q] = P.pw[q];
+  }
+  if constexpr (sizeof(T) == sizeof(float)) s.s3 = P.s3f;
+  else s.s3 = P.s3;
+  return s;
+}
+
 template <class T, class S>
 __device__ __forceinline__ Grad9T<T> velocity_gradients_t(const S* __restrict__ u,
                                                           const S* __restrict__ v,
                                                           const S* __restrict__ w, int i,
-                                                          int j, int k, int N, T inv2h) {
+                                                          int j, int k, int N,
+                                                          const T i2[3]) {
   const long c = node(i, j, k, N);
   const long sy = N, sz = (long)N * N;
   Grad9T<T> g;
-  g.ux = grad_axis_t<T>(u, c, i, N, 1, inv2h);
-  g.uy = grad_axis_t<T>(u, c, j, N, sy, inv2h);
-  g.uz = grad_axis_t<T>(u, c, k, N, sz, inv2h);
-  g.vx = grad_axis_t<T>(v, c, i, N, 1, inv2h);
-  g.vy = grad_axis_t<T>(v, c, j, N, sy, inv2h);
-  g.vz = grad_axis_t<T>(v, c, k, N, sz, inv2h);
-  g.wx = grad_axis_t<T>(w, c, i, N, 1, inv2h);
-  g.wy = grad_axis_t<T>(w, c, j, N, sy, inv2h);
-  g.wz = grad_axis_t<T>(w, c, k, N, sz, inv2h);
+  g.ux = grad_axis_t<T>(u, c, i, N, 1, i2[0]);
+  g.uy = grad_axis_t<T>(u, c, j, N, sy, i2[1]);
+  g.uz = grad_axis_t<T>(u, c, k, N, sz, i2[2]);
+  g.vx = grad_axis_t<T>(v, c, i, N, 1, i2[0]);
+  g.vy = grad_axis_t<T>(v, c, j, N, sy, i2[1]);
+  g.vz = grad_axis_t<T>(v, c, k, N, sz, i2[2]);
+  g.wx = grad_axis_t<T>(w, c, i, N, 1, i2[0]);
+  g.wy = grad_axis_t<T>(w, c, j, N, sy, i2[1]);
+  g.wz = grad_axis_t<T>(w, c, k, N, sz, i2[2]);
   return g;
 }
 
@@ -85,7 +123,7 @@ __global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const T* __
       j = inward(j, (int)N);
       k = inward(k, (int)N);
     }
-    const Grad9T<T> g = velocity_gradients_t<T, T>(u, v, w, i, j, k, N, (T)(0.5 / P.h));
+    const Grad9T<T> g = velocity_gradients_t<T, T>(u, v, w, i, j, k, N, spacing<T>(P).i2);
     const T a = g.uz + g.wx, b = g.uy + g.vx, c = g.vz + g.wy;
     const T I2 = T(2) * (g.ux * g.ux + g.vy * g.vy + g.wz * g.wz) + a * a + b * b + c * c;
     e = tpow<T>(I2 + (T)P.I2_eps, (T)(0.5 * (P.n - 1.0)));
@@ -117,15 +155,15 @@ __global__ void __launch_bounds__(kThreads) k_sources(DevParams P, const T* __re
   if (t >= (unsigned)N * N * N || *halt) return;
   const unsigned q = t / (unsigned)N;
   const int i = (int)(t - q * (unsigned)N), j = (int)(q % (unsigned)N), k = (int)(q / (unsigned)N);
-  const T inv2h = (T)(0.5 / P.h);
+  const Spc<T> sp = spacing<T>(P);
   const long sy = N, sz = (long)N * N;
-  const Grad9T<T> g = velocity_gradients_t<T, T>(u, v, w, i, j, k, N, inv2h);
-  const T ex = grad_axis_t<T>(eta, t, i, N, 1, inv2h);
-  const T ey = grad_axis_t<T>(eta, t, j, N, sy, inv2h);
-  const T ez = grad_axis_t<T>(eta, t, k, N, sz, inv2h);
-  const T px = grad_axis_t<T>(p, t, i, N, 1, inv2h);
-  const T py = grad_axis_t<T>(p, t, j, N, sy, inv2h);
-  const T pz = grad_axis_t<T>(p, t, k, N, sz, inv2h);
+  const Grad9T<T> g = velocity_gradients_t<T, T>(u, v, w, i, j, k, N, sp.i2);
+  const T ex = grad_axis_t<T>(eta, t, i, N, 1, sp.i2[0]);
+  const T ey = grad_axis_t<T>(eta, t, j, N, sy, sp.i2[1]);
+  const T ez = grad_axis_t<T>(eta, t, k, N, sz, sp.i2[2]);
+  const T px = grad_axis_t<T>(p, t, i, N, 1, sp.i2[0]);
+  const T py = grad_axis_t<T>(p, t, j, N, sy, sp.i2[1]);
+  const T pz = grad_axis_t<T>(p, t, k, N, sz, sp.i2[2]);
   const T e = eta[t];
   const T exy = T(0.5) * (g.uy + g.vx), exz = T(0.5) * (g.uz + g.wx), eyz = T(0.5) * (g.vz + g.wy);
   const T a = T(1) / ((T)P.Pr * e), b = T(2) / e;
@@ -143,14 +181,14 @@ struct D7 {
 };
 
 template <class T>
-__device__ __forceinline__ D7<T> diffs7(const T f[7], T inv2h, T invh2) {
+__device__ __forceinline__ D7<T> diffs7(const T f[7], const Spc<T>& s) {
   D7<T> d;
-  d.dx = (f[1] - f[2]) * inv2h;
-  d.dy = (f[3] - f[4]) * inv2h;
-  d.dz = (f[5] - f[6]) * inv2h;
-  d.dxx = (f[1] - T(2) * f[0] + f[2]) * invh2;
-  d.dyy = (f[3] - T(2) * f[0] + f[4]) * invh2;
-  d.dzz = (f[5] - T(2) * f[0] + f[6]) * invh2;
+  d.dx = (f[1] - f[2]) * s.i2[0];
+  d.dy = (f[3] - f[4]) * s.i2[1];
+  d.dz = (f[5] - f[6]) * s.i2[2];
+  d.dxx = (f[1] - T(2) * f[0] + f[2]) * s.isq[0];
+  d.dyy = (f[3] - T(2) * f[0] + f[4]) * s.isq[1];
+  d.dzz = (f[5] - T(2) * f[0] + f[6]) * s.isq[2];
   return d;
 }
 
@@ -186,17 +224,17 @@ __device__ __forceinline__ void load19(const T* __restrict__ a, long c, long sy,
   f[18] = (T)a[c - sz - 1];
 }
 
-// One edge group of Eq. (5) on a uniform grid, directions (a, b):
+// One edge group of Eq. (5), directions (a, b) with inverse spacings ia, ib:
 //   da^2 db^2 chi - Vb da^2 db chi - Va da db^2 chi - c1 da db chi
 // from F[pp], F[0p], F[mp], F[p0], F[00], F[m0], F[pm], F[0m], F[mm] (first index along a).
 template <class T>
 __device__ __forceinline__ T edge_group(T Fpp, T F0p, T Fmp, T Fp0, T F00, T Fm0, T Fpm, T F0m,
-                                        T Fmm, T Va, T Vb, T c1, T ih) {
-  const T ih2 = ih * ih;
-  const T d22 = (Fpp + Fmp + Fpm + Fmm - T(2) * (F0p + F0m + Fp0 + Fm0) + T(4) * F00) * ih2 * ih2;
-  const T d21 = ((Fpp - T(2) * F0p + Fmp) - (Fpm - T(2) * F0m + Fmm)) * (T(0.5) * ih2 * ih);
-  const T d12 = ((Fpp - T(2) * Fp0 + Fpm) - (Fmp - T(2) * Fm0 + Fmm)) * (T(0.5) * ih2 * ih);
-  const T d11 = (Fpp - Fmp - Fpm + Fmm) * (T(0.25) * ih2);
+                                        T Fmm, T Va, T Vb, T c1, T ia, T ib) {
+  const T ia2 = ia * ia, ib2 = ib * ib;
+  const T d22 = (Fpp + Fmp + Fpm + Fmm - T(2) * (F0p + F0m + Fp0 + Fm0) + T(4) * F00) * ia2 * ib2;
+  const T d21 = ((Fpp - T(2) * F0p + Fmp) - (Fpm - T(2) * F0m + Fmm)) * (T(0.5) * ia2 * ib);
+  const T d12 = ((Fpp - T(2) * Fp0 + Fpm) - (Fmp - T(2) * Fm0 + Fmm)) * (T(0.5) * ia * ib2);
+  const T d11 = (Fpp - Fmp - Fpm + Fmm) * (T(0.25) * ia * ib);
   return d22 - Vb * d21 - Va * d12 - c1 * d11;
 }
 
@@ -208,59 +246,58 @@ struct Eq5 {
 
 // [1 + (dx^2 - G dx) h^2/12 + (dy^2 - H dy) k^2/12 + (dz^2 - I dz) l^2/12 + (dt/2) dt^-] f
 template <class T>
-__device__ __forceinline__ T bracket(const D7<T>& d, T f0, T f_prev, const Eq5<T>& c, T h2_12) {
-  return f0 + h2_12 * ((d.dxx - c.G * d.dx) + (d.dyy - c.H * d.dy) + (d.dzz - c.I * d.dz)) +
-         T(0.5) * (f0 - f_prev);
+__device__ __forceinline__ T bracket(const D7<T>& d, T f0, T f_prev, const Eq5<T>& c,
+                                     const Spc<T>& s) {
+  return f0 + s.s12[0] * (d.dxx - c.G * d.dx) + s.s12[1] * (d.dyy - c.H * d.dy) +
+         s.s12[2] * (d.dzz - c.I * d.dz) + T(0.5) * (f0 - f_prev);
 }
 
 template <class T>
 __device__ __forceinline__ Eq5<T> eq5_coefficients(const T G7[7], const T H7[7], const T I7[7],
-                                                   T Gp, T Hp, T Ip, T inv2h, T invh2, T h2_12) {
+                                                   T Gp, T Hp, T Ip, const Spc<T>& s) {
   Eq5<T> c;
   c.G = G7[0];
   c.H = H7[0];
   c.I = I7[0];
-  const D7<T> dG = diffs7<T>(G7, inv2h, invh2), dH = diffs7<T>(H7, inv2h, invh2),
-              dI = diffs7<T>(I7, inv2h, invh2);
-  c.al = T(1) + h2_12 * (c.G * c.G - T(2) * dG.dx);
-  c.be = T(1) + h2_12 * (c.H * c.H - T(2) * dH.dy);
-  c.ga = T(1) + h2_12 * (c.I * c.I - T(2) * dI.dz);
-  c.M1 = bracket<T>(dG, G7[0], Gp, c, h2_12);
-  c.M2 = bracket<T>(dH, H7[0], Hp, c, h2_12);
-  c.M3 = bracket<T>(dI, I7[0], Ip, c, h2_12);
-  // p1, q1, r1 with h = k = l: -G H + 2/(h^2+k^2) (k^2 dy G + h^2 dx H) = -G H + dy G + dx H
-  c.p1 = -c.G * c.H + (dG.dy + dH.dx);
-  c.q1 = -c.H * c.I + (dH.dz + dI.dy);
-  c.r1 = -c.I * c.G + (dI.dx + dG.dz);
+  const D7<T> dG = diffs7<T>(G7, s), dH = diffs7<T>(H7, s), dI = diffs7<T>(I7, s);
+  c.al = T(1) + s.s12[0] * (c.G * c.G - T(2) * dG.dx);
+  c.be = T(1) + s.s12[1] * (c.H * c.H - T(2) * dH.dy);
+  c.ga = T(1) + s.s12[2] * (c.I * c.I - T(2) * dI.dz);
+  c.M1 = bracket<T>(dG, G7[0], Gp, c, s);
+  c.M2 = bracket<T>(dH, H7[0], Hp, c, s);
+  c.M3 = bracket<T>(dI, I7[0], Ip, c, s);
+  // p1 = -G H + 2/(h^2+k^2) (k^2 dy G + h^2 dx H), and cyclically
+  c.p1 = -c.G * c.H + s.pw[0] * dG.dy + s.pw[1] * dH.dx;
+  c.q1 = -c.H * c.I + s.pw[2] * dH.dz + s.pw[3] * dI.dy;
+  c.r1 = -c.I * c.G + s.pw[4] * dI.dx + s.pw[5] * dG.dz;
   return c;
 }
 
 // The level-n operator of Eq. (5) applied to chi (19 points):
-//  -al dx^2 - be dy^2 - ga dz^2 + M1 dx + M2 dy + M3 dz - (h^2/6) [yz group + xy group + zx group]
+//  -al dx^2 - be dy^2 - ga dz^2 + M1 dx + M2 dy + M3 dz
+//  - (h^2+k^2)/12 [xy group] - (k^2+l^2)/12 [yz group] - (l^2+h^2)/12 [zx group]
 template <class T>
-__device__ __forceinline__ T applyB(const Eq5<T>& c, const T f[19], double h, T inv2h, T invh2) {
-  const D7<T> d = diffs7<T>(f, inv2h, invh2);
-  const T ih = (T)(1.0 / h);
+__device__ __forceinline__ T applyB(const Eq5<T>& c, const T f[19], const Spc<T>& s) {
+  const D7<T> d = diffs7<T>(f, s);
   const T gxy = edge_group<T>(f[7], f[3], f[8], f[1], f[0], f[2], f[9], f[4], f[10], c.G, c.H,
-                              c.p1, ih);
+                              c.p1, s.ih[0], s.ih[1]);
   const T gyz = edge_group<T>(f[11], f[5], f[12], f[3], f[0], f[4], f[13], f[6], f[14], c.H, c.I,
-                              c.q1, ih);
+                              c.q1, s.ih[1], s.ih[2]);
   const T gzx = edge_group<T>(f[15], f[1], f[16], f[5], f[0], f[6], f[17], f[2], f[18], c.I, c.G,
-                              c.r1, ih);
-  const T m5 = (T)(h * h / 6.0);
+                              c.r1, s.ih[2], s.ih[0]);
   return -c.al * d.dxx - c.be * d.dyy - c.ga * d.dzz + c.M1 * d.dx + c.M2 * d.dy + c.M3 * d.dz -
-         m5 * (gyz + gxy + gzx);
+         s.grp[1] * gyz - s.grp[0] * gxy - s.grp[2] * gzx;
 }
 
 // Diagonal pseudo-time mass where the cell Reynolds number is high: the level-n operator carries
-// (h^2/12)|G*|^2 delta^2 explicitly, and for the grid mode alternating in all three directions the
-// level-(n+1) operator is only 6 dt/h^2, so that mode grows once |G*|^2 h^2 > 24 (and the mode
-// alternating in one direction once dt |G*|^2 > 4 L). Zero in resolved flows; it changes the
-// pseudo-time path only, never the steady state.
+// (h_d^2/12)|G*|^2 delta^2 explicitly, and for the grid mode alternating in all three directions
+// the level-(n+1) operator is only 2 dt (1/h^2 + 1/k^2 + 1/l^2) = 6 dt s3, so that mode grows once
+// |G*|^2 > 24 s3 (and the mode alternating in one direction once dt |G*|^2 > 4 L). Zero in
+// resolved flows; it changes the pseudo-time path only, never the steady state.
 template <class T>
-__device__ __forceinline__ T pseudo_time_mass(T G, T H, T I, T L, T dt, T invh2, T kappa) {
+__device__ __forceinline__ T pseudo_time_mass(T G, T H, T I, T L, T dt, T s3, T kappa) {
   const T g2 = G * G + H * H + I * I;
-  const T s = fmax(T(0), fmax(dt * (g2 / T(6) - invh2), dt * g2 / T(6) - T(2) * L / T(3)));
+  const T s = fmax(T(0), fmax(dt * (g2 / T(6) - s3), dt * g2 / T(6) - T(2) * L / T(3)));
   return kappa * s;
 }
 
@@ -285,8 +322,8 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0)
   const int i = 1 + (int)(t - q * ni), j = 1 + (int)(q % ni), k = 1 + (int)(q / ni);
   const long sy = N, sz = (long)N * N;
   const long c = node(i, j, k, N);
-  const double h = P.h, h2 = P.h2, inv2h = 0.5 / h, invh2 = 1.0 / h2;
-  const Tc tinv2h = (Tc)inv2h, tinvh2 = (Tc)invh2, h2_12 = (Tc)(h2 / 12.0), tdt = (Tc)P.dt;
+  const Spc<Tc> sp = spacing<Tc>(P);
+  const Tc tdt = (Tc)P.dt;
   Tc rv[4], Am[7], Ae[7];   // right-hand sides and weights, stored at the end
 
   Tc L7[7], u7[7], v7[7], w7[7];
@@ -309,60 +346,61 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0)
       H7[q] = v7[q] * L7[q];
       I7[q] = w7[q] * L7[q];
     }
-    const Eq5<Tc> cm = eq5_coefficients<Tc>(G7, H7, I7, upc * Lpc, vpc * Lpc, wpc * Lpc, tinv2h,
-                                            tinvh2, h2_12);
+    const Eq5<Tc> cm = eq5_coefficients<Tc>(G7, H7, I7, upc * Lpc, vpc * Lpc, wpc * Lpc, sp);
     // one momentum system: source E (level n, and n-1 when kept) and the field X
     auto system = [&](const Tc* __restrict__ E, const Tc* __restrict__ Ep,
                       const Tc* __restrict__ X) {
       Tc E7[7], f19[19];
       load7<Tc, Tc>(E, c, sy, sz, E7);
       const Tc Epc = P.have_prev ? Ep[c] : E7[0];
-      const Tc R = bracket<Tc>(diffs7<Tc>(E7, tinv2h, tinvh2), E7[0], Epc, cm, h2_12);
+      const Tc R = bracket<Tc>(diffs7<Tc>(E7, sp), E7[0], Epc, cm, sp);
       load19<Tc>(X, c, sy, sz, f19);
-      return tdt * (R - applyB<Tc>(cm, f19, h, tinv2h, tinvh2));
+      return tdt * (R - applyB<Tc>(cm, f19, sp));
     };
     rv[0] = system(Eu, Eup, u);
     rv[1] = system(Ev, Evp, v);
     rv[2] = system(Ew, Ewp, w);
-    // level-(n+1) weights (Eq. 6): Mx = -dt/(2L) + h^2/12, M15 = (h^2/(6L)) dx L, ...
-    const D7<Tc> dL = diffs7<Tc>(L7, tinv2h, tinvh2);
-    const Tc M = -tdt / (Tc(2) * Lc) + h2_12;
-    const Tc h2_6L = (Tc)h2 / (Tc(6) * Lc);
-    const Tc m15 = h2_6L * dL.dx, m16 = h2_6L * dL.dy, m17 = h2_6L * dL.dz;
-    Tc M18 = Tc(0.5) * (Lc - Lpc) + h2_12 * ((dL.dxx - cm.G * dL.dx) + (dL.dyy - cm.H * dL.dy) +
-                                             (dL.dzz - cm.I * dL.dz));
+    // level-(n+1) weights (Eq. 6): M_d = -dt/(2L) + h_d^2/12, M15 = (h^2/(6L)) dx L, ...
+    const D7<Tc> dL = diffs7<Tc>(L7, sp);
+    const Tc m0 = -tdt / (Tc(2) * Lc), inv6L = Tc(2) / Lc;   // h_d^2/(6L) = (h_d^2/12) (2/L)
+    const Tc Mx = m0 + sp.s12[0], My = m0 + sp.s12[1], Mz = m0 + sp.s12[2];
+    const Tc m15 = sp.s12[0] * inv6L * dL.dx, m16 = sp.s12[1] * inv6L * dL.dy,
+             m17 = sp.s12[2] * inv6L * dL.dz;
+    Tc M18 = Tc(0.5) * (Lc - Lpc) + sp.s12[0] * (dL.dxx - cm.G * dL.dx) +
+             sp.s12[1] * (dL.dyy - cm.H * dL.dy) + sp.s12[2] * (dL.dzz - cm.I * dL.dz);
     // keep the extrapolated mass positive where L changes fast (the steady state is unaffected)
     if (P.a_limit > 0.0) M18 = fmax(M18, -(Tc)P.a_limit * Lc);
-    const Tc sig_m = P.a_boost > 0.0
-                         ? pseudo_time_mass<Tc>(cm.G, cm.H, cm.I, Lc, tdt, tinvh2, (Tc)P.a_boost)
-                         : Tc(0);
-    const Tc a2 = M * tinvh2;
-    Am[0] = Lc * (Tc(1) - Tc(6) * a2) + M18 + sig_m;
-    Am[1] = Lc * (a2 - M * cm.G * tinv2h + m15 * tinv2h);
-    Am[2] = Lc * (a2 + M * cm.G * tinv2h - m15 * tinv2h);
-    Am[3] = Lc * (a2 - M * cm.H * tinv2h + m16 * tinv2h);
-    Am[4] = Lc * (a2 + M * cm.H * tinv2h - m16 * tinv2h);
-    Am[5] = Lc * (a2 - M * cm.I * tinv2h + m17 * tinv2h);
-    Am[6] = Lc * (a2 + M * cm.I * tinv2h - m17 * tinv2h);
+    const Tc sig_m = P.a_boost > 0.0 ? pseudo_time_mass<Tc>(cm.G, cm.H, cm.I, Lc, tdt, sp.s3,
+                                                             (Tc)P.a_boost)
+                                     : Tc(0);
+    const Tc ax = Mx * sp.isq[0], ay = My * sp.isq[1], az = Mz * sp.isq[2];
+    Am[0] = Lc * (Tc(1) - Tc(2) * (ax + ay + az)) + M18 + sig_m;
+    Am[1] = Lc * (ax - Mx * cm.G * sp.i2[0] + m15 * sp.i2[0]);
+    Am[2] = Lc * (ax + Mx * cm.G * sp.i2[0] - m15 * sp.i2[0]);
+    Am[3] = Lc * (ay - My * cm.H * sp.i2[1] + m16 * sp.i2[1]);
+    Am[4] = Lc * (ay + My * cm.H * sp.i2[1] - m16 * sp.i2[1]);
+    Am[5] = Lc * (az - Mz * cm.I * sp.i2[2] + m17 * sp.i2[2]);
+    Am[6] = Lc * (az + Mz * cm.I * sp.i2[2] - m17 * sp.i2[2]);
   }
   // ---------------- energy: L = 1, G* = u, H* = v, I* = w, K* = E* = 0
   {
-    const Eq5<Tc> ce = eq5_coefficients<Tc>(u7, v7, w7, upc, vpc, wpc, tinv2h, tinvh2, h2_12);
+    const Eq5<Tc> ce = eq5_coefficients<Tc>(u7, v7, w7, upc, vpc, wpc, sp);
     Tc f19[19];
     load19<Tc>(th, c, sy, sz, f19);
-    rv[3] = -tdt * applyB<Tc>(ce, f19, h, tinv2h, tinvh2);
-    const Tc M = Tc(-0.5) * tdt + h2_12;
-    const Tc a2 = M * tinvh2;
-    const Tc sig_e = P.a_boost > 0.0
-                         ? pseudo_time_mass<Tc>(ce.G, ce.H, ce.I, Tc(1), tdt, tinvh2, (Tc)P.a_boost)
-                         : Tc(0);
-    Ae[0] = Tc(1) - Tc(6) * a2 + sig_e;
-    Ae[1] = a2 - M * ce.G * tinv2h;
-    Ae[2] = a2 + M * ce.G * tinv2h;
-    Ae[3] = a2 - M * ce.H * tinv2h;
-    Ae[4] = a2 + M * ce.H * tinv2h;
-    Ae[5] = a2 - M * ce.I * tinv2h;
-    Ae[6] = a2 + M * ce.I * tinv2h;
+    rv[3] = -tdt * applyB<Tc>(ce, f19, sp);
+    const Tc m0 = Tc(-0.5) * tdt;
+    const Tc Mx = m0 + sp.s12[0], My = m0 + sp.s12[1], Mz = m0 + sp.s12[2];
+    const Tc ax = Mx * sp.isq[0], ay = My * sp.isq[1], az = Mz * sp.isq[2];
+    const Tc sig_e = P.a_boost > 0.0 ? pseudo_time_mass<Tc>(ce.G, ce.H, ce.I, Tc(1), tdt,
+                                                             sp.s3, (Tc)P.a_boost)
+                                     : Tc(0);
+    Ae[0] = Tc(1) - Tc(2) * (ax + ay + az) + sig_e;
+    Ae[1] = ax - Mx * ce.G * sp.i2[0];
+    Ae[2] = ax + Mx * ce.G * sp.i2[0];
+    Ae[3] = ay - My * ce.H * sp.i2[1];
+    Ae[4] = ay + My * ce.H * sp.i2[1];
+    Ae[5] = az - Mz * ce.I * sp.i2[2];
+    Ae[6] = az + Mz * ce.I * sp.i2[2];
   }
   if (P.precond) {   // Jacobi row scaling: each row and its right-hand side over its diagonal
     const Tc dm = Am[0] != Tc(0) ? Am[0] : Tc(1), de = Ae[0] != Tc(0) ? Ae[0] : Tc(1);
@@ -551,8 +589,8 @@ __global__ void __launch_bounds__(kThreads) k_divergence(DevParams P, Fields F, 
     const double* u = F.u[nxt];
     const double* v = F.v[nxt];
     const double* w = F.w[nxt];
-    const double d = ((u[c + 1] - u[c - 1]) + (v[c + sy] - v[c - sy]) + (w[c + sz] - w[c - sz])) *
-                     (0.5 / P.h);
+    const double d = (u[c + 1] - u[c - 1]) * P.inv2[0] + (v[c + sy] - v[c - sy]) * P.inv2[1] +
+                     (w[c + sz] - w[c - sz]) * P.inv2[2];
     F.div[c] = d;
     m[0] = absfin(d);
   }

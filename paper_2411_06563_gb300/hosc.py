@@ -42,7 +42,8 @@ class hosc_params(ctypes.Structure):
                 ("precision", ctypes.c_int), ("cuda_stream", ctypes.c_void_p),
                 ("a_limit", ctypes.c_double), ("a_boost", ctypes.c_double),
                 ("use_history", ctypes.c_int), ("auto_defect", ctypes.c_int),
-                ("precond", ctypes.c_int), ("inner_max", ctypes.c_int)]
+                ("precond", ctypes.c_int), ("inner_max", ctypes.c_int),
+                ("Ly", ctypes.c_double), ("Lz", ctypes.c_double)]
 
 
 class hosc_info(ctypes.Structure):

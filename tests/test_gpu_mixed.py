@@ -29,16 +29,21 @@ def _params(N, Ra, n, dt, precision, **kw):
     return p
 
 
-@pytest.mark.parametrize("N,Ra,n", [(13, 1e4, 0.75), (22, 2e3, 1.0), (17, 5e3, 1.25)])
-def test_one_step_from_seeded_state(N, Ra, n):
+@pytest.mark.parametrize("N,Ra,n,Ly,Lz", [(13, 1e4, 0.75, 1.0, 1.0), (22, 2e3, 1.0, 1.0, 1.0),
+                                           (17, 5e3, 1.25, 1.0, 1.0), (17, 5e3, 0.75, 0.7, 1.5)])
+def test_one_step_from_seeded_state(N, Ra, n, Ly, Lz):
     """One mixed step against the oracle's FP64 step from a seeded (far from steady) state: the
-    increment chi^{n+1} - chi^n agrees to FP32 accuracy, 2e-5 relative to its size."""
+    increment chi^{n+1} - chi^n agrees to FP32 accuracy, 2e-5 relative to its size in the cube.
+    The FP32 solve stops at a relative residual of 3e-6, and the error of the increment is that
+    residual times the operator's conditioning, which the unequal spacings of a box raise (here
+    k : l = 1 : 2.1): 5e-5 there (2.5e-5 measured)."""
+    tol = 2e-5 if (Ly, Lz) == (1.0, 1.0) else 5e-5
     dt = 0.002
-    p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-12)
+    p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-12, Ly=Ly, Lz=Lz)
     op = O.Params(N=N, Ra=Ra, n=n, dt=dt, lam=p.lambda_, tol_lin=1e-12, a_limit=p.a_limit,
-                  a_boost=p.a_boost)
+                  a_boost=p.a_boost, Ly=Ly, Lz=Lz)
     st = inputs.cavity_state(N, Ra, seed=100 + N)
-    g = O.Grid(N)
+    g = O.Grid.of(op)
     new, _ = O.step(dict(st, prev=None, steps=0), op, g)
     with H.Cavity(p) as cav:
         for name, which in FIELDS:
@@ -49,7 +54,7 @@ def test_one_step_from_seeded_state(N, Ra, n):
             got = cav.get(which)
             inc_ref = new[name] - st[name]
             scale = max(np.max(np.abs(inc_ref)), 1e-12)
-            assert np.max(np.abs((got - st[name]) - inc_ref)) <= 2e-5 * scale + 1e-12, name
+            assert np.max(np.abs((got - st[name]) - inc_ref)) <= tol * scale + 1e-12, name
 
 
 def _steady(p, max_steps):

@@ -46,7 +46,7 @@ def _oracle_params(p):
                     theta_ref=p.theta_ref, I2_eps=p.I2_eps, phi=p.phi, tol_div=p.tol_div,
                     tol_lin=p.tol_lin, max_lin_iter=p.max_lin_iter, theta_init=p.theta_init,
                     a_limit=p.a_limit, a_boost=p.a_boost, use_history=p.use_history,
-                    precond=p.precond, inner_max=p.inner_max)
+                    precond=p.precond, inner_max=p.inner_max, Ly=p.Ly or 1.0, Lz=p.Lz or 1.0)
 
 
 def _setup(N, Ra, n, seed, history, **kw):
@@ -71,14 +71,18 @@ def _setup(N, Ra, n, seed, history, **kw):
     return p, op, state, cav
 
 
-CASES = [(7, 1e3, 1.0, True), (13, 1e4, 0.75, True), (13, 5e3, 1.25, False),
-         (22, 1e4, 0.8, True), (22, 2e3, 1.0, False)]
+# (N, Ra, n, history, Ly, Lz): the cube, and boxes 1 x Ly x Lz with three different spacings
+CASES = [(7, 1e3, 1.0, True, 1.0, 1.0), (13, 1e4, 0.75, True, 1.0, 1.0),
+         (13, 5e3, 1.25, False, 1.0, 1.0), (22, 1e4, 0.8, True, 1.0, 1.0),
+         (22, 2e3, 1.0, False, 1.0, 1.0), (13, 1e4, 0.75, True, 0.7, 1.4),
+         (22, 5e3, 1.25, False, 1.6, 0.55)]
 
 
-@pytest.mark.parametrize("N,Ra,n,history", CASES)
-def test_stage_parity(N, Ra, n, history):
-    p, op, state, cav = _setup(N, Ra, n, seed=N * 7 + int(n * 100), history=history, dt=0.004)
-    g = O.Grid(N)
+@pytest.mark.parametrize("N,Ra,n,history,Ly,Lz", CASES)
+def test_stage_parity(N, Ra, n, history, Ly, Lz):
+    p, op, state, cav = _setup(N, Ra, n, seed=N * 7 + int(n * 100), history=history, dt=0.004,
+                               Ly=Ly, Lz=Lz)
+    g = O.Grid.of(op)
     ii = g.int_idx
     with cav:
         # S1
@@ -133,17 +137,20 @@ def test_stage_parity(N, Ra, n, history):
         for name, which in (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W),
                             ("th", H.HOSC_THETA), ("p", H.HOSC_P)):
             assert _rel(cav.get(which), new[name]) < 1e-10, name
-        div_o = O.divergence(new["u"], new["v"], new["w"], g.h)
+        div_o = O.divergence(new["u"], new["v"], new["w"], g.h, g.k, g.l)
         assert _rel(cav.get(H.HOSC_DIV).ravel()[ii], div_o.ravel()[ii]) < 1e-9
 
 
-@pytest.mark.parametrize("N,n,hist", [(21, 1.0, 1), (21, 0.75, 1), (16, 1.25, 1), (17, 0.75, 0)])
-def test_trajectory_from_rest(N, n, hist):
+@pytest.mark.parametrize("N,n,hist,Ly,Lz", [(21, 1.0, 1, 1.0, 1.0), (21, 0.75, 1, 1.0, 1.0),
+                                             (16, 1.25, 1, 1.0, 1.0), (17, 0.75, 0, 1.0, 1.0),
+                                             (17, 0.75, 1, 0.8, 1.3)])
+def test_trajectory_from_rest(N, n, hist, Ly, Lz):
     """Several steps from the initial state (fluid at rest), the configuration marched to
-    steady state: fields, step change and divergence agree after every step."""
-    p = _params(N, 1e3, n, dt=0.005, use_history=hist)
+    steady state: fields, step change and divergence agree after every step (the cube and a
+    box)."""
+    p = _params(N, 1e3, n, dt=0.005, use_history=hist, Ly=Ly, Lz=Lz)
     op = _oracle_params(p)
-    g = O.Grid(N)
+    g = O.Grid.of(op)
     st = O.initial_state(op)
     with H.Cavity(p) as cav:
         assert _rel(cav.get(H.HOSC_THETA), st["th"]) == 0.0
@@ -162,8 +169,9 @@ def test_trajectory_from_rest(N, n, hist):
 
 
 def test_diagnostics_parity():
-    for N, n in ((13, 0.75), (14, 1.0), (21, 1.25)):
-        p = _params(N, 1e4, n)
+    for N, n, Ly, Lz in ((13, 0.75, 1.0, 1.0), (14, 1.0, 1.0, 1.0), (21, 1.25, 1.0, 1.0),
+                         (13, 0.75, 0.6, 1.5), (14, 1.0, 1.8, 0.7)):
+        p = _params(N, 1e4, n, Ly=Ly, Lz=Lz)
         op = _oracle_params(p)
         st = inputs.cavity_state(N, 1e4, seed=N)
         with H.Cavity(p) as cav:
@@ -245,6 +253,9 @@ def test_errors_and_limits():
     bad.dt = -1.0
     st_, h = H.hosc_create(bad)
     assert st_ == H.HOSC_EINVAL and not h.value
+    for Ly, Lz in ((-1.0, 1.0), (1.0, 100.0), (0.01, 1.0), (float("nan"), 1.0)):
+        st_, h = H.hosc_create(_params(9, 1e3, 1.0, Ly=Ly, Lz=Lz))
+        assert st_ == H.HOSC_EINVAL and not h.value, (Ly, Lz)
 
 
 def test_small_and_even_grids():
