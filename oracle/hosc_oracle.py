@@ -86,7 +86,7 @@ class Params:
     def __init__(self, N, Ra, Pr=1.0, n=1.0, dt=0.02, lam=None, theta_ref=0.5, I2_eps=1e-10,
                  phi=1e-4, tol_div=1e-6, tol_lin=1e-12, max_lin_iter=2000, theta_init=0.5,
                  a_limit=0.25, a_boost=1.0, use_history=1, precond=0, inner_max=0, Ly=1.0,
-                 Lz=1.0):
+                 Lz=1.0, solver=0):
         self.N = int(N)
         # Box 1 x Ly x Lz (lengths in units of the hot-cold wall distance) on N nodes per side:
         # spacings h = 1/(N-1), k = Ly/(N-1), l = Lz/(N-1) (the scheme of Sec. 2.2 is written
@@ -115,6 +115,8 @@ class Params:
         # >= 1: up to this many inner pressure iterations per step (see step); 0: one pressure
         # correction per step
         self.inner_max = int(inner_max)
+        # 0: BiCGSTAB (the reading of Sec. 2.2's solver used throughout); 1: BiCGSTAB(2)
+        self.solver = int(solver)
         self.theta_ref = float(theta_ref)
         self.theta_init = float(theta_init)
         self.I2_eps = float(I2_eps)
@@ -360,14 +362,93 @@ def solve_bicgstab(A, b, x0, tol, max_iter):
     return x, max_iter, 4
 
 
+def solve_bicgstab_l(A, b, x0, tol, max_iter, ell=2, trace=None):
+    """BiCGSTAB(ell) (Sleijpen and Fokkema 1993): ell BiCG steps, then a minimal-residual update
+    over the ell new residual directions (modified Gram-Schmidt), per cycle. A reading of the
+    'hybrid' BiCGSTAB of Sec. 2.2 (a hybrid of BiCG and GMRES(ell)); ell = 1 is BiCGSTAB.
+
+    The shadow residual is r_0 = b - A x0. Stops at the end of a cycle when ||r||_2 <= tol
+    ||r_0||_2. Iterations are counted as ell per cycle (two operator applications each, the unit
+    of solve_bicgstab). Returns (x, iterations, status), status 0 = converged, 4 = iteration
+    limit or breakdown. ``trace``, when given, is called after every cycle with the residuals
+    r_0..r_ell of the BiCG part (before the minimal-residual update) and the new residual.
+    """
+    x = x0.copy()
+    r = [b - A @ x] + [None] * ell
+    r0n = math.sqrt(float(r[0] @ r[0]))
+    if r0n == 0.0:
+        return x, 0, 0
+    rt = r[0].copy()                       # shadow residual
+    u = [np.zeros_like(b)] + [None] * ell
+    rho0, alpha, omega = 1.0, 0.0, 1.0
+    it = 0
+    while it < max_iter:
+        rho0 = -omega * rho0
+        for j in range(ell):               # BiCG part
+            rho1 = float(rt @ r[j])
+            if rho0 == 0.0:
+                return x, it, 4
+            beta = alpha * rho1 / rho0
+            rho0 = rho1
+            for i in range(j + 1):
+                u[i] = r[i] - beta * u[i]
+            u[j + 1] = A @ u[j]
+            gam = float(rt @ u[j + 1])
+            if gam == 0.0:
+                return x, it, 4
+            alpha = rho0 / gam
+            for i in range(j + 1):
+                r[i] = r[i] - alpha * u[i + 1]
+            r[j + 1] = A @ r[j]
+            x = x + alpha * u[0]
+        # minimal-residual part: modified Gram-Schmidt on r_1..r_ell
+        bicg = [v.copy() for v in r] if trace else None
+        tau = np.zeros((ell + 1, ell + 1))
+        sigma = np.zeros(ell + 1)
+        gp = np.zeros(ell + 1)             # gamma'
+        for j in range(1, ell + 1):
+            for i in range(1, j):
+                tau[i, j] = float(r[j] @ r[i]) / sigma[i]
+                r[j] = r[j] - tau[i, j] * r[i]
+            sigma[j] = float(r[j] @ r[j])
+            if sigma[j] == 0.0:
+                return x, it, 4
+            gp[j] = float(r[0] @ r[j]) / sigma[j]
+        g = np.zeros(ell + 1)              # gamma
+        g[ell] = gp[ell]
+        omega = g[ell]
+        for j in range(ell - 1, 0, -1):
+            g[j] = gp[j] - sum(tau[j, i] * g[i] for i in range(j + 1, ell + 1))
+        gpp = np.zeros(ell + 1)            # gamma''
+        for j in range(1, ell):
+            gpp[j] = g[j + 1] + sum(tau[j, i] * g[i + 1] for i in range(j + 1, ell))
+        x = x + g[1] * r[0]
+        r[0] = r[0] - gp[ell] * r[ell]
+        u[0] = u[0] - g[ell] * u[ell]
+        for j in range(1, ell):
+            u[0] = u[0] - g[j] * u[j]
+            x = x + gpp[j] * r[j]
+            r[0] = r[0] - gp[j] * r[j]
+        it += ell
+        if trace:
+            trace(bicg, r[0].copy())
+        rn = math.sqrt(float(r[0] @ r[0]))
+        if not math.isfinite(rn):
+            return x, it, 4
+        if rn <= tol * r0n:
+            return x, it, 0
+    return x, it, 4
+
+
 def solve_system(g, dt, c, A, chi, tol, max_iter, direct=False, chi_wall_new=None,
-                 precond=0):
+                 precond=0, solver=0):
     """One implicit HOSC solve, Eq. (6): A chi^{n+1} = Q chi^n + dt R with Q = A - dt B.
 
     Unknowns are the interior nodes. Wall values of chi^{n+1} are ``chi_wall_new`` when given
     (a field whose wall nodes hold level-(n+1) values), else the level-n wall values (reading R6).
     With precond = 1 every row of the interior system and its right-hand side are divided by the
     row's diagonal entry before BiCGSTAB (Jacobi row scaling; the solution does not change).
+    solver = 1 selects BiCGSTAB(2) (solve_bicgstab_l) instead of BiCGSTAB.
     Returns (chi_new, iterations, status).
     """
     chi_f = chi.ravel()
@@ -386,6 +467,8 @@ def solve_system(g, dt, c, A, chi, tol, max_iter, direct=False, chi_wall_new=Non
     if direct:
         import scipy.sparse.linalg as spla
         x, its, st = spla.spsolve(A_II.tocsc(), rhs), 0, 0
+    elif solver == 1:
+        x, its, st = solve_bicgstab_l(A_II, rhs, chi_f[ii], tol, max_iter, ell=2)
     else:
         x, its, st = solve_bicgstab(A_II, rhs, chi_f[ii], tol, max_iter)
     out = wall.copy()
@@ -569,7 +652,7 @@ def step(state, prm, g=None, direct=False):
         A = A_e if name == "th" else A_m
         new[name], iters[name], st = solve_system(g, prm.dt, coefs[name], A, state[name],
                                                   prm.tol_lin, prm.max_lin_iter, direct=direct,
-                                                  precond=prm.precond)
+                                                  precond=prm.precond, solver=prm.solver)
         status = status or st
     new["th"] = apply_theta_bc(new["th"])
     sp3 = (g.h, g.k, g.l)
@@ -592,7 +675,8 @@ def step(state, prm, g=None, direct=False):
         for name in ("u", "v", "w"):
             new[name], iters[name], st = solve_system(g, prm.dt, coefs[name], A_m, state[name],
                                                       prm.tol_lin, prm.max_lin_iter,
-                                                      direct=direct, precond=prm.precond)
+                                                      direct=direct, precond=prm.precond,
+                                                      solver=prm.solver)
             status = status or st
         D = divergence(new["u"], new["v"], new["w"], *sp3)
         d_max = float(np.max(np.abs(D)))

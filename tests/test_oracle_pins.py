@@ -344,6 +344,74 @@ def test_row_scaled_bicgstab_matches_direct_solve():
         np.testing.assert_allclose(a[key], b[key], rtol=0, atol=1e-10 * max(1.0, np.abs(b[key]).max()))
 
 
+def _nonsymmetric_system(N=9, seed=6):
+    """The interior momentum system of one step (n = 0.75, strong convection): nonsymmetric."""
+    prm = O.Params(N=N, Ra=2e4, n=0.75, tol_lin=1e-13)
+    g = O.Grid(N)
+    rng = np.random.default_rng(seed)
+    st = O.initial_state(prm)
+    for key in ("u", "v", "w"):
+        f = np.zeros((N, N, N))
+        f[1:-1, 1:-1, 1:-1] = 20.0 * rng.standard_normal((N - 2,) * 3)
+        st[key] = f
+    lev = O.level_coefficients(st, prm)
+    c = O._system_coefficients(g, prm, lev, None)["u"]
+    A = O.assemble_A(g, prm.dt, c, prm.a_limit, prm.a_boost)
+    ii = g.int_idx
+    A_II = A[ii][:, ii].tocsr()
+    return A_II, rng.standard_normal(len(ii))
+
+
+def test_bicgstab_ell1_is_bicgstab():
+    """BiCGSTAB(ell) with ell = 1 is BiCGSTAB: after the same number of iterations (stopped by
+    the iteration limit) both give the same iterate, up to rounding."""
+    A, b = _nonsymmetric_system()
+    for k in (1, 2, 5, 9):
+        x1, i1, _ = O.solve_bicgstab(A, b, np.zeros_like(b), 1e-300, k)
+        x2, i2, _ = O.solve_bicgstab_l(A, b, np.zeros_like(b), 1e-300, k, ell=1)
+        assert i1 == i2 == k
+        assert np.max(np.abs(x1 - x2)) <= 1e-11 * np.max(np.abs(x1)), k
+
+
+def test_bicgstab2_matches_direct_solve():
+    """BiCGSTAB(2) on a nonsymmetric system reaches the sparse LU solution, and the whole step
+    with solver = 1 equals the step with a direct solve. Every cycle has the two defining
+    properties of the method: the BiCG part leaves r_1 = A r_0 and r_2 = A r_1, and the
+    minimal-residual update makes the new residual r_0 - g_1 r_1 - g_2 r_2 the least-squares
+    one, orthogonal to r_1 and r_2 (so a wrong Gram-Schmidt coefficient fails here even though
+    the iteration would still converge)."""
+    import scipy.sparse.linalg as spla
+    A, b = _nonsymmetric_system()
+    ref = spla.spsolve(A.tocsc(), b)
+    cycles = []
+    x, its, st = O.solve_bicgstab_l(A, b, np.zeros_like(b), 1e-12, 400, ell=2,
+                                    trace=lambda rs, rn: cycles.append((rs, rn)))
+    assert st == 0 and its % 2 == 0 and len(cycles) == its // 2
+    assert np.max(np.abs(x - ref)) <= 1e-9 * np.max(np.abs(ref))
+    for rs, rn in cycles[:6]:
+        r0, r1, r2 = rs
+        scale = np.linalg.norm(r1)
+        assert np.linalg.norm(A @ r0 - r1) <= 1e-10 * scale
+        assert np.linalg.norm(A @ r1 - r2) <= 1e-10 * np.linalg.norm(r2)
+        for v in (r1, r2):
+            assert abs(rn @ v) <= 1e-10 * np.linalg.norm(rn) * np.linalg.norm(v)
+        assert np.linalg.norm(rn) <= np.linalg.norm(r0) * (1 + 1e-12)
+    prm = O.Params(N=7, Ra=2e3, n=0.8, tol_lin=1e-13, solver=1)
+    g = O.Grid(7)
+    rng = np.random.default_rng(3)
+    st0 = O.initial_state(prm)
+    for key in ("u", "v", "w"):
+        f = np.zeros((7, 7, 7))
+        f[1:-1, 1:-1, 1:-1] = rng.standard_normal((5, 5, 5))
+        st0[key] = f
+    st0["th"] = O.apply_theta_bc(rng.random((7, 7, 7)))
+    a, info = O.step(st0, prm, g)
+    d, _ = O.step(st0, prm, g, direct=True)
+    assert info["status"] == 0 and all(v % 2 == 0 for v in info["iters"].values())
+    for key in ("u", "v", "w", "th", "p"):
+        np.testing.assert_allclose(a[key], d[key], rtol=0, atol=1e-10 * max(1.0, np.abs(d[key]).max()))
+
+
 def test_inner_pressure_iterations_reduce_the_divergence():
     """Inner pressure iterations (p <- p - lambda div V, the momentum systems solved again each
     pass) are an Uzawa-type iteration on the step's momentum-continuity system: on a smooth
