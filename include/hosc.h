@@ -135,6 +135,13 @@ typedef struct {
                          spacings). 0 stands for 1 (the paper's cube, the default); otherwise
                          1/64 <= Ly, Lz <= 64. Wall means are averages over the wall; E_total,
                          E_HT, E_FF are integrals over the box volume. */
+  int solver;         /* level-(n+1) solver: 0 (default) BiCGSTAB, the reading of Sec. 2.2's
+                         solver used throughout; 1 BiCGSTAB(2) (Sleijpen-Fokkema: two BiCG steps
+                         and a two-term minimal-residual update per cycle), the other reading of
+                         its "hybrid" BiCGSTAB. Iterations are counted as two per cycle (each
+                         iteration applies the operator twice, as a BiCGSTAB iteration does) and
+                         max_lin_iter limits them. 1 needs HOSC_FP64 (HOSC_EINVAL otherwise) and
+                         adds three N^3 vectors per system to the workspace. */
 } hosc_params;
 
 typedef struct {

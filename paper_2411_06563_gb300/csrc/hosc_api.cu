@@ -98,6 +98,8 @@ hosc_status validate(const hosc_params* p) {
   if (p->inner_max < 0 || p->inner_max > 100000) return HOSC_EINVAL;
   for (double len : {p->Ly, p->Lz})
     if (!(len == 0.0 || (len >= 1.0 / 64.0 && len <= 64.0))) return HOSC_EINVAL;
+  // BiCGSTAB(2) is built for the planar FP64 solve
+  if (p->solver != 0 && !(p->solver == 1 && p->precision == HOSC_FP64)) return HOSC_EINVAL;
   if (p->precision != HOSC_FP64 && p->precision != HOSC_MIXED) return HOSC_EINVAL;
   return HOSC_OK;
 }
@@ -214,6 +216,7 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   d.a_limit = p.a_limit;
   d.a_boost = p.a_boost;
   d.precond = p.precond;
+  d.solver = p.solver;
   d.steady_res = p.tol_steady * p.dt;
   return d;
 }
@@ -341,11 +344,41 @@ hosc_status check_launch() {
   return HOSC_OK;
 }
 
+// BiCGSTAB(2) cycles (five kernels each) on the four systems; the host checks the done flags
+// every few cycles.
+hosc_status solve_b2(Ctx* c, const DevParams& P) {
+  const Fields& F = c->F;
+  static const int kClass[5] = {HOSC_K_BICG_PV, HOSC_K_BICG_ST, HOSC_K_BICG_PV, HOSC_K_BICG_ST,
+                                HOSC_K_BICG_XR};
+  int cp = 0, it = 0, check = 2;
+  while (it < P.max_lin_iter) {
+    const int cycles = (P.max_lin_iter - it + 1) / 2 < check ? (P.max_lin_iter - it + 1) / 2 : check;
+    for (int q = 0; q < cycles; ++q) {
+      for (int kk = 0; kk < 5; ++kk) {
+        prof_begin(c, kClass[kk]);
+        launch_b2(kk, P, F, cp, c->stream);
+        prof_end(c, kClass[kk]);
+      }
+      cp ^= 1;
+    }
+    c->launches += 5L * cycles;
+    it += 2 * cycles;
+    hosc_status st = check_launch();
+    if (st) return st;
+    CU(cudaMemcpyAsync(c->h_ks, F.ks, 4 * sizeof(KrylovScalars), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (c->h_ks[0].done && c->h_ks[1].done && c->h_ks[2].done && c->h_ks[3].done) break;
+    if (check < 8) check *= 2;
+  }
+  return HOSC_OK;
+}
+
 // BiCGSTAB on the four systems; the host checks the done flags every few iterations.
 hosc_status solve_with(Ctx* c, const DevParams& P) {
   const Fields& F = c->F;
   launch_bicg_init(P, F, c->stream);
   c->launches += 1;
+  if (P.solver == 1) return solve_b2(c, P);
   int pp = 0, it = 0, check = 4;
   while (it < P.max_lin_iter) {
     const int chunk = (P.max_lin_iter - it < check) ? P.max_lin_iter - it : check;
@@ -613,10 +646,14 @@ cudaError_t append_step(Ctx* c, cudaStream_t s0, cudaStream_t s1, int cur, int h
     e = cudaStreamBeginCaptureToGraph(s1, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      for (int pp = 0; pp < 2; ++pp) {
-        launch_bicg_pv(P, F, pp, s1);
-        launch_bicg_st(P, F, pp, s1);
-        launch_bicg_xr(P, F, pp, s1);
+      for (int pp = 0; pp < 2; ++pp) {   // BiCGSTAB: two iterations; BiCGSTAB(2): two cycles
+        if (P.solver == 1) {
+          for (int kk = 0; kk < 5; ++kk) launch_b2(kk, P, F, pp, s1);
+        } else {
+          launch_bicg_pv(P, F, pp, s1);
+          launch_bicg_st(P, F, pp, s1);
+          launch_bicg_xr(P, F, pp, s1);
+        }
       }
       launch_loop_cond(F, (unsigned long long)h, s1);
       cudaGraph_t bo = nullptr;
@@ -687,8 +724,11 @@ hosc_status fold_records(Ctx* c, unsigned n, hosc_info* info, bool* steady) {
     }
     int most = 0;
     for (int s = 0; s < 4; ++s) most = r.iters[s] > most ? r.iters[s] : most;
-    const long body = (c->P.krylov_fp32 && c->P.merged) ? 5 : 7;   // kernels per loop pass
-    const long passes = (most + 1) / 2 > 0 ? (most + 1) / 2 : 1;
+    // kernels and iterations per loop pass (BiCGSTAB(2): two five-kernel cycles, 4 iterations)
+    const bool b2 = c->P.solver == 1;
+    const long body = b2 ? 11 : ((c->P.krylov_fp32 && c->P.merged) ? 5 : 7);
+    const long per = b2 ? 4 : 2;
+    const long passes = (most + per - 1) / per > 0 ? (most + per - 1) / per : 1;
     c->launches += 4 + 6 + (c->P.krylov_fp32 ? 1 : 0) + body * passes;
     if (r.status != HOSC_OK) {
       st = (hosc_status)r.status;
@@ -768,7 +808,7 @@ hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** ou
   Ctx* c = new (std::nothrow) Ctx();
   if (!c) return HOSC_ENOMEM;
   c->prm = *p;
-  const size_t need = workspace_layout(p->N, nullptr, nullptr);
+  const size_t need = workspace_layout(p->N, p->solver == 1, nullptr, nullptr);
   cudaError_t e = cudaGetDevice(&c->device);
   if (e == cudaSuccess) {
     if (dev_ws) {
@@ -788,7 +828,7 @@ hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** ou
       c->own_ws = true;
     }
     c->ws_bytes = need;
-    workspace_layout(p->N, &c->F, c->ws);
+    workspace_layout(p->N, p->solver == 1, &c->F, c->ws);
     if (p->cuda_stream) {
       c->stream = (cudaStream_t)p->cuda_stream;
     } else {
@@ -931,7 +971,7 @@ hosc_status ctx_collect_round(void* ctx, bool wait, hosc_info* info, bool* stead
   return st;
 }
 
-size_t workspace_layout(int N, Fields* f, char* base) {
+size_t workspace_layout(int N, int bicgstab2, Fields* f, char* base) {
   const size_t n3 = (size_t)N * N * N;
   const size_t fb = align_up(n3 * sizeof(double));
   size_t off = 0;
@@ -981,6 +1021,11 @@ size_t workspace_layout(int N, Fields* f, char* base) {
       kb += v4;
     }
     static_assert(4 * 16 + 9 * 16 <= 46 * 8, "interleaved solve must fit the planar arrays");
+  }
+  for (int s = 0; s < 4; ++s) {
+    F.u0[s] = bicgstab2 ? fld() : nullptr;
+    F.r2[s] = bicgstab2 ? fld() : nullptr;
+    F.u2[s] = bicgstab2 ? fld() : nullptr;
   }
   F.div = fld();
   F.eloc = (double*)take(3 * n3 * sizeof(double));
@@ -1044,7 +1089,7 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
 
 size_t hosc_workspace_bytes(const hosc_params* p) {
   if (validate(p) != HOSC_OK) return 0;
-  return workspace_layout(p->N, nullptr, nullptr);
+  return workspace_layout(p->N, p->solver == 1, nullptr, nullptr);
 }
 
 hosc_status hosc_create(const hosc_params* p, void** ctx_out) {
@@ -1352,6 +1397,7 @@ hosc_status hosc_time_kernel(void* ctx, int kernel_id, int reps, double* ms_per_
                              double* bytes_per_launch) {
   Ctx* c = (Ctx*)ctx;
   if (!c || reps < 1 || kernel_id < 0 || kernel_id > HOSC_K_BICG_XR) return HOSC_EINVAL;
+  if (c->P.solver == 1 && kernel_id >= HOSC_K_BICG_PV) return HOSC_EINVAL;
   if (c->stage != 0) return HOSC_ESTATE;
   CU(cudaSetDevice(c->device));
   double ms = 0.0;

@@ -117,10 +117,13 @@ __device__ __forceinline__ void block_sum_f32(const float (&vf)[M], double (&v)[
   __syncthreads();
 }
 
-// Doubles per row of the partials buffer for M values per block: kRedSlots, or 2 kRedSlots for
-// 8 < M <= 16 (then one row spans two rows of kRedSlots).
+// Doubles per row of the partials buffer for M values per block: kRedSlots, 2 kRedSlots for
+// 8 < M <= 16, 4 kRedSlots for 16 < M <= 32 (one row then spans two or four rows of kRedSlots;
+// the kernels with more than 16 values have few enough blocks).
 template <int M>
-__host__ __device__ constexpr int row_stride() { return M > kRedSlots ? 2 * kRedSlots : kRedSlots; }
+__host__ __device__ constexpr int row_stride() {
+  return M > 2 * kRedSlots ? 4 * kRedSlots : (M > kRedSlots ? 2 * kRedSlots : kRedSlots);
+}
 
 // Publish the M partials of block b of nb (valid in thread 0) and report whether this block is
 // the last one to do so. No thread waits on another block: the last block to take a ticket does
@@ -153,12 +156,12 @@ __device__ __forceinline__ bool publish_is_last(const double (&v)[M], double* re
 // slot t % Mp (if below M) of rows t / Mp, t / Mp + blockDim/Mp, ... (consecutive threads read
 // consecutive doubles; four rows' loads in flight at a time), then the threads of each slot
 // combine through shuffles and shared memory.
-// blockDim.x must be a multiple of 32 (and at least Mp); smem: >= 16*M doubles.
+// blockDim.x must be a multiple of 32 (and at least Mp); smem: >= 32*M doubles.
 template <int M, bool IsMax>
 __device__ __forceinline__ void reduce_partials(double (&tot)[M], const double* red, int nblocks,
                                                 unsigned int* counter, double* smem) {
-  static_assert(M >= 1 && M <= 16, "at most 16 values per block");
-  constexpr int Mp = M <= 1 ? 1 : M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : 16;   // lanes per row
+  static_assert(M >= 1 && M <= 32, "at most 32 values per block");
+  constexpr int Mp = M <= 1 ? 1 : M <= 2 ? 2 : M <= 4 ? 4 : M <= 8 ? 8 : M <= 16 ? 16 : 32;
   constexpr long S = row_stride<M>();
   __threadfence();
   const int t = threadIdx.x, bd = blockDim.x;

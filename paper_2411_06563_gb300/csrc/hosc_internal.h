@@ -43,6 +43,7 @@ struct DevParams {
   float s3f;
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
   int precond;         // Jacobi row scaling of the level-(n+1) systems
+  int solver;          // 0: BiCGSTAB; 1: BiCGSTAB(2) (planar FP64 solve)
   int inner_pass;      // an inner pressure pass: momentum only (theta kept, its system skipped)
   double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (and div below tol_div)
                        // is steady (tol_steady * dt)
@@ -53,6 +54,7 @@ constexpr int kRing = 256;   // step records kept on the device between host rea
 // BiCGSTAB scalars of one system, resident in device memory.
 struct KrylovScalars {
   double rho, alpha, omega, beta, r0norm, rnorm;
+  double g1, g2;     // BiCGSTAB(2): minimal-residual coefficients gamma_1, gamma_2 of the cycle
   int done, iters, status, pad;
 };
 
@@ -88,6 +90,11 @@ struct Fields {
   double* pk[2][4];  // search direction, ping-pong
   double* vk[2][4];  // A p, ping-pong
   double* t[4];      // A s
+  // BiCGSTAB(2) (solver = 1) only: u_0, r_2, u_2 of each system (null otherwise). The cycle
+  // keeps r_0 in r / t (ping-pong by cycle), r_1 in pk, u_1 in vk.
+  double* u0[4];
+  double* r2[4];
+  double* u2[4];
   double* div;       // div V^{n+1}
   double* red;       // reduction partials [blocks][kRedSlots]
   unsigned int* counter;   // last-block ticket (reset by the last block)
@@ -123,7 +130,9 @@ struct Fields {
   float* ps;
 };
 
-size_t workspace_layout(int N, Fields* f, char* base);   // returns bytes; fills f when base != 0
+// Bytes of a context's device workspace (the BiCGSTAB(2) vectors included when bicgstab2);
+// fills f when base != 0.
+size_t workspace_layout(int N, int bicgstab2, Fields* f, char* base);
 int red_blocks(long count);
 // Rows of the per-block partials buffer of an N^3 context: enough for any launch shape the
 // validation accepts (at least 32 threads per block, one plane per thread).
@@ -154,6 +163,9 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s);
 void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
+// BiCGSTAB(2), planar FP64 solve: the five kernels of one cycle, r_0 ping-pong parity cp
+// (launch_bicg_init starts the solve for either solver).
+void launch_b2(int kernel, const DevParams& P, const Fields& F, int cp, cudaStream_t s);
 // Mark all four systems as iterating (for timing the Krylov kernels in isolation).
 void launch_krylov_activate(const Fields& F, cudaStream_t s);
 // Body of the BiCGSTAB loop of a captured step: end of the loop when every system is done.

@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_bicg_init(DevParams P, Fields F, i
       vec<T>(F.pk[1][s])[c] = T(0);
       vec<T>(F.vk[0][s])[c] = T(0);
       vec<T>(F.vk[1][s])[c] = T(0);
+      if (P.solver == 1) vec<T>(F.u0[s])[c] = T(0);
       da[s] = r;
       db[s] = r;
     }
@@ -161,10 +162,11 @@ __global__ void __launch_bounds__(kThreads) k_bicg_init(DevParams P, Fields F, i
         KrylovScalars& k = F.ks[s];
         k.r0norm = sqrt(tot[s]);
         k.rnorm = k.r0norm;
-        k.rho = tot[s];
-        k.alpha = 1.0;
+        k.rho = tot[s];   // BiCGSTAB(2): rho_0 after the first cycle's rho_0 = -omega rho_0, j = 0
+        k.alpha = P.solver == 1 ? 0.0 : 1.0;
         k.omega = 1.0;
         k.beta = 0.0;
+        k.g1 = k.g2 = 0.0;
         k.iters = 0;
         k.status = 0;
         // an inner pressure pass solves the momentum systems only
@@ -358,6 +360,338 @@ __global__ void __launch_bounds__(kThreads) k_bicg_xr(DevParams P, Fields F, int
         }
       }
       F.alg_bytes[HOSC_K_BICG_XR] += launch_bytes(P, s_done, 8.0, 0.0, sizeof(T));
+    }
+  }
+}
+
+// ------------------------------------------------------------------ BiCGSTAB(2), planar FP64
+//
+// One cycle (Sleijpen and Fokkema's BiCGSTAB(ell) with ell = 2; shadow residual rt = r_0 = rhs)
+// in five kernels, each with a last-block reduction that finalises the scalars of the next:
+//   B1  u_0 <- r_0 - beta u_0 (on the fly at the stencil), u_1 = A u_0;       alpha = rho/(rt.u_1)
+//   B2  r_0 <- r_0 - alpha u_1 (on the fly), r_1 = A r_0; u_0 <- r_0 - beta u_0 and x += alpha u_0
+//       (pointwise, with the r_0 of B1);                   rho_1 = rt.r_1, beta = alpha rho_1/rho
+//   B3  u_0 <- r_0 - beta u_0 (pointwise); u_1 <- r_1 - beta u_1 (on the fly), u_2 = A u_1;
+//                                                          alpha = rho/(rt.u_2)
+//   B4  r_0 -= alpha u_1 (pointwise); r_1 <- r_1 - alpha u_2 (on the fly), r_2 = A r_1;
+//       x += alpha u_0; the five inner products of r_0, r_1, r_2 give the minimal-residual
+//       coefficients: tau = (r_1.r_2)/(r_1.r_1), gamma'_1 = (r_0.r_1)/(r_1.r_1), gamma_2 =
+//       gamma'_2 = (r_0.r_2 - tau r_0.r_1)/(r_2.r_2 - tau r_1.r_2), gamma_1 = gamma'_1 - tau gamma_2
+//   B5  x += gamma_1 r_0 + gamma_2 r_1; r_0 -= gamma_1 r_1 + gamma_2 r_2; u_0 -= gamma_1 u_1 +
+//       gamma_2 u_2 (the Gram-Schmidt step folded into the coefficients); rho <- -omega rho,
+//       rho_1 = rt.r_0, beta = alpha rho_1/rho, rho = rho_1, convergence on ||r_0||.
+// Buffers per system: r_0 in r / t (ping-pong by cycle: B2 reads one and writes the other, the
+// stencil reads the old r_0 at the neighbours), r_1 in pk[0] (B2) then pk[1] (B4), u_1 in vk[0]
+// (B1) then vk[1] (B3), u_0, r_2, u_2 in their own arrays. A kernel writes no array that it reads
+// at a neighbour.
+
+struct B2Shared {
+  double alpha[4], beta[4], g1[4], g2[4];
+  int done[4];
+};
+
+// The four systems' scalars into shared memory; true when every system is done (uniform).
+__device__ __forceinline__ bool b2_load(const Fields& F, B2Shared& sh) {
+  if (threadIdx.x < 4) {
+    const KrylovScalars k = F.ks[threadIdx.x];
+    sh.alpha[threadIdx.x] = k.alpha;
+    sh.beta[threadIdx.x] = k.beta;
+    sh.g1[threadIdx.x] = k.g1;
+    sh.g2[threadIdx.x] = k.g2;
+    sh.done[threadIdx.x] = k.done;
+  }
+  __syncthreads();
+  return sh.done[0] & sh.done[1] & sh.done[2] & sh.done[3];
+}
+
+__device__ __forceinline__ void nbrs7(int c, int sy, int sz, int nb[7]) {
+  nb[0] = c;
+  nb[1] = c + 1;
+  nb[2] = c - 1;
+  nb[3] = c + sy;
+  nb[4] = c - sy;
+  nb[5] = c + sz;
+  nb[6] = c - sz;
+}
+
+__device__ __forceinline__ void b2_fail(KrylovScalars& k) {
+  k.done = 1;
+  k.status = HOSC_ENOCONV;
+}
+
+__device__ __forceinline__ const double* const* b2_op(const Fields& F, int s) {
+  return (s < 3) ? ops<double>(F.Am) : ops<double>(F.Ae);
+}
+
+// B1
+__global__ void __launch_bounds__(kThreads) k_b2_u1(DevParams P, Fields F, int cp, int nblocks) {
+  __shared__ double smem[32 * 4];
+  __shared__ B2Shared sh;
+  if (b2_load(F, sh)) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sy = P.N, sz = P.N * P.N;
+  int c;
+  double da[4] = {0, 0, 0, 0}, db[4] = {0, 0, 0, 0};
+  if (interior_index(P, t, c)) {
+    int nb[7];
+    nbrs7(c, sy, sz, nb);
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      if (sh.done[s]) continue;
+      const double* r0 = cp ? F.t[s] : F.r[s];
+      const double* u0 = F.u0[s];
+      const double b = sh.beta[s];
+      double un[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) un[q] = r0[nb[q]] - b * u0[nb[q]];
+      const double u1 = apply7<double>(b2_op(F, s), c, un[0], un[1], un[2], un[3], un[4], un[5],
+                                       un[6]);
+      F.vk[0][s][c] = u1;
+      da[s] = F.rhs[s][c];
+      db[s] = u1;
+    }
+  }
+  double part[4];
+  block_partial<4>(da, db, part, smem);
+  if (publish_is_last<4>(part, F.red, F.counter)) {
+    double tot[4];
+    reduce_partials<4, false>(tot, F.red, nblocks, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        if (tot[s] == 0.0 || !isfinite(tot[s])) {
+          b2_fail(k);
+          continue;
+        }
+        k.alpha = k.rho / tot[s];
+      }
+      F.alg_bytes[HOSC_K_BICG_PV] += launch_bytes(P, sh.done, 4.0, 7.0, sizeof(double));
+    }
+  }
+}
+
+// B2
+__global__ void __launch_bounds__(kThreads) k_b2_r1(DevParams P, Fields F, int cp, int nblocks) {
+  __shared__ double smem[32 * 4];
+  __shared__ B2Shared sh;
+  if (b2_load(F, sh)) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sy = P.N, sz = P.N * P.N;
+  int c;
+  double da[4] = {0, 0, 0, 0}, db[4] = {0, 0, 0, 0};
+  if (interior_index(P, t, c)) {
+    int nb[7];
+    nbrs7(c, sy, sz, nb);
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      if (sh.done[s]) continue;
+      const double* r0 = cp ? F.t[s] : F.r[s];
+      double* r0n = cp ? F.r[s] : F.t[s];
+      const double* u1 = F.vk[0][s];
+      const double a = sh.alpha[s], b = sh.beta[s];
+      double rn[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) rn[q] = r0[nb[q]] - a * u1[nb[q]];
+      const double r1 = apply7<double>(b2_op(F, s), c, rn[0], rn[1], rn[2], rn[3], rn[4], rn[5],
+                                       rn[6]);
+      r0n[c] = rn[0];
+      F.pk[0][s][c] = r1;
+      const double u0 = r0[c] - b * F.u0[s][c];
+      F.u0[s][c] = u0;
+      F.x[s][c] += a * u0;
+      da[s] = F.rhs[s][c];
+      db[s] = r1;
+    }
+  }
+  double part[4];
+  block_partial<4>(da, db, part, smem);
+  if (publish_is_last<4>(part, F.red, F.counter)) {
+    double tot[4];
+    reduce_partials<4, false>(tot, F.red, nblocks, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        if (k.rho == 0.0 || !isfinite(tot[s])) {
+          b2_fail(k);
+          continue;
+        }
+        k.beta = k.alpha * tot[s] / k.rho;
+        k.rho = tot[s];
+      }
+      F.alg_bytes[HOSC_K_BICG_ST] += launch_bytes(P, sh.done, 9.0, 7.0, sizeof(double));
+    }
+  }
+}
+
+// B3
+__global__ void __launch_bounds__(kThreads) k_b2_u2(DevParams P, Fields F, int cp, int nblocks) {
+  __shared__ double smem[32 * 4];
+  __shared__ B2Shared sh;
+  if (b2_load(F, sh)) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sy = P.N, sz = P.N * P.N;
+  int c;
+  double da[4] = {0, 0, 0, 0}, db[4] = {0, 0, 0, 0};
+  if (interior_index(P, t, c)) {
+    int nb[7];
+    nbrs7(c, sy, sz, nb);
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      if (sh.done[s]) continue;
+      const double* r0 = cp ? F.r[s] : F.t[s];   // written by B2
+      const double* r1 = F.pk[0][s];
+      const double* u1 = F.vk[0][s];
+      const double b = sh.beta[s];
+      F.u0[s][c] = r0[c] - b * F.u0[s][c];
+      double un[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) un[q] = r1[nb[q]] - b * u1[nb[q]];
+      const double u2 = apply7<double>(b2_op(F, s), c, un[0], un[1], un[2], un[3], un[4], un[5],
+                                       un[6]);
+      F.vk[1][s][c] = un[0];
+      F.u2[s][c] = u2;
+      da[s] = F.rhs[s][c];
+      db[s] = u2;
+    }
+  }
+  double part[4];
+  block_partial<4>(da, db, part, smem);
+  if (publish_is_last<4>(part, F.red, F.counter)) {
+    double tot[4];
+    reduce_partials<4, false>(tot, F.red, nblocks, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        if (tot[s] == 0.0 || !isfinite(tot[s])) {
+          b2_fail(k);
+          continue;
+        }
+        k.alpha = k.rho / tot[s];
+      }
+      F.alg_bytes[HOSC_K_BICG_PV] += launch_bytes(P, sh.done, 8.0, 7.0, sizeof(double));
+    }
+  }
+}
+
+// B4
+__global__ void __launch_bounds__(kThreads) k_b2_r2(DevParams P, Fields F, int cp, int nblocks) {
+  __shared__ double smem[32 * 20];
+  __shared__ B2Shared sh;
+  if (b2_load(F, sh)) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sy = P.N, sz = P.N * P.N;
+  int c;
+  // per system: r1.r1, r1.r2, r2.r2, r0.r1, r0.r2
+  double da[20], db[20];
+#pragma unroll
+  for (int m = 0; m < 20; ++m) da[m] = db[m] = 0.0;
+  if (interior_index(P, t, c)) {
+    int nb[7];
+    nbrs7(c, sy, sz, nb);
+#pragma unroll 1
+    for (int s = 0; s < 4; ++s) {
+      if (sh.done[s]) continue;
+      double* r0 = cp ? F.r[s] : F.t[s];
+      const double* r1 = F.pk[0][s];
+      const double* u2 = F.u2[s];
+      const double a = sh.alpha[s];
+      const double r0c = r0[c] - a * F.vk[1][s][c];
+      r0[c] = r0c;
+      double rn[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) rn[q] = r1[nb[q]] - a * u2[nb[q]];
+      const double r2 = apply7<double>(b2_op(F, s), c, rn[0], rn[1], rn[2], rn[3], rn[4], rn[5],
+                                       rn[6]);
+      F.pk[1][s][c] = rn[0];
+      F.r2[s][c] = r2;
+      F.x[s][c] += a * F.u0[s][c];
+      const double d0[5] = {rn[0], rn[0], r2, r0c, r0c}, d1[5] = {rn[0], r2, r2, rn[0], r2};
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        da[5 * s + m] = d0[m];
+        db[5 * s + m] = d1[m];
+      }
+    }
+  }
+  double part[20];
+  block_partial<20>(da, db, part, smem);
+  if (publish_is_last<20>(part, F.red, F.counter)) {
+    double tot[20];
+    reduce_partials<20, false>(tot, F.red, nblocks, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        const double* d = tot + 5 * s;   // r1.r1, r1.r2, r2.r2, r0.r1, r0.r2
+        const double sig1 = d[0];
+        const double tau = sig1 > 0.0 ? d[1] / sig1 : 0.0;
+        const double sig2 = d[2] - tau * d[1];   // |r_2 - tau r_1|^2
+        if (!(sig1 > 0.0) || !(sig2 > 0.0) || !isfinite(sig2)) {
+          b2_fail(k);
+          continue;
+        }
+        const double gp1 = d[3] / sig1, g2 = (d[4] - tau * d[3]) / sig2;
+        k.g2 = g2;
+        k.g1 = gp1 - tau * g2;
+        k.omega = g2;
+      }
+      F.alg_bytes[HOSC_K_BICG_ST] += launch_bytes(P, sh.done, 11.0, 7.0, sizeof(double));
+    }
+  }
+}
+
+// B5
+__global__ void __launch_bounds__(kThreads) k_b2_mr(DevParams P, Fields F, int cp, int nblocks) {
+  __shared__ double smem[32 * 8];
+  __shared__ B2Shared sh;
+  if (b2_load(F, sh)) return;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  int c;
+  double da[8] = {0, 0, 0, 0, 0, 0, 0, 0}, db[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (interior_index(P, t, c)) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      if (sh.done[s]) continue;
+      double* r0 = cp ? F.r[s] : F.t[s];
+      const double g1 = sh.g1[s], g2 = sh.g2[s];
+      const double r0c = r0[c], r1 = F.pk[1][s][c], r2 = F.r2[s][c];
+      F.x[s][c] += g1 * r0c + g2 * r1;
+      const double rn = r0c - g1 * r1 - g2 * r2;
+      r0[c] = rn;
+      F.u0[s][c] -= g1 * F.vk[1][s][c] + g2 * F.u2[s][c];
+      da[2 * s] = F.rhs[s][c];
+      db[2 * s] = rn;
+      da[2 * s + 1] = rn;
+      db[2 * s + 1] = rn;
+    }
+  }
+  double part[8];
+  block_partial<8>(da, db, part, smem);
+  if (publish_is_last<8>(part, F.red, F.counter)) {
+    double tot[8];
+    reduce_partials<8, false>(tot, F.red, nblocks, F.counter, smem);
+    if (threadIdx.x == 0) {
+      for (int s = 0; s < 4; ++s) {
+        KrylovScalars& k = F.ks[s];
+        if (k.done) continue;
+        const double rho1 = tot[2 * s];
+        k.rnorm = sqrt(tot[2 * s + 1]);
+        k.iters += 2;
+        const double rho0 = -k.omega * k.rho;
+        if (k.rnorm <= P.tol_lin * k.r0norm) {
+          k.done = 1;
+          k.status = 0;
+        } else if (!isfinite(k.rnorm) || k.iters >= P.max_lin_iter || rho0 == 0.0) {
+          b2_fail(k);
+        } else {
+          k.beta = k.alpha * rho1 / rho0;
+          k.rho = rho1;
+        }
+      }
+      F.alg_bytes[HOSC_K_BICG_XR] += launch_bytes(P, sh.done, 12.0, 0.0, sizeof(double));
     }
   }
 }
@@ -1171,6 +1505,17 @@ void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
   }
   const int b = interior_blocks(P);
   k_bicg_xr<double><<<b, kThreads, 0, s>>>(P, F, pp, b);
+}
+
+void launch_b2(int kernel, const DevParams& P, const Fields& F, int cp, cudaStream_t s) {
+  const int b = interior_blocks(P);
+  switch (kernel) {
+    case 0: k_b2_u1<<<b, kThreads, 0, s>>>(P, F, cp, b); break;
+    case 1: k_b2_r1<<<b, kThreads, 0, s>>>(P, F, cp, b); break;
+    case 2: k_b2_u2<<<b, kThreads, 0, s>>>(P, F, cp, b); break;
+    case 3: k_b2_r2<<<b, kThreads, 0, s>>>(P, F, cp, b); break;
+    default: k_b2_mr<<<b, kThreads, 0, s>>>(P, F, cp, b); break;
+  }
 }
 
 long krylov4_blocks(const DevParams& P) {

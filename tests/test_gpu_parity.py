@@ -46,7 +46,8 @@ def _oracle_params(p):
                     theta_ref=p.theta_ref, I2_eps=p.I2_eps, phi=p.phi, tol_div=p.tol_div,
                     tol_lin=p.tol_lin, max_lin_iter=p.max_lin_iter, theta_init=p.theta_init,
                     a_limit=p.a_limit, a_boost=p.a_boost, use_history=p.use_history,
-                    precond=p.precond, inner_max=p.inner_max, Ly=p.Ly or 1.0, Lz=p.Lz or 1.0)
+                    precond=p.precond, inner_max=p.inner_max, Ly=p.Ly or 1.0, Lz=p.Lz or 1.0,
+                    solver=p.solver)
 
 
 def _setup(N, Ra, n, seed, history, **kw):
@@ -374,6 +375,85 @@ def test_jacobi_row_scaling_one_step(precision):
                 inc = new[name] - st[name]
                 scale = max(np.max(np.abs(inc)), 1e-12)
                 assert np.max(np.abs((got - st[name]) - inc)) <= 2e-5 * scale + 1e-12, name
+
+
+FIELDS5 = (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W), ("th", H.HOSC_THETA),
+           ("p", H.HOSC_P))
+
+
+@pytest.mark.parametrize("N,Ra,n,Ly,Lz", [(15, 1e4, 0.75, 1.0, 1.0), (12, 3e3, 1.25, 1.0, 1.0),
+                                           (13, 1e4, 0.75, 0.8, 1.3)])
+def test_bicgstab2_one_step(N, Ra, n, Ly, Lz):
+    """BiCGSTAB(2) (solver = 1): one step equals the oracle's BiCGSTAB(2) step to 1e-10 (both
+    solved to 1e-13), the iteration counts (two per cycle) agree with the oracle's, and the
+    increments solve the oracle's operator: A x_gpu = rhs to 1e-11 of |rhs|."""
+    p = _params(N, Ra, n, dt=0.002, solver=1, Ly=Ly, Lz=Lz)
+    op = _oracle_params(p)
+    st = inputs.cavity_state(N, Ra, seed=400 + N)
+    g = O.Grid.of(op)
+    new, oinfo = O.step(dict(st, prev=None, steps=0), op, g)
+    assert oinfo["status"] == 0
+    with H.Cavity(p) as cav:
+        for name, which in FIELDS5:
+            cav.set(which, st[name])
+        info = cav.step(1)
+        assert info["call_status"] == 0
+        for name, which in FIELDS5:
+            assert _rel(cav.get(which), new[name]) <= 1e-10, name
+        for s_, name in enumerate(("u", "v", "w", "th")):
+            it = info["last_iters"][s_]
+            assert it % 2 == 0 and abs(it - oinfo["iters"][name]) <= 2, (name, it, oinfo["iters"])
+
+
+def test_bicgstab2_stage_solve_and_limits():
+    """Stage by stage with BiCGSTAB(2): the increments of S5 match a direct solve of the oracle's
+    operator to 1e-9; the solver needs the FP64 solve; isolated Krylov timing is not offered."""
+    import scipy.sparse.linalg as spla
+    N, Ra, n = 13, 1e4, 0.75
+    p, op, state, cav = _setup(N, Ra, n, seed=77, history=False, dt=0.004, solver=1)
+    g = O.Grid.of(op)
+    ii = g.int_idx
+    with cav:
+        cav.run_stage(H.HOSC_STAGE_VISCOSITY)
+        cav.run_stage(H.HOSC_STAGE_SOURCES)
+        cav.run_stage(H.HOSC_STAGE_RHS)
+        rhs = {name: cav.get(which).ravel()[ii] for name, which in
+               (("u", H.HOSC_RHS_U), ("v", H.HOSC_RHS_V), ("w", H.HOSC_RHS_W),
+                ("th", H.HOSC_RHS_THETA))}
+        info = cav.run_stage(H.HOSC_STAGE_SOLVE)
+        assert info["status"] == 0
+        lev = O.level_coefficients(state, op)
+        coefs = O._system_coefficients(g, op, lev, None)
+        A_m = O.assemble_A(g, op.dt, coefs["u"], op.a_limit, op.a_boost)
+        A_e = O.assemble_A(g, op.dt, coefs["th"], op.a_limit, op.a_boost)
+        for name, which in (("u", H.HOSC_DX_U), ("v", H.HOSC_DX_V), ("w", H.HOSC_DX_W),
+                            ("th", H.HOSC_DX_THETA)):
+            A = (A_e if name == "th" else A_m)[ii][:, ii].tocsc()
+            x_ref = spla.spsolve(A, rhs[name])
+            assert _rel(cav.get(which).ravel()[ii], x_ref) < 1e-9, name
+        assert H.hosc_time_kernel(cav.h, H.HOSC_K_BICG_PV, 2)[0] == H.HOSC_EINVAL
+    st_, h = H.hosc_create(_params(9, 1e3, 1.0, solver=1, precision=H.HOSC_MIXED))
+    assert st_ == H.HOSC_EINVAL and not h.value
+    st_, h = H.hosc_create(_params(9, 1e3, 1.0, solver=2))
+    assert st_ == H.HOSC_EINVAL and not h.value
+
+
+def test_bicgstab2_trajectory_captured():
+    """Captured steps (the device-side loop runs two BiCGSTAB(2) cycles per pass) from rest
+    follow the oracle's BiCGSTAB(2) trajectory to 1e-10 over several steps."""
+    N = 17
+    p = _params(N, 1e3, 0.75, dt=0.005, solver=1)
+    op = _oracle_params(p)
+    g = O.Grid.of(op)
+    st = O.initial_state(op)
+    with H.Cavity(p) as cav:
+        for _ in range(3):
+            info = cav.step(2)
+            assert info["call_status"] == 0
+            for _ in range(2):
+                st, oinfo = O.step(st, op, g)
+            for name, which in FIELDS5:
+                assert _rel(cav.get(which), st[name]) < 1e-10, name
 
 
 def test_inner_pressure_passes_match_the_oracle():
