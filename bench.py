@@ -430,9 +430,10 @@ def main():
     stream = torch.cuda.current_stream()
     spinup = wl["spinup"] if args.spinup is None else args.spinup
 
-    def make(precision, precond=0):
+    def make(precision, precond=0, solver=0):
         p = H.hosc_default_params(N, wl["Ra"], wl["Pr"], wl["n"])
         p.precond = precond
+        p.solver = solver
         p.dt = wl["dt"]
         p.lambda_ = min(0.25 * h * h / p.dt, 0.1 * wl["Pr"])
         p.tol_lin = 1e-10
@@ -460,18 +461,29 @@ def main():
 
     fp64_compare = None
     if args.precision == "mixed" and not args.no_fp64_compare:
-        # the plain all-FP64 path on the same workload, for context
-        p64, c64 = make("fp64")
-        k64 = max(5, args.steps // 4)
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        ea.record(stream)
-        c64.step(k64)
-        eb.record(stream)
-        torch.cuda.synchronize()
-        fp64_compare = {"value": (N - 2) ** 3 * k64 * ws / (ea.elapsed_time(eb) * 1e-3),
-                        "steps": k64, "ms_per_step": ea.elapsed_time(eb) / k64}
-        c64.close()
+        # the plain all-FP64 path on the same workload, for context, with BiCGSTAB and with
+        # BiCGSTAB(2) (the two readings of the paper's solver): iterations x bytes per step
+        fp64_compare = {}
+        for name, solver in (("bicgstab", 0), ("bicgstab2", 1)):
+            p64, c64 = make("fp64", solver=solver)
+            k64 = max(5, args.steps // 4)
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            barrier()
+            ea.record(stream)
+            i64 = c64.step(k64)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            fp64_compare[name] = {
+                "value": (N - 2) ** 3 * k64 * ws / (ea.elapsed_time(eb) * 1e-3),
+                "steps": k64, "ms_per_step": ea.elapsed_time(eb) / k64,
+                # iterations: operator-application pairs per system and step (a BiCGSTAB(2)
+                # cycle counts two)
+                "iters_per_step": i64["lin_iters"] / (4.0 * i64["steps"]),
+                # algorithmic bytes per iteration and interior node, four systems: BiCGSTAB
+                # 96 words (p/v 38, s/t 26, x/r 32); BiCGSTAB(2) 224 words per two-iteration
+                # cycle (B1 30, B2 50, B3 46, B4 54, B5 44)
+                "krylov_bytes_per_iteration_per_node": 768 if solver == 0 else 896}
+            c64.close()
     p, cav = make(args.precision)
 
     # ------------------------------------------------------------- timed region (device-resident)

@@ -236,7 +236,9 @@ hosc_status hosc_profile_read(void* ctx, int kernel_id, double* total_ms, long* 
  * Returns the mean milliseconds per launch and the algorithmic bytes of one launch. The fields
  * u, v, w, theta, p and the history keep their values; the derived arrays and the Krylov
  * buffers are overwritten and recomputed by the next step. HOSC_EINVAL for another id or
- * reps < 1, HOSC_ESTATE in the middle of a stage-by-stage step. */
+ * reps < 1, and for the BiCGSTAB classes when solver = 1 (BiCGSTAB(2): its five kernels are
+ * counted under the p/v, s/t and x/r classes by hosc_profile_read but not timed alone);
+ * HOSC_ESTATE in the middle of a stage-by-stage step. */
 hosc_status hosc_time_kernel(void* ctx, int kernel_id, int reps, double* ms_per_launch,
                              double* bytes_per_launch);
 

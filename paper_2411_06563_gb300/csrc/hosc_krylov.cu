@@ -638,7 +638,7 @@ __global__ void __launch_bounds__(kThreads) k_b2_r2(DevParams P, Fields F, int c
         k.g1 = gp1 - tau * g2;
         k.omega = g2;
       }
-      F.alg_bytes[HOSC_K_BICG_ST] += launch_bytes(P, sh.done, 11.0, 7.0, sizeof(double));
+      F.alg_bytes[HOSC_K_BICG_ST] += launch_bytes(P, sh.done, 10.0, 7.0, sizeof(double));
     }
   }
 }
@@ -691,7 +691,7 @@ __global__ void __launch_bounds__(kThreads) k_b2_mr(DevParams P, Fields F, int c
           k.rho = rho1;
         }
       }
-      F.alg_bytes[HOSC_K_BICG_XR] += launch_bytes(P, sh.done, 12.0, 0.0, sizeof(double));
+      F.alg_bytes[HOSC_K_BICG_XR] += launch_bytes(P, sh.done, 11.0, 0.0, sizeof(double));
     }
   }
 }
