@@ -62,16 +62,27 @@ __device__ __forceinline__ void warp_sum(double (&v)[M]) {
     for (int off = 16; off > 0; off >>= 1) v[m] += __shfl_down_sync(0xffffffffu, v[m], off);
 }
 
+// Larger of two non-negative doubles (+inf allowed). For such values the IEEE order is the order
+// of their bit patterns as integers, so the comparison runs on the integer units: GB300 issues
+// FP64 instructions at a small fraction of its integer rate. Every max-reduction here reduces
+// magnitudes.
+__device__ __forceinline__ double max_nonneg(double a, double b) {
+  const long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+  return __longlong_as_double(x > y ? x : y);
+}
+
 template <int M>
 __device__ __forceinline__ void warp_max(double (&v)[M]) {
 #pragma unroll
   for (int m = 0; m < M; ++m)
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[m] = fmax(v[m], __shfl_down_sync(0xffffffffu, v[m], off));
+    for (int off = 16; off > 0; off >>= 1)
+      v[m] = max_nonneg(v[m], __shfl_down_sync(0xffffffffu, v[m], off));
 }
 
-// Sum (or max) of M values over the block; the result is valid in thread 0. Fixed order, so the
-// result is the same run to run for the same launch shape. smem: >= 32*M doubles.
+// Sum (or max, of non-negative values) of M values over the block; the result is valid in
+// thread 0. Fixed order, so the result is the same run to run for the same launch shape.
+// smem: >= 32*M doubles.
 template <int M, bool IsMax>
 __device__ __forceinline__ void block_reduce(double (&v)[M], double* smem) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -166,7 +177,7 @@ __device__ __forceinline__ void reduce_partials(double (&tot)[M], const double* 
   __threadfence();
   const int t = threadIdx.x, bd = blockDim.x;
   const int m = t % Mp, rstep = bd / Mp;
-  auto op = [](double a, double b) { return IsMax ? fmax(a, b) : a + b; };
+  auto op = [](double a, double b) { return IsMax ? max_nonneg(a, b) : a + b; };
   double acc = 0.0;
   int r = m < M ? t / Mp : nblocks;   // lanes past the M values read nothing
   for (; r + 3 * rstep < nblocks; r += 4 * rstep) {

@@ -801,8 +801,7 @@ __global__ void __launch_bounds__(kThreads) k4_init(DevParams P, Fields F) {
     const float4 z = f4(0.f);
     const float4 r = inner ? F.kr0[c] : z;
     F.kr[c] = r;
-    F.kx[c] = z;
-    F.kt[c] = z;
+    F.kx[c] = z;   // t needs no zeros: k4_st writes it before k4_xr reads it, inside only
     F.kp[0][c] = z;
     F.kp[1][c] = z;
     F.kv[0][c] = z;

@@ -15,7 +15,15 @@ namespace hosc {
 
 namespace {
 
-__device__ __forceinline__ double absfin(double x) { return isfinite(x) ? fabs(x) : INFINITY; }
+// |x|, or +inf when x is not finite, on the integer units (see max_nonneg).
+__device__ __forceinline__ double absfin(double x) {
+  const long long b = __double_as_longlong(x) & 0x7fffffffffffffffLL;
+  return b < 0x7ff0000000000000LL ? __longlong_as_double(b) : INFINITY;
+}
+__device__ __forceinline__ float absfinf(float x) {
+  const int b = __float_as_int(x) & 0x7fffffff;
+  return b < 0x7f800000 ? __int_as_float(b) : INFINITY;
+}
 __device__ __forceinline__ int inward(int a, int N) { return a == 0 ? 1 : (a == N - 1 ? N - 2 : a); }
 __device__ __forceinline__ int on_wall(int a, int N) { return (a == 0) | (a == N - 1); }
 
@@ -456,18 +464,21 @@ __global__ void __launch_bounds__(kThreads) k_apply_increment(DevParams P, Field
         xv = x4.y;
         xw = x4.z;
         xt = x4.w;
+        // magnitudes in float (exact), widened once
+        m[0] = fmaxf(fmaxf(absfinf(x4.x), absfinf(x4.y)), absfinf(x4.z));
+        m[1] = absfinf(x4.w);
       } else {
         xu = F.x[0][t];
         xv = F.x[1][t];
         xw = F.x[2][t];
         xt = F.x[3][t];
+        m[0] = max_nonneg(max_nonneg(absfin(xu), absfin(xv)), absfin(xw));
+        m[1] = absfin(xt);
       }
       F.u[1 - cur][t] = F.u[cur][t] + xu;
       F.v[1 - cur][t] = F.v[cur][t] + xv;
       F.w[1 - cur][t] = F.w[cur][t] + xw;
       F.th[t] += xt;
-      m[0] = fmax(fmax(absfin(xu), absfin(xv)), absfin(xw));
-      m[1] = absfin(xt);
     } else {
       F.u[1 - cur][t] = F.u[cur][t];
       F.v[1 - cur][t] = F.v[cur][t];
