@@ -203,6 +203,15 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   for (int q = 0; q < 6; ++q) d.pwf[q] = (float)d.pw[q];
   d.s3 = (d.isq[0] + d.isq[1] + d.isq[2]) / 3.0;
   d.s3f = (float)d.s3;
+  d.eta_exp = 0.5 * (p.n - 1.0);
+  d.dtf = (float)p.dt;
+  d.Prf = (float)p.Pr;
+  d.Raf = (float)p.Ra;
+  d.theta_reff = (float)p.theta_ref;
+  d.I2_epsf = (float)p.I2_eps;
+  d.eta_expf = (float)d.eta_exp;
+  d.a_limitf = (float)p.a_limit;
+  d.a_boostf = (float)p.a_boost;
   d.Ra = p.Ra;
   d.Pr = p.Pr;
   d.n = p.n;

@@ -41,6 +41,9 @@ struct DevParams {
   double s3;         // (1/h^2 + 1/k^2 + 1/l^2)/3: threshold of the pseudo-time mass (1/h^2 when
                      // h = k = l)
   float s3f;
+  double eta_exp;    // (n - 1)/2, the exponent of the regularised viscosity
+  // float copies of the scalars the float sweeps use (converted once on the host)
+  float dtf, Prf, Raf, theta_reff, I2_epsf, eta_expf, a_limitf, a_boostf;
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
   int precond;         // Jacobi row scaling of the level-(n+1) systems
   int solver;          // 0: BiCGSTAB; 1: BiCGSTAB(2) (planar FP64 solve)

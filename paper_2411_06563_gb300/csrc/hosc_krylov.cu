@@ -789,14 +789,15 @@ __device__ __forceinline__ double bytes4(const DevParams& P, double float4_words
 }
 
 // r = r_0, x = 0, p = v = 0 at interior nodes, every vector zero on the walls; ||r_0||^2.
+// Grid-stride over all N^3 nodes: each thread sums several nodes before the one block reduction.
 __global__ void __launch_bounds__(kThreads) k4_init(DevParams P, Fields F) {
   __shared__ double smem[32 * 4];
-  const int N = P.N;
-  const int n3 = N * N * N;
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned N = P.N;
+  const unsigned n3 = N * N * N;
   FF acc[4] = {};
-  if (c < n3) {
-    const int i = c % N, j = (c / N) % N, k = c / (N * N);
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += gridDim.x * blockDim.x) {
+    const unsigned q = c / N;
+    const unsigned i = c - q * N, j = q % N, k = q / N;
     const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
     const float4 z = f4(0.f);
     const float4 r = inner ? F.kr0[c] : z;
@@ -1450,7 +1451,9 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
   }
   if (P.krylov_fp32) {
     const long n3 = (long)P.N * P.N * P.N;
-    k4_init<<<red_blocks(n3), kThreads, 0, s>>>(P, F);
+    const int most = 8 * device_sms();   // resident blocks of one wave
+    const int b = red_blocks(n3) < most ? red_blocks(n3) : most;
+    k4_init<<<b, kThreads, 0, s>>>(P, F);
     return;
   }
   const int b = interior_blocks(P);

@@ -36,6 +36,13 @@ template <> __device__ __forceinline__ double tpow<double>(double x, double y) {
 template <> __device__ __forceinline__ float tpow<float>(float x, float y) { return powf(x, y); }
 
 
+// A scalar parameter in the arithmetic type T: the double, or its float copy made on the host.
+template <class T>
+__device__ __forceinline__ T par(double d, float f) {
+  if constexpr (sizeof(T) == sizeof(float)) return f;
+  else return d;
+}
+
 template <class T, class S>
 __device__ __forceinline__ T grad_axis_t(const S* __restrict__ f, long c, int a, int N, long st,
                                          T inv2h) {
@@ -134,10 +141,10 @@ __global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const T* __
     const Grad9T<T> g = velocity_gradients_t<T, T>(u, v, w, i, j, k, N, spacing<T>(P).i2);
     const T a = g.uz + g.wx, b = g.uy + g.vx, c = g.vz + g.wy;
     const T I2 = T(2) * (g.ux * g.ux + g.vy * g.vy + g.wz * g.wz) + a * a + b * b + c * c;
-    e = tpow<T>(I2 + (T)P.I2_eps, (T)(0.5 * (P.n - 1.0)));
+    e = tpow<T>(I2 + par<T>(P.I2_eps, P.I2_epsf), par<T>(P.eta_exp, P.eta_expf));
   }
   eta[t] = e;
-  L[t] = T(1) / ((T)P.Pr * e);
+  L[t] = T(1) / (par<T>(P.Pr, P.Prf) * e);
 }
 
 // ------------------------------------------------------------------------------------ S2
@@ -174,9 +181,10 @@ __global__ void __launch_bounds__(kThreads) k_sources(DevParams P, const T* __re
   const T pz = grad_axis_t<T>(p, t, k, N, sz, sp.i2[2]);
   const T e = eta[t];
   const T exy = T(0.5) * (g.uy + g.vx), exz = T(0.5) * (g.uz + g.wx), eyz = T(0.5) * (g.vz + g.wy);
-  const T a = T(1) / ((T)P.Pr * e), b = T(2) / e;
+  const T a = T(1) / (par<T>(P.Pr, P.Prf) * e), b = T(2) / e;
   Eu[t] = -px * a + b * (g.ux * ex + exy * ey + exz * ez);
-  Ev[t] = -py * a + b * (exy * ex + g.vy * ey + eyz * ez) + (T)P.Ra * ((T)th[t] - (T)P.theta_ref) / e;
+  Ev[t] = -py * a + b * (exy * ex + g.vy * ey + eyz * ez) +
+          par<T>(P.Ra, P.Raf) * ((T)th[t] - par<T>(P.theta_ref, P.theta_reff)) / e;
   Ew[t] = -pz * a + b * (exz * ex + eyz * ey + g.wz * ez);
 }
 
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0)
   const long sy = N, sz = (long)N * N;
   const long c = node(i, j, k, N);
   const Spc<Tc> sp = spacing<Tc>(P);
-  const Tc tdt = (Tc)P.dt;
+  const Tc tdt = par<Tc>(P.dt, P.dtf);
   Tc rv[4], Am[7], Ae[7];   // right-hand sides and weights, stored at the end
 
   Tc L7[7], u7[7], v7[7], w7[7];
@@ -377,10 +385,10 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0)
     Tc M18 = Tc(0.5) * (Lc - Lpc) + sp.s12[0] * (dL.dxx - cm.G * dL.dx) +
              sp.s12[1] * (dL.dyy - cm.H * dL.dy) + sp.s12[2] * (dL.dzz - cm.I * dL.dz);
     // keep the extrapolated mass positive where L changes fast (the steady state is unaffected)
-    if (P.a_limit > 0.0) M18 = fmax(M18, -(Tc)P.a_limit * Lc);
-    const Tc sig_m = P.a_boost > 0.0 ? pseudo_time_mass<Tc>(cm.G, cm.H, cm.I, Lc, tdt, sp.s3,
-                                                             (Tc)P.a_boost)
-                                     : Tc(0);
+    const Tc alim = par<Tc>(P.a_limit, P.a_limitf), kap = par<Tc>(P.a_boost, P.a_boostf);
+    if (alim > Tc(0)) M18 = fmax(M18, -alim * Lc);
+    const Tc sig_m =
+        kap > Tc(0) ? pseudo_time_mass<Tc>(cm.G, cm.H, cm.I, Lc, tdt, sp.s3, kap) : Tc(0);
     const Tc ax = Mx * sp.isq[0], ay = My * sp.isq[1], az = Mz * sp.isq[2];
     Am[0] = Lc * (Tc(1) - Tc(2) * (ax + ay + az)) + M18 + sig_m;
     Am[1] = Lc * (ax - Mx * cm.G * sp.i2[0] + m15 * sp.i2[0]);
@@ -399,9 +407,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0)
     const Tc m0 = Tc(-0.5) * tdt;
     const Tc Mx = m0 + sp.s12[0], My = m0 + sp.s12[1], Mz = m0 + sp.s12[2];
     const Tc ax = Mx * sp.isq[0], ay = My * sp.isq[1], az = Mz * sp.isq[2];
-    const Tc sig_e = P.a_boost > 0.0 ? pseudo_time_mass<Tc>(ce.G, ce.H, ce.I, Tc(1), tdt,
-                                                             sp.s3, (Tc)P.a_boost)
-                                     : Tc(0);
+    const Tc kap = par<Tc>(P.a_boost, P.a_boostf);
+    const Tc sig_e =
+        kap > Tc(0) ? pseudo_time_mass<Tc>(ce.G, ce.H, ce.I, Tc(1), tdt, sp.s3, kap) : Tc(0);
     Ae[0] = Tc(1) - Tc(2) * (ax + ay + az) + sig_e;
     Ae[1] = ax - Mx * ce.G * sp.i2[0];
     Ae[2] = ax + Mx * ce.G * sp.i2[0];
