@@ -62,3 +62,56 @@ def test_host_only_calls_without_gpu(libpath):
     bad.N = 3
     assert hosc.hosc_workspace_bytes(bad) == 0
     assert hosc.hosc_strerror(hosc.HOSC_ENOCONV).startswith("BiCGSTAB")
+
+
+def _c_layout(struct, fields, tmp_path):
+    """sizeof and offsetof of a header struct, from a C program compiled here with gcc."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    prog = ["#include <stdio.h>", "#include <stddef.h>", '#include "hosc.h"', "int main(void) {",
+            '  printf("%%zu\\n", sizeof(%s));' % struct]
+    prog += ['  printf("%%zu\\n", offsetof(%s, %s));' % (struct, f) for f in fields]
+    prog += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(prog) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-x", "c", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(v) for v in out[1:]]
+
+
+@pytest.mark.parametrize("name", ["hosc_params", "hosc_info", "hosc_diag", "hosc_pool_info"])
+def test_binding_structs_match_the_header(name, tmp_path):
+    """The ctypes structures of the binding have the header's size and field offsets (the
+    header is C; it is compiled here as C, without the CUDA toolkit)."""
+    from paper_2411_06563_gb300 import hosc
+    cls = getattr(hosc, name)
+    fields = [f[0] for f in cls._fields_]
+    cnames = ["lambda" if f == "lambda_" else f for f in fields]
+    size, offs = _c_layout(name, cnames, tmp_path)
+    assert ctypes.sizeof(cls) == size
+    assert [getattr(cls, f).offset for f in fields] == offs
+
+
+def test_box_and_solver_validation_on_the_host(libpath):
+    """Box lengths and the solver option are checked without a device; BiCGSTAB(2) adds three
+    N^3 vectors per system to the workspace."""
+    from paper_2411_06563_gb300 import hosc
+    p = hosc.hosc_default_params(21, 1e3, 1.0, 1.0)
+    assert p.Ly == 1.0 and p.Lz == 1.0 and p.solver == 0
+    base = hosc.hosc_workspace_bytes(p)
+    for Ly, Lz, ok in ((0.0, 0.0, True), (0.5, 2.0, True), (-1.0, 1.0, False),
+                       (1.0, 65.0, False), (0.01, 1.0, False)):
+        p.Ly, p.Lz = Ly, Lz
+        assert (hosc.hosc_workspace_bytes(p) > 0) == ok, (Ly, Lz)
+    p.Ly = p.Lz = 1.0
+    p.solver = 1
+    assert hosc.hosc_workspace_bytes(p) >= base + 12 * 21 ** 3 * 8
+    p.precision = hosc.HOSC_MIXED
+    assert hosc.hosc_workspace_bytes(p) == 0     # BiCGSTAB(2) is built for the FP64 solve
+    p.precision = hosc.HOSC_FP64
+    p.solver = 2
+    assert hosc.hosc_workspace_bytes(p) == 0
