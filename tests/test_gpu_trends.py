@@ -11,7 +11,14 @@ number at steady state, and Nu falls with n. So this ordering is not asserted at
 
 import pytest
 
+from golden_values import table
+
 pytestmark = pytest.mark.gpu
+
+RAS = (1e2, 1e3, 1e4, 1e5)
+TABLE3 = {(Ra, row[0]): row[1 + q] for row in table("table3_total_entropy.txt")
+          for q, Ra in enumerate(RAS)}
+TABLE4 = {(Ra, row[0]): row[1 + q] for row in table("table4_bejan.txt") for q, Ra in enumerate(RAS)}
 
 H = pytest.importorskip("paper_2411_06563_gb300.hosc")
 from paper_2411_06563_gb300 import serve as S  # noqa: E402
@@ -53,3 +60,21 @@ def test_heat_transfer_rises_and_bejan_falls_with_ra(steady):
         assert hi["Be"] < lo["Be"], n
         for d in (lo, hi):   # hot and cold walls carry the same heat at steady state
             assert abs(d["Nu_hot_mean"] - d["Nu_cold_mean"]) < 1e-3 * d["Nu_hot_mean"]
+
+
+def test_total_entropy_near_table3(steady):
+    """E_total of the 15^3 cavities lies within 10 % of Table 3's 51^3 values (7.4 % at most
+    measured). Near conduction Table 3 sits about 4 % above the exact value 1, which is
+    consistent with a factor (N/(N-1))^2 = 1.0404 in the paper's integral; the rest of the gap
+    is the coarse grid."""
+    for (Ra, n), d in steady.items():
+        ref = TABLE3[(Ra, n)]
+        assert abs(d["E_total"] / ref - 1.0) < 0.10, (Ra, n, d["E_total"], ref)
+
+
+def test_newtonian_bejan_near_table4(steady):
+    """For n = 1, where the viscosity in E_FF is 1 and the friction term has no reading to
+    choose, Be of the 15^3 cavities lies within 0.05 of Table 4's 51^3 values (0.976 against
+    0.975 at Ra = 1e3, 0.699 against 0.672 at Ra = 1e4)."""
+    for Ra in (1e3, 1e4):
+        assert abs(steady[(Ra, 1.0)]["Be"] - TABLE4[(Ra, 1.0)]) < 0.05, Ra
