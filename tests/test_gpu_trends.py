@@ -78,3 +78,4 @@ def test_newtonian_bejan_near_table4(steady):
     0.975 at Ra = 1e3, 0.699 against 0.672 at Ra = 1e4)."""
     for Ra in (1e3, 1e4):
         assert abs(steady[(Ra, 1.0)]["Be"] - TABLE4[(Ra, 1.0)]) < 0.05, Ra
+
