@@ -48,8 +48,8 @@ notes of the repository):
       one-sided along the wall normal, central along the wall.
 * R8  delta_t^- f = (f^n - f^{n-1})/dt for the coefficient fields; it is zero at the first step.
 * R9  M18 is read from the delta_t^+ bracket of Eq. (5) itself (the printed M18 line is garbled).
-* R10 Nu_local = -d theta/dx at the hot wall (fourth-order one-sided), Nu_avg(z) = int_0^1 dy
-      (Simpson), Nu_max = max_z Nu_avg(z) (the quantity of Table 2), Nu_mean = surface mean.
+* R10 Nu_local = -d theta/dx at the hot wall (fourth-order one-sided), Nu_avg(z) = its mean over
+      y (Simpson), Nu_max = max_z Nu_avg(z) (the quantity of Table 2), Nu_mean = surface mean.
 * R11 chi* = phi* = phi (default 1e-4), so E_FF = phi * eta * I2; Be = int E_HT / int E_local.
 * R12 The initial interior temperature is theta_init (default 1/2 = theta_ref): the fluid at rest
       with constant pressure is then in equilibrium with the buoyancy term at t = 0.
@@ -60,9 +60,20 @@ notes of the repository):
 * R19 Where the cell Reynolds number |G*| h is high, a diagonal pseudo-time mass is added to the
       level-(n+1) operator (see pseudo_time_mass). R18 and R19 change A only: the discrete steady
       state B chi = R of Eq. (5) is the paper's.
+* R22 Optional inner pressure passes within a step (the "previous pressure iteration" of
+      Sec. 2.2), see step; the default is one correction per step (R5).
+* R23 A box 1 x Ly x Lz with N nodes per side (spacings h, k, l), the general form of Eqs. (5)-(6);
+      the cube by default.
+* R24 solver = 1: BiCGSTAB(2), the other reading of the "hybrid" BiCGSTAB (solve_bicgstab_l).
+
+Parity unpinned (no value in the paper fixes them; each sets the pseudo-time path or regularises,
+and the steady state B chi = R does not depend on R18, R19, lambda or dt, which the steady-state
+pin checks): the regulariser eps of R1, the limiter a_limit of R18, the pseudo-time mass of R19,
+the relaxation lambda and the pseudo-time step dt.
 
 Layout: a field is a numpy array f[z, y, x] of shape (N, N, N); node (i, j, k) sits at
-x = i*h, y = j*k, z = k*l with h = k = l = 1/(N-1). The flattened index is i + N*(j + N*k).
+x = i*h, y = j*k, z = k*l with spacings h = 1/(N-1), k = Ly/(N-1), l = Lz/(N-1). The flattened
+index is i + N*(j + N*k).
 """
 
 import math
@@ -72,7 +83,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "Params", "Grid", "scalar_coefficients", "assemble_A", "apply_B", "solve_bicgstab",
-    "solve_system", "viscosity", "momentum_sources", "initial_state", "step", "solve_steady",
+    "solve_bicgstab_l", "solve_system", "viscosity", "momentum_sources", "initial_state", "step", "solve_steady",
     "apply_theta_bc", "apply_pressure_bc", "divergence", "diagnostics", "steady_certificate",
     "grad_full", "strain_gradients",
 ]
