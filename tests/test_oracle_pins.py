@@ -95,6 +95,26 @@ def test_mehrstellen_unequal_spacings():
     np.testing.assert_allclose(c["R"][ii], (E + corr)[ii], rtol=1e-13, atol=1e-12)
 
 
+@pytest.mark.parametrize("Ly,Lz", [(1.0, 1.0), (0.6, 1.45)])
+def test_checkerboard_mode_of_the_operators(Ly, Lz):
+    """Constant L, G* = H* = I* = K* = 0, no pseudo-time mass: on the grid mode that alternates
+    in all three directions (interior rows, the mode extended to the walls) the level-(n+1)
+    operator is 2 dt S with S = 1/h^2 + 1/k^2 + 1/l^2 (its compact mass h_d^2/12 cancels
+    exactly, whatever the spacings) and the level-n operator is (4/3) S, so one pseudo-time
+    step multiplies the mode by 1 - dt (4/3) S / (2 dt S) = 1/3."""
+    N, dt, Lc = 9, 0.003, 1.7
+    g = O.Grid(N, Ly, Lz)
+    one, zero = np.ones(N ** 3), np.zeros(N ** 3)
+    c = O.scalar_coefficients(g, dt, Lc * one, zero, zero, zero, zero, zero)
+    A = O.assemble_A(g, dt, c, a_limit=0.0, a_boost=0.0)
+    x, y, z = (np.rint(a.ravel() / s) for a, s in zip(g.coords(), (g.h, g.k, g.l)))
+    mode = (-1.0) ** (x + y + z)
+    S = 1 / g.h ** 2 + 1 / g.k ** 2 + 1 / g.l ** 2
+    ii = g.int_idx
+    np.testing.assert_allclose((A @ mode)[ii], 2 * dt * S * mode[ii], rtol=1e-12)
+    np.testing.assert_allclose(O.apply_B(g, c, mode)[ii], 4.0 / 3.0 * S * mode[ii], rtol=1e-12)
+
+
 # ------------------------------------------------------------------ manufactured solution
 
 PI = math.pi
