@@ -7,14 +7,15 @@
  * power-law stress tau* = 2 eta eps, eta = I2^((n-1)/2) (Eqs. 6-8), gravity along -y; hot wall
  * theta = 1 at x = 0, cold wall theta = 0 at x = 1, the other walls adiabatic, no slip on every
  * wall, zero normal pressure gradient on every wall. Parameters Ra, Pr and n (Sec. 2.1), the
- * uniform N^3 node grid with h = k = l = 1/(N-1) and the pseudo-time step dt (Sec. 3.1).
+ * uniform N^3 node grid with h = k = l = 1/(N-1) (or, for a box 1 x Ly x Lz, h = 1/(N-1),
+ * k = Ly/(N-1), l = Lz/(N-1); see hosc_params) and the pseudo-time step dt (Sec. 3.1).
  *
  * One pseudo-time step (Sec. 2.2):
  *   S1  power-law viscosity eta and L = 1/(Pr eta) from the local strain rate (Eqs. 7-8);
  *   S2  momentum sources E* (pressure gradient, eps . grad eta, buoyancy);
  *   S3  the fourth-order compact right-hand sides of Eq. (5)/(6) for u, v, w and theta;
  *   S4  the seven-point level-(n+1) operator of Eq. (5) (weights L1..L7 of Eq. 6);
- *   S5  unpreconditioned BiCGSTAB on the four systems;
+ *   S5  unpreconditioned BiCGSTAB on the four systems (BiCGSTAB(2) as an option);
  *   S6  wall conditions; S7 div V and the modified artificial-compressibility correction
  *       p <- p - lambda div V (Sec. 2.2, last paragraph); S8 the steady-state change max|chi^{n+1}-chi^n|.
  * Diagnostics (Sec. 4.2-4.3): local / average Nusselt numbers, entropy generation, Bejan number.
@@ -22,7 +23,7 @@
  * Conventions
  *  - Every call returns an hosc_status; nothing aborts and no C++ exception crosses the ABI.
  *  - Fields are N^3 arrays of double, x fastest: node (i, j, k) at index i + N*(j + N*k),
- *    x_i = i/(N-1), y_j = j/(N-1), z_k = k/(N-1).
+ *    x_i = i/(N-1), y_j = j Ly/(N-1), z_k = k Lz/(N-1) (Ly = Lz = 1 for the cube).
  *  - Host buffers passed in are owned by the caller and only read/written during the call.
  *  - A context owns its device memory (or uses a caller-supplied device workspace) and all work
  *    is enqueued on one CUDA stream (the caller's, or one it creates). A context must not be used
@@ -86,7 +87,7 @@ typedef enum {
   HOSC_STAGE_VISCOSITY = 0, /* S1: eta, L */
   HOSC_STAGE_SOURCES = 1,   /* S2: E* of the three momentum equations */
   HOSC_STAGE_RHS = 2,       /* S3/S4: right-hand sides and the level-(n+1) operators */
-  HOSC_STAGE_SOLVE = 3,     /* S5: BiCGSTAB on the four systems */
+  HOSC_STAGE_SOLVE = 3,     /* S5: BiCGSTAB (or BiCGSTAB(2)) on the four systems */
   HOSC_STAGE_UPDATE = 4     /* S6-S8: increments, walls, div V, pressure, history */
 } hosc_stage;
 
@@ -146,7 +147,8 @@ typedef struct {
 
 typedef struct {
   long steps;         /* steps taken by this call */
-  long lin_iters;     /* BiCGSTAB iterations summed over systems and steps of this call */
+  long lin_iters;     /* BiCGSTAB iterations summed over systems and steps of this call (two per
+                         BiCGSTAB(2) cycle) */
   int last_iters[4];  /* iterations of the last step's u, v, w, theta solves */
   double res_steady;  /* max over u, v, w, theta of max|chi^{n+1} - chi^n| of the last step */
   double div_max;     /* max|div V^{n+1}| at interior nodes of the last step */
