@@ -625,6 +625,29 @@ def test_steady_state_balance_entropy_and_certificate():
         assert np.max(np.abs(st2[key] - st[key])) < 1e-5 * max(1.0, np.abs(st[key]).max())
 
 
+def test_steady_state_is_unique():
+    """The steady state reached from rest is reached again from a random start (no-slip random
+    velocities, random temperature with the wall conditions), which breaks every symmetry: the
+    fields agree to 1e-10 of their size. The steady state of this power-law cavity is unique, so
+    comparing final fields between the oracle and the GPU path is well posed."""
+    N = 9
+    h = 1.0 / (N - 1)
+    prm = O.Params(N=N, Ra=1e3, n=0.75, dt=0.01, lam=0.25 * h * h / 0.01, tol_lin=1e-11,
+                   tol_div=1e-7)
+    a, ia = O.solve_steady(prm, 6000, tol_steady=1e-9)
+    rng = np.random.default_rng(21)
+    st = O.initial_state(prm)
+    for key in ("u", "v", "w"):
+        f = np.zeros((N, N, N))
+        f[1:-1, 1:-1, 1:-1] = 2.0 * rng.standard_normal((N - 2,) * 3)
+        st[key] = f
+    st["th"] = O.apply_theta_bc(rng.random((N, N, N)))
+    b, ib = O.solve_steady(prm, 8000, tol_steady=1e-9, state=st)
+    assert ia["status"] == 0 and ib["status"] == 0
+    for key in ("u", "v", "w", "th", "p"):
+        assert np.max(np.abs(a[key] - b[key])) <= 1e-9 * max(1.0, np.abs(a[key]).max()), key
+
+
 TABLE2 = {Ra: nu for Ra, nu in table("table2_newtonian_nu_max.txt")}
 
 
