@@ -78,8 +78,9 @@ def _c_layout(struct, fields, tmp_path):
     src.write_text("\n".join(prog) + "\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-x", "c", "-I", os.path.join(ROOT, "include"), str(src), "-o",
-                    str(exe)], check=True)
-    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+                    str(exe)], check=True, capture_output=True, timeout=120)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True,
+                         timeout=60).stdout.split()
     return int(out[0]), [int(v) for v in out[1:]]
 
 
@@ -115,3 +116,43 @@ def test_box_and_solver_validation_on_the_host(libpath):
     p.precision = hosc.HOSC_FP64
     p.solver = 2
     assert hosc.hosc_workspace_bytes(p) == 0
+
+
+def test_c_client_links_and_calls_host_entry_points(libpath, tmp_path):
+    """A plain C program includes the header, links the library and calls the entry points that
+    need no device (defaults, validation, workspace sizing, error strings): the boundary is usable
+    from C without Python or the CUDA toolkit."""
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "client.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "hosc.h"
+int main(void) {
+  hosc_params p;
+  if (hosc_default_params(&p, 21, 1e3, 1.0, 0.75) != HOSC_OK) return 1;
+  if (p.N != 21 || p.Ly != 1.0 || p.solver != 0) return 2;
+  size_t b = hosc_workspace_bytes(&p);
+  if (b == 0) return 3;
+  p.solver = 1;
+  if (hosc_workspace_bytes(&p) <= b) return 4;     /* BiCGSTAB(2) vectors */
+  p.N = 3;
+  if (hosc_workspace_bytes(&p) != 0) return 5;      /* invalid: N < 5 */
+  if (hosc_default_params(NULL, 21, 1e3, 1.0, 1.0) != HOSC_EINVAL) return 6;
+  if (strlen(hosc_strerror(HOSC_ENOCONV)) == 0) return 7;
+  printf("ok %zu\n", b);
+  return 0;
+}
+""")
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(libpath)
+    lib = os.path.basename(libpath)
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe),
+                    os.path.join(libdir, lib), "-Wl,-rpath," + libdir], check=True,
+                   capture_output=True, timeout=120)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert out.stdout.startswith("ok ")
