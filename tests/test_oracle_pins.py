@@ -532,6 +532,33 @@ def test_box_gradients_sources_and_wall_averages():
     np.testing.assert_allclose(d["E_HT"], tx ** 2 + ty ** 2 + tz ** 2, rtol=0, atol=1e-11)
 
 
+def test_wall_extrapolations_are_exact_on_quadratics():
+    """The zero-normal-gradient wall rules (pressure on every wall, R5; theta on the adiabatic y
+    and z walls, R6) set the wall value (4 f_1 - f_2)/3, the second-order one-sided statement of
+    df/dn = 0: exact for a quadratic with zero slope at that wall. Checked on each wall with
+    f = s^2 in the wall-normal distance s, away from the edges the later walls overwrite."""
+    N = 9
+    g = O.Grid(N)
+    x, y, z = g.coords()
+    inner = slice(2, -2)
+    for axis, coord in ((2, x), (1, y), (0, z)):
+        for f in (coord ** 2, (1.0 - coord) ** 2):
+            p = O.apply_pressure_bc(f + 0.0)
+            walls = [np.take(p, 0, axis=axis), np.take(p, -1, axis=axis)]
+            exact = [np.take(f, 0, axis=axis), np.take(f, -1, axis=axis)]
+            side = 0 if f[0, 0, 0] == 0.0 else 1   # the wall where f has zero slope
+            np.testing.assert_allclose(walls[side][inner, inner], exact[side][inner, inner],
+                                       atol=1e-14)
+    for axis, coord in ((1, y), (0, z)):       # theta: adiabatic y and z walls
+        for f in (coord ** 2, (1.0 - coord) ** 2):
+            t = O.apply_theta_bc(f + 0.0)
+            side = 0 if np.take(f, 0, axis=axis).max() == 0.0 else -1
+            np.testing.assert_allclose(np.take(t, side, axis=axis)[inner, inner],
+                                       np.take(f, side, axis=axis)[inner, inner], atol=1e-14)
+    t = O.apply_theta_bc(np.full((N, N, N), 0.3))
+    assert np.all(t[:, :, 0] == 1.0) and np.all(t[:, :, -1] == 0.0)   # isothermal x walls
+
+
 def test_conduction_reached_from_rest_ra0():
     prm = O.Params(N=9, Ra=0.0, n=0.75, tol_lin=1e-10)
     st, info = O.solve_steady(prm, 400, tol_steady=1e-10)
