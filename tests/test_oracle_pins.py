@@ -532,6 +532,27 @@ def test_box_gradients_sources_and_wall_averages():
     np.testing.assert_allclose(d["E_HT"], tx ** 2 + ty ** 2 + tz ** 2, rtol=0, atol=1e-11)
 
 
+def test_second_invariant_and_viscosity_closed_forms():
+    """Eq. (8) and the power law of Eq. (7) on linear velocity fields, for which every difference
+    formula is exact: simple shear u = g y gives I2 = g^2, planar extension u = a x, v = -a y
+    gives I2 = 4 a^2, and their sum adds (2 a^2 + 2 a^2 + g^2); eta = (I2 + eps)^((n-1)/2) at
+    every node, and on the cube edges (R1b) the value of the node inward along the wall normals,
+    which for these fields is the same."""
+    N, gam, a, n = 7, 3.0, 1.5, 0.75
+    prm = O.Params(N=N, Ra=0.0, n=n)
+    g = O.Grid(N)
+    x, y, z = g.coords()
+    zero = np.zeros_like(x)
+    cases = ((gam * y, zero, zero, gam ** 2), (a * x, -a * y, zero, 4 * a * a),
+             (a * x + gam * y, -a * y, zero, 4 * a * a + gam ** 2))
+    for u, v, w, I2 in cases:
+        eta, I2n, _ = O.viscosity(u, v, w, prm)
+        np.testing.assert_allclose(I2n, I2, rtol=1e-12)
+        np.testing.assert_allclose(eta, (I2 + prm.I2_eps) ** (0.5 * (n - 1.0)), rtol=1e-12)
+    eta, _, _ = O.viscosity(zero, zero, zero, O.Params(N=N, Ra=0.0, n=1.0))
+    assert np.all(eta == 1.0)   # n = 1: exactly Newtonian
+
+
 def test_wall_extrapolations_are_exact_on_quadratics():
     """The zero-normal-gradient wall rules (pressure on every wall, R5; theta on the adiabatic y
     and z walls, R6) set the wall value (4 f_1 - f_2)/3, the second-order one-sided statement of
