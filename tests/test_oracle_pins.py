@@ -553,6 +553,46 @@ def test_second_invariant_and_viscosity_closed_forms():
     assert np.all(eta == 1.0)   # n = 1: exactly Newtonian
 
 
+def _stress_source_error(N):
+    """Max error of E* (p = 0, Ra = 0) against the conservative form of the power-law momentum
+    equation: for a solenoidal V, div(2 eta eps)/eta = lap V + (2/eta) eps . grad eta, so E*
+    must equal div(2 eta eps)/eta - lap V, here evaluated independently with numpy's
+    second-order differences of the stress tensor in flux form."""
+    prm = O.Params(N=N, Ra=0.0, Pr=0.7, n=1.0)
+    g = O.Grid(N)
+    x, y, z = g.coords()
+    h = g.h
+    pi = math.pi
+    # solenoidal: u = d psi/dy, v = -d psi/dx with psi = sin(pi x) sin(pi y) (1 + z/2)
+    s_z = 1.0 + 0.5 * z
+    u = pi * np.sin(pi * x) * np.cos(pi * y) * s_z
+    v = -pi * np.cos(pi * x) * np.sin(pi * y) * s_z
+    w = np.zeros_like(x)
+    eta = 1.0 + 0.3 * np.sin(x + 2.0 * y + 0.5 * z)
+    gr = O.strain_gradients(u, v, w, h)
+    Eu, Ev, Ew = O.momentum_sources(u, v, w, np.zeros_like(x), np.zeros_like(x), eta, gr, prm)
+    d = lambda f, ax: np.gradient(f, h, axis=ax, edge_order=2)   # axes: 0 z, 1 y, 2 x
+    vel = (u, v, w)
+    axes = (2, 1, 0)
+    eps = [[0.5 * (d(vel[i], axes[j]) + d(vel[j], axes[i])) for j in range(3)] for i in range(3)]
+    err = 0.0
+    for i, E in enumerate((Eu, Ev, Ew)):
+        div = sum(d(2.0 * eta * eps[i][j], axes[j]) for j in range(3))
+        lap = sum(d(d(vel[i], axes[j]), axes[j]) for j in range(3))
+        ref = div / eta - lap
+        sl = (slice(2, -2),) * 3
+        err = max(err, float(np.max(np.abs(E[sl] - ref[sl]))))
+    return err
+
+
+def test_momentum_sources_match_the_conservative_stress():
+    """Reading R2 of the momentum sources against the conservative form div(2 eta eps) of the
+    power-law stress (Sec. 2.1): the difference falls at second order with h, so the factor 2
+    and the index pattern of eps . grad eta are those of the stress divergence."""
+    e1, e2 = _stress_source_error(33), _stress_source_error(65)
+    assert math.log2(e1 / e2) > 1.8, (e1, e2)
+
+
 def test_wall_extrapolations_are_exact_on_quadratics():
     """The zero-normal-gradient wall rules (pressure on every wall, R5; theta on the adiabatic y
     and z walls, R6) set the wall value (4 f_1 - f_2)/3, the second-order one-sided statement of
