@@ -12,6 +12,9 @@ stand in for developed flow states and for the batched / served request mixes:
   [0.75, 1.25] (seed 20241106).
 * ``request_stream``: Poisson arrivals, N in {21, 31, ..., 101}, log10 Ra uniform in [2, 5],
   n in {0.75, 1.0, 1.25} (seed 20241107).
+* ``steady_mix``: small cavities that reach steady state at dt = 0.02 (N in {17, 21}, log10 Ra
+  uniform in [2, 3], n uniform in [0.9, 1.1]; seed 20241108), for the equal-accuracy comparison.
+* ``perturbed``: a nearby state (a previous time level for the history terms).
 
 Arrays are float64 of shape (N, N, N) indexed [z, y, x].
 """
