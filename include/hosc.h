@@ -306,10 +306,13 @@ int hosc_get_phase(void* ctx);
 long hosc_kernel_launches(void* ctx);
 
 /* Allocation-free BiCGSTAB solve of the four level-(n+1) systems of one step, for callers that
- * cannot call cudaMalloc: code that runs while a stream is being captured into a CUDA graph (where
- * cudaMalloc is not permitted), loops with a fixed memory budget that must not synchronise the
- * device (cudaMalloc may), and hosts whose own allocator already owns the device memory. The
- * paper has no counterpart; this is an interface of this library.
+ * cannot call cudaMalloc: hosts whose own allocator (a framework's caching allocator, a memory
+ * pool sized at start-up) already owns the device memory, so that a cudaMalloc beside it would
+ * fail or fragment the pool, and solvers that run under a fixed device-memory budget decided
+ * before the first step. The paper has no counterpart; this is an interface of this library.
+ * The call is synchronous: every 4 to 16 iterations it copies the four systems' solver scalars to
+ * a host array and waits for the stream (cudaStreamSynchronize) to test convergence, and it
+ * returns once the solve has finished.
  *
  * Solves A_mom x_s = rhs_s for s = u, v, w and A_ene x_theta = rhs_theta with the same kernels as
  * hosc_step (FP64 BiCGSTAB from x = 0, stop when ||r|| <= tol ||r_0||), on the interior nodes of

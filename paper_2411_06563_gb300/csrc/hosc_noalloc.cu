@@ -2,7 +2,9 @@
 // any device allocation. The Krylov vectors, reduction partials and solver scalars live in one
 // file-scope device array of fixed size (HOSC_NOALLOC_MAX_N nodes per side), shared by every call
 // in the process; inputs and outputs are the caller's device arrays. The kernels are the ones of
-// the context path (hosc_krylov.cu), so the result equals the context's solve.
+// the context path (hosc_krylov.cu), so the result equals the context's solve. The host checks
+// convergence every 4 to 16 iterations: it copies the four systems' solver scalars to the host and
+// synchronises the stream, so a call returns only once its solve has finished.
 
 #include <cuda_runtime.h>
 #include <string.h>
@@ -25,6 +27,16 @@ constexpr size_t kVectorsBytes = 24 * ((kVecBytes + kAlignB - 1) / kAlignB * kAl
 constexpr size_t kMaxBlocks = (kMaxNodes + kThreads - 1) / kThreads;
 constexpr size_t kControlBytes = 64 * 1024 + kMaxBlocks * kRedSlots * sizeof(double);
 constexpr size_t kScratchBytes = kVectorsBytes + kControlBytes;
+// Offsets of the control block: solver scalars at 0, ticket counter at 512, halt flag at 768,
+// per-kernel byte counters at 1024, reduction partials from 4096 on.
+constexpr size_t kOffCounter = 512, kOffHalt = 768, kOffBytes = 1024, kOffRed = 4096;
+static_assert(4 * sizeof(KrylovScalars) <= kOffCounter, "solver scalars overlap the counter");
+static_assert(kOffCounter + sizeof(unsigned int) <= kOffHalt, "counter overlaps the halt flag");
+static_assert(kOffHalt + sizeof(int) <= kOffBytes, "halt flag overlaps the byte counters");
+static_assert(kOffBytes + HOSC_K_COUNT * sizeof(double) <= kOffRed,
+              "byte counters overlap the reduction partials");
+static_assert(kOffRed + kMaxBlocks * kRedSlots * sizeof(double) <= kControlBytes,
+              "reduction partials exceed the control block");
 
 // The scratch. In host code this name is only a stand-in for the symbol: its device address comes
 // from cudaGetSymbolAddress, once per device.
@@ -81,11 +93,11 @@ extern "C" hosc_status hosc_bicgstab_noalloc(int N, const double* const* weights
   }
   const size_t vec_used = (size_t)(p - base);
   char* ctl = base + kVectorsBytes;
-  F.ks = (KrylovScalars*)ctl;                                   // 4 x 64 bytes
-  F.counter = (unsigned int*)(ctl + 512);
-  F.halt = (int*)(ctl + 768);
-  F.alg_bytes = (double*)(ctl + 1024);
-  F.red = (double*)(ctl + 4096);
+  F.ks = (KrylovScalars*)ctl;                      // 4 x sizeof(KrylovScalars) = 320 bytes
+  F.counter = (unsigned int*)(ctl + kOffCounter);
+  F.halt = (int*)(ctl + kOffHalt);
+  F.alg_bytes = (double*)(ctl + kOffBytes);
+  F.red = (double*)(ctl + kOffRed);
   for (int q = 0; q < 7; ++q) {
     F.Am[q] = const_cast<double*>(weights[q]);
     F.Ae[q] = const_cast<double*>(weights[7 + q]);
@@ -97,7 +109,7 @@ extern "C" hosc_status hosc_bicgstab_noalloc(int N, const double* const* weights
   // Every call shares the scratch and finds the previous call's contents: the vectors must read
   // zero on the walls and the ticket counter and halt flag must start at zero.
   if (cudaMemsetAsync(base, 0, vec_used, sm) != cudaSuccess) return HOSC_ECUDA;
-  if (cudaMemsetAsync(ctl, 0, 4096, sm) != cudaSuccess) return HOSC_ECUDA;
+  if (cudaMemsetAsync(ctl, 0, kOffRed, sm) != cudaSuccess) return HOSC_ECUDA;
 
   DevParams P;
   memset(&P, 0, sizeof(P));

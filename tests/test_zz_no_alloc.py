@@ -1,12 +1,11 @@
 """The allocation-free solve entry point (hosc_bicgstab_noalloc) against the context's own
 BiCGSTAB stage, through the C ABI.
 
-Callers that cannot call cudaMalloc (code running during a stream capture, budgeted loops that
-must not synchronise the device, hosts whose allocator owns all device memory) pass their own
-input and output arrays; the scratch of the solve lives in a fixed device array inside the
-library. Here the inputs are the right-hand sides and operator weights a context computed for one
-step, copied into caller-owned torch buffers, and the outputs must match the increments the
-context's solve produced (relative 1e-12, the FP64 parity tolerance of the solve is 1e-9), on two
+Callers that cannot call cudaMalloc (hosts whose allocator or memory pool already owns the device
+memory, solvers held to a device-memory budget fixed at start-up) pass their own input and output
+arrays; the scratch of the solve lives in a fixed device array inside the library. Here the
+inputs are the right-hand sides and operator weights a context computed for one step, copied into
+caller-owned torch buffers, and the outputs must match the increments the context's solve produced (relative 1e-12, the FP64 parity tolerance of the solve is 1e-9), on two
 calls in a row with different grid sizes (the second call finds the first call's scratch).
 """
 
