@@ -66,10 +66,18 @@ notes of the repository):
       the cube by default.
 * R24 solver = 1: BiCGSTAB(2), the other reading of the "hybrid" BiCGSTAB (solve_bicgstab_l).
 
+Pinned readings without a printed value: R18 (the limited operator differs from the unlimited
+one only on the diagonal, exactly where M18/L is below -a_limit, and both reach one steady
+state), R19 (the frozen-coefficient amplification of the two highest grid modes, worked out by
+hand from Eq. 5: the mass starts exactly where the unmassed amplification of the checkerboard
+mode reaches zero, or where that of the one-direction mode passes -1, and keeps both within
+[-1, 1]), R1b (a field whose edge strain differs from its neighbours'), R11 (E_FF in closed form
+on linear fields).
+
 Parity unpinned (no value in the paper fixes them; each sets the pseudo-time path or regularises,
-and the steady state B chi = R does not depend on R18, R19, lambda or dt, which the steady-state
-pin checks): the regulariser eps of R1, the limiter a_limit of R18, the pseudo-time mass of R19,
-the relaxation lambda and the pseudo-time step dt.
+and the steady state B chi = R does not depend on lambda or dt, which the steady-state pin
+checks): the regulariser eps of R1 (the 9^3 steady state is the same to ten digits for eps from
+1e-12 to 1e-8), the relaxation lambda and the pseudo-time step dt.
 
 Layout: a field is a numpy array f[z, y, x] of shape (N, N, N); node (i, j, k) sits at
 x = i*h, y = j*k, z = k*l with spacings h = 1/(N-1), k = Ly/(N-1), l = Lz/(N-1). The flattened

@@ -756,6 +756,22 @@ def test_newtonian_limit_table2_ra1e3_coarse():
     assert abs(flux - d["Nu_hot_mean"]) / d["Nu_hot_mean"] < 2e-2
 
 
+def test_newtonian_limit_table2_ra1e4_coarse():
+    """n = 1, Pr = 0.71, Ra = 1e4: Table 2 prints max Nu_avg = 2.256 on 51^3. On 17^3 the
+    oracle's steady state gives 2.2815 (1.1 % above) and on 21^3 2.2689 (0.6 % above); a
+    fourth-order Richardson extrapolation of the two, 2.260, is within 0.2 % of the printed value.
+    The test runs 17^3 with a 1.5 % tolerance, and checks the hot/cold wall balance."""
+    N = 17
+    dt = 0.0022
+    prm = O.Params(N=N, Ra=1e4, Pr=0.71, n=1.0, dt=dt, lam=1.2, tol_lin=1e-9, use_history=0)
+    st, info = O.solve_steady(prm, 4000, tol_steady=1e-6 * dt, div_stop=np.inf)
+    assert info["status"] == 0 and info["res"] < 1e-6 * dt
+    d = O.diagnostics(st, prm)
+    assert d["Nu_hot_max"] == pytest.approx(TABLE2[1e4], rel=1.5e-2)
+    assert d["Nu_hot_max"] > TABLE2[1e4]          # approached from above as the grid refines
+    assert abs(d["Nu_hot_mean"] - d["Nu_cold_mean"]) < 1e-6 * d["Nu_hot_mean"]
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("Ra,dt", [(1e3, 0.02), (1e4, 0.004), (1e5, 5e-4)])
 def test_newtonian_limit_table2_51(Ra, dt):
@@ -768,3 +784,211 @@ def test_newtonian_limit_table2_51(Ra, dt):
     assert info["status"] == 0
     d = O.diagnostics(st, prm)
     assert d["Nu_hot_max"] == pytest.approx(TABLE2[Ra], rel=1.5e-2)
+
+
+# ------------------------------------------------- reading R19: the pseudo-time mass, and R18
+
+def _mode_ratio(g, op_vals, mode):
+    """op_vals / mode at interior nodes; the mode is an eigenvector there when all the ratios
+    agree (constant coefficients), and the common value is returned."""
+    ii = g.int_idx
+    r = op_vals[ii] / mode[ii]
+    assert np.max(np.abs(r - r[0])) <= 1e-10 * max(1.0, abs(r[0]))
+    return float(r[0])
+
+
+def _amplification(g, dt, Lc, G, mode, boost):
+    """Frozen-coefficient amplification of one pseudo-time step chi <- chi - dt A^-1 B chi on a
+    grid mode (R = 0): 1 - dt b / a with a, b the eigenvalues of the level-(n+1) and level-n
+    operators of Eq. (5) on that mode (constant L and G*, K* = 0, no history)."""
+    N = g.N
+    one = np.ones(N ** 3)
+    c = O.scalar_coefficients(g, dt, Lc * one, G[0] * one, G[1] * one, G[2] * one, 0 * one,
+                              0 * one)
+    A = O.assemble_A(g, dt, c, a_limit=0.0, a_boost=boost)
+    a = _mode_ratio(g, A @ mode, mode)
+    b = _mode_ratio(g, O.apply_B(g, c, mode), mode)
+    return 1.0 - dt * b / a, a, b
+
+
+@pytest.mark.parametrize("Ly,Lz", [(1.0, 1.0), (0.6, 1.45)])
+def test_pseudo_time_mass_checkerboard_mode(Ly, Lz):
+    """Reading R19 on the mode alternating in all three directions. By hand from Eq. (5) with
+    constant L and G*: every first difference of the mode vanishes and delta_d^2 -> -4/h_d^2, so
+    the level-(n+1) operator is 2 dt S (S = sum 1/h_d^2) plus the mass, and the level-n
+    operator is (4/3) S + |G*|^2/3 (the compact terms alpha, beta, gamma add G_d^2/3 and the
+    three edge groups take 8S/3 back). Without the mass the amplification is therefore
+    1/3 - |G*|^2/(6S): it reaches 0 at |G*|^2 = 2S and passes -1 at |G*|^2 = 8S (the mode then
+    grows). The mass must be zero while that amplification is >= 0, start exactly where it
+    reaches 0 (a factor 3 on S in the onset moves it to -2/3), and keep the amplification in
+    (-1, 0] for every larger |G*|. The operators are the oracle's; the closed forms are not."""
+    N, dt, Lc = 9, 0.003, 1.3
+    g = O.Grid(N, Ly, Lz)
+    x, y, z = (np.rint(a.ravel() / s) for a, s in zip(g.coords(), (g.h, g.k, g.l)))
+    mode = (-1.0) ** (x + y + z)
+    S = 1 / g.h ** 2 + 1 / g.k ** 2 + 1 / g.l ** 2
+    direction = np.array([0.6, -0.48, 0.64])      # unit vector: G* not along an axis
+    for q in (0.0, 0.5, 1.0, 1.5, 1.999, 2.0, 2.001, 3.0, 6.0, 7.9, 8.0, 8.1, 20.0, 400.0):
+        G = math.sqrt(q * S) * direction
+        g0, a0, b0 = _amplification(g, dt, Lc, G, mode, 0.0)
+        assert a0 == pytest.approx(2 * dt * S, rel=1e-10)
+        assert b0 == pytest.approx(4 * S / 3 + q * S / 3, rel=1e-10)
+        assert g0 == pytest.approx(1.0 / 3.0 - q / 6.0, abs=1e-10)
+        assert (abs(g0) > 1.0 + 1e-12) == (q > 8.0)
+        g1, a1, _ = _amplification(g, dt, Lc, G, mode, 1.0)
+        massed = a1 - a0 > 1e-12 * a0
+        if q <= 2.0:
+            assert not massed, q       # no mass while the unmassed amplification is >= 0
+            assert g1 == pytest.approx(g0, abs=1e-12)
+        else:
+            assert massed, q
+            assert -1.0 < g1 <= 1e-12, q
+        # the mass's onset is where the unmassed amplification is zero
+        assert massed == (g0 < -1e-9)
+
+
+def test_pseudo_time_mass_one_direction_mode():
+    """Reading R19 on the mode alternating along x only, constant along y and z. By hand from
+    Eq. (5): the level-(n+1) operator is (2/3) L + 2 dt/h^2 (+ mass) and the level-n operator
+    4/h^2 + G_x^2/3, so without the mass the amplification passes -1 exactly when
+    dt G_x^2 > 4 L (the stability bound of the scheme as printed). With G* along x the second
+    term of the mass (dt |G*|^2/6 - 2L/3) starts exactly there and holds the amplification at
+    -1 or above for larger dt, on a grid fine enough that the first term stays zero."""
+    N, Lc = 9, 0.8
+    g = O.Grid(N)
+    x = np.rint(g.coords()[0].ravel() / g.h)
+    mode = (-1.0) ** x
+    h2 = g.h ** 2
+    G = np.array([9.0, 0.0, 0.0])
+    for ratio in (0.2, 0.9, 1.0, 1.1, 2.0, 5.0, 50.0):      # dt G^2 / (4 L)
+        dt = ratio * 4.0 * Lc / G[0] ** 2
+        g0, a0, b0 = _amplification(g, dt, Lc, G, mode, 0.0)
+        assert a0 == pytest.approx(2.0 * Lc / 3.0 + 2.0 * dt / h2, rel=1e-10)
+        assert b0 == pytest.approx(4.0 / h2 + G[0] ** 2 / 3.0, rel=1e-10)
+        assert (g0 < -1.0 - 1e-12) == (ratio > 1.0)
+        g1, a1, _ = _amplification(g, dt, Lc, G, mode, 1.0)
+        assert G[0] ** 2 <= 2.0 * 3.0 / h2     # first term of the mass inactive on this grid
+        assert (a1 - a0 > 1e-12 * a0) == (ratio > 1.0)
+        assert g1 >= -1.0 - 1e-12 and g1 <= 1.0
+        if ratio > 1.0:
+            assert g1 == pytest.approx(-1.0, abs=1e-12)
+
+
+def test_m18_limiter_acts_only_on_the_diagonal_below_its_limit():
+    """Reading R18 on coefficients with a steep viscosity (L varies by a factor of about 50
+    across the grid and dropped by half since the previous level): the limited operator differs
+    from the unlimited one on the diagonal only, never lowers it, and leaves it unchanged where
+    the diagonal bracket M18/L is above -a_limit. M18/L is recovered from the unlimited matrix
+    itself: its diagonal is L (1 + sum_d (dt/L - h_d^2/6)/h_d^2 + M18/L) because
+    delta_d^2 has diagonal -2/h_d^2 and delta_d none. Where it is below -a_limit, the limited
+    diagonal holds exactly -a_limit in its place."""
+    N, dt, lim = 9, 0.004, 0.25
+    g = O.Grid(N, 0.8, 1.2)
+    x, y, z = (a.ravel() for a in g.coords())
+    L = np.exp(2.0 * np.sin(3.0 * x + 1.0) * np.cos(2.0 * y) + 1.5 * z)
+    one, zero = np.ones(N ** 3), np.zeros(N ** 3)
+    G, Hh, I = 3.0 * np.sin(5 * y), 2.0 * np.cos(4 * z), -np.sin(3 * x)
+    prev = dict(L=L * (1.0 + 1.2 * np.sin(4.0 * x * y + 3.0 * z)), G=G, H=Hh, I=I, K=zero,
+                E=zero)
+    c = O.scalar_coefficients(g, dt, L, G, Hh, I, zero, zero, prev=prev)
+    A0 = O.assemble_A(g, dt, c, a_limit=0.0, a_boost=0.0)
+    A1 = O.assemble_A(g, dt, c, a_limit=lim, a_boost=0.0)
+    diff = (A1 - A0).tocoo()
+    off = diff.row != diff.col
+    assert np.all(np.abs(diff.data[off]) <= 1e-12 * np.abs(A0).max())
+    ii = g.int_idx
+    base = 1.0 + sum((dt / L - s * s / 6.0) / (s * s) for s in (g.h, g.k, g.l))
+    m0 = A0.diagonal() / L - base
+    m1 = A1.diagonal() / L - base
+    below = m0[ii] < -lim
+    assert 0 < below.sum() < len(ii)           # the limiter acts at some nodes, not all
+    assert np.all(A1.diagonal()[ii] >= A0.diagonal()[ii] - 1e-12 * np.abs(A0.diagonal()).max())
+    np.testing.assert_allclose(m1[ii][~below], m0[ii][~below], rtol=0, atol=1e-9)
+    np.testing.assert_allclose(m1[ii][below], -lim, rtol=0, atol=1e-9)
+
+
+LAM_M18 = 1.0
+
+
+def test_m18_limiter_does_not_change_the_steady_state():
+    """Reading R18 changes the level-(n+1) operator only, so the fixed point B chi = R is the
+    same with and without it: from a random start with history (the viscosity changes fast, so
+    the limiter acts on the first steps and the trajectories part), both marches reach one
+    steady state, to 1e-9 of the fields."""
+    N = 9
+    rng = np.random.default_rng(18)
+    st0 = O.initial_state(O.Params(N=N, Ra=1e3, n=0.75))
+    for key in ("u", "v", "w"):
+        f = np.zeros((N, N, N))
+        f[1:-1, 1:-1, 1:-1] = 3.0 * rng.standard_normal((N - 2,) * 3)
+        st0[key] = f
+    out = []
+    for lim in (0.0, 0.25):
+        prm = O.Params(N=N, Ra=1e3, n=0.75, dt=0.01, lam=LAM_M18, tol_lin=1e-12, tol_div=1e-9,
+                       a_limit=lim, use_history=1)
+        g = O.Grid(N)
+        st, _ = O.step(dict(st0), prm, g)
+        st, _ = O.step(st, prm, g)
+        early = st["u"].copy()
+        st, info = O.solve_steady(prm, 6000, tol_steady=1e-11, state=st, g=g)
+        assert info["status"] == 0 and info["res"] < 1e-11
+        out.append((early, st))
+    assert np.max(np.abs(out[0][0] - out[1][0])) > 1e-6      # the limiter acted early on
+    for key in ("u", "v", "w", "th", "p"):
+        a, b = out[0][1][key], out[1][1][key]
+        assert np.max(np.abs(a - b)) <= 1e-9 * max(1.0, np.abs(a).max()), key
+
+
+# --------------------------------------------- entropy of fluid friction (R11), edge rule (R1b)
+
+@pytest.mark.parametrize("n", [0.75, 1.0, 1.25])
+def test_fluid_friction_entropy_closed_forms(n):
+    """Sec. 4.3 with reading R11: E_FF = phi eta I2. On linear fields every difference is exact:
+    simple shear u = g y has I2 = g^2, planar extension u = a x, v = -a y has I2 = 4 a^2; with
+    theta = 1 - x, E_HT = 1. So E_FF = phi (I2 + eps)^((n-1)/2) I2 at every node, E_total is
+    that constant plus one times the volume (Simpson is exact on constants), and
+    Be = 1 / (1 + E_FF) (Table 4's global ratio)."""
+    N, gam, a = 9, 2.5, 1.5
+    for Ly, Lz in ((1.0, 1.0), (0.7, 1.3)):
+        prm = O.Params(N=N, Ra=0.0, n=n, Ly=Ly, Lz=Lz, phi=1e-2)
+        g = O.Grid.of(prm)
+        x, y, z = g.coords()
+        zero = np.zeros_like(x)
+        for u, v, I2 in ((gam * y, zero, gam ** 2), (a * x, -a * y, 4.0 * a * a)):
+            st = dict(u=u, v=v, w=zero.copy(), th=1.0 - x, p=zero.copy())
+            d = O.diagnostics(st, prm)
+            eff = prm.phi * (I2 + prm.I2_eps) ** (0.5 * (n - 1.0)) * I2
+            np.testing.assert_allclose(d["E_FF"], eff, rtol=1e-11)
+            np.testing.assert_allclose(d["E_HT"], 1.0, rtol=1e-12)
+            vol = Ly * Lz
+            assert d["E_FF_total"] == pytest.approx(eff * vol, rel=1e-11)
+            assert d["E_total"] == pytest.approx((1.0 + eff) * vol, rel=1e-11)
+            assert d["Be"] == pytest.approx(1.0 / (1.0 + eff), rel=1e-11)
+
+
+def test_edge_viscosity_from_the_inward_diagonal_node():
+    """Reading R1b on a field whose strain rate differs between an edge node and its
+    neighbours: u = y^2 (second-order differences are exact on quadratics) has I2 = 4 y^2, so
+    the raw power law at the edges y = 0 is eps^((n-1)/2), far from the interior values. On the
+    nodes that lie on two or three walls, eta must be the raw value at the node one step inward
+    along every wall normal (y -> h or 1 - h, whatever the x and z walls); on faces and inside it
+    is the node's own value. Copying along one normal only would leave y = 0 on the
+    x-and-y-wall edges and fail."""
+    N, n = 7, 0.75
+    prm = O.Params(N=N, Ra=0.0, n=n)
+    g = O.Grid(N)
+    x, y, z = g.coords()
+    zero = np.zeros_like(x)
+    eta, I2, _ = O.viscosity(y * y, zero, zero, prm)
+    np.testing.assert_allclose(I2, 4.0 * y * y, rtol=1e-12, atol=1e-14)
+    raw = lambda yy: (4.0 * yy * yy + prm.I2_eps) ** (0.5 * (n - 1.0))
+    h = g.h
+    walls = lambda a: (a == 0) | (a == N - 1)
+    idx = np.indices((N, N, N))          # k (z), j (y), i (x)
+    nwall = walls(idx[0]).astype(int) + walls(idx[1]) + walls(idx[2])
+    j = idx[1]
+    j_in = np.where(j == 0, 1, np.where(j == N - 1, N - 2, j))
+    expect = np.where(nwall >= 2, raw(j_in * h), raw(j * h))
+    np.testing.assert_allclose(eta, expect, rtol=1e-12)
+    # the edge rule changes the value: at y = 0 edges the raw law is eps^((n-1)/2)
+    assert raw(0.0) > 10.0 * raw(h)
