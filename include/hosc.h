@@ -174,6 +174,19 @@ typedef struct {
  * dt, set lambda again (it must stay below h^2/dt). */
 hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, double n);
 
+/* Parameters for a steady solve (a pseudo-time march to the fixed point B chi = R of Eq. 5, which
+ * depends on neither dt nor lambda): the defaults of hosc_default_params, then
+ *   lambda = Pr min(1, 2 eta_bl), dt = min(dt_stab, 0.9 h^2 / lambda), use_history = 0,
+ * with h = 1/(N-1), u = max(1, 1.5 c sqrt(Ra)), c = 0.12 * 2^(4 (1 - n)) (a velocity scale of the
+ * converged cavity), eta_bl = min(1, (u^2 sqrt(Ra))^((n-1)/2)) for n < 1 (the boundary-layer
+ * viscosity; 1 otherwise), dt_stab = min(0.02, Pr eta_min / u^2) with eta_min = eta_bl for n < 1,
+ * 1 for n = 1 and I2_eps^((n-1)/2) for n > 1 (a factor 4 inside the bound dt |G*|^2 <= 4 L of
+ * the explicit compact terms). A large lambda speeds up the slowest pressure modes, which
+ * contract by a fixed fraction of lambda per step; lambda dt must stay below h^2. The rule uses
+ * the cube's spacing: for a box (Ly, Lz) set dt and lambda again. HOSC_EINVAL for N < 5, Ra < 0,
+ * Pr <= 0 or n <= 0. */
+hosc_status hosc_steady_params(hosc_params* p, int N, double Ra, double Pr, double n);
+
 /* Bytes of device workspace a context with these parameters needs (0 if invalid). */
 size_t hosc_workspace_bytes(const hosc_params* p);
 

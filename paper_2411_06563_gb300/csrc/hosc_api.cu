@@ -1096,6 +1096,37 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
   return HOSC_OK;
 }
 
+hosc_status hosc_steady_params(hosc_params* p, int N, double Ra, double Pr, double n) {
+  const hosc_status st = hosc_default_params(p, N, Ra, Pr, n);
+  if (st) return st;
+  if (!(Ra >= 0.0) || !(Pr > 0.0) || !(n > 0.0) || !isfinite(Ra)) return HOSC_EINVAL;
+  const double h = 1.0 / (N - 1);
+  // Velocity scale of the steady cavity, 1.5 c(n) sqrt(Ra) with c = 0.12 * 2^(4 (1 - n)) (about
+  // 1.5 times the peak speeds of converged cavities), and the smallest apparent viscosity of the
+  // flow: for n < 1 in the boundary layers (shear rate u Ra^(1/4), I2 ~ u^2 Ra^(1/2)), for n > 1
+  // where the shear vanishes (the regularised law at rest).
+  const double c = 0.12 * pow(2.0, 4.0 * (1.0 - n));
+  const double u = fmax(1.0, 1.5 * c * sqrt(Ra));
+  double eta_min = 1.0, eta_bl = 1.0;
+  if (n < 1.0) {
+    eta_bl = fmin(1.0, pow(u * u * sqrt(fmax(Ra, 1.0)), 0.5 * (n - 1.0)));
+    eta_min = eta_bl;
+  } else if (n > 1.0) {
+    eta_min = pow(p->I2_eps, 0.5 * (n - 1.0));
+  }
+  // The explicit compact terms of Eq. (5) bound dt |G*|^2 / L <= 4 (G* = u L, L = 1/(Pr eta));
+  // a factor 4 inside it, at most the paper's 0.02.
+  const double dt_stab = fmin(0.02, 1.0 / (u * u / (Pr * eta_min)));
+  // Relaxation: the slowest pressure modes contract by a fixed fraction of lambda per step, so
+  // lambda is taken large, Pr where the fluid is not strongly shear-thinning and Pr * 2 eta in
+  // the boundary layers otherwise; the highest grid mode of the pressure correction needs
+  // lambda dt below h^2, so dt gives way to lambda (0.9 h^2 / lambda).
+  p->lambda = Pr * fmin(1.0, 2.0 * eta_bl);
+  p->dt = fmin(dt_stab, 0.9 * h * h / p->lambda);
+  p->use_history = 0;
+  return HOSC_OK;
+}
+
 size_t hosc_workspace_bytes(const hosc_params* p) {
   if (validate(p) != HOSC_OK) return 0;
   return workspace_layout(p->N, p->solver == 1, nullptr, nullptr);

@@ -107,6 +107,8 @@ def lib():
     sig = {
         "hosc_default_params": (ctypes.c_int, [ctypes.POINTER(hosc_params), ctypes.c_int,
                                                ctypes.c_double, ctypes.c_double, ctypes.c_double]),
+        "hosc_steady_params": (ctypes.c_int, [ctypes.POINTER(hosc_params), ctypes.c_int,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "hosc_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(hosc_params)]),
         "hosc_create": (ctypes.c_int, [ctypes.POINTER(hosc_params), ctypes.POINTER(_P)]),
         "hosc_create_in": (ctypes.c_int, [ctypes.POINTER(hosc_params), _P, ctypes.c_size_t,
@@ -188,6 +190,16 @@ def hosc_default_params(N, Ra, Pr=1.0, n=1.0, **overrides):
     st = lib().hosc_default_params(ctypes.byref(p), int(N), float(Ra), float(Pr), float(n))
     if st:
         raise HoscError(st, "hosc_default_params")
+    for k, v in overrides.items():
+        setattr(p, "lambda_" if k == "lam" else k, v)
+    return p
+
+
+def hosc_steady_params(N, Ra, Pr=1.0, n=1.0, **overrides):
+    p = hosc_params()
+    st = lib().hosc_steady_params(ctypes.byref(p), int(N), float(Ra), float(Pr), float(n))
+    if st:
+        raise HoscError(st, "hosc_steady_params")
     for k, v in overrides.items():
         setattr(p, "lambda_" if k == "lam" else k, v)
     return p

@@ -2,7 +2,7 @@
 
 The pool (native) advances many cavity solves together, one round of captured steps per member
 at a time, and completes each member when it is steady, failed or out of steps. This module
-chooses each request's pseudo-time step, drives the pool for a fixed batch, and runs the serving
+sets each request's parameters, drives the pool for a fixed batch, and runs the serving
 loop: requests arrive on a (simulated) clock, wait in FIFO order until the device-memory budget
 admits them, advance with everything else on the GPU, and leave when they complete; the loop
 reports solves/s and percentiles of arrival-to-completion time.
@@ -19,39 +19,16 @@ import numpy as np
 from . import hosc as H
 
 
-def pseudo_time_step(N, Ra, n, Pr=1.0, I2_eps=1e-10):
-    """Pseudo-time step for a cavity (N, Ra, n, Pr), from the stability bound of the scheme as
-    printed in Eq. (5): the explicit compact term bounds dt * G*^2 / L <= 4 with G* = u L,
-    L = 1 / (Pr eta) (frozen-coefficient von Neumann analysis of the highest mode). The velocity
-    scale is taken as 1.5 c(n) sqrt(Ra) with c = 0.12 * 2^(4 (1 - n)) (about 1.5x the peak
-    speeds of the steady cavities). For n < 1 the thinnest fluid is in the boundary layers, shear
-    rate u Ra^(1/4), so eta ~ (u^2 Ra^(1/2))^((n-1)/2); for n > 1 it is where the shear vanishes,
-    eta = I2_eps^((n-1)/2) (the regularised viscosity at rest). dt keeps dt u^2 L <= 1 (a factor
-    4 inside the bound) and is at most the paper's 0.02."""
-    c = 0.12 * 2.0 ** (4.0 * (1.0 - n))
-    u = max(1.0, 1.5 * c * math.sqrt(max(Ra, 0.0)))
-    eta = 1.0
-    if n < 1.0:
-        i2 = u * u * math.sqrt(max(Ra, 1.0))
-        eta = min(1.0, i2 ** ((n - 1.0) / 2.0))
-    elif n > 1.0:
-        eta = I2_eps ** ((n - 1.0) / 2.0)
-    L = 1.0 / (Pr * eta)
-    return min(0.02, 1.0 / (u * u * L))
-
-
 def request_params(N, Ra, n, Pr=1.0, precision=None, tol_steady=1e-6, tol_div=1e-6):
-    """hosc_params for one cavity solve of a batch or a request stream: pseudo-time step from
-    pseudo_time_step, lambda = min(h^2/(4 dt), Pr/10), no delta_t^- history, mixed precision by
-    default (FP32 sweeps, FP64 defect sweeps once the step change stalls)."""
-    p = H.hosc_default_params(N, Ra, Pr, n)
-    p.dt = pseudo_time_step(N, Ra, n, Pr)
-    h = 1.0 / (N - 1)
-    p.lambda_ = min(0.25 * h * h / p.dt, 0.1 * Pr)
+    """hosc_params for one cavity solve of a batch or a request stream: the library's steady-solve
+    rule (hosc_steady_params: pseudo-time step from the stability estimate of the scheme and the
+    pressure relaxation, lambda = Pr min(1, 2 eta_bl), no delta_t^- history), linear tolerance
+    1e-10, mixed precision by default (FP32 sweeps, FP64 defect sweeps once the step change
+    stalls)."""
+    p = H.hosc_steady_params(N, Ra, Pr, n)
     p.tol_lin = 1e-10
     p.tol_steady = tol_steady
     p.tol_div = tol_div
-    p.use_history = 0
     p.precision = H.HOSC_MIXED if precision is None else precision
     return p
 

@@ -1,4 +1,4 @@
-"""Host logic of the serving loop and the pseudo-time step rule, on the CPU with a stand-in pool
+"""Host logic of the serving loop and the steady-solve parameter rule, on the CPU with a stand-in pool
 and a simulated clock (the native pool itself is exercised by tests/test_gpu_pool.py)."""
 
 import math
@@ -123,19 +123,34 @@ def test_percentile_definition():
     assert S.percentile([1.0] * 99 + [100.0], 99) == pytest.approx(1.99)
 
 
-def test_pseudo_time_step_rule():
-    """The rule keeps dt u^2 L <= 1 for its velocity scale, is at most 0.02, and gives the step
-    of the Newtonian 21^3 Ra = 1e3 configuration (0.02) unchanged."""
-    assert S.pseudo_time_step(21, 1e3, 1.0) == 0.02
-    for N, Ra, n in [(41, 1e4, 0.75), (101, 1e5, 0.75), (61, 1e5, 1.25), (21, 1e2, 1.0)]:
-        dt = S.pseudo_time_step(N, Ra, n)
-        assert 0 < dt <= 0.02
+def test_steady_params_rule():
+    """hosc_steady_params (host-only): dt keeps dt u^2 L <= 1 for the rule's velocity scale, is at
+    most 0.02, and keeps lambda dt = 0.9 h^2 or below (the highest pressure mode); lambda is Pr
+    except in strongly shear-thinning flows; no delta_t^- history. The Newtonian 21^3 Ra = 1e3
+    configuration gets lambda = 1 and dt = 0.9 h^2."""
+    from paper_2411_06563_gb300 import hosc as H
+    p = H.hosc_steady_params(21, 1e3, 1.0, 1.0)
+    assert p.lambda_ == 1.0 and p.dt == pytest.approx(0.9 / 400.0, rel=1e-15)
+    assert p.use_history == 0
+    for N, Ra, n, Pr in [(41, 1e4, 0.75, 1.0), (101, 1e5, 0.75, 1.0), (61, 1e5, 1.25, 1.0),
+                         (21, 1e2, 1.0, 1.0), (51, 1e4, 1.0, 0.71)]:
+        p = H.hosc_steady_params(N, Ra, Pr, n)
+        h = 1.0 / (N - 1)
+        assert 0 < p.dt <= 0.02
+        assert p.lambda_ * p.dt <= 0.9 * h * h * (1 + 1e-12)
         c = 0.12 * 2.0 ** (4 * (1 - n))
         u = max(1.0, 1.5 * c * math.sqrt(Ra))
-        assert dt * u * u <= 1.0 + 1e-12   # L >= 1 only loosens it
+        assert p.dt * u * u / Pr <= 1.0 + 1e-12   # L = 1/(Pr eta) >= 1/Pr only tightens it
+        assert 0 < p.lambda_ <= Pr
     # thinner fluids and faster flows need smaller steps
-    assert S.pseudo_time_step(41, 1e5, 0.75) < S.pseudo_time_step(41, 1e5, 1.0)
-    assert S.pseudo_time_step(41, 1e5, 1.0) < S.pseudo_time_step(41, 1e4, 1.0)
+    dt = lambda N, Ra, n: H.hosc_steady_params(N, Ra, 1.0, n).dt
+    assert dt(41, 1e5, 0.75) < dt(41, 1e5, 1.0)
+    assert dt(41, 1e5, 1.0) < dt(41, 1e4, 1.0)
+    assert H.hosc_steady_params(41, 1e4, 1.0, 0.75).lambda_ < 1.0
+    with pytest.raises(H.HoscError):
+        H.hosc_steady_params(21, -1.0, 1.0, 1.0)
+    r = S.request_params(31, 1e3, 0.75)
+    assert r.precision == H.HOSC_MIXED and r.tol_lin == 1e-10 and r.use_history == 0
 
 
 def test_batch_and_stream_recipes_are_seeded():
