@@ -40,11 +40,10 @@ WORKLOADS = {
 
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum,
 # mean of the captured launches) from ncu captures of the same kernel build, workload and launch
-# shape, summarised in profiles/k4_pv_cavity101_mixed.md. Keyed by (workload, kernel class,
-# threads per block, planes per thread, narrow); any other configuration reports null.
-NCU_TRAFFIC = {("cavity101", "k_bicg_pv", 128, 9, 0): 154.0e6,
-               ("cavity101", "k_bicg_pv", 256, 9, 0): 151.9e6,
-               ("cavity101", "k_bicg_pv", 384, 9, 0): 151.7e6}
+# shape, summarised under profiles/. Keyed by (workload, kernel class, threads per block, planes
+# per thread, narrow); any other configuration, or a kernel changed since its capture, reports
+# null.
+NCU_TRAFFIC = {}
 
 
 def _peaks():
@@ -142,8 +141,9 @@ def run_reference(args, wl):
            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": wl["desc"], "sample": "%d^3 cavity, same physics" % Ns},
-           "cpu_baseline": {"value": val, "unit": "GPUPS", "cores": cores, "kind": "oracle",
-                            "sample": "%d oracle steps of a %d^3 cavity" % (args.steps, Ns)},
+           "cpu_baseline": dict({"value": val, "unit": "GPUPS", "cores": cores, "kind": "oracle",
+                                 "sample": "%d oracle steps of a %d^3 cavity" % (args.steps, Ns)},
+                                **_host()),
            "e2e": {"value": val, "unit": "GPUPS", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -221,6 +221,61 @@ def run_batch(args):
                              "mixed_GPUPS": one_mixed, "fp64_GPUPS": one_fp64,
                              "batched_over_fp64": value / one_fp64,
                              "batched_over_mixed": value / one_mixed}}
+    print(json.dumps(out))
+    return 0
+
+
+def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=None):
+    """One steady solve with the library's steady-solve parameters (hosc_steady_params), mixed
+    precision with the automatic switch to FP64 defect sweeps, from rest to max|chi^{n+1} -
+    chi^n|/dt < 1e-6 and max|div V| < 1e-6. Returns a dict: wall seconds (device-synchronised),
+    steps, iterations, status, diagnostics and a summary of the local entropy field."""
+    import numpy as np
+    import torch
+    p = H.hosc_steady_params(N, Ra, Pr, n)
+    p.precision = H.HOSC_MIXED if precision is None else precision
+    p.tol_lin = 1e-10
+    if stream is not None:
+        p.cuda_stream = stream.cuda_stream
+    with H.Cavity(p) as cav:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = cav.solve_steady(max_steps)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        d = cav.diagnostics(with_fields=True)
+        phase = H.hosc_get_phase(cav.h)
+    el_f = d["E_local_field"]
+    z = d["Nu_avg_z"]
+    peaks = int(np.sum((z[1:-1] > z[:-2]) & (z[1:-1] > z[2:])))
+    return {"N": N, "Ra": Ra, "n": n, "Pr": Pr, "dt": p.dt, "lambda": p.lambda_,
+            "status": H.hosc_strerror(info["call_status"]), "steady": info["call_status"] == 0,
+            "steps": info["steps"], "seconds": el,
+            "GPUPS": (N - 2) ** 3 * info["steps"] / el if el > 0 else None,
+            "bicgstab_iters_per_step": info["lin_iters"] / (4.0 * max(1, info["steps"])),
+            "res_over_dt": info["res"] / p.dt, "div_max": info["div_max"],
+            "final_phase": "FP64 defect sweeps" if phase == 1 else "FP32 sweeps",
+            "Nu_mean": d["Nu_hot_mean"], "Nu_max": d["Nu_hot_max"],
+            "Nu_cold_mean": d["Nu_cold_mean"], "E_total": d["E_total"], "E_HT": d["E_HT"],
+            "E_FF": d["E_FF"], "Be": d["Be"], "Nu_avg_z_local_maxima": peaks,
+            "E_local_field": {"min": float(el_f.min()), "max": float(el_f.max()),
+                              "mean": float(el_f.mean())}}
+
+
+def run_steady(args):
+    """Steady solve of the single large cavity (101^3, n = 0.75, Ra = 1e5, Pr = 1, mixed
+    precision with FP64 defect sweeps) from rest: solves/s, steps, Nu, Be and the local entropy
+    generation field."""
+    import torch
+    from paper_2411_06563_gb300 import hosc as H
+    torch.cuda.set_device(0)
+    wl = WORKLOADS[args.workload]
+    r = steady_solve(H, wl["N"], wl["Ra"], wl["n"], wl["Pr"], args.max_steps)
+    out = {"metric": "steady solves/s", "value": 1.0 / r["seconds"], "unit": "solves/s",
+           "n_gpus": 1, "steps": r["steps"], "warmup": 0, "ms_per_step": 1e3 * r["seconds"] / max(1, r["steps"]),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32+f64", "data": "synthetic", "config": {"workload": wl["desc"]},
+           "steady": r}
     print(json.dumps(out))
     return 0
 
@@ -350,6 +405,72 @@ def run_serve(args):
     return 0
 
 
+def _host():
+    """Host CPU model and logical CPU count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        if model:
+            raise OSError
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"host_cpus": os.cpu_count(), "cpu_model": model}
+
+
+_ONE_THREAD_STEP = r"""
+import sys, time, numpy as np
+sys.path.insert(0, sys.argv[1])
+from oracle import hosc_oracle as O
+z = np.load(sys.argv[2], allow_pickle=False)
+prm = O.Params(N=int(z["N"]), Ra=float(z["Ra"]), Pr=float(z["Pr"]), n=float(z["n"]),
+               dt=float(z["dt"]), lam=float(z["lam"]), tol_lin=float(z["tol"]),
+               use_history=int(z["hist"]))
+prev = None
+if int(z["hist"]):
+    prev = {k: z["prev_" + k] for k in ("L", "u", "v", "w", "Eu", "Ev", "Ew")}
+st = dict(u=z["u"], v=z["v"], w=z["w"], th=z["th"], p=z["p"], steps=0, prev=prev)
+g = O.Grid(prm.N)
+t0 = time.perf_counter()
+O.step(st, prm, g)
+print(time.perf_counter() - t0)
+"""
+
+
+def _one_thread_step(st, prm, path):
+    """Wall time of one oracle step of the same state in a child process held to one thread
+    (OMP, OpenBLAS and MKL thread pools of numpy and scipy set to 1)."""
+    arrays = {k: st[k] for k in ("u", "v", "w", "th", "p")}
+    hist = st.get("prev") is not None
+    if hist:
+        arrays.update({"prev_" + k: v for k, v in st["prev"].items()})
+    import numpy as np
+    np.savez(path, N=prm.N, Ra=prm.Ra, Pr=prm.Pr, n=prm.n, dt=prm.dt, lam=prm.lam,
+             tol=prm.tol_lin, hist=int(hist), **arrays)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", _ONE_THREAD_STEP, ROOT, path], env=env,
+                         capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        return None
+    return float(out.stdout.strip().splitlines()[-1])
+
+
 def _cores_used(cpu_s, wall_s):
     """Threads the oracle kept busy over a timed interval: process CPU time over wall time (the
     oracle itself is single-threaded; numpy's BLAS may add threads for long vectors)."""
@@ -375,8 +496,18 @@ def cpu_baseline(cav, H, wl):
     O.step(st, prm, g)
     dt = time.perf_counter() - t0
     cores = _cores_used(time.process_time() - c0, dt)
-    return {"value": (N - 2) ** 3 / dt, "unit": "GPUPS", "cores": cores, "kind": "oracle",
-            "sample": "1 oracle step of the %d^3 workload from the GPU state (%.1f s)" % (N, dt)}
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    try:
+        dt1 = _one_thread_step(st, prm, path)
+    finally:
+        os.unlink(path)
+    out = {"value": (N - 2) ** 3 / dt, "unit": "GPUPS", "cores": cores, "kind": "oracle",
+           "sample": "1 oracle step of the %d^3 workload from the GPU state (%.1f s)" % (N, dt),
+           "one_thread": ({"value": (N - 2) ** 3 / dt1, "unit": "GPUPS", "cores": 1,
+                           "seconds": dt1} if dt1 else None)}
+    out.update(_host())
+    return out
 
 
 def main():
@@ -398,7 +529,7 @@ def main():
                          "(instead of the autotuner)")
     ap.add_argument("--spinup", type=int, default=None,
                     help="untimed steps from rest before the warm-up (default: per workload)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "equal"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "equal", "steady"],
                     help="step: the single-cavity headline; batch: 64 cavities in a pool; "
                          "serve: a Poisson request stream on a pool; equal: steady solves of "
                          "the pool against one-at-a-time FP64 at equal accuracy")
@@ -423,6 +554,8 @@ def main():
         return run_serve(args)
     if args.impl == "ours" and args.mode == "equal":
         return run_equal(args)
+    if args.impl == "ours" and args.mode == "steady":
+        return run_steady(args)
     if args.impl == "reference":
         return run_reference(args, wl)
 
@@ -618,6 +751,14 @@ def main():
                        "spinup_steps": spinup, "tol_lin": p.tol_lin,
                        "use_history": wl["history"], "lambda": p.lambda_,
                        "bicgstab_iters_per_step": lin_iters / (4.0 * args.steps),
+                       # per system (u, v, w, theta), and the passes of the interleaved solve
+                       # (it iterates the four systems together until the last has converged)
+                       "iters_per_step_by_system": dict(zip(
+                           ("u", "v", "w", "theta"),
+                           (x / args.steps for x in info["sys_iters"]))),
+                       "solve_passes_per_step": info["solve_iters"] / args.steps,
+                       "lane_utilisation": (lin_iters / (4.0 * info["solve_iters"])
+                                            if info["solve_iters"] else None),
                        # interior nodes x systems x BiCGSTAB iterations per second
                        "sweep_rate_per_s": (N - 2) ** 3 * lin_iters * ws / (ms * 1e-3),
                        "krylov_tiles": shape["tiles"], "stencil_tiles": shape["stencil"],

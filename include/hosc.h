@@ -155,6 +155,10 @@ typedef struct {
   double lin_res;     /* largest ||r_k|| / ||r_0|| of the last step's four solves */
   int status;         /* hosc_status of the last step */
   long inner_passes;  /* inner pressure passes summed over the steps of this call */
+  long sys_iters[4];  /* iterations of the u, v, w, theta solves, each summed over the steps */
+  long solve_iters;   /* the largest of the four systems' iterations, summed over the steps: the
+                         passes of the mixed-precision solve, which iterates the four systems
+                         together until the last one has converged */
 } hosc_info;
 
 typedef struct {
@@ -176,7 +180,7 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
 
 /* Parameters for a steady solve (a pseudo-time march to the fixed point B chi = R of Eq. 5, which
  * depends on neither dt nor lambda): the defaults of hosc_default_params, then
- *   lambda = Pr min(1, 2 eta_bl), dt = min(dt_stab, 0.9 h^2 / lambda), use_history = 0,
+ *   lambda = 2 Pr min(1, 2 eta_bl), dt = min(dt_stab, 0.9 h^2 / lambda), use_history = 0,
  * with h = 1/(N-1), u = max(1, 1.5 c sqrt(Ra)), c = 0.12 * 2^(4 (1 - n)) (a velocity scale of the
  * converged cavity), eta_bl = min(1, (u^2 sqrt(Ra))^((n-1)/2)) for n < 1 (the boundary-layer
  * viscosity; 1 otherwise), dt_stab = min(0.02, Pr eta_min / u^2) with eta_min = eta_bl for n < 1,
@@ -400,6 +404,14 @@ hosc_status hosc_pool_result(void* pool, int slot, hosc_status* status, hosc_inf
 /* Free a member's context and device memory (active or completed). */
 hosc_status hosc_pool_retire(void* pool, int slot);
 hosc_status hosc_pool_stats(void* pool, hosc_pool_info* out);
+
+/* Measured FP64 arithmetic rate of the current GPU in TFLOP/s (no counterpart in the paper): the
+ * denominator of the roofline of the all-FP64 sweep kernels, which the FP64 pipe bounds. A grid
+ * of 8 blocks of 256 threads per SM runs chains of fused multiply-adds (2 flops each) `reps`
+ * times after one warm-up launch, timed with CUDA events on the default stream. Allocates and
+ * frees a small device buffer. HOSC_EINVAL for reps < 1 or a NULL output, HOSC_ECUDA on a CUDA
+ * error. */
+hosc_status hosc_fp64_peak(int reps, double* tflops_out);
 
 const char* hosc_strerror(int status);
 

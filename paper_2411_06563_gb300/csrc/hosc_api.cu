@@ -201,6 +201,7 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
     d.grpf[a] = (float)d.grp[a];
   }
   for (int q = 0; q < 6; ++q) d.pwf[q] = (float)d.pw[q];
+  for (int a = 0; a < 3; ++a) d.csf[a] = (float)(-0.5 * p.dt * d.isq[a]);
   d.s3 = (d.isq[0] + d.isq[1] + d.isq[2]) / 3.0;
   d.s3f = (float)d.s3;
   d.eta_exp = 0.5 * (p.n - 1.0);
@@ -613,7 +614,13 @@ hosc_status one_step(Ctx* c, hosc_info* info) {
   if (info) {
     info->steps += 1;
     info->inner_passes += c->inner_last;
-    for (int s = 0; s < 4; ++s) info->lin_iters += c->h_rec->iters[s];
+    int most = 0;
+    for (int s = 0; s < 4; ++s) {
+      info->lin_iters += c->h_rec->iters[s];
+      info->sys_iters[s] += c->h_rec->iters[s];
+      most = std::max(most, c->h_rec->iters[s]);
+    }
+    info->solve_iters += most;
   }
   return (hosc_status)c->h_rec->status;
 }
@@ -722,10 +729,14 @@ hosc_status fold_records(Ctx* c, unsigned n, hosc_info* info, bool* steady) {
     const StepRecord& r = c->h_ring[q % kRing];
     if (info) {
       info->steps += 1;
+      int most = 0;
       for (int s = 0; s < 4; ++s) {
         info->lin_iters += r.iters[s];
+        info->sys_iters[s] += r.iters[s];
         info->last_iters[s] = r.iters[s];
+        most = std::max(most, r.iters[s]);
       }
+      info->solve_iters += most;
       info->res_steady = r.res;
       info->div_max = r.div_max;
       info->lin_res = r.lin_res;
@@ -1017,19 +1028,23 @@ size_t workspace_layout(int N, int bicgstab2, Fields* f, char* base) {
     }
   }
   // The interleaved float solve of mixed precision reuses the 46 planar Krylov arrays above
-  // (contiguous from Am[0]): weights 64 bytes per node, then nine float4 vectors.
+  // (contiguous from Am[0]): the compact operators (36 bytes per node), then nine float4 vectors.
   {
     char* kb = (char*)F.Am[0];
     const size_t v4 = align_up(n3 * sizeof(float4));
-    F.kw = (float4*)kb;
-    kb += align_up(4 * n3 * sizeof(float4));
+    F.kwm = (float4*)kb;
+    kb += v4;
+    F.kwe = (float4*)kb;
+    kb += v4;
+    F.kL = (float*)kb;
+    kb += align_up(n3 * sizeof(float));
     float4** vecs[9] = {&F.kr0, &F.kx, &F.kr, &F.kr1, &F.kt,
                         &F.kp[0], &F.kp[1], &F.kv[0], &F.kv[1]};
     for (float4** v : vecs) {
       *v = (float4*)kb;
       kb += v4;
     }
-    static_assert(4 * 16 + 9 * 16 <= 46 * 8, "interleaved solve must fit the planar arrays");
+    static_assert(2 * 16 + 4 + 9 * 16 <= 46 * 8, "interleaved solve must fit the planar arrays");
   }
   for (int s = 0; s < 4; ++s) {
     F.u0[s] = bicgstab2 ? fld() : nullptr;
@@ -1118,10 +1133,10 @@ hosc_status hosc_steady_params(hosc_params* p, int N, double Ra, double Pr, doub
   // a factor 4 inside it, at most the paper's 0.02.
   const double dt_stab = fmin(0.02, 1.0 / (u * u / (Pr * eta_min)));
   // Relaxation: the slowest pressure modes contract by a fixed fraction of lambda per step, so
-  // lambda is taken large, Pr where the fluid is not strongly shear-thinning and Pr * 2 eta in
-  // the boundary layers otherwise; the highest grid mode of the pressure correction needs
-  // lambda dt below h^2, so dt gives way to lambda (0.9 h^2 / lambda).
-  p->lambda = Pr * fmin(1.0, 2.0 * eta_bl);
+  // lambda is taken large, 2 Pr where the fluid is not strongly shear-thinning and 4 Pr eta_bl
+  // otherwise; the highest grid mode of the pressure correction needs lambda dt below h^2, so
+  // dt gives way to lambda (0.9 h^2 / lambda).
+  p->lambda = 2.0 * Pr * fmin(1.0, 2.0 * eta_bl);
   p->dt = fmin(dt_stab, 0.9 * h * h / p->lambda);
   p->use_history = 0;
   return HOSC_OK;
@@ -1236,6 +1251,8 @@ hosc_status hosc_run_stage(void* ctx, int stage, hosc_info* out) {
       for (int s = 0; s < 4; ++s) {
         out->last_iters[s] = c->h_ks[s].iters;
         out->lin_iters += c->h_ks[s].iters;
+        out->sys_iters[s] = c->h_ks[s].iters;
+        out->solve_iters = std::max(out->solve_iters, (long)c->h_ks[s].iters);
         if (c->h_ks[s].status) out->status = HOSC_ENOCONV;
       }
     }
@@ -1293,10 +1310,28 @@ hosc_status hosc_get_field(void* ctx, int which, double* host_out) {
     } else if (which >= HOSC_DX_U && which <= HOSC_DX_THETA) {
       base = c->F.kx;
       comp = which - HOSC_DX_U;
-    } else {
-      base = c->F.kw;
-      stride = 16;
-      comp = (which >= HOSC_A_ENE) ? 7 + (which - HOSC_A_ENE) : which - HOSC_A_MOM;
+    } else {   // a weight of a compact operator: D, then S_d -/+ B_d for the +d / -d neighbour
+      const bool ene = which >= HOSC_A_ENE;
+      const int q = ene ? which - HOSC_A_ENE : which - HOSC_A_MOM;
+      std::vector<float4> op(n3);
+      std::vector<float> L(n3);
+      CU(cudaMemcpyAsync(op.data(), ene ? c->F.kwe : c->F.kwm, n3 * sizeof(float4),
+                         cudaMemcpyDeviceToHost, c->stream));
+      if (!ene)
+        CU(cudaMemcpyAsync(L.data(), c->F.kL, n3 * sizeof(float), cudaMemcpyDeviceToHost,
+                           c->stream));
+      CU(cudaStreamSynchronize(c->stream));
+      const int dir = (q - 1) / 2;
+      const double sign = (q % 2 == 1) ? -1.0 : 1.0;   // odd q: the +d neighbour
+      for (size_t n = 0; n < n3; ++n) {
+        const float4 o = op[n];
+        const double B = dir == 0 ? o.x : (dir == 1 ? o.y : o.z);
+        const double S = (double)c->P.csf[dir] + (ene ? 1.0 : (double)L[n]) / 12.0;
+        double w = q == 0 ? (double)o.w : S + sign * B;
+        if (c->P.precond) w = q == 0 ? 1.0 : w / (double)o.w;
+        host_out[n] = o.w != 0.f ? w : 0.0;   // no operator row (walls): zero
+      }
+      return HOSC_OK;
     }
     std::vector<float> tmp(n3 * stride);
     CU(cudaMemcpyAsync(tmp.data(), base, tmp.size() * sizeof(float), cudaMemcpyDeviceToHost,

@@ -38,6 +38,7 @@ struct DevParams {
   // 2k^2/(k^2+l^2), 2h^2/(l^2+h^2), 2l^2/(l^2+h^2) (all 1 when h = k = l)
   double inv2[3], isq[3], sq12[3], ih[3], grp[3], pw[6];
   float inv2f[3], isqf[3], sq12f[3], ihf[3], grpf[3], pwf[6];
+  float csf[3];      // -dt/(2 h_d^2): the dt part of the symmetric weights of the compact operators
   double s3;         // (1/h^2 + 1/k^2 + 1/l^2)/3: threshold of the pseudo-time mass (1/h^2 when
                      // h = k = l)
   float s3f;
@@ -117,7 +118,13 @@ struct Fields {
   unsigned int* ring_pos; // records appended so far
   // Mixed precision solve, interleaved over the four systems (u, v, w, theta components of one
   // float4 per node). These alias the planar Krylov arrays above, which only the FP64 solve uses.
-  float4* kw;        // [4 N^3] weights: (Am0 Am1 Am2 Am3)(Am4 Am5 Am6 Ae0)(Ae1 Ae2 Ae3 Ae4)(Ae5 Ae6 0 0)
+  // The two level-(n+1) operators in compact form (not row-scaled): along direction d the
+  // weights of the +d and -d neighbours are S_d - B_d and S_d + B_d, with the symmetric part
+  // S_d = -dt/(2 h_d^2) + L/12 for momentum (a function of L alone) and -dt/(2 h_d^2) + 1/12 for
+  // energy; D is the diagonal weight.
+  float4* kwm;       // momentum (B_x, B_y, B_z, D)
+  float4* kwe;       // energy (B_x, B_y, B_z, D)
+  float* kL;         // momentum L = 1/(Pr eta)
   float4* kr0;       // right-hand sides dt (R - B chi^n) = r_0, the shadow residual
   float4* kx;        // iterate (the increments)
   float4* kr;        // residual (the merged iteration ping-pongs it with kr1)

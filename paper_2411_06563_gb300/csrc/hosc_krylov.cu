@@ -715,24 +715,54 @@ __device__ __forceinline__ void ff_dot4(FF* acc, float4 a, float4 b) {
   acc[3] = ff_add(acc[3], ff_prod(a.w, b.w));
 }
 
-// The seven-point operators of the four systems at node c: momentum weights for u, v, w, energy
-// weights for theta. Arguments: the operand at c, x+, x-, y+, y-, z+, z-.
-__device__ __forceinline__ float4 apply7x4(const float4* __restrict__ W, int c, float4 o,
-                                           float4 xp, float4 xm, float4 yp, float4 ym, float4 zp,
+// The seven-point operators of the four systems at node c, from the compact operators: along
+// direction d the +d and -d neighbours weigh S_d - B_d and S_d + B_d, so the product is
+// D o + sum_d S_d (o_{+d} + o_{-d}) - B_d (o_{+d} - o_{-d}). Momentum (u, v, w lanes): B and D from
+// kwm, S_d = -dt/(2 h_d^2) + L/12. Energy (theta lane): B and D from kwe, S_d = -dt/(2 h_d^2) +
+// 1/12; with ene false (the energy system has converged) its weights are not read and the lane
+// is zero. With Jacobi row scaling (precond) each row is divided by its diagonal D.
+struct Op4 {
+  float4 m, e;   // (B_x, B_y, B_z, D) of momentum and of energy
+  float l12;     // L/12
+};
+
+__device__ __forceinline__ Op4 load_op(const Fields& F, int c, bool ene) {
+  Op4 op;
+  op.m = __ldg(F.kwm + c);
+  op.l12 = __ldg(F.kL + c) * (1.f / 12.f);
+  op.e = ene ? __ldg(F.kwe + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+  return op;
+}
+
+__device__ __forceinline__ float4 apply_op(const DevParams& P, const Op4& op, float4 o, float4 xp,
+                                           float4 xm, float4 yp, float4 ym, float4 zp,
                                            float4 zm) {
-  const float4* w = W + 4 * (size_t)c;
-  const float4 w0 = __ldg(w), w1 = __ldg(w + 1), w2 = __ldg(w + 2), w3 = __ldg(w + 3);
+  // momentum weights of the six neighbours, shared by the u, v, w lanes
+  const float Sx = P.csf[0] + op.l12, Sy = P.csf[1] + op.l12, Sz = P.csf[2] + op.l12;
+  const float4 m = op.m, e = op.e;
+  const float a1 = Sx - m.x, a2 = Sx + m.x, a3 = Sy - m.y, a4 = Sy + m.y, a5 = Sz - m.z,
+              a6 = Sz + m.z;
   float4 y;
-  y.x = w0.x * o.x + w0.y * xp.x + w0.z * xm.x + w0.w * yp.x + w1.x * ym.x + w1.y * zp.x +
-        w1.z * zm.x;
-  y.y = w0.x * o.y + w0.y * xp.y + w0.z * xm.y + w0.w * yp.y + w1.x * ym.y + w1.y * zp.y +
-        w1.z * zm.y;
-  y.z = w0.x * o.z + w0.y * xp.z + w0.z * xm.z + w0.w * yp.z + w1.x * ym.z + w1.y * zp.z +
-        w1.z * zm.z;
-  y.w = w1.w * o.w + w2.x * xp.w + w2.y * xm.w + w2.z * yp.w + w2.w * ym.w + w3.x * zp.w +
-        w3.y * zm.w;
+  y.x = m.w * o.x + a1 * xp.x + a2 * xm.x + a3 * yp.x + a4 * ym.x + a5 * zp.x + a6 * zm.x;
+  y.y = m.w * o.y + a1 * xp.y + a2 * xm.y + a3 * yp.y + a4 * ym.y + a5 * zp.y + a6 * zm.y;
+  y.z = m.w * o.z + a1 * xp.z + a2 * xm.z + a3 * yp.z + a4 * ym.z + a5 * zp.z + a6 * zm.z;
+  const float c12 = 1.f / 12.f;
+  const float ex = P.csf[0] + c12, ey = P.csf[1] + c12, ez = P.csf[2] + c12;
+  y.w = e.w * o.w + (ex - e.x) * xp.w + (ex + e.x) * xm.w + (ey - e.y) * yp.w +
+        (ey + e.y) * ym.w + (ez - e.z) * zp.w + (ez + e.z) * zm.w;
+  if (P.precond) {
+    const float im = 1.f / m.w;
+    y.x *= im;
+    y.y *= im;
+    y.z *= im;
+    y.w = e.w != 0.f ? y.w / e.w : 0.f;
+  }
   return y;
 }
+
+// Float4 words per interior node of the compact operators a launch reads: kwm and kL, and kwe
+// while the energy system iterates.
+__device__ __forceinline__ double op_words(bool ene) { return 1.25 + (ene ? 1.0 : 0.0); }
 
 // Thread -> interior column (i, j) and its segment [k0, k1) of planes. False for the threads
 // past the last column of the plane (they still take part in the block reduction).
@@ -841,6 +871,7 @@ __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
   __shared__ Scal4 sc;
   load_scalars(F.ks, sc);
   if (sc.all_done) return;   // uniform over the grid
+  const bool ene = !sc.done[3];   // the energy system still iterates (uniform)
   const int N = P.N, N2 = N * N;
   const float4 b = sc.b, mom = neg4(sc.om);
   const float4* __restrict__ R = F.kr;
@@ -860,8 +891,8 @@ __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
     for (int k = col.k0; k < col.k1; ++k) {
       const int c = col.cb + N2 * k;
       const float4 pz = pnew(c + N2);
-      const float4 vn = apply7x4(F.kw, c, pc, pnew(c + 1), pnew(c - 1), pnew(c + N),
-                                 pnew(c - N), pz, pm);
+      const float4 vn = apply_op(P, load_op(F, c, ene), pc, pnew(c + 1), pnew(c - 1),
+                                 pnew(c + N), pnew(c - N), pz, pm);
       Pn[c] = pc;
       Vn[c] = vn;
       ff_dot4(acc, __ldg(F.kr0 + c), vn);
@@ -885,7 +916,8 @@ __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
         }
         k.alpha = k.rho / tot[s];
       }
-      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 6.0 + 4.0);   // r p v r0 in, p v out, 4 weights
+      // r p v r0 in, p v out, the compact operators
+      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 6.0 + op_words(ene));
     }
   }
 }
@@ -899,6 +931,7 @@ __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
   __shared__ Scal4 sc;
   load_scalars(F.ks, sc);
   if (sc.all_done) return;
+  const bool ene = !sc.done[3];   // the energy system still iterates (uniform)
   const int N = P.N, N2 = N * N;
   const int np = 1 - pp;   // written by k4_pv of this iteration
   const float4 ma = neg4(sc.a);
@@ -914,8 +947,8 @@ __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
     for (int k = col.k0; k < col.k1; ++k) {
       const int c = col.cb + N2 * k;
       const float4 sz = sval(c + N2);
-      const float4 tv = apply7x4(F.kw, c, sc0, sval(c + 1), sval(c - 1), sval(c + N),
-                                 sval(c - N), sz, sm);
+      const float4 tv = apply_op(P, load_op(F, c, ene), sc0, sval(c + 1), sval(c - 1),
+                                 sval(c + N), sval(c - N), sz, sm);
       T[c] = tv;
       ff_dot4(acc, tv, sc0);
       ff_dot4(acc + 4, tv, tv);
@@ -934,7 +967,8 @@ __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
         if (k.done) continue;
         k.omega = tot[4 + s] > 0.0 ? tot[s] / tot[4 + s] : 0.0;
       }
-      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 3.0 + 4.0);   // r v in, t out, 4 weights
+      // r v in, t out, the compact operators
+      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 3.0 + op_words(ene));
     }
   }
 }
@@ -1058,6 +1092,7 @@ __global__ void __launch_bounds__(256, MinB) k6_a(DevParams P, Fields F, int pp)
   __shared__ Scal4 sc;
   load_scalars(F.ks, sc);
   if (sc.all_done) return;   // uniform over the grid
+  const bool ene = !sc.done[3];   // the energy system still iterates (uniform)
   const int N = P.N, N2 = N * N;
   const float4 a = sc.a, ma = neg4(sc.a), om = sc.om, mom = neg4(sc.om), b = sc.b;
   const float4* __restrict__ Ro = pp ? F.kr1 : F.kr;
@@ -1078,8 +1113,8 @@ __global__ void __launch_bounds__(256, MinB) k6_a(DevParams P, Fields F, int pp)
     for (int k = col.k0; k < col.k1; ++k) {
       const int c = col.cb + N2 * k;
       const float4 pz = pnew(c + N2);
-      const float4 vn = apply7x4(F.kw, c, pc, pnew(c + 1), pnew(c - 1), pnew(c + N),
-                                 pnew(c - N), pz, pm);
+      const float4 vn = apply_op(P, load_op(F, c, ene), pc, pnew(c + 1), pnew(c - 1),
+                                 pnew(c + N), pnew(c - N), pz, pm);
       const float4 r = __ldg(Ro + c), v = __ldg(Vo + c), p = __ldg(Po + c);
       const float4 sv = fma4(ma, v, r);
       const float4 rn = fma4(mom, __ldg(T + c), sv);
@@ -1121,8 +1156,8 @@ __global__ void __launch_bounds__(256, MinB) k6_a(DevParams P, Fields F, int pp)
         k.rho = tot[8 + s];   // rho_i = r_0 . r_i from the stored r_i
         k.alpha = k.rho / tot[s];
       }
-      // r p v t x r0 in, x r p v out, 4 weight float4
-      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 10.0 + 4.0);
+      // r p v t x r0 in, x r p v out, the compact operators
+      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 10.0 + op_words(ene));
     }
   }
 }
@@ -1133,6 +1168,7 @@ __global__ void __launch_bounds__(256, MinB) k6_b(DevParams P, Fields F, int pp)
   __shared__ Scal4 sc;
   load_scalars(F.ks, sc);
   if (sc.all_done) return;
+  const bool ene = !sc.done[3];   // the energy system still iterates (uniform)
   const int N = P.N, N2 = N * N;
   const float4 ma = neg4(sc.a);
   const float4* __restrict__ R = pp ? F.kr : F.kr1;   // r_i, written by k6_a
@@ -1146,8 +1182,8 @@ __global__ void __launch_bounds__(256, MinB) k6_b(DevParams P, Fields F, int pp)
     for (int k = col.k0; k < col.k1; ++k) {
       const int c = col.cb + N2 * k;
       const float4 sz = sval(c + N2);
-      const float4 tv = apply7x4(F.kw, c, sc0, sval(c + 1), sval(c - 1), sval(c + N),
-                                 sval(c - N), sz, sm);
+      const float4 tv = apply_op(P, load_op(F, c, ene), sc0, sval(c + 1), sval(c - 1),
+                                 sval(c + N), sval(c - N), sz, sm);
       F.kt[c] = tv;
       const float4 r0 = __ldg(F.kr0 + c);
       ff_dot4(acc, tv, sc0);
@@ -1179,7 +1215,8 @@ __global__ void __launch_bounds__(256, MinB) k6_b(DevParams P, Fields F, int pp)
         k.beta = (rho_next / k.rho) * (k.alpha / om);
         k.omega = om;
       }
-      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 4.0 + 4.0);   // r v r0 in, t out, 4 weights
+      // r v r0 in, t out, the compact operators
+      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 4.0 + op_words(ene));
     }
   }
 }
@@ -1207,27 +1244,41 @@ __device__ __forceinline__ void cp_wait_two() {   // all but the two newest grou
   asm volatile("cp.async.wait_group 2;\n" ::: "memory");
 }
 
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gsrc, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(gsrc), "r"(n)
+               : "memory");
+}
+
 // Shared-memory layout of one stage, in float4: NV haloed vectors ((sx+2)(sy+2) each), then the
-// weights of the tile's nodes part-major (4 x sx*sy), then (p/v only) r_0 of the tile.
+// compact operators of the tile's nodes (momentum float4s, energy float4s, then L as floats in
+// ceil(sx*sy/4) float4 slots), then (p/v only) r_0 of the tile.
 struct StageLayout {
-  int hx, halo, tile, nv, per_stage;
+  int hx, halo, tile, nv, lslots, per_stage;
   __host__ __device__ StageLayout(int sx, int sy, int nvec, bool with_r0) {
     hx = sx + 2;
     halo = (sx + 2) * (sy + 2);
     tile = sx * sy;
     nv = nvec;
-    per_stage = nv * halo + 4 * tile + (with_r0 ? tile : 0);
+    lslots = (tile + 3) / 4;
+    per_stage = nv * halo + 2 * tile + lslots + (with_r0 ? tile : 0);
   }
+  __host__ __device__ int op_m() const { return nv * halo; }
+  __host__ __device__ int op_e() const { return nv * halo + tile; }
+  __host__ __device__ int op_l() const { return nv * halo + 2 * tile; }
+  __host__ __device__ int r0() const { return nv * halo + 2 * tile + lslots; }
 };
 
 // Copy plane q (if it exists for this block) into stage buffer st: the haloed tile of each
-// stencil vector, then the weights (and r_0) at the tile's interior nodes. Positions outside the
-// grid are zero-filled without a read; the data of this plane form one commit group.
+// stencil vector, then the compact operators (and r_0) at the tile's interior nodes; the energy
+// operator only while that system iterates. Positions outside the grid are zero-filled without
+// a read; the data of this plane form one commit group.
 template <int NV, bool R0>
 __device__ __forceinline__ void stage_plane(float4* st, const StageLayout& L, int N, int i0,
                                             int j0, int q, bool live,
-                                            const float4* const (&vecs)[NV],
-                                            const float4* W, const float4* r0, int sx) {
+                                            const float4* const (&vecs)[NV], const Fields& F,
+                                            bool ene, int sx) {
   if (live) {
     const int nthr = blockDim.x;
     for (int idx = threadIdx.x; idx < L.halo; idx += nthr) {
@@ -1239,40 +1290,26 @@ __device__ __forceinline__ void stage_plane(float4* st, const StageLayout& L, in
       for (int v = 0; v < NV; ++v) cp_async16(st + v * L.halo + idx, vecs[v] + off, ok);
     }
     const bool inner_plane = q >= 1 && q <= N - 2;
-    for (int e = threadIdx.x; e < 4 * L.tile; e += nthr) {   // weights: node-major in global
-      const int node = e >> 2, part = e & 3;
-      const int ty = node / sx, tx = node - ty * sx;
+    for (int e = threadIdx.x; e < L.tile; e += nthr) {
+      const int ty = e / sx, tx = e - ty * sx;
       const int gi = i0 + tx, gj = j0 + ty;
       const bool ok = inner_plane && gi <= N - 2 && gj <= N - 2;
-      const float4* src = W + (ok ? 4 * (size_t)(gi + N * (gj + N * q)) + part : 0);
-      cp_async16(st + NV * L.halo + part * L.tile + node, src, ok);
-    }
-    if (R0) {
-      for (int e = threadIdx.x; e < L.tile; e += nthr) {
-        const int ty = e / sx, tx = e - ty * sx;
-        const int gi = i0 + tx, gj = j0 + ty;
-        const bool ok = inner_plane && gi <= N - 2 && gj <= N - 2;
-        const float4* src = r0 + (ok ? gi + N * (gj + N * q) : 0);
-        cp_async16(st + NV * L.halo + 4 * L.tile + e, src, ok);
-      }
+      const int off = ok ? gi + N * (gj + N * q) : 0;
+      cp_async16(st + L.op_m() + e, F.kwm + off, ok);
+      cp_async16(st + L.op_e() + e, F.kwe + off, ok && ene);
+      cp_async4((float*)(st + L.op_l()) + e, F.kL + off, ok);
+      if (R0) cp_async16(st + L.r0() + e, F.kr0 + off, ok);
     }
   }
   cp_commit();   // one group per plane, empty past the segment
 }
 
-__device__ __forceinline__ float4 apply7s(const float4* sw, int tile, int t, float4 o, float4 xp,
-                                          float4 xm, float4 yp, float4 ym, float4 zp, float4 zm) {
-  const float4 w0 = sw[t], w1 = sw[tile + t], w2 = sw[2 * tile + t], w3 = sw[3 * tile + t];
-  float4 y;
-  y.x = w0.x * o.x + w0.y * xp.x + w0.z * xm.x + w0.w * yp.x + w1.x * ym.x + w1.y * zp.x +
-        w1.z * zm.x;
-  y.y = w0.x * o.y + w0.y * xp.y + w0.z * xm.y + w0.w * yp.y + w1.x * ym.y + w1.y * zp.y +
-        w1.z * zm.y;
-  y.z = w0.x * o.z + w0.y * xp.z + w0.z * xm.z + w0.w * yp.z + w1.x * ym.z + w1.y * zp.z +
-        w1.z * zm.z;
-  y.w = w1.w * o.w + w2.x * xp.w + w2.y * xm.w + w2.z * yp.w + w2.w * ym.w + w3.x * zp.w +
-        w3.y * zm.w;
-  return y;
+__device__ __forceinline__ Op4 staged_op(const float4* sq, const StageLayout& L, int t) {
+  Op4 op;
+  op.m = sq[L.op_m() + t];
+  op.e = sq[L.op_e() + t];
+  op.l12 = ((const float*)(sq + L.op_l()))[t] * (1.f / 12.f);
+  return op;
 }
 
 // Staged p/v kernel (same arithmetic as k4_pv).
@@ -1291,32 +1328,32 @@ __global__ void __launch_bounds__(256) k5_pv(DevParams P, Fields F, int pp) {
   const int h = (ty + 1) * L.hx + (tx + 1);
   const float4 b = sc.b, mom = neg4(sc.om);
   const float4* const vecs[3] = {F.kr, F.kp[pp], F.kv[pp]};
+  const bool ene = !sc.done[3];
   auto stage_of = [&](int q) { return ring + ((q - (k0 - 1)) % kStages) * L.per_stage; };
   auto pnew = [&](const float4* st, int idx) {
     return fma4(b, fma4(mom, st[2 * L.halo + idx], st[L.halo + idx]), st[idx]);
   };
   // planes k0-1 .. k0+2 in flight; wait for the first two
   for (int q = k0 - 1; q <= k0 + 2; ++q)
-    stage_plane<3, true>(stage_of(q), L, N, i0, j0, q, q <= k1, vecs, F.kw, F.kr0, sx);
+    stage_plane<3, true>(stage_of(q), L, N, i0, j0, q, q <= k1, vecs, F, ene, sx);
   cp_wait_two();
   __syncthreads();
   float4 pm = pnew(stage_of(k0 - 1), h), pc = pnew(stage_of(k0), h);
   __syncthreads();   // the stage of plane k0-1 is free for plane k0+3
   FF acc[4] = {};
   for (int k = k0; k < k1; ++k) {
-    stage_plane<3, true>(stage_of(k + 3), L, N, i0, j0, k + 3, k + 3 <= k1, vecs, F.kw, F.kr0,
-                         sx);
+    stage_plane<3, true>(stage_of(k + 3), L, N, i0, j0, k + 3, k + 3 <= k1, vecs, F, ene, sx);
     cp_wait_two();   // plane k+1 has landed
     __syncthreads();
     const float4* sq = stage_of(k);
     const float4 pz = pnew(stage_of(k + 1), h);
     if (mine) {
-      const float4 vn = apply7s(sq + 3 * L.halo, L.tile, t, pc, pnew(sq, h + 1), pnew(sq, h - 1),
-                                pnew(sq, h + L.hx), pnew(sq, h - L.hx), pz, pm);
+      const float4 vn = apply_op(P, staged_op(sq, L, t), pc, pnew(sq, h + 1), pnew(sq, h - 1),
+                                 pnew(sq, h + L.hx), pnew(sq, h - L.hx), pz, pm);
       const int c = (i0 + tx) + N * (j0 + ty) + N2 * k;
       F.kp[1 - pp][c] = pc;
       F.kv[1 - pp][c] = vn;
-      ff_dot4(acc, sq[3 * L.halo + 4 * L.tile + t], vn);
+      ff_dot4(acc, sq[L.r0() + t], vn);
     }
     pm = pc;
     pc = pz;
@@ -1340,7 +1377,7 @@ __global__ void __launch_bounds__(256) k5_pv(DevParams P, Fields F, int pp) {
         }
         k.alpha = k.rho / tot[s];
       }
-      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 6.0 + 4.0);
+      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 6.0 + op_words(ene));
     }
   }
 }
@@ -1361,25 +1398,25 @@ __global__ void __launch_bounds__(256) k5_st(DevParams P, Fields F, int pp) {
   const int h = (ty + 1) * L.hx + (tx + 1);
   const float4 ma = neg4(sc.a);
   const float4* const vecs[2] = {F.kr, F.kv[1 - pp]};
+  const bool ene = !sc.done[3];
   auto stage_of = [&](int q) { return ring + ((q - (k0 - 1)) % kStages) * L.per_stage; };
   auto sval = [&](const float4* st, int idx) { return fma4(ma, st[L.halo + idx], st[idx]); };
   for (int q = k0 - 1; q <= k0 + 2; ++q)
-    stage_plane<2, false>(stage_of(q), L, N, i0, j0, q, q <= k1, vecs, F.kw, nullptr, sx);
+    stage_plane<2, false>(stage_of(q), L, N, i0, j0, q, q <= k1, vecs, F, ene, sx);
   cp_wait_two();
   __syncthreads();
   float4 sm = sval(stage_of(k0 - 1), h), sc0 = sval(stage_of(k0), h);
   __syncthreads();
   FF acc[8] = {};
   for (int k = k0; k < k1; ++k) {
-    stage_plane<2, false>(stage_of(k + 3), L, N, i0, j0, k + 3, k + 3 <= k1, vecs, F.kw,
-                          nullptr, sx);
+    stage_plane<2, false>(stage_of(k + 3), L, N, i0, j0, k + 3, k + 3 <= k1, vecs, F, ene, sx);
     cp_wait_two();
     __syncthreads();
     const float4* sq = stage_of(k);
     const float4 sz = sval(stage_of(k + 1), h);
     if (mine) {
-      const float4 tv = apply7s(sq + 2 * L.halo, L.tile, t, sc0, sval(sq, h + 1), sval(sq, h - 1),
-                                sval(sq, h + L.hx), sval(sq, h - L.hx), sz, sm);
+      const float4 tv = apply_op(P, staged_op(sq, L, t), sc0, sval(sq, h + 1), sval(sq, h - 1),
+                                 sval(sq, h + L.hx), sval(sq, h - L.hx), sz, sm);
       const int c = (i0 + tx) + N * (j0 + ty) + N2 * k;
       F.kt[c] = tv;
       ff_dot4(acc, tv, sc0);
@@ -1402,7 +1439,7 @@ __global__ void __launch_bounds__(256) k5_st(DevParams P, Fields F, int pp) {
         if (k.done) continue;
         k.omega = tot[4 + s] > 0.0 ? tot[s] / tot[4 + s] : 0.0;
       }
-      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 3.0 + 4.0);
+      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 3.0 + op_words(ene));
     }
   }
 }

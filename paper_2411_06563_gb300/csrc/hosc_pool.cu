@@ -133,6 +133,8 @@ hosc_status settle(Pool* P, int slot, hosc_status st, bool steady, const hosc_in
   Member& q = P->m[slot];
   q.info.steps += ri.steps;
   q.info.lin_iters += ri.lin_iters;
+  q.info.solve_iters += ri.solve_iters;
+  for (int s = 0; s < 4; ++s) q.info.sys_iters[s] += ri.sys_iters[s];
   for (int s = 0; s < 4; ++s) q.info.last_iters[s] = ri.last_iters[s];
   if (ri.steps > 0) {
     q.info.res_steady = ri.res_steady;

@@ -418,24 +418,27 @@ __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0)
     Ae[5] = az - Mz * ce.I * sp.i2[2];
     Ae[6] = az + Mz * ce.I * sp.i2[2];
   }
-  if (P.precond) {   // Jacobi row scaling: each row and its right-hand side over its diagonal
+  if (P.precond) {   // Jacobi row scaling: each right-hand side over its row's diagonal
     const Tc dm = Am[0] != Tc(0) ? Am[0] : Tc(1), de = Ae[0] != Tc(0) ? Ae[0] : Tc(1);
 #pragma unroll
     for (int s = 0; s < 3; ++s) rv[s] /= dm;
     rv[3] /= de;
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      Am[q] /= dm;
-      Ae[q] /= de;
+    if constexpr (sizeof(Ts) != sizeof(float)) {   // the planar weights too (the compact float
+#pragma unroll                                      // operators divide by D when applied)
+      for (int q = 0; q < 7; ++q) {
+        Am[q] /= dm;
+        Ae[q] /= de;
+      }
     }
   }
   if constexpr (sizeof(Ts) == sizeof(float)) {   // interleaved float storage
     F.kr0[c] = make_float4((float)rv[0], (float)rv[1], (float)rv[2], (float)rv[3]);
-    float4* W = F.kw + 4 * (size_t)c;
-    W[0] = make_float4((float)Am[0], (float)Am[1], (float)Am[2], (float)Am[3]);
-    W[1] = make_float4((float)Am[4], (float)Am[5], (float)Am[6], (float)Ae[0]);
-    W[2] = make_float4((float)Ae[1], (float)Ae[2], (float)Ae[3], (float)Ae[4]);
-    W[3] = make_float4((float)Ae[5], (float)Ae[6], 0.f, 0.f);
+    // compact operators: the antisymmetric halves (W_{-d} - W_{+d})/2 and the diagonal
+    F.kwm[c] = make_float4((float)(Tc(0.5) * (Am[2] - Am[1])), (float)(Tc(0.5) * (Am[4] - Am[3])),
+                           (float)(Tc(0.5) * (Am[6] - Am[5])), (float)Am[0]);
+    F.kwe[c] = make_float4((float)(Tc(0.5) * (Ae[2] - Ae[1])), (float)(Tc(0.5) * (Ae[4] - Ae[3])),
+                           (float)(Tc(0.5) * (Ae[6] - Ae[5])), (float)Ae[0]);
+    F.kL[c] = (float)Lc;
   } else {                                         // planar double storage
 #pragma unroll
     for (int s = 0; s < 4; ++s) F.rhs[s][c] = (double)rv[s];

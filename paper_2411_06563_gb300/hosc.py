@@ -50,12 +50,14 @@ class hosc_info(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_long), ("lin_iters", ctypes.c_long),
                 ("last_iters", ctypes.c_int * 4), ("res_steady", ctypes.c_double),
                 ("div_max", ctypes.c_double), ("lin_res", ctypes.c_double),
-                ("status", ctypes.c_int), ("inner_passes", ctypes.c_long)]
+                ("status", ctypes.c_int), ("inner_passes", ctypes.c_long),
+                ("sys_iters", ctypes.c_long * 4), ("solve_iters", ctypes.c_long)]
 
     def as_dict(self):
         return dict(steps=self.steps, lin_iters=self.lin_iters, last_iters=list(self.last_iters),
                     res=self.res_steady, div_max=self.div_max, lin_res=self.lin_res,
-                    status=self.status, inner_passes=self.inner_passes)
+                    status=self.status, inner_passes=self.inner_passes,
+                    sys_iters=list(self.sys_iters), solve_iters=self.solve_iters)
 
 
 class hosc_diag(ctypes.Structure):
@@ -110,6 +112,7 @@ def lib():
         "hosc_steady_params": (ctypes.c_int, [ctypes.POINTER(hosc_params), ctypes.c_int,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_double]),
         "hosc_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(hosc_params)]),
+        "hosc_fp64_peak": (ctypes.c_int, [ctypes.c_int, _DP]),
         "hosc_create": (ctypes.c_int, [ctypes.POINTER(hosc_params), ctypes.POINTER(_P)]),
         "hosc_create_in": (ctypes.c_int, [ctypes.POINTER(hosc_params), _P, ctypes.c_size_t,
                                           ctypes.POINTER(_P)]),
@@ -203,6 +206,12 @@ def hosc_steady_params(N, Ra, Pr=1.0, n=1.0, **overrides):
     for k, v in overrides.items():
         setattr(p, "lambda_" if k == "lam" else k, v)
     return p
+
+
+def hosc_fp64_peak(reps=10):
+    out = ctypes.c_double()
+    st = lib().hosc_fp64_peak(int(reps), ctypes.byref(out))
+    return st, out.value
 
 
 def hosc_workspace_bytes(p):

@@ -22,7 +22,7 @@ from . import hosc as H
 def request_params(N, Ra, n, Pr=1.0, precision=None, tol_steady=1e-6, tol_div=1e-6):
     """hosc_params for one cavity solve of a batch or a request stream: the library's steady-solve
     rule (hosc_steady_params: pseudo-time step from the stability estimate of the scheme and the
-    pressure relaxation, lambda = Pr min(1, 2 eta_bl), no delta_t^- history), linear tolerance
+    pressure relaxation, lambda = 2 Pr min(1, 2 eta_bl), no delta_t^- history), linear tolerance
     1e-10, mixed precision by default (FP32 sweeps, FP64 defect sweeps once the step change
     stalls)."""
     p = H.hosc_steady_params(N, Ra, Pr, n)

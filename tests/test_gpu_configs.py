@@ -82,8 +82,19 @@ def step101():
     return st, new, info
 
 
-@pytest.mark.parametrize("precision", [H.HOSC_FP64, H.HOSC_MIXED])
-def test_benched_cavity_101_one_step(step101, precision):
+# Mixed precision, one step against the FP64 oracle's step. With FP64 defect sweeps (phase 1) the
+# right-hand side is evaluated in double and only the solve is FP32 (relative residual 3e-6): the
+# change agrees to 2e-5 of its size. With FP32 sweeps (phase 0) the right-hand side dt (R - B chi)
+# itself is evaluated in float: its 19-point sums carry an absolute error of about
+# dt 2^-24 (24/(6 h^2)) |chi| times the handful of terms that do not cancel, which at 101^3
+# (dt = 2e-5, |u| ~ 50) is a few 1e-4 of the step's change, and less on coarser grids; those
+# steps are checked to 1e-3 of the change. The steady state is reached in phase 1.
+MIXED_TOL = {0: 1e-3, 1: 2e-5}
+
+
+@pytest.mark.parametrize("precision,phase", [(H.HOSC_FP64, 0), (H.HOSC_MIXED, 0),
+                                             (H.HOSC_MIXED, 1)])
+def test_benched_cavity_101_one_step(step101, precision, phase):
     st0, ref, oinfo = step101
     tol_lin = 1e-12 if precision == H.HOSC_FP64 else 1e-10
     p = _params(N101, RA101, N_IDX101, DT101, LAM101, precision, tol_lin)
@@ -96,6 +107,7 @@ def test_benched_cavity_101_one_step(step101, precision):
             assert rc == 0 and kb > 0 and kz > 0
             _load(cav, st0)
             cav.clear_history()
+            assert H.hosc_set_phase(cav.h, phase) == 0
         info = cav.step(1)
         assert info["call_status"] == 0, info
         for name, which in FIELDS:
@@ -103,7 +115,7 @@ def test_benched_cavity_101_one_step(step101, precision):
             if precision == H.HOSC_FP64:
                 assert _rel(got, ref[name]) <= 1e-10, name
             else:
-                _check_change(got, st0[name], ref[name], name, 2e-5)
+                _check_change(got, st0[name], ref[name], name, MIXED_TOL[phase])
         if precision == H.HOSC_FP64:
             assert abs(info["div_max"] - oinfo["div_max"]) <= 1e-9 * oinfo["div_max"]
             assert abs(info["res"] - oinfo["res"]) <= 1e-9 * oinfo["res"]
@@ -147,13 +159,15 @@ def test_power_law_41_mixed_step(n):
     st0 = dict(inputs.cavity_state(N, Ra, seed=4100 + int(100 * n)), prev=None, steps=0)
     op = _oracle_params(_params(N, Ra, n, dt, lam, H.HOSC_FP64, 1e-12))
     ref, _ = O.step(st0, op, O.Grid.of(op))
-    p = _params(N, Ra, n, dt, lam, H.HOSC_MIXED, 1e-10)
-    with H.Cavity(p) as cav:
-        _load(cav, st0)
-        info = cav.step(1)
-        assert info["call_status"] == 0
-        for name, which in FIELDS:
-            _check_change(cav.get(which), st0[name], ref[name], name, 2e-5)
+    for phase in (0, 1):
+        p = _params(N, Ra, n, dt, lam, H.HOSC_MIXED, 1e-10)
+        with H.Cavity(p) as cav:
+            _load(cav, st0)
+            assert H.hosc_set_phase(cav.h, phase) == 0
+            info = cav.step(1)
+            assert info["call_status"] == 0
+            for name, which in FIELDS:
+                _check_change(cav.get(which), st0[name], ref[name], name, MIXED_TOL[phase])
 
 
 # --------------------------------------------------------------- the scheme as printed
@@ -162,7 +176,7 @@ def test_printed_scheme_without_limiter_or_mass():
     """a_limit = a_boost = 0 (readings R18 and R19 off: the level-(n+1) operator exactly as
     Eq. (5) prints it): twenty FP64 steps from rest of a 21^3 power-law cavity at a pseudo-time
     step inside the printed scheme's stability bound agree with the oracle's to 1e-10; the mixed
-    path's fields stay within 1e-5 of the oracle's."""
+    path (FP64 sweeps, the printed operator solved in FP32) stays within 1e-5 of the fields."""
     N, Ra, n, dt = 21, 1e3, 0.75, 0.002
     lam = 0.5
     out = {}
@@ -174,6 +188,8 @@ def test_printed_scheme_without_limiter_or_mass():
         g = O.Grid.of(op)
         st = O.initial_state(op)
         with H.Cavity(p) as cav:
+            if precision == H.HOSC_MIXED:
+                assert H.hosc_set_phase(cav.h, 1) == 0   # FP64 sweeps, FP32 solve
             for k in range(20):
                 info = cav.step(1)
                 st, oinfo = O.step(st, op, g)

@@ -185,9 +185,13 @@ def test_tiles_limits_and_autotune():
 
 
 def test_interleaved_fields_read_back():
-    """In mixed precision the right-hand sides and weights live in interleaved float arrays;
-    hosc_get_field returns each component as its own N^3 array. With FP64 sweeps (phase 1) they
-    are the FP64 path's values rounded once to float: within 2^-24 of each value."""
+    """In mixed precision the right-hand sides live in an interleaved float array and the two
+    level-(n+1) operators in compact float form (per node the diagonal, the antisymmetric halves
+    B_d of each direction, and L, from which the symmetric halves follow); hosc_get_field
+    returns each right-hand side and each of the 14 weights as its own N^3 array. With FP64
+    sweeps (phase 1) the right-hand sides are the FP64 path's values rounded once to float
+    (within 2^-24 of each value) and every weight is the FP64 weight within a few float roundings
+    of its row's largest weight (2^-21)."""
     N = 13
     st = inputs.cavity_state(N, 1e4, seed=31)
     got = {}
@@ -204,5 +208,12 @@ def test_interleaved_fields_read_back():
                          [H.HOSC_RHS_U + s for s in range(4)] +
                          [H.HOSC_A_MOM + q for q in range(7)] +
                          [H.HOSC_A_ENE + q for q in range(7)]}
+    rows = {}
+    for base in (H.HOSC_A_MOM, H.HOSC_A_ENE):
+        rows[base] = np.max(np.abs(np.stack([got[H.HOSC_FP64][base + q] for q in range(7)])), axis=0)
     for w, ref in got[H.HOSC_FP64].items():
-        assert np.all(np.abs(got[H.HOSC_MIXED][w] - ref) <= 2.0 ** -24 * np.abs(ref) + 1e-37), w
+        if w < H.HOSC_A_MOM:
+            tol = 2.0 ** -24 * np.abs(ref) + 1e-37
+        else:
+            tol = 2.0 ** -21 * rows[H.HOSC_A_ENE if w >= H.HOSC_A_ENE else H.HOSC_A_MOM]
+        assert np.all(np.abs(got[H.HOSC_MIXED][w] - ref) <= tol), w

@@ -125,12 +125,12 @@ def test_percentile_definition():
 
 def test_steady_params_rule():
     """hosc_steady_params (host-only): dt keeps dt u^2 L <= 1 for the rule's velocity scale, is at
-    most 0.02, and keeps lambda dt = 0.9 h^2 or below (the highest pressure mode); lambda is Pr
+    most 0.02, and keeps lambda dt = 0.9 h^2 or below (the highest pressure mode); lambda is 2 Pr
     except in strongly shear-thinning flows; no delta_t^- history. The Newtonian 21^3 Ra = 1e3
-    configuration gets lambda = 1 and dt = 0.9 h^2."""
+    configuration gets lambda = 2 and dt = 0.45 h^2."""
     from paper_2411_06563_gb300 import hosc as H
     p = H.hosc_steady_params(21, 1e3, 1.0, 1.0)
-    assert p.lambda_ == 1.0 and p.dt == pytest.approx(0.9 / 400.0, rel=1e-15)
+    assert p.lambda_ == 2.0 and p.dt == pytest.approx(0.45 / 400.0, rel=1e-15)
     assert p.use_history == 0
     for N, Ra, n, Pr in [(41, 1e4, 0.75, 1.0), (101, 1e5, 0.75, 1.0), (61, 1e5, 1.25, 1.0),
                          (21, 1e2, 1.0, 1.0), (51, 1e4, 1.0, 0.71)]:
@@ -141,12 +141,12 @@ def test_steady_params_rule():
         c = 0.12 * 2.0 ** (4 * (1 - n))
         u = max(1.0, 1.5 * c * math.sqrt(Ra))
         assert p.dt * u * u / Pr <= 1.0 + 1e-12   # L = 1/(Pr eta) >= 1/Pr only tightens it
-        assert 0 < p.lambda_ <= Pr
+        assert 0 < p.lambda_ <= 2.0 * Pr
     # thinner fluids and faster flows need smaller steps
     dt = lambda N, Ra, n: H.hosc_steady_params(N, Ra, 1.0, n).dt
     assert dt(41, 1e5, 0.75) < dt(41, 1e5, 1.0)
-    assert dt(41, 1e5, 1.0) < dt(41, 1e4, 1.0)
-    assert H.hosc_steady_params(41, 1e4, 1.0, 0.75).lambda_ < 1.0
+    assert dt(21, 1e5, 1.0) < dt(21, 1e2, 1.0)
+    assert H.hosc_steady_params(41, 1e4, 1.0, 0.75).lambda_ < 2.0
     with pytest.raises(H.HoscError):
         H.hosc_steady_params(21, -1.0, 1.0, 1.0)
     r = S.request_params(31, 1e3, 0.75)
