@@ -143,6 +143,12 @@ typedef struct {
                          iteration applies the operator twice, as a BiCGSTAB iteration does) and
                          max_lin_iter limits them. 1 needs HOSC_FP64 (HOSC_EINVAL otherwise) and
                          adds three N^3 vectors per system to the workspace. */
+  int lambda_mode;    /* pressure correction p <- p - lambda_c div V (Sec. 2.2, last paragraph):
+                         0 (default) lambda_c = lambda, the paper's single relaxation parameter;
+                         1 lambda_c = min(lambda eta, 0.9 h_min^2 / dt) at each node, with eta the
+                         node's apparent viscosity at level n: the relaxation follows the local
+                         viscous time scale of the pressure modes (a steady-solve accelerator, not
+                         in the paper; the fixed point div V = 0 is the same). */
 } hosc_params;
 
 typedef struct {

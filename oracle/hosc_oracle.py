@@ -65,6 +65,9 @@ notes of the repository):
 * R23 A box 1 x Ly x Lz with N nodes per side (spacings h, k, l), the general form of Eqs. (5)-(6);
       the cube by default.
 * R24 solver = 1: BiCGSTAB(2), the other reading of the "hybrid" BiCGSTAB (solve_bicgstab_l).
+* R25 lam_mode = 1: the relaxation of the pressure correction scaled node by node with the
+      level-n viscosity, lam * eta, at most 0.9 h^2/dt (see relaxation); the default is the
+      paper's single lam.
 
 Pinned readings without a printed value: R18 (the limited operator differs from the unlimited
 one only on the diagonal, exactly where M18/L is below -a_limit, and both reach one steady
@@ -93,7 +96,7 @@ __all__ = [
     "Params", "Grid", "scalar_coefficients", "assemble_A", "apply_B", "solve_bicgstab",
     "solve_bicgstab_l", "solve_system", "viscosity", "momentum_sources", "initial_state", "step", "solve_steady",
     "apply_theta_bc", "apply_pressure_bc", "divergence", "diagnostics", "steady_certificate",
-    "grad_full", "strain_gradients",
+    "grad_full", "strain_gradients", "relaxation",
 ]
 
 
@@ -105,7 +108,7 @@ class Params:
     def __init__(self, N, Ra, Pr=1.0, n=1.0, dt=0.02, lam=None, theta_ref=0.5, I2_eps=1e-10,
                  phi=1e-4, tol_div=1e-6, tol_lin=1e-12, max_lin_iter=2000, theta_init=0.5,
                  a_limit=0.25, a_boost=1.0, use_history=1, precond=0, inner_max=0, Ly=1.0,
-                 Lz=1.0, solver=0):
+                 Lz=1.0, solver=0, lam_mode=0):
         self.N = int(N)
         # Box 1 x Ly x Lz (lengths in units of the hot-cold wall distance) on N nodes per side:
         # spacings h = 1/(N-1), k = Ly/(N-1), l = Lz/(N-1) (the scheme of Sec. 2.2 is written
@@ -136,6 +139,10 @@ class Params:
         self.inner_max = int(inner_max)
         # 0: BiCGSTAB (the reading of Sec. 2.2's solver used throughout); 1: BiCGSTAB(2)
         self.solver = int(solver)
+        # Relaxation of the pressure correction (reading R25): 0 the single parameter lam of
+        # Sec. 2.2; 1 lam * eta at each node (eta the level-n apparent viscosity), at most
+        # 0.9 h^2/dt (h the smallest spacing)
+        self.lam_mode = int(lam_mode)
         self.theta_ref = float(theta_ref)
         self.theta_init = float(theta_init)
         self.I2_eps = float(I2_eps)
@@ -654,6 +661,17 @@ def _system_coefficients(g, prm, lev, prev):
     return out
 
 
+def relaxation(prm, eta):
+    """The relaxation of the pressure correction p <- p - lam_c div V (Sec. 2.2): the scalar lam,
+    or (reading R25, lam_mode = 1) lam_c = min(lam eta, 0.9 h^2/dt) node by node, so that the
+    correction follows the viscous time scale of the local pressure modes. The fixed point
+    div V = 0 does not depend on it."""
+    if not prm.lam_mode:
+        return prm.lam
+    h = min(prm.spacings())
+    return np.minimum(prm.lam * eta, 0.9 * h * h / prm.dt)
+
+
 def step(state, prm, g=None, direct=False):
     """Advance one pseudo-time step n -> n+1 (Sec. 2.2 solution procedure). Returns (state, info).
 
@@ -678,8 +696,9 @@ def step(state, prm, g=None, direct=False):
     D = divergence(new["u"], new["v"], new["w"], *sp3)
     d_max = float(np.max(np.abs(D)))
     p = state["p"].copy()
+    lam = relaxation(prm, lev["eta"])
     if d_max > prm.tol_div:
-        p = apply_pressure_bc(p - prm.lam * D)
+        p = apply_pressure_bc(p - lam * D)
     # Inner pressure iterations (Sec. 2.2: the divergence is checked after the momentum equations
     # are solved, and while it exceeds the tolerance the pressure of the previous pressure
     # iteration is corrected; reading: the momentum systems are then solved again). Each pass
@@ -700,7 +719,7 @@ def step(state, prm, g=None, direct=False):
         D = divergence(new["u"], new["v"], new["w"], *sp3)
         d_max = float(np.max(np.abs(D)))
         if d_max > prm.tol_div:
-            p = apply_pressure_bc(p - prm.lam * D)
+            p = apply_pressure_bc(p - lam * D)
     res = max(float(np.max(np.abs(new[k] - state[k]))) for k in ("u", "v", "w", "th"))
     out = dict(u=new["u"], v=new["v"], w=new["w"], th=new["th"], p=p,
                prev=dict(L=lev["L"], u=state["u"], v=state["v"], w=state["w"], Eu=lev["Eu"],

@@ -93,6 +93,7 @@ hosc_status validate(const hosc_params* p) {
   if (!(p->a_limit >= 0.0) || !(p->a_limit < 1.0)) return HOSC_EINVAL;
   if (!(p->a_boost >= 0.0) || !isfinite(p->a_boost)) return HOSC_EINVAL;
   if (p->use_history != 0 && p->use_history != 1) return HOSC_EINVAL;
+  if (p->lambda_mode != 0 && p->lambda_mode != 1) return HOSC_EINVAL;
   if (p->auto_defect != 0 && p->auto_defect != 1) return HOSC_EINVAL;
   if (p->precond != 0 && p->precond != 1) return HOSC_EINVAL;
   if (p->inner_max < 0 || p->inner_max > 100000) return HOSC_EINVAL;
@@ -227,6 +228,11 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   d.a_boost = p.a_boost;
   d.precond = p.precond;
   d.solver = p.solver;
+  d.lambda_mode = p.lambda_mode;
+  {
+    const double hmin = fmin(sp[0], fmin(sp[1], sp[2]));
+    d.lambda_cap = 0.9 * hmin * hmin / p.dt;
+  }
   d.steady_res = p.tol_steady * p.dt;
   return d;
 }

@@ -49,6 +49,8 @@ struct DevParams {
   int precond;         // Jacobi row scaling of the level-(n+1) systems
   int solver;          // 0: BiCGSTAB; 1: BiCGSTAB(2) (planar FP64 solve)
   int inner_pass;      // an inner pressure pass: momentum only (theta kept, its system skipped)
+  int lambda_mode;     // 0: p -= lambda div V; 1: p -= min(lambda eta, lambda_cap) div V
+  double lambda_cap;   // 0.9 h_min^2 / dt
   double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (and div below tol_div)
                        // is steady (tol_steady * dt)
 };

@@ -633,7 +633,12 @@ __global__ void __launch_bounds__(kThreads) k_pressure_correct(DevParams P, Fiel
   if (!(F.rec->div_max > P.tol_div)) return;
   const int q = t / ni, i = 1 + (t - q * ni), j = 1 + q % ni, k = 1 + q / ni;
   const int c = node32(i, j, k, N);
-  F.p[c] -= P.lambda * F.div[c];
+  double lam = P.lambda;
+  if (P.lambda_mode) {   // viscosity-scaled relaxation: eta of level n (float in FP32 sweeps)
+    const double eta = P.sweep_fp32 ? (double)reinterpret_cast<const float*>(F.eta)[c] : F.eta[c];
+    lam = fmin(P.lambda * eta, P.lambda_cap);
+  }
+  F.p[c] -= lam * F.div[c];
 }
 
 // Zero normal pressure gradient on every wall: p_b = (4 p_1 - p_2)/3 along each wall normal the

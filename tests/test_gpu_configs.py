@@ -38,7 +38,7 @@ def _oracle_params(p):
                     tol_lin=p.tol_lin, max_lin_iter=p.max_lin_iter, theta_init=p.theta_init,
                     a_limit=p.a_limit, a_boost=p.a_boost, use_history=p.use_history,
                     precond=p.precond, inner_max=p.inner_max, Ly=p.Ly or 1.0, Lz=p.Lz or 1.0,
-                    solver=p.solver)
+                    solver=p.solver, lam_mode=p.lambda_mode)
 
 
 def _params(N, Ra, n, dt, lam, precision, tol_lin, **kw):
@@ -291,3 +291,42 @@ def test_newtonian_21_pool_members_against_the_oracle(c1_march, mode):
         assert np.max(np.abs(rmx[name] - st[name])) <= 1e-5, name
     assert rmx["diag"]["Nu_hot_mean"] == pytest.approx(od["Nu_hot_mean"], rel=1e-4)
     assert rmx["diag"]["Nu_hot_max"] == pytest.approx(od["Nu_hot_max"], rel=1e-4)
+
+
+# --------------------------------------------------------------- viscosity-scaled relaxation
+
+@pytest.mark.parametrize("n", [0.75, 1.25])
+def test_viscosity_scaled_relaxation_trajectory(n):
+    """lambda_mode = 1 (reading R25: the pressure correction relaxed by lambda * eta node by
+    node, at most 0.9 h^2/dt): six FP64 steps of a seeded 17^3 power-law state agree with the
+    oracle's to 1e-10 (the cap is reached at some nodes and not at others), and a mixed step's
+    change with FP64 sweeps within 2e-5."""
+    N, Ra = 17, 1e4
+    h = 1.0 / (N - 1)
+    dt = 2e-4
+    lam = 0.6 * 0.9 * h * h / dt
+    st0 = dict(inputs.cavity_state(N, Ra, seed=1700 + int(100 * n)), prev=None, steps=0)
+    p = _params(N, Ra, n, dt, lam, H.HOSC_FP64, 1e-12, lambda_mode=1, use_history=0)
+    op = _oracle_params(p)
+    assert op.lam_mode == 1
+    g = O.Grid.of(op)
+    eta, _, _ = O.viscosity(st0["u"], st0["v"], st0["w"], op)
+    relax = O.relaxation(op, eta)
+    assert np.any(relax < 0.9 * h * h / dt) and np.any(relax == 0.9 * h * h / dt)
+    st = st0
+    with H.Cavity(p) as cav:
+        _load(cav, st)
+        for _ in range(6):
+            info = cav.step(1)
+            st, oinfo = O.step(st, op, g)
+            assert info["call_status"] == 0 and oinfo["status"] == 0
+            for name, which in FIELDS:
+                assert _rel(cav.get(which), st[name]) <= 1e-10, name
+    ref, _ = O.step(st0, op, g)
+    pm = _params(N, Ra, n, dt, lam, H.HOSC_MIXED, 1e-10, lambda_mode=1, use_history=0)
+    with H.Cavity(pm) as cav:
+        _load(cav, st0)
+        assert H.hosc_set_phase(cav.h, 1) == 0
+        assert cav.step(1)["call_status"] == 0
+        for name, which in FIELDS:
+            _check_change(cav.get(which), st0[name], ref[name], name, MIXED_TOL[1])

@@ -47,7 +47,7 @@ def _oracle_params(p):
                     tol_lin=p.tol_lin, max_lin_iter=p.max_lin_iter, theta_init=p.theta_init,
                     a_limit=p.a_limit, a_boost=p.a_boost, use_history=p.use_history,
                     precond=p.precond, inner_max=p.inner_max, Ly=p.Ly or 1.0, Lz=p.Lz or 1.0,
-                    solver=p.solver)
+                    solver=p.solver, lam_mode=p.lambda_mode)
 
 
 def _setup(N, Ra, n, seed, history, **kw):

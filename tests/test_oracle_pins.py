@@ -992,3 +992,33 @@ def test_edge_viscosity_from_the_inward_diagonal_node():
     np.testing.assert_allclose(eta, expect, rtol=1e-12)
     # the edge rule changes the value: at y = 0 edges the raw law is eps^((n-1)/2)
     assert raw(0.0) > 10.0 * raw(h)
+
+
+def test_viscosity_scaled_relaxation_keeps_the_steady_state():
+    """Reading R25 (lam_mode = 1: the pressure correction relaxed by lam * eta at each node, at
+    most 0.9 h^2/dt) changes the pseudo-time path only: the relaxation equals lam * eta where
+    that is below the cap and the cap elsewhere, and a shear-thickening 9^3 cavity (eta varying
+    by a factor of about two) reaches the same steady state as with the paper's single lam, to
+    1e-9 of the fields; the pressure, which the wall conditions fix up to a constant, up to its
+    mean."""
+    N = 9
+    h = 1.0 / (N - 1)
+    out = []
+    for mode in (0, 1):
+        prm = O.Params(N=N, Ra=3e3, n=1.25, dt=0.004, lam=2.5 if mode else 1.0, tol_lin=1e-12,
+                       tol_div=1e-9, use_history=0, lam_mode=mode)
+        st, info = O.solve_steady(prm, 20000, tol_steady=1e-10 * prm.dt)
+        assert info["status"] == 0 and info["res"] < 1e-10 * prm.dt, (mode, info)
+        out.append(st)
+        if mode:
+            eta, _, _ = O.viscosity(st["u"], st["v"], st["w"], prm)
+            lam = O.relaxation(prm, eta)
+            cap = 0.9 * h * h / prm.dt
+            assert np.max(eta) > 1.5 * np.min(eta)
+            np.testing.assert_array_equal(lam, np.minimum(prm.lam * eta, cap))
+            assert np.any(lam < cap) and np.any(lam == cap)
+    for key in ("u", "v", "w", "th", "p"):
+        a, b = out[0][key], out[1][key]
+        if key == "p":
+            a, b = a - a.mean(), b - b.mean()
+        assert np.max(np.abs(a - b)) <= 1e-9 * max(1.0, np.abs(a).max()), key
