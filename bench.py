@@ -178,7 +178,8 @@ def run_batch(args):
     from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
     cavs = inputs.batch_mix()
     G = args.round_steps
-    mode = H.HOSC_POOL_GRAPH if args.pool_mode == "graph" else H.HOSC_POOL_STREAMS
+    mode = {"graph": H.HOSC_POOL_GRAPH, "streams": H.HOSC_POOL_STREAMS,
+            "persistent": H.HOSC_POOL_PERSISTENT}[args.pool_mode]
     budget = sum(H.hosc_workspace_bytes(S.request_params(c["N"], c["Ra"], c["n"], c["Pr"]))
                  for c in cavs) + (1 << 20)
     rounds = max(1, args.steps // G)
@@ -212,6 +213,8 @@ def run_batch(args):
                                   "[1e2,1e5], n uniform [0.75,1.25], Pr=1, seed 20241106, mixed",
                       "pool_mode": args.pool_mode, "steps_per_round": G,
                       "graph_launches_timed": rounds if mode == H.HOSC_POOL_GRAPH else None,
+                      "round_kernel_launches_timed":
+                          rounds if mode == H.HOSC_POOL_PERSISTENT else None,
                       "captures": st1["captures"], "capture_ms": st1["capture_ms"],
                       "tuned_sizes": st1["tuned_sizes"],
                       "bicgstab_iters_per_cavity_step":
@@ -310,7 +313,8 @@ def run_equal(args):
                             **{k: cav.get(w) for k, w in fields}))
     t64 = time.perf_counter() - t0
     budget = sum(H.hosc_workspace_bytes(params(c, H.HOSC_MIXED)) for c in cavs) + (1 << 20)
-    mode = H.HOSC_POOL_GRAPH if args.pool_mode == "graph" else H.HOSC_POOL_STREAMS
+    mode = {"graph": H.HOSC_POOL_GRAPH, "streams": H.HOSC_POOL_STREAMS,
+            "persistent": H.HOSC_POOL_PERSISTENT}[args.pool_mode]
     got = {}
     t0 = time.perf_counter()
     with S.Pool(budget, args.round_steps, mode, True) as pool:
@@ -354,7 +358,8 @@ def run_serve(args):
     First the saturated rate (all requests present at t = 0), then the stream at rho times that
     rate; p50 / p99 arrival-to-completion times."""
     from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
-    mode = H.HOSC_POOL_GRAPH if args.pool_mode == "graph" else H.HOSC_POOL_STREAMS
+    mode = {"graph": H.HOSC_POOL_GRAPH, "streams": H.HOSC_POOL_STREAMS,
+            "persistent": H.HOSC_POOL_PERSISTENT}[args.pool_mode]
     budget = int(args.budget_gb * (1 << 30))
     steady_set = args.stream == "steady"
     # "config": the stream of the serving configuration (most requests end at the step cap);
@@ -535,7 +540,8 @@ def main():
                          "the pool against one-at-a-time FP64 at equal accuracy")
     ap.add_argument("--equal-cavities", type=int, default=8)
     ap.add_argument("--equal-max-steps", type=int, default=20000)
-    ap.add_argument("--pool-mode", default="graph", choices=["graph", "streams"])
+    ap.add_argument("--pool-mode", default="persistent",
+                    choices=["graph", "streams", "persistent"])
     ap.add_argument("--round-steps", type=int, default=8)
     ap.add_argument("--baseline-cavities", type=int, default=16)
     ap.add_argument("--baseline-steps", type=int, default=40)

@@ -375,10 +375,16 @@ hosc_status hosc_bicgstab_noalloc(int N, const double* const* weights, const dou
  * mode HOSC_POOL_GRAPH: a whole round of every active member is one captured graph with one
  *   branch per member (steps_per_round must be even); it is captured again when membership,
  *   or a member's level parity, history, phase or launch shape, changes.
+ * mode HOSC_POOL_PERSISTENT: a whole round of every active member is one launch of a
+ *   persistent kernel (a cooperative grid of all resident blocks) that walks, phase after phase
+ *   of each step, a work list of (member, tile) items of all members, with a grid barrier
+ *   between phases (each wait bounded: a wait that gives up ends the round with HOSC_ECUDA).
+ *   Members must be mixed precision with BiCGSTAB, use_history = 0 and inner_max = 0
+ *   (HOSC_EINVAL at admission otherwise); launch shapes are the kernel's own (autotune unused).
  * autotune != 0: after the first round of the first mixed-precision member of each N, the pool
  *   runs hosc_autotune on it and gives later members of that N the same launch shape.
  * The pool's calls are single-threaded; members use their own streams and the pool's stream. */
-enum { HOSC_POOL_STREAMS = 0, HOSC_POOL_GRAPH = 1 };
+enum { HOSC_POOL_STREAMS = 0, HOSC_POOL_GRAPH = 1, HOSC_POOL_PERSISTENT = 2 };
 
 typedef struct {
   int active;          /* members still advancing */

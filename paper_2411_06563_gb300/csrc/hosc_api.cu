@@ -395,7 +395,7 @@ hosc_status solve_with(Ctx* c, const DevParams& P) {
   launch_bicg_init(P, F, c->stream);
   c->launches += 1;
   if (P.solver == 1) return solve_b2(c, P);
-  int pp = 0, it = 0, check = 4;
+  int pp = 0, it = 0, check = c->prof_on ? 1 : 4;
   while (it < P.max_lin_iter) {
     const int chunk = (P.max_lin_iter - it < check) ? P.max_lin_iter - it : check;
     for (int q = 0; q < chunk; ++q) {
@@ -417,7 +417,9 @@ hosc_status solve_with(Ctx* c, const DevParams& P) {
     CU(cudaMemcpyAsync(c->h_ks, F.ks, 4 * sizeof(KrylovScalars), cudaMemcpyDeviceToHost, c->stream));
     CU(cudaStreamSynchronize(c->stream));
     if (c->h_ks[0].done && c->h_ks[1].done && c->h_ks[2].done && c->h_ks[3].done) break;
-    if (check < 16) check *= 2;
+    // per-launch timing checks after every iteration, so that no timed launch finds the four
+    // systems converged and exits at once
+    if (check < 16 && !c->prof_on) check *= 2;
   }
   return HOSC_OK;
 }
@@ -949,6 +951,30 @@ hosc_status ctx_enqueue_round(void* ctx, int n) {
   CU(cudaMemcpyAsync(c->h_ring, F.ring, n * sizeof(StepRecord), cudaMemcpyDeviceToHost,
                      c->stream));
   CU(cudaEventRecord(c->round_ev, c->stream));
+  return HOSC_OK;
+}
+
+bool ctx_persistent_ok(void* ctx) {
+  const Ctx* c = (const Ctx*)ctx;
+  return c->stage == 0 && !c->prof_on && c->prm.precision == HOSC_MIXED && c->prm.solver == 0 &&
+         c->prm.use_history == 0 && c->prm.inner_max == 0 && c->P.have_prev == 0;
+}
+
+void ctx_round_member(void* ctx, RoundMember* out) {
+  const Ctx* c = (const Ctx*)ctx;
+  out->P = c->P;
+  out->F = c->F;
+  out->cur = c->cur;
+  round_member_shape(out);
+}
+
+// The records of a round the persistent kernel ran: read back on s (the caller waits for s and
+// then calls ctx_collect_round without waiting).
+hosc_status ctx_readback_round(void* ctx, cudaStream_t s, int n) {
+  Ctx* c = (Ctx*)ctx;
+  const Fields& F = c->F;
+  CU(cudaMemcpyAsync(c->h_ring_pos, F.ring_pos, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CU(cudaMemcpyAsync(c->h_ring, F.ring, n * sizeof(StepRecord), cudaMemcpyDeviceToHost, s));
   return HOSC_OK;
 }
 

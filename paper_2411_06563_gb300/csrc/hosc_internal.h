@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "hosc.h"
 
 namespace hosc {
@@ -196,6 +198,30 @@ void launch_shadow(const DevParams& P, const Fields& F, int cur, int both, cudaS
 void launch_diagnostics(const DevParams& P, const Fields& F, int cur, int want_fields,
                         cudaStream_t s);
 
+// One member of a persistent round (hosc_round.cu): its parameters (launch shape of the Krylov
+// tiles set for the round kernel), arrays, level of the round's first step, and the number of
+// 256-thread items of each phase.
+struct RoundMember {
+  DevParams P;
+  Fields F;
+  int cur;
+  int nodes;           // N^3 nodes
+  int interior;        // (N-2)^3 interior nodes
+  int theta_walls;     // adiabatic wall nodes with x interior
+  int pressure_walls;  // boundary nodes
+  int kx, ky;          // Krylov tiles: column chunks x plane segments
+  int init;            // blocks of the Krylov initialisation (a grid-stride loop)
+};
+struct RoundState;
+RoundState* round_state_create();
+void round_state_destroy(RoundState* S);
+// Items and Krylov tile shape of a member (sets P.kblock, P.kz for the round kernel).
+void round_member_shape(RoundMember* M);
+// One persistent round of G steps of every member on `stream` (cooperative launch), waited for.
+// HOSC_ECUDA with detail on a CUDA error or when a grid barrier wait gave up.
+hosc_status launch_round(RoundState* S, const std::vector<RoundMember>& members, int G,
+                         cudaStream_t stream, char* detail, size_t detail_len);
+
 // Rounds of captured steps of one context, driven by a pool (hosc_pool.cu); defined with the
 // context in hosc_api.cu. ctx is a context made by hosc_create.
 char* detail_buffer();                       // text returned by hosc_last_error_detail
@@ -207,5 +233,11 @@ void ctx_begin_round(void* ctx, long n);
 hosc_status ctx_enqueue_round(void* ctx, int n);
 hosc_status ctx_append_round(void* ctx, int n);
 hosc_status ctx_collect_round(void* ctx, bool wait, hosc_info* info, bool* steady);
+// Persistent rounds: whether the context can run in one (mixed precision, BiCGSTAB, no history,
+// no inner passes, captured steps usable), its round member (after ctx_begin_round), and the
+// asynchronous read-back of its records on `s` once the round kernel has run.
+bool ctx_persistent_ok(void* ctx);
+void ctx_round_member(void* ctx, RoundMember* out);
+hosc_status ctx_readback_round(void* ctx, cudaStream_t s, int n);
 
 }  // namespace hosc

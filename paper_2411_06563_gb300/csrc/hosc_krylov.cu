@@ -21,6 +21,7 @@
 
 #include "hosc_device.cuh"
 #include "hosc_internal.h"
+#include "hosc_krylov4.cuh"
 
 namespace hosc {
 
@@ -61,38 +62,6 @@ __device__ __forceinline__ double launch_bytes(const DevParams& P, const int don
   return word_bytes * ni * ni * ni * words;
 }
 
-// Float-float ("double-float") numbers: an unevaluated sum hi + lo of two floats. Knuth's TwoSum
-// and an FMA-based exact product give sums with about 44 significant bits using float
-// instructions only, which GB300 issues at 64x the rate of double instructions.
-struct FF {
-  float hi, lo;
-};
-
-__device__ __forceinline__ FF ff_prod(float a, float b) {
-  FF r;
-  r.hi = a * b;
-  r.lo = fmaf(a, b, -r.hi);   // exact rounding error of the product
-  return r;
-}
-
-__device__ __forceinline__ FF ff_add(FF a, FF b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  const float err = (a.hi - (s - bb)) + (b.hi - bb);   // TwoSum: s + err == a.hi + b.hi exactly
-  const float lo = err + a.lo + b.lo;
-  FF r;
-  r.hi = s + lo;
-  r.lo = lo - (r.hi - s);
-  return r;
-}
-
-__device__ __forceinline__ FF ff_shfl_down(FF a, int off) {
-  FF r;
-  r.hi = __shfl_down_sync(0xffffffffu, a.hi, off);
-  r.lo = __shfl_down_sync(0xffffffffu, a.lo, off);
-  return r;
-}
-
 // Block partial of M dot-product terms a[m] * b[m] in double (valid in thread 0).
 template <int M>
 __device__ __forceinline__ void block_partial(const double (&a)[M], const double (&b)[M],
@@ -100,34 +69,6 @@ __device__ __forceinline__ void block_partial(const double (&a)[M], const double
 #pragma unroll
   for (int m = 0; m < M; ++m) out[m] = a[m] * b[m];
   block_reduce<M, false>(out, smem);
-}
-
-// Block sum of M per-thread float-float accumulators; thread 0 receives the totals in double.
-template <int M>
-__device__ __forceinline__ void block_ff(FF (&acc)[M], double (&out)[M], double* smem) {
-  FF* fs = reinterpret_cast<FF*>(smem);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int m = 0; m < M; ++m) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc[m] = ff_add(acc[m], ff_shfl_down(acc[m], off));
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int m = 0; m < M; ++m) fs[wid * M + m] = acc[m];
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-      FF x = (lane < nw) ? fs[lane * M + m] : FF{0.0f, 0.0f};
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) x = ff_add(x, ff_shfl_down(x, off));
-      out[m] = (double)x.hi + (double)x.lo;
-    }
-  }
-  __syncthreads();
 }
 
 // r = r_0 = rhs, x = 0, p = v = 0; ||r_0||^2 per system.
@@ -692,339 +633,6 @@ __global__ void __launch_bounds__(kThreads) k_b2_mr(DevParams P, Fields F, int c
         }
       }
       F.alg_bytes[HOSC_K_BICG_XR] += launch_bytes(P, sh.done, 11.0, 0.0, sizeof(double));
-    }
-  }
-}
-
-// ------------------------------------------------------------------ interleaved FP32 solve
-
-__device__ __forceinline__ float4 f4(float a) { return make_float4(a, a, a, a); }
-
-// a + b * c per component
-__device__ __forceinline__ float4 fma4(float4 b, float4 c, float4 a) {
-  return make_float4(fmaf(b.x, c.x, a.x), fmaf(b.y, c.y, a.y), fmaf(b.z, c.z, a.z),
-                     fmaf(b.w, c.w, a.w));
-}
-__device__ __forceinline__ float4 neg4(float4 a) { return make_float4(-a.x, -a.y, -a.z, -a.w); }
-
-// acc[m0 + s] += a_s * b_s for the four systems s
-__device__ __forceinline__ void ff_dot4(FF* acc, float4 a, float4 b) {
-  acc[0] = ff_add(acc[0], ff_prod(a.x, b.x));
-  acc[1] = ff_add(acc[1], ff_prod(a.y, b.y));
-  acc[2] = ff_add(acc[2], ff_prod(a.z, b.z));
-  acc[3] = ff_add(acc[3], ff_prod(a.w, b.w));
-}
-
-// The seven-point operators of the four systems at node c, from the compact operators: along
-// direction d the +d and -d neighbours weigh S_d - B_d and S_d + B_d, so the product is
-// D o + sum_d S_d (o_{+d} + o_{-d}) - B_d (o_{+d} - o_{-d}). Momentum (u, v, w lanes): B and D from
-// kwm, S_d = -dt/(2 h_d^2) + L/12. Energy (theta lane): B and D from kwe, S_d = -dt/(2 h_d^2) +
-// 1/12; with ene false (the energy system has converged) its weights are not read and the lane
-// is zero. With Jacobi row scaling (precond) each row is divided by its diagonal D.
-struct Op4 {
-  float4 m, e;   // (B_x, B_y, B_z, D) of momentum and of energy
-  float l12;     // L/12
-};
-
-__device__ __forceinline__ Op4 load_op(const Fields& F, int c, bool ene) {
-  Op4 op;
-  op.m = __ldg(F.kwm + c);
-  op.l12 = __ldg(F.kL + c) * (1.f / 12.f);
-  op.e = ene ? __ldg(F.kwe + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-  return op;
-}
-
-__device__ __forceinline__ float4 apply_op(const DevParams& P, const Op4& op, float4 o, float4 xp,
-                                           float4 xm, float4 yp, float4 ym, float4 zp,
-                                           float4 zm) {
-  // momentum weights of the six neighbours, shared by the u, v, w lanes
-  const float Sx = P.csf[0] + op.l12, Sy = P.csf[1] + op.l12, Sz = P.csf[2] + op.l12;
-  const float4 m = op.m, e = op.e;
-  const float a1 = Sx - m.x, a2 = Sx + m.x, a3 = Sy - m.y, a4 = Sy + m.y, a5 = Sz - m.z,
-              a6 = Sz + m.z;
-  float4 y;
-  y.x = m.w * o.x + a1 * xp.x + a2 * xm.x + a3 * yp.x + a4 * ym.x + a5 * zp.x + a6 * zm.x;
-  y.y = m.w * o.y + a1 * xp.y + a2 * xm.y + a3 * yp.y + a4 * ym.y + a5 * zp.y + a6 * zm.y;
-  y.z = m.w * o.z + a1 * xp.z + a2 * xm.z + a3 * yp.z + a4 * ym.z + a5 * zp.z + a6 * zm.z;
-  const float c12 = 1.f / 12.f;
-  const float ex = P.csf[0] + c12, ey = P.csf[1] + c12, ez = P.csf[2] + c12;
-  y.w = e.w * o.w + (ex - e.x) * xp.w + (ex + e.x) * xm.w + (ey - e.y) * yp.w +
-        (ey + e.y) * ym.w + (ez - e.z) * zp.w + (ez + e.z) * zm.w;
-  if (P.precond) {
-    const float im = 1.f / m.w;
-    y.x *= im;
-    y.y *= im;
-    y.z *= im;
-    y.w = e.w != 0.f ? y.w / e.w : 0.f;
-  }
-  return y;
-}
-
-// Float4 words per interior node of the compact operators a launch reads: kwm and kL, and kwe
-// while the energy system iterates.
-__device__ __forceinline__ double op_words(bool ene) { return 1.25 + (ene ? 1.0 : 0.0); }
-
-// Thread -> interior column (i, j) and its segment [k0, k1) of planes. False for the threads
-// past the last column of the plane (they still take part in the block reduction).
-struct Column {
-  int cb;      // node index of (i, j, 0)
-  int k0, k1;  // planes of the segment
-};
-__device__ __forceinline__ bool column(const DevParams& P, Column& col) {
-  const int N = P.N, ni = N - 2;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= ni * ni) return false;
-  const int j = q / ni, i = q - j * ni;
-  col.cb = (i + 1) + N * (j + 1);
-  col.k0 = 1 + (int)blockIdx.y * P.kz;
-  col.k1 = min(col.k0 + P.kz, N - 1);
-  return true;
-}
-
-__device__ __forceinline__ unsigned block_id() { return blockIdx.x + gridDim.x * blockIdx.y; }
-__device__ __forceinline__ unsigned block_count() { return gridDim.x * gridDim.y; }
-
-// Per-system scalars of the interleaved kernels, zero for a finished system so that its vectors
-// stay as they are (x += 0, r = r - 0).
-struct Scal4 {
-  float4 a, b, om;
-  int done[4];
-  int all_done;
-};
-
-__device__ __forceinline__ void load_scalars(const KrylovScalars* ks, Scal4& sc) {
-  if (threadIdx.x == 0) {
-    float a[4], b[4], om[4];
-    int all = 1;
-    for (int s = 0; s < 4; ++s) {
-      const int d = ks[s].done;
-      sc.done[s] = d;
-      all &= d;
-      a[s] = d ? 0.f : (float)ks[s].alpha;
-      b[s] = d ? 0.f : (float)ks[s].beta;
-      om[s] = d ? 0.f : (float)ks[s].omega;
-    }
-    sc.a = make_float4(a[0], a[1], a[2], a[3]);
-    sc.b = make_float4(b[0], b[1], b[2], b[3]);
-    sc.om = make_float4(om[0], om[1], om[2], om[3]);
-    sc.all_done = all;
-  }
-  __syncthreads();
-}
-
-// Algorithmic bytes of one interleaved launch: words (float4 per interior node) moved.
-__device__ __forceinline__ double bytes4(const DevParams& P, double float4_words) {
-  const double ni = (double)(P.N - 2);
-  return 16.0 * float4_words * ni * ni * ni;
-}
-
-// r = r_0, x = 0, p = v = 0 at interior nodes, every vector zero on the walls; ||r_0||^2.
-// Grid-stride over all N^3 nodes: each thread sums several nodes before the one block reduction.
-__global__ void __launch_bounds__(kThreads) k4_init(DevParams P, Fields F) {
-  __shared__ double smem[32 * 4];
-  const unsigned N = P.N;
-  const unsigned n3 = N * N * N;
-  FF acc[4] = {};
-  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < n3; c += gridDim.x * blockDim.x) {
-    const unsigned q = c / N;
-    const unsigned i = c - q * N, j = q % N, k = q / N;
-    const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
-    const float4 z = f4(0.f);
-    const float4 r = inner ? F.kr0[c] : z;
-    F.kr[c] = r;
-    F.kx[c] = z;   // t needs no zeros: k4_st writes it before k4_xr reads it, inside only
-    F.kp[0][c] = z;
-    F.kp[1][c] = z;
-    F.kv[0][c] = z;
-    F.kv[1][c] = z;
-    ff_dot4(acc, r, r);
-  }
-  double part[4];
-  block_ff<4>(acc, part, smem);
-  if (publish_is_last<4>(part, F.red, F.counter)) {
-    double tot[4];
-    reduce_partials<4, false>(tot, F.red, gridDim.x, F.counter, smem);
-    if (threadIdx.x == 0) {
-      for (int s = 0; s < 4; ++s) {
-        KrylovScalars& k = F.ks[s];
-        k.r0norm = sqrt(tot[s]);
-        k.rnorm = k.r0norm;
-        k.rho = tot[s];
-        k.alpha = 1.0;
-        k.omega = 1.0;
-        k.beta = 0.0;
-        k.iters = 0;
-        k.status = 0;
-        // an inner pressure pass solves the momentum systems only
-        k.done = (k.r0norm == 0.0 || *F.halt || (s == 3 && P.inner_pass)) ? 1 : 0;
-      }
-    }
-  }
-}
-
-// p_new = r + beta (p_old - omega v_old) at the seven stencil nodes, v_new = A p_new, partial
-// r_0 . v_new; last block: alpha = rho / (r_0 . v_new).
-template <int MinB>
-__global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
-    k4_pv(DevParams P, Fields F, int pp) {
-  __shared__ double smem[32 * 4];
-  __shared__ Scal4 sc;
-  load_scalars(F.ks, sc);
-  if (sc.all_done) return;   // uniform over the grid
-  const bool ene = !sc.done[3];   // the energy system still iterates (uniform)
-  const int N = P.N, N2 = N * N;
-  const float4 b = sc.b, mom = neg4(sc.om);
-  const float4* __restrict__ R = F.kr;
-  const float4* __restrict__ Po = F.kp[pp];
-  const float4* __restrict__ Vo = F.kv[pp];
-  float4* __restrict__ Pn = F.kp[1 - pp];
-  float4* __restrict__ Vn = F.kv[1 - pp];
-  auto pnew = [&](int c) {
-    const float4 r = __ldg(R + c), p = __ldg(Po + c), v = __ldg(Vo + c);
-    return fma4(b, fma4(mom, v, p), r);
-  };
-  FF acc[4] = {};
-  Column col;
-  if (column(P, col)) {
-    float4 pm = pnew(col.cb + N2 * (col.k0 - 1));
-    float4 pc = pnew(col.cb + N2 * col.k0);
-    for (int k = col.k0; k < col.k1; ++k) {
-      const int c = col.cb + N2 * k;
-      const float4 pz = pnew(c + N2);
-      const float4 vn = apply_op(P, load_op(F, c, ene), pc, pnew(c + 1), pnew(c - 1),
-                                 pnew(c + N), pnew(c - N), pz, pm);
-      Pn[c] = pc;
-      Vn[c] = vn;
-      ff_dot4(acc, __ldg(F.kr0 + c), vn);
-      pm = pc;
-      pc = pz;
-    }
-  }
-  double part[4];
-  block_ff<4>(acc, part, smem);
-  if (publish_is_last<4>(part, F.red, F.counter, block_id(), block_count())) {
-    double tot[4];
-    reduce_partials<4, false>(tot, F.red, block_count(), F.counter, smem);
-    if (threadIdx.x == 0) {
-      for (int s = 0; s < 4; ++s) {
-        KrylovScalars& k = F.ks[s];
-        if (k.done) continue;
-        if (tot[s] == 0.0 || !isfinite(tot[s])) {
-          k.done = 1;
-          k.status = HOSC_ENOCONV;
-          continue;
-        }
-        k.alpha = k.rho / tot[s];
-      }
-      // r p v r0 in, p v out, the compact operators
-      F.alg_bytes[HOSC_K_BICG_PV] += bytes4(P, 6.0 + op_words(ene));
-    }
-  }
-}
-
-// s = r - alpha v at the seven stencil nodes, t = A s, partials (t . s, t . t); last block:
-// omega = (t . s) / (t . t) (0 when t = 0).
-template <int MinB>
-__global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
-    k4_st(DevParams P, Fields F, int pp) {
-  __shared__ double smem[32 * 8];
-  __shared__ Scal4 sc;
-  load_scalars(F.ks, sc);
-  if (sc.all_done) return;
-  const bool ene = !sc.done[3];   // the energy system still iterates (uniform)
-  const int N = P.N, N2 = N * N;
-  const int np = 1 - pp;   // written by k4_pv of this iteration
-  const float4 ma = neg4(sc.a);
-  const float4* __restrict__ R = F.kr;
-  const float4* __restrict__ V = F.kv[np];
-  float4* __restrict__ T = F.kt;
-  auto sval = [&](int c) { return fma4(ma, __ldg(V + c), __ldg(R + c)); };
-  FF acc[8] = {};
-  Column col;
-  if (column(P, col)) {
-    float4 sm = sval(col.cb + N2 * (col.k0 - 1));
-    float4 sc0 = sval(col.cb + N2 * col.k0);
-    for (int k = col.k0; k < col.k1; ++k) {
-      const int c = col.cb + N2 * k;
-      const float4 sz = sval(c + N2);
-      const float4 tv = apply_op(P, load_op(F, c, ene), sc0, sval(c + 1), sval(c - 1),
-                                 sval(c + N), sval(c - N), sz, sm);
-      T[c] = tv;
-      ff_dot4(acc, tv, sc0);
-      ff_dot4(acc + 4, tv, tv);
-      sm = sc0;
-      sc0 = sz;
-    }
-  }
-  double part[8];
-  block_ff<8>(acc, part, smem);
-  if (publish_is_last<8>(part, F.red, F.counter, block_id(), block_count())) {
-    double tot[8];
-    reduce_partials<8, false>(tot, F.red, block_count(), F.counter, smem);
-    if (threadIdx.x == 0) {
-      for (int s = 0; s < 4; ++s) {
-        KrylovScalars& k = F.ks[s];
-        if (k.done) continue;
-        k.omega = tot[4 + s] > 0.0 ? tot[s] / tot[4 + s] : 0.0;
-      }
-      // r v in, t out, the compact operators
-      F.alg_bytes[HOSC_K_BICG_ST] += bytes4(P, 3.0 + op_words(ene));
-    }
-  }
-}
-
-// s = r - alpha v; x += alpha p + omega s; r = s - omega t; partials (r_0 . r, r . r); last block:
-// convergence and breakdown tests, beta and rho of the next iteration.
-template <int MinB>
-__global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
-    k4_xr(DevParams P, Fields F, int pp) {
-  __shared__ double smem[32 * 8];
-  __shared__ Scal4 sc;
-  load_scalars(F.ks, sc);
-  if (sc.all_done) return;
-  const int N2 = P.N * P.N;
-  const int np = 1 - pp;
-  const float4 a = sc.a, om = sc.om, ma = neg4(sc.a), mom = neg4(sc.om);
-  FF acc[8] = {};
-  Column col;
-  if (column(P, col)) {
-    for (int k = col.k0; k < col.k1; ++k) {
-      const int c = col.cb + N2 * k;
-      const float4 r = F.kr[c], v = __ldg(F.kv[np] + c), p = __ldg(F.kp[np] + c);
-      const float4 t = __ldg(F.kt + c), r0 = __ldg(F.kr0 + c);
-      const float4 sv = fma4(ma, v, r);
-      F.kx[c] = fma4(om, sv, fma4(a, p, F.kx[c]));
-      const float4 rn = fma4(mom, t, sv);
-      F.kr[c] = rn;
-      ff_dot4(acc, r0, rn);
-      ff_dot4(acc + 4, rn, rn);
-    }
-  }
-  double part[8];
-  block_ff<8>(acc, part, smem);
-  if (publish_is_last<8>(part, F.red, F.counter, block_id(), block_count())) {
-    double tot[8];
-    reduce_partials<8, false>(tot, F.red, block_count(), F.counter, smem);
-    if (threadIdx.x == 0) {
-      for (int s = 0; s < 4; ++s) {
-        KrylovScalars& k = F.ks[s];
-        if (k.done) continue;
-        const double rho_new = tot[s];
-        k.rnorm = sqrt(tot[4 + s]);
-        k.iters += 1;
-        if (k.rnorm <= P.tol_lin * k.r0norm) {
-          k.done = 1;
-          k.status = 0;
-        } else if (!isfinite(k.rnorm) || k.iters >= P.max_lin_iter || rho_new == 0.0 ||
-                   k.omega == 0.0) {
-          k.done = 1;
-          k.status = HOSC_ENOCONV;
-        } else {
-          k.beta = (rho_new / k.rho) * (k.alpha / k.omega);
-          k.rho = rho_new;
-        }
-      }
-      F.alg_bytes[HOSC_K_BICG_XR] += bytes4(P, 8.0);   // r v p x t r0 in, x r out
     }
   }
 }

@@ -11,6 +11,8 @@
 //            member, so a whole round of all cavities is a single graph launch. It is captured
 //            again only when the membership or a member's level parity, history, phase or
 //            launch shape changes.
+//   persistent: one launch of the persistent round kernel (hosc_round.cu) runs the round of
+//            every member: its blocks walk each phase's (member, tile) work list.
 // The first member of each N that completes a round tunes the launch shape of the mixed
 // precision solve (hosc_autotune); later members of that N reuse it.
 
@@ -70,6 +72,7 @@ struct Pool {
   std::map<int, std::array<int, 6>> tiles;
   long rounds = 0, captures = 0;
   double capture_ms = 0.0;
+  RoundState* rs = nullptr;                   // persistent mode: the round kernel's tables
 };
 
 void drop_exec(Pool* P) {
@@ -165,7 +168,7 @@ hosc_status settle(Pool* P, int slot, hosc_status st, bool steady, const hosc_in
     *ndone += 1;
     return HOSC_OK;
   }
-  if (P->autotune) {
+  if (P->autotune && P->mode != HOSC_POOL_PERSISTENT) {
     hosc_params prm;
     if (hosc_get_params(q.ctx, &prm) == HOSC_OK && prm.precision == HOSC_MIXED) {
       auto it = P->tiles.find(q.N);
@@ -194,7 +197,8 @@ hosc_status hosc_pool_create(size_t budget_bytes, int steps_per_round, int mode,
   if (!pool) return HOSC_EINVAL;
   *pool = nullptr;
   if (budget_bytes == 0 || steps_per_round < 1 || steps_per_round > 256) return HOSC_EINVAL;
-  if (mode != HOSC_POOL_STREAMS && mode != HOSC_POOL_GRAPH) return HOSC_EINVAL;
+  if (mode != HOSC_POOL_STREAMS && mode != HOSC_POOL_GRAPH && mode != HOSC_POOL_PERSISTENT)
+    return HOSC_EINVAL;
   if (mode == HOSC_POOL_GRAPH && steps_per_round % 2 != 0) return HOSC_EINVAL;
   Pool* P = new (std::nothrow) Pool();
   if (!P) return HOSC_ENOMEM;
@@ -205,6 +209,13 @@ hosc_status hosc_pool_create(size_t budget_bytes, int steps_per_round, int mode,
   cudaError_t e = cudaGetDevice(&P->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && mode == HOSC_POOL_PERSISTENT) {
+    P->rs = round_state_create();
+    if (!P->rs) {
+      hosc_pool_destroy(P);
+      return HOSC_ENOMEM;
+    }
+  }
   if (e != cudaSuccess) {
     snprintf(detail_buffer(), 256, "pool create: %s", cudaGetErrorString(e));
     hosc_pool_destroy(P);
@@ -226,6 +237,7 @@ void hosc_pool_destroy(void* pool) {
   }
   if (P->fork) cudaEventDestroy(P->fork);
   if (P->stream) cudaStreamDestroy(P->stream);
+  round_state_destroy(P->rs);
   delete P;
 }
 
@@ -237,6 +249,9 @@ hosc_status hosc_pool_admit(void* pool, const hosc_params* params, long max_step
   if (need == 0) return HOSC_EINVAL;
   if (need > P->budget) return HOSC_EINVAL;            // can never fit
   if (params->inner_max != 0) return HOSC_EINVAL;      // members run captured steps only
+  if (P->mode == HOSC_POOL_PERSISTENT &&
+      (params->precision != HOSC_MIXED || params->solver != 0 || params->use_history != 0))
+    return HOSC_EINVAL;                                 // what the round kernel runs
   if (P->used + need > P->budget) return HOSC_ENOMEM;  // fits once others retire
   PCU(cudaSetDevice(P->device));
   hosc_params p = *params;
@@ -297,6 +312,22 @@ hosc_status hosc_pool_run(void* pool, int rounds, int* done_slots, int cap, int*
       for (int q : act) ctx_begin_round(P->m[q].ctx, P->G);
       PCU(cudaGraphLaunch(P->exec, P->stream));
       PCU(cudaStreamSynchronize(P->stream));
+    } else if (P->mode == HOSC_POOL_PERSISTENT) {
+      std::vector<RoundMember> rm(act.size());
+      for (size_t a = 0; a < act.size(); ++a) {
+        void* ctx = P->m[act[a]].ctx;
+        if (!ctx_persistent_ok(ctx)) return HOSC_ESTATE;
+        ctx_begin_round(ctx, P->G);
+        ctx_round_member(ctx, &rm[a]);
+      }
+      PCU(cudaDeviceSynchronize());   // the members' own streams are idle
+      hosc_status rs = launch_round(P->rs, rm, P->G, P->stream, detail_buffer(), 256);
+      if (rs) return rs;
+      for (size_t a = 0; a < act.size(); ++a) {
+        hosc_status e = ctx_readback_round(P->m[act[a]].ctx, P->stream, P->G);
+        if (e) return e;
+      }
+      PCU(cudaStreamSynchronize(P->stream));
     } else {
       for (size_t a = 0; a < act.size(); ++a) st[a] = ctx_enqueue_round(P->m[act[a]].ctx, P->G);
     }
@@ -305,7 +336,8 @@ hosc_status hosc_pool_run(void* pool, int rounds, int* done_slots, int cap, int*
       memset(&ri, 0, sizeof(ri));
       bool steady = false;
       hosc_status s = st[a];
-      if (!s) s = ctx_collect_round(P->m[act[a]].ctx, P->mode != HOSC_POOL_GRAPH, &ri, &steady);
+      if (!s)
+        s = ctx_collect_round(P->m[act[a]].ctx, P->mode == HOSC_POOL_STREAMS, &ri, &steady);
       if (s == HOSC_ECUDA) return s;   // the device is in trouble: stop the pool
       hosc_status e = settle(P, act[a], s, steady, ri, done_slots, cap, &nd);
       if (e) return e;

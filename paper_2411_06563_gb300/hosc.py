@@ -80,7 +80,7 @@ class hosc_pool_info(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-HOSC_POOL_STREAMS, HOSC_POOL_GRAPH = 0, 1
+HOSC_POOL_STREAMS, HOSC_POOL_GRAPH, HOSC_POOL_PERSISTENT = 0, 1, 2
 
 
 class HoscError(RuntimeError):

@@ -3,15 +3,15 @@ against the FP64 oracle.
 
 * the benched single cavity (101^3, n = 0.75, Ra = 1e5, Pr = 1): one step from a seeded developed
   state at the launch shape the autotuner picks, all-FP64 (fields 1e-10 relative) and mixed
-  precision (each field's change within 2e-5 of the oracle's change, the FP32 solve's accuracy);
+  precision (each field's change within 1e-3 of the oracle's change, and the FP32 solution's
+  residual in the oracle's system, see MIXED_TOL);
 * the power-law 41^3 cavities (Ra = 1e4, n = 0.75 and 1.25): a short FP64 trajectory at the
-  workload's pseudo-time step (1e-10), and one mixed step (2e-5 of the change);
+  workload's pseudo-time step (1e-10), and one mixed step (as above);
 * the scheme exactly as printed (no M18 limiter, no pseudo-time mass): an FP64 trajectory from
   rest (1e-10) and a mixed one (1e-5 of the fields).
 
 Tolerances: 1e-10 relative is the all-FP64 target; the mixed path solves each level-(n+1) system
-in FP32 to a relative residual of 3e-6, so one step's change carries about that relative error
-(2e-5 leaves room for the conditioning of the 101^3 operators).
+in FP32 to a relative residual of 3e-6 (see MIXED_TOL for what that bounds).
 """
 
 import numpy as np
@@ -82,14 +82,36 @@ def step101():
     return st, new, info
 
 
-# Mixed precision, one step against the FP64 oracle's step. With FP64 defect sweeps (phase 1) the
-# right-hand side is evaluated in double and only the solve is FP32 (relative residual 3e-6): the
-# change agrees to 2e-5 of its size. With FP32 sweeps (phase 0) the right-hand side dt (R - B chi)
-# itself is evaluated in float: its 19-point sums carry an absolute error of about
-# dt 2^-24 (24/(6 h^2)) |chi| times the handful of terms that do not cancel, which at 101^3
-# (dt = 2e-5, |u| ~ 50) is a few 1e-4 of the step's change, and less on coarser grids; those
-# steps are checked to 1e-3 of the change. The steady state is reached in phase 1.
-MIXED_TOL = {0: 1e-3, 1: 2e-5}
+# Mixed precision, one step against the FP64 oracle's step. The level-(n+1) systems are solved in
+# FP32 until the relative residual is 3e-6, so the increment carries a relative error of up to
+# kappa(A) * 3e-6: about 3e-4 of the largest change at 101^3 (kappa ~ 100 for the advective
+# momentum operators at this cell Reynolds number), 1e-4 at 41^3. The change is checked to 1e-3 of
+# its size, and, with FP64 sweeps (phase 1, the right-hand side evaluated in double), the FP32
+# solution is checked directly against the oracle's system: ||A x_gpu - b||_2 <= 3e-5 ||b||_2 for
+# each of the four systems (the 3e-6 stopping test plus the float rounding of the operator and
+# of the vectors). With FP32 sweeps (phase 0) the right-hand side is a float evaluation of the
+# oracle's, so only the change is compared.
+MIXED_TOL = {0: 1e-3, 1: 1e-3}
+RESID_TOL = 3e-5
+
+
+def _increment_residuals(st0, got, op):
+    """||A x - b||_2 / ||b||_2 of the GPU's increments x in the oracle's increment systems
+    A (chi^{n+1} - chi^n) = dt (R - B chi^n) at interior nodes (u, v, w, theta)."""
+    g = O.Grid.of(op)
+    ii = g.int_idx
+    lev = O.level_coefficients(dict(st0, prev=None), op)
+    coefs = O._system_coefficients(g, op, lev, None)
+    A_m = O.assemble_A(g, op.dt, coefs["u"], op.a_limit, op.a_boost)[ii][:, ii]
+    A_e = O.assemble_A(g, op.dt, coefs["th"], op.a_limit, op.a_boost)[ii][:, ii]
+    out = {}
+    for name in ("u", "v", "w", "th"):
+        c = coefs[name]
+        b = op.dt * (c["R"] - O.apply_B(g, c, st0[name].ravel()))[ii]
+        x = (got[name] - st0[name]).ravel()[ii]
+        A = A_e if name == "th" else A_m
+        out[name] = float(np.linalg.norm(A @ x - b) / max(np.linalg.norm(b), 1e-300))
+    return out
 
 
 @pytest.mark.parametrize("precision,phase", [(H.HOSC_FP64, 0), (H.HOSC_MIXED, 0),
@@ -110,12 +132,16 @@ def test_benched_cavity_101_one_step(step101, precision, phase):
             assert H.hosc_set_phase(cav.h, phase) == 0
         info = cav.step(1)
         assert info["call_status"] == 0, info
+        gotf = {}
         for name, which in FIELDS:
-            got = cav.get(which)
+            got = gotf[name] = cav.get(which)
             if precision == H.HOSC_FP64:
                 assert _rel(got, ref[name]) <= 1e-10, name
             else:
                 _check_change(got, st0[name], ref[name], name, MIXED_TOL[phase])
+        if precision == H.HOSC_MIXED and phase == 1:
+            res = _increment_residuals(st0, gotf, _oracle_params(p))
+            assert max(res.values()) <= RESID_TOL, res
         if precision == H.HOSC_FP64:
             assert abs(info["div_max"] - oinfo["div_max"]) <= 1e-9 * oinfo["div_max"]
             assert abs(info["res"] - oinfo["res"]) <= 1e-9 * oinfo["res"]
@@ -166,8 +192,13 @@ def test_power_law_41_mixed_step(n):
             assert H.hosc_set_phase(cav.h, phase) == 0
             info = cav.step(1)
             assert info["call_status"] == 0
+            gotf = {}
             for name, which in FIELDS:
-                _check_change(cav.get(which), st0[name], ref[name], name, MIXED_TOL[phase])
+                gotf[name] = cav.get(which)
+                _check_change(gotf[name], st0[name], ref[name], name, MIXED_TOL[phase])
+            if phase == 1:
+                res = _increment_residuals(st0, gotf, op)
+                assert max(res.values()) <= RESID_TOL, res
 
 
 # --------------------------------------------------------------- the scheme as printed
@@ -328,5 +359,9 @@ def test_viscosity_scaled_relaxation_trajectory(n):
         _load(cav, st0)
         assert H.hosc_set_phase(cav.h, 1) == 0
         assert cav.step(1)["call_status"] == 0
+        gotf = {}
         for name, which in FIELDS:
-            _check_change(cav.get(which), st0[name], ref[name], name, MIXED_TOL[1])
+            gotf[name] = cav.get(which)
+            _check_change(gotf[name], st0[name], ref[name], name, MIXED_TOL[1])
+        res = _increment_residuals(st0, gotf, op)
+        assert max(res.values()) <= RESID_TOL, res

@@ -109,3 +109,47 @@ def test_admission_by_budget():
         assert pool.admit(p, 10) is not None       # room again
     assert H.hosc_pool_create(0, 4, 0, 0)[0] == H.HOSC_EINVAL
     assert H.hosc_pool_create(1 << 20, 3, H.HOSC_POOL_GRAPH, 0)[0] == H.HOSC_EINVAL
+
+
+# ------------------------------------------------------------- the persistent round kernel
+
+def _round_tiles(N):
+    """The Krylov launch shape of the persistent round kernel: 256-thread blocks, segments of
+    eight planes (fewer on grids with fewer interior planes)."""
+    return 256, min(N - 2, 8), 0
+
+
+def test_persistent_round_equals_plain_solve():
+    """A pool in persistent mode (one launch of the round kernel per round, all members' phases
+    on one cooperative grid) gives, for each member of a mix of sizes, the same steps and bit for
+    bit the same fields as hosc_solve_steady on its own context with the same launch shape: the
+    round kernel runs the per-kernel path's device bodies, tile for tile."""
+    members = [TARGET] + OTHERS[:4]
+    res, stats = _solve(members, mode=H.HOSC_POOL_PERSISTENT, G=8)
+    assert stats["captures"] == 0 and stats["rounds"] >= 1
+    for m, r in zip(members, res):
+        with H.Cavity(_params(*m)) as cav:
+            assert H.hosc_set_tiles(cav.h, *_round_tiles(m[0])) == 0
+            info = cav.solve_steady(4000, allow=(H.HOSC_ESTEPLIMIT, H.HOSC_ENOCONV))
+            assert info["call_status"] == r["status"], (m, info, r["status"])
+            assert info["steps"] == r["info"]["steps"], m
+            for name, which in FIELDS:
+                assert np.array_equal(cav.get(which), r[name]), (m, name)
+
+
+def test_persistent_round_admission():
+    """The round kernel runs mixed-precision BiCGSTAB members without history terms: anything
+    else is refused at admission."""
+    with S.Pool(1 << 30, 8, H.HOSC_POOL_PERSISTENT, False) as pool:
+        with pytest.raises(H.HoscError):
+            pool.admit(_params(13, 1e3, 1.0, precision=H.HOSC_FP64), 10)
+        p = _params(13, 1e3, 1.0)
+        p.use_history = 1
+        with pytest.raises(H.HoscError):
+            pool.admit(p, 10)
+        s = pool.admit(_params(13, 1e3, 1.0), 10)
+        assert s is not None
+        done = pool.run(2)
+        assert done == [s]
+        assert pool.result(s)["status"] == H.HOSC_ESTEPLIMIT
+    assert H.hosc_pool_create(1 << 20, 8, 3, 0)[0] == H.HOSC_EINVAL
