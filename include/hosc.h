@@ -117,8 +117,9 @@ typedef struct {
                          second-order-in-time scheme); 0: delta_t^- = 0 at every step, a
                          first-order pseudo-time march with the same steady state */
   int auto_defect;    /* HOSC_MIXED: 1 switches from FP32 to FP64 defect sweeps by itself when the
-                         step change stalls (200 steps without a 5 % improvement); 0 keeps the
-                         phase chosen with hosc_set_phase */
+                         step change stalls: 200 steps without a 5 % improvement once it is below
+                         1e-3 of the largest step change of the solve, or 2000 steps at any level;
+                         0 keeps the phase chosen with hosc_set_phase */
   int precond;        /* 0: BiCGSTAB on the systems as assembled (the paper's unpreconditioned
                          solver, the default); 1: Jacobi row scaling, each row of the level-(n+1)
                          system and its right-hand side divided by the row's diagonal before the

@@ -49,6 +49,7 @@ struct Ctx {
   // mixed precision: 0 = FP32 sweeps, 1 = FP64 defect sweeps (FP32 Krylov in both)
   int phase = 0;
   double best_res = INFINITY;
+  double peak_res = 0.0;   // largest step change seen by the stall watch
   long since_best = 0;
   bool shadow_valid = false;   // float copies of the state match the state
   // one captured step per (phase, cur, have_prev); BiCGSTAB runs as a device-side while loop
@@ -163,9 +164,13 @@ bool tiles_valid(const Ctx* c, int kblock, int kz, int narrow) {
 
 // FP32 Krylov vectors cannot resolve relative residuals far below their rounding.
 constexpr double kFp32TolFloor = 3e-6;
-// Steps without a 5 % improvement of the step change after which mixed precision switches from
-// FP32 to FP64 defect sweeps.
+// Mixed precision switches from FP32 to FP64 defect sweeps when the step change has stalled: no
+// 5 % improvement in kStallSteps steps once it is below kStallDrop times the largest step change
+// of the solve (the FP32 noise floor lies far below the start-up transient, whose own plateaus
+// must not trigger the switch), or in kStallLong steps whatever its level.
 constexpr long kStallSteps = 200;
+constexpr long kStallLong = 2000;
+constexpr double kStallDrop = 1e-3;
 
 DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   DevParams d{};   // every field not set below (launch shapes, inner_pass, ...) starts at zero
@@ -345,6 +350,7 @@ hosc_status set_initial_state(Ctx* c) {
   c->phase = 0;
   c->shadow_valid = false;
   c->best_res = INFINITY;
+  c->peak_res = 0.0;
   c->since_best = 0;
   c->P = device_params(c->prm, 0, 0);
   apply_tiles(c);
@@ -603,10 +609,12 @@ void set_phase(Ctx* c, int phase) {
 
 void watch_stall(Ctx* c, double res) {
   if (c->prm.precision != HOSC_MIXED || c->phase != 0 || !c->prm.auto_defect) return;
+  if (!(res <= c->peak_res)) c->peak_res = res;
   if (res < 0.95 * c->best_res) {
     c->best_res = res;
     c->since_best = 0;
-  } else if (++c->since_best >= kStallSteps) {
+  } else if (++c->since_best >= kStallLong ||
+             (c->since_best >= kStallSteps && c->best_res < kStallDrop * c->peak_res)) {
     set_phase(c, 1);
   }
 }
@@ -1491,6 +1499,7 @@ hosc_status hosc_set_phase(void* ctx, int phase) {
   if (c->prm.precision != HOSC_MIXED) return phase == 0 ? HOSC_OK : HOSC_EINVAL;
   set_phase(c, phase);
   c->best_res = INFINITY;
+  c->peak_res = 0.0;
   c->since_best = 0;
   return HOSC_OK;
 }

@@ -31,6 +31,7 @@ namespace {
 
 constexpr unsigned long long kBarrierNs = 5000000000ull;   // 5 s
 constexpr int kRoundThreads = 256;
+constexpr int kRoundMinBlocks = 2;   // resident blocks per SM the register budget is set for
 
 // Item counts per member of each phase class (blocks of 256 threads).
 enum { kNodes = 0, kInterior, kThetaWalls, kPressureWalls, kKrylov, kInit, kOne, kClasses };
@@ -212,7 +213,7 @@ __device__ __forceinline__ void raise_continue(const RoundDev& R, const RoundMem
   if (!(ks[0].done && ks[1].done && ks[2].done && ks[3].done)) atomicExch(R.cont + it, 1);
 }
 
-__global__ void __launch_bounds__(kRoundThreads, 2) k_round(RoundDev R) {
+__global__ void __launch_bounds__(kRoundThreads, kRoundMinBlocks) k_round(RoundDev R) {
   // the round's start: every member runs, stops at its first steady step, no records yet
   for (int q = blockIdx.x; q < R.count; q += gridDim.x) {
     if (threadIdx.x == 0) {
