@@ -283,6 +283,56 @@ def run_steady(args):
     return 0
 
 
+def run_table1(args):
+    """The grid study of Table 1 (Sec. 3.1): n = 0.75, Ra = 1e4, Pr = 1, the three-level scheme,
+    marched from rest to t = 100 on each requested grid (dt = 5e-4, inside the stability bound of
+    the printed scheme at this Ra; mixed precision with FP64 defect sweeps once the step change
+    stalls), with theta, u, v, w at the probes (0.6, 0.6, 0.6) and (0.4, 0.4, 0.4) beside the
+    printed values. The steady state is centro-symmetric here (theta_ref = 1/2), so the printed
+    (0.6, 0.6, 0.6) values are also set beside this march's (0.4, 0.4, 0.4) ones."""
+    import torch
+    from paper_2411_06563_gb300 import hosc as H
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from golden_values import table
+    from test_gpu_table1 import table1_params
+    torch.cuda.set_device(0)
+    printed = {(r[0], int(r[3])): r[4:] for r in table("table1_probes.txt")}
+    out = []
+    for N in (int(x) for x in args.table1_sizes.split(",")):
+        p = table1_params(N, H.HOSC_MIXED)
+        p.tol_lin = 1e-10
+        steps = int(round(100.0 / p.dt))
+        with H.Cavity(p) as cav:
+            t0 = time.perf_counter()
+            done = 0
+            while done < steps:
+                info = cav.step(min(5000, steps - done))
+                done += info["steps"]
+                if info["call_status"] not in (0,):
+                    break
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            f = {k: cav.get(w) for k, w in (("th", H.HOSC_THETA), ("u", H.HOSC_U),
+                                           ("v", H.HOSC_V), ("w", H.HOSC_W))}
+            phase = H.hosc_get_phase(cav.h)
+        probes = {}
+        for x in (0.6, 0.4):
+            i = int(round(x * (N - 1)))
+            probes[str(x)] = [float(f[k][i, i, i]) for k in ("th", "u", "v", "w")]
+        row = {"N": N, "dt": p.dt, "lambda": p.lambda_, "steps": done, "t": done * p.dt,
+               "status": H.hosc_strerror(info["call_status"]), "seconds": el,
+               "res_over_dt_last": info["res"] / p.dt, "div_max_last": info["div_max"],
+               "final_phase": "FP64 defect sweeps" if phase == 1 else "FP32 sweeps",
+               "probes_theta_u_v_w": probes,
+               "printed": {str(x): list(printed.get((x, N), [])) for x in (0.6, 0.4)}}
+        out.append(row)
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    res = {"metric": "Table 1 march to t = 100", "value": None, "unit": "probe values",
+           "n_gpus": 1, "data": "synthetic", "table1": out}
+    print(json.dumps(res))
+    return 0
+
+
 def run_equal(args):
     """Steady solves at equal accuracy: a seeded set of small cavities (N in {17, 21}, Ra
     log-uniform in [1e2, 1e3], n uniform in [0.9, 1.1], Pr = 1, dt = 0.02, lambda = 0.1,
@@ -534,11 +584,13 @@ def main():
                          "(instead of the autotuner)")
     ap.add_argument("--spinup", type=int, default=None,
                     help="untimed steps from rest before the warm-up (default: per workload)")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "equal", "steady"],
+    ap.add_argument("--mode", default="step",
+                    choices=["step", "batch", "serve", "equal", "steady", "table1"],
                     help="step: the single-cavity headline; batch: 64 cavities in a pool; "
                          "serve: a Poisson request stream on a pool; equal: steady solves of "
                          "the pool against one-at-a-time FP64 at equal accuracy")
     ap.add_argument("--equal-cavities", type=int, default=8)
+    ap.add_argument("--table1-sizes", default="11,51")
     ap.add_argument("--equal-max-steps", type=int, default=20000)
     ap.add_argument("--pool-mode", default="persistent",
                     choices=["graph", "streams", "persistent"])
@@ -562,6 +614,8 @@ def main():
         return run_equal(args)
     if args.impl == "ours" and args.mode == "steady":
         return run_steady(args)
+    if args.impl == "ours" and args.mode == "table1":
+        return run_table1(args)
     if args.impl == "reference":
         return run_reference(args, wl)
 

@@ -194,8 +194,10 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
  * 1 for n = 1 and I2_eps^((n-1)/2) for n > 1 (a factor 4 inside the bound dt |G*|^2 <= 4 L of
  * the explicit compact terms). A large lambda speeds up the slowest pressure modes, which
  * contract by a fixed fraction of lambda per step; lambda dt must stay below h^2. The rule uses
- * the cube's spacing: for a box (Ly, Lz) set dt and lambda again. HOSC_EINVAL for N < 5, Ra < 0,
- * Pr <= 0 or n <= 0. */
+ * the cube's spacing: for a box (Ly, Lz) set dt and lambda again. tol_div = tol_steady h /
+ * (2 lambda): while the pressure correction runs, the step change it causes (about lambda
+ * tol_div / h per unit pseudo-time) stays below tol_steady (if tol_steady is changed, set tol_div
+ * again). HOSC_EINVAL for N < 5, Ra < 0, Pr <= 0 or n <= 0. */
 hosc_status hosc_steady_params(hosc_params* p, int N, double Ra, double Pr, double n);
 
 /* Bytes of device workspace a context with these parameters needs (0 if invalid). */

@@ -32,9 +32,14 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+# Per-source flags: the persistent round kernel reads, in later phases of one launch, arrays that
+# other SMs wrote in earlier ones, so its global loads are cached in L2 only (coherent).
+EXTRA = {"hosc_round.cu": ["-Xptxas", "-dlcm=cg"]}
+
+
 def _compile(src, verbose):
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-    cmd = [nvcc()] + ARCH + FLAGS + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + ARCH + FLAGS + EXTRA.get(os.path.basename(src), []) + ["-c", src, "-o", obj]
     if verbose:
         cmd += ["-Xptxas", "-v"]
     res = subprocess.run(cmd, capture_output=True, text=True)

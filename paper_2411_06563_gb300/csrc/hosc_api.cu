@@ -1179,6 +1179,11 @@ hosc_status hosc_steady_params(hosc_params* p, int N, double Ra, double Pr, doub
   p->lambda = 2.0 * Pr * fmin(1.0, 2.0 * eta_bl);
   p->dt = fmin(dt_stab, 0.9 * h * h / p->lambda);
   p->use_history = 0;
+  // A correction p -= lambda div V moves the velocity by about dt lambda |div V| / h in a step, so
+  // while it is applied the step change max|chi^{n+1} - chi^n| / dt stays near lambda tol_div / h:
+  // tol_div is set so that this is half of tol_steady (else the correction, switched on and off
+  // around tol_div, holds the step change above tol_steady on fine grids).
+  p->tol_div = 0.5 * p->tol_steady * h / p->lambda;
   return HOSC_OK;
 }
 

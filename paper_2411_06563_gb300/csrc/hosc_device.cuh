@@ -2,6 +2,20 @@
 // block reductions and the last-block reduction of per-block partials.
 #pragma once
 
+// Loads of arrays that a kernel only reads. A kernel launch reads them through the read-only
+// (non-coherent) cache with restrict-qualified pointers. The persistent round kernel of the pool
+// (hosc_round.cu, built with HOSC_PERSISTENT_BUILD) writes these arrays in one phase and reads
+// them in a later one of the same launch, so there they are plain loads cached in L2 only
+// (coherent across SMs), and pointers are not restrict-qualified.
+#ifdef HOSC_PERSISTENT_BUILD
+#define HOSC_RESTRICT
+#define HOSC_LDG(p) __ldcg(p)
+#else
+#define HOSC_RESTRICT __restrict__
+#define HOSC_LDG(p) __ldg(p)
+#endif
+
+
 #include <cuda_runtime.h>
 
 #include "hosc_internal.h"
@@ -14,7 +28,7 @@ __device__ __forceinline__ long node(int i, int j, int k, int N) {
 
 // Derivative along one axis at a node whose coordinate along that axis is a (0..N-1); st is the
 // memory stride of that axis. Central inside, second-order one-sided at the two walls.
-__device__ __forceinline__ double grad_axis(const double* __restrict__ f, long c, int a, int N,
+__device__ __forceinline__ double grad_axis(const double* HOSC_RESTRICT f, long c, int a, int N,
                                             long st, double inv2h) {
   if (a == 0) return (-3.0 * f[c] + 4.0 * f[c + st] - f[c + 2 * st]) * inv2h;
   if (a == N - 1) return (3.0 * f[c] - 4.0 * f[c - st] + f[c - 2 * st]) * inv2h;
@@ -26,9 +40,9 @@ struct Grad9 {
 };
 
 // The nine velocity gradients at node (i, j, k); ix, iy, iz = 1/(2 h_d) of the three directions.
-__device__ __forceinline__ Grad9 velocity_gradients(const double* __restrict__ u,
-                                                    const double* __restrict__ v,
-                                                    const double* __restrict__ w, int i, int j,
+__device__ __forceinline__ Grad9 velocity_gradients(const double* HOSC_RESTRICT u,
+                                                    const double* HOSC_RESTRICT v,
+                                                    const double* HOSC_RESTRICT w, int i, int j,
                                                     int k, int N, double ix, double iy,
                                                     double iz) {
   const long c = node(i, j, k, N);

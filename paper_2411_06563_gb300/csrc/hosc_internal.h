@@ -221,6 +221,10 @@ void round_member_shape(RoundMember* M);
 // HOSC_ECUDA with detail on a CUDA error or when a grid barrier wait gave up.
 hosc_status launch_round(RoundState* S, const std::vector<RoundMember>& members, int G,
                          cudaStream_t stream, char* detail, size_t detail_len);
+// The same round in the work-list form: each member advances through its own phases, whose
+// tiles any block takes from a shared queue (no grid barrier).
+hosc_status launch_flow(RoundState* S, const std::vector<RoundMember>& members, int G,
+                        cudaStream_t stream, char* detail, size_t detail_len);
 
 // Rounds of captured steps of one context, driven by a pool (hosc_pool.cu); defined with the
 // context in hosc_api.cu. ctx is a context made by hosc_create.

@@ -112,9 +112,9 @@ struct Op4 {
 
 __device__ __forceinline__ Op4 load_op(const Fields& F, int c, bool ene) {
   Op4 op;
-  op.m = __ldg(F.kwm + c);
-  op.l12 = __ldg(F.kL + c) * (1.f / 12.f);
-  op.e = ene ? __ldg(F.kwe + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+  op.m = HOSC_LDG(F.kwm + c);
+  op.l12 = HOSC_LDG(F.kL + c) * (1.f / 12.f);
+  op.e = ene ? HOSC_LDG(F.kwe + c) : make_float4(0.f, 0.f, 0.f, 0.f);
   return op;
 }
 
@@ -277,13 +277,13 @@ __device__ __forceinline__ void k4_pv_body(const DevParams& P, const Fields& F, 
   const bool ene = !sc.done[3];   // the energy system still iterates (uniform)
   const int N = P.N, N2 = N * N;
   const float4 b = sc.b, mom = neg4(sc.om);
-  const float4* __restrict__ R = F.kr;
-  const float4* __restrict__ Po = F.kp[pp];
-  const float4* __restrict__ Vo = F.kv[pp];
-  float4* __restrict__ Pn = F.kp[1 - pp];
-  float4* __restrict__ Vn = F.kv[1 - pp];
+  const float4* HOSC_RESTRICT R = F.kr;
+  const float4* HOSC_RESTRICT Po = F.kp[pp];
+  const float4* HOSC_RESTRICT Vo = F.kv[pp];
+  float4* HOSC_RESTRICT Pn = F.kp[1 - pp];
+  float4* HOSC_RESTRICT Vn = F.kv[1 - pp];
   auto pnew = [&](int c) {
-    const float4 r = __ldg(R + c), p = __ldg(Po + c), v = __ldg(Vo + c);
+    const float4 r = HOSC_LDG(R + c), p = HOSC_LDG(Po + c), v = HOSC_LDG(Vo + c);
     return fma4(b, fma4(mom, v, p), r);
   };
   FF acc[4] = {};
@@ -298,7 +298,7 @@ __device__ __forceinline__ void k4_pv_body(const DevParams& P, const Fields& F, 
                                  pnew(c + N), pnew(c - N), pz, pm);
       Pn[c] = pc;
       Vn[c] = vn;
-      ff_dot4(acc, __ldg(F.kr0 + c), vn);
+      ff_dot4(acc, HOSC_LDG(F.kr0 + c), vn);
       pm = pc;
       pc = pz;
     }
@@ -343,10 +343,10 @@ __device__ __forceinline__ void k4_st_body(const DevParams& P, const Fields& F, 
   const int N = P.N, N2 = N * N;
   const int np = 1 - pp;   // written by k4_pv of this iteration
   const float4 ma = neg4(sc.a);
-  const float4* __restrict__ R = F.kr;
-  const float4* __restrict__ V = F.kv[np];
-  float4* __restrict__ T = F.kt;
-  auto sval = [&](int c) { return fma4(ma, __ldg(V + c), __ldg(R + c)); };
+  const float4* HOSC_RESTRICT R = F.kr;
+  const float4* HOSC_RESTRICT V = F.kv[np];
+  float4* HOSC_RESTRICT T = F.kt;
+  auto sval = [&](int c) { return fma4(ma, HOSC_LDG(V + c), HOSC_LDG(R + c)); };
   FF acc[8] = {};
   Column col;
   if (column(P, col, vg)) {
@@ -404,8 +404,8 @@ __device__ __forceinline__ bool k4_xr_body(const DevParams& P, const Fields& F, 
   if (column(P, col, vg)) {
     for (int k = col.k0; k < col.k1; ++k) {
       const int c = col.cb + N2 * k;
-      const float4 r = F.kr[c], v = __ldg(F.kv[np] + c), p = __ldg(F.kp[np] + c);
-      const float4 t = __ldg(F.kt + c), r0 = __ldg(F.kr0 + c);
+      const float4 r = F.kr[c], v = HOSC_LDG(F.kv[np] + c), p = HOSC_LDG(F.kp[np] + c);
+      const float4 t = HOSC_LDG(F.kt + c), r0 = HOSC_LDG(F.kr0 + c);
       const float4 sv = fma4(ma, v, r);
       F.kx[c] = fma4(om, sv, fma4(a, p, F.kx[c]));
       const float4 rn = fma4(mom, t, sv);

@@ -321,7 +321,7 @@ hosc_status hosc_pool_run(void* pool, int rounds, int* done_slots, int cap, int*
         ctx_round_member(ctx, &rm[a]);
       }
       PCU(cudaDeviceSynchronize());   // the members' own streams are idle
-      hosc_status rs = launch_round(P->rs, rm, P->G, P->stream, detail_buffer(), 256);
+      hosc_status rs = launch_flow(P->rs, rm, P->G, P->stream, detail_buffer(), 256);
       if (rs) return rs;
       for (size_t a = 0; a < act.size(); ++a) {
         hosc_status e = ctx_readback_round(P->m[act[a]].ctx, P->stream, P->G);

@@ -47,7 +47,7 @@ __device__ __forceinline__ T par(double d, float f) {
 }
 
 template <class T, class S>
-__device__ __forceinline__ T grad_axis_t(const S* __restrict__ f, long c, int a, int N, long st,
+__device__ __forceinline__ T grad_axis_t(const S* HOSC_RESTRICT f, long c, int a, int N, long st,
                                          T inv2h) {
   if (a == 0) return (T(-3) * (T)f[c] + T(4) * (T)f[c + st] - (T)f[c + 2 * st]) * inv2h;
   if (a == N - 1) return (T(3) * (T)f[c] - T(4) * (T)f[c - st] + (T)f[c - 2 * st]) * inv2h;
@@ -97,9 +97,9 @@ __device__ __forceinline__ Spc<T> spacing(const DevParams& P) {
 }
 
 template <class T, class S>
-__device__ __forceinline__ Grad9T<T> velocity_gradients_t(const S* __restrict__ u,
-                                                          const S* __restrict__ v,
-                                                          const S* __restrict__ w, int i,
+__device__ __forceinline__ Grad9T<T> velocity_gradients_t(const S* HOSC_RESTRICT u,
+                                                          const S* HOSC_RESTRICT v,
+                                                          const S* HOSC_RESTRICT w, int i,
                                                           int j, int k, int N,
                                                           const T i2[3]) {
   const long c = node(i, j, k, N);
@@ -124,10 +124,10 @@ __device__ __forceinline__ Grad9T<T> velocity_gradients_t(const S* __restrict__ 
 // no-slip walls vanish identically, I2 is taken at the node one step inward along each of those
 // wall normals.
 template <class T>
-__device__ __forceinline__ void k_viscosity_body(const DevParams& P, const T* __restrict__ u,
-                                                 const T* __restrict__ v, const T* __restrict__ w,
-                                                 T* __restrict__ eta, T* __restrict__ L,
-                                                 const int* __restrict__ halt, unsigned vbx) {
+__device__ __forceinline__ void k_viscosity_body(const DevParams& P, const T* HOSC_RESTRICT u,
+                                                 const T* HOSC_RESTRICT v, const T* HOSC_RESTRICT w,
+                                                 T* HOSC_RESTRICT eta, T* HOSC_RESTRICT L,
+                                                 const int* HOSC_RESTRICT halt, unsigned vbx) {
   const unsigned N = P.N;
   const unsigned t = vbx * blockDim.x + threadIdx.x;
   if (t >= N * N * N || *halt) return;
@@ -150,11 +150,11 @@ __device__ __forceinline__ void k_viscosity_body(const DevParams& P, const T* __
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const T* __restrict__ u,
-                                                        const T* __restrict__ v,
-                                                        const T* __restrict__ w,
-                                                        T* __restrict__ eta, T* __restrict__ L,
-                                                        const int* __restrict__ halt) {
+__global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const T* HOSC_RESTRICT u,
+                                                        const T* HOSC_RESTRICT v,
+                                                        const T* HOSC_RESTRICT w,
+                                                        T* HOSC_RESTRICT eta, T* HOSC_RESTRICT L,
+                                                        const int* HOSC_RESTRICT halt) {
   k_viscosity_body(P, u, v, w, eta, L, halt, blockIdx.x);
 }
 
@@ -167,12 +167,12 @@ __global__ void __launch_bounds__(kThreads) k_viscosity(DevParams P, const T* __
 //   E*_z = -p_z/(Pr eta) + (2/eta)(eps_xz eta_x + eps_yz eta_y + eps_zz eta_z)
 // Gradients are central inside and one-sided at wall nodes.
 template <class T>
-__device__ __forceinline__ void k_sources_body(const DevParams& P, const T* __restrict__ u,
-                                               const T* __restrict__ v, const T* __restrict__ w,
-                                               const T* __restrict__ th, const T* __restrict__ p,
-                                               const T* __restrict__ eta, T* __restrict__ Eu,
-                                               T* __restrict__ Ev, T* __restrict__ Ew,
-                                               const int* __restrict__ halt, unsigned vbx) {
+__device__ __forceinline__ void k_sources_body(const DevParams& P, const T* HOSC_RESTRICT u,
+                                               const T* HOSC_RESTRICT v, const T* HOSC_RESTRICT w,
+                                               const T* HOSC_RESTRICT th, const T* HOSC_RESTRICT p,
+                                               const T* HOSC_RESTRICT eta, T* HOSC_RESTRICT Eu,
+                                               T* HOSC_RESTRICT Ev, T* HOSC_RESTRICT Ew,
+                                               const int* HOSC_RESTRICT halt, unsigned vbx) {
   const int N = P.N;
   const unsigned t = vbx * blockDim.x + threadIdx.x;
   if (t >= (unsigned)N * N * N || *halt) return;
@@ -197,15 +197,15 @@ __device__ __forceinline__ void k_sources_body(const DevParams& P, const T* __re
 }
 
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_sources(DevParams P, const T* __restrict__ u,
-                                                     const T* __restrict__ v,
-                                                     const T* __restrict__ w,
-                                                     const T* __restrict__ th,
-                                                     const T* __restrict__ p,
-                                                     const T* __restrict__ eta,
-                                                     T* __restrict__ Eu, T* __restrict__ Ev,
-                                                     T* __restrict__ Ew,
-                                                     const int* __restrict__ halt) {
+__global__ void __launch_bounds__(kThreads) k_sources(DevParams P, const T* HOSC_RESTRICT u,
+                                                     const T* HOSC_RESTRICT v,
+                                                     const T* HOSC_RESTRICT w,
+                                                     const T* HOSC_RESTRICT th,
+                                                     const T* HOSC_RESTRICT p,
+                                                     const T* HOSC_RESTRICT eta,
+                                                     T* HOSC_RESTRICT Eu, T* HOSC_RESTRICT Ev,
+                                                     T* HOSC_RESTRICT Ew,
+                                                     const int* HOSC_RESTRICT halt) {
   k_sources_body(P, u, v, w, th, p, eta, Eu, Ev, Ew, halt, blockIdx.x);
 }
 
@@ -230,7 +230,7 @@ __device__ __forceinline__ D7<T> diffs7(const T f[7], const Spc<T>& s) {
 }
 
 template <class T, class S>
-__device__ __forceinline__ void load7(const S* __restrict__ a, long c, long sy, long sz, T f[7]) {
+__device__ __forceinline__ void load7(const S* HOSC_RESTRICT a, long c, long sy, long sz, T f[7]) {
   f[0] = (T)a[c];
   f[1] = (T)a[c + 1];
   f[2] = (T)a[c - 1];
@@ -244,7 +244,7 @@ __device__ __forceinline__ void load7(const S* __restrict__ a, long c, long sy, 
 // 7 x+y+, 8 x-y+, 9 x+y-, 10 x-y-, 11 y+z+, 12 y-z+, 13 y+z-, 14 y-z-,
 // 15 z+x+, 16 z-x+, 17 z+x-, 18 z-x-.
 template <class T>
-__device__ __forceinline__ void load19(const T* __restrict__ a, long c, long sy, long sz,
+__device__ __forceinline__ void load19(const T* HOSC_RESTRICT a, long c, long sy, long sz,
                                        T f[19]) {
   load7<T, T>(a, c, sy, sz, f);
   f[7] = (T)a[c + 1 + sy];
@@ -344,14 +344,14 @@ __device__ __forceinline__ T pseudo_time_mass(T G, T H, T I, T L, T dt, T s3, T 
 template <class Tc, class Ts>
 // The float build is bounded to 80 registers (three 256-thread blocks per SM); the double builds
 // keep the compiler's choice.
-__device__ __forceinline__ void k_rhs_body(const DevParams& P, const Tc* __restrict__ u,
-                                           const Tc* __restrict__ v, const Tc* __restrict__ w,
-                                           const Tc* __restrict__ th, const Tc* __restrict__ L,
-                                           const Tc* __restrict__ Eu, const Tc* __restrict__ Ev,
-                                           const Tc* __restrict__ Ew, const Tc* __restrict__ Lp,
-                                           const Tc* __restrict__ up, const Tc* __restrict__ vp,
-                                           const Tc* __restrict__ wp, const Tc* __restrict__ Eup,
-                                           const Tc* __restrict__ Evp, const Tc* __restrict__ Ewp,
+__device__ __forceinline__ void k_rhs_body(const DevParams& P, const Tc* HOSC_RESTRICT u,
+                                           const Tc* HOSC_RESTRICT v, const Tc* HOSC_RESTRICT w,
+                                           const Tc* HOSC_RESTRICT th, const Tc* HOSC_RESTRICT L,
+                                           const Tc* HOSC_RESTRICT Eu, const Tc* HOSC_RESTRICT Ev,
+                                           const Tc* HOSC_RESTRICT Ew, const Tc* HOSC_RESTRICT Lp,
+                                           const Tc* HOSC_RESTRICT up, const Tc* HOSC_RESTRICT vp,
+                                           const Tc* HOSC_RESTRICT wp, const Tc* HOSC_RESTRICT Eup,
+                                           const Tc* HOSC_RESTRICT Evp, const Tc* HOSC_RESTRICT Ewp,
                                            const Fields& F, unsigned vbx) {
   const int N = P.N;
   const unsigned ni = N - 2;
@@ -387,8 +387,8 @@ __device__ __forceinline__ void k_rhs_body(const DevParams& P, const Tc* __restr
     }
     const Eq5<Tc> cm = eq5_coefficients<Tc>(G7, H7, I7, upc * Lpc, vpc * Lpc, wpc * Lpc, sp);
     // one momentum system: source E (level n, and n-1 when kept) and the field X
-    auto system = [&](const Tc* __restrict__ E, const Tc* __restrict__ Ep,
-                      const Tc* __restrict__ X) {
+    auto system = [&](const Tc* HOSC_RESTRICT E, const Tc* HOSC_RESTRICT Ep,
+                      const Tc* HOSC_RESTRICT X) {
       Tc E7[7], f19[19];
       load7<Tc, Tc>(E, c, sy, sz, E7);
       const Tc Epc = P.have_prev ? Ep[c] : E7[0];
@@ -475,12 +475,12 @@ __device__ __forceinline__ void k_rhs_body(const DevParams& P, const Tc* __restr
 
 template <class Tc, class Ts>
 __global__ void __launch_bounds__(kThreads, sizeof(Tc) == sizeof(float) ? 3 : 0) k_rhs(
-    DevParams P, const Tc* __restrict__ u, const Tc* __restrict__ v,
-    const Tc* __restrict__ w, const Tc* __restrict__ th, const Tc* __restrict__ L,
-    const Tc* __restrict__ Eu, const Tc* __restrict__ Ev, const Tc* __restrict__ Ew,
-    const Tc* __restrict__ Lp, const Tc* __restrict__ up, const Tc* __restrict__ vp,
-    const Tc* __restrict__ wp, const Tc* __restrict__ Eup, const Tc* __restrict__ Evp,
-    const Tc* __restrict__ Ewp, Fields F) {
+    DevParams P, const Tc* HOSC_RESTRICT u, const Tc* HOSC_RESTRICT v,
+    const Tc* HOSC_RESTRICT w, const Tc* HOSC_RESTRICT th, const Tc* HOSC_RESTRICT L,
+    const Tc* HOSC_RESTRICT Eu, const Tc* HOSC_RESTRICT Ev, const Tc* HOSC_RESTRICT Ew,
+    const Tc* HOSC_RESTRICT Lp, const Tc* HOSC_RESTRICT up, const Tc* HOSC_RESTRICT vp,
+    const Tc* HOSC_RESTRICT wp, const Tc* HOSC_RESTRICT Eup, const Tc* HOSC_RESTRICT Evp,
+    const Tc* HOSC_RESTRICT Ewp, Fields F) {
   k_rhs_body<Tc, Ts>(P, u, v, w, th, L, Eu, Ev, Ew, Lp, up, vp, wp, Eup, Evp, Ewp, F,
                      blockIdx.x);
 }
@@ -771,14 +771,14 @@ __global__ void k_arm(int* halt, unsigned int* ring_pos, int* steady_stop, int s
 
 namespace {
 // Float copies of the state for the FP32 sweeps (one rounding per node and step).
-__device__ __forceinline__ void k_shadow_body(int n3, const double* __restrict__ u,
-                                              const double* __restrict__ v,
-                                              const double* __restrict__ w,
-                                              const double* __restrict__ th,
-                                              const double* __restrict__ p, float* __restrict__ us,
-                                              float* __restrict__ vs, float* __restrict__ ws,
-                                              float* __restrict__ ths, float* __restrict__ ps,
-                                              const int* __restrict__ halt, unsigned vbx) {
+__device__ __forceinline__ void k_shadow_body(int n3, const double* HOSC_RESTRICT u,
+                                              const double* HOSC_RESTRICT v,
+                                              const double* HOSC_RESTRICT w,
+                                              const double* HOSC_RESTRICT th,
+                                              const double* HOSC_RESTRICT p, float* HOSC_RESTRICT us,
+                                              float* HOSC_RESTRICT vs, float* HOSC_RESTRICT ws,
+                                              float* HOSC_RESTRICT ths, float* HOSC_RESTRICT ps,
+                                              const int* HOSC_RESTRICT halt, unsigned vbx) {
   const int t = vbx * blockDim.x + threadIdx.x;
   if (t >= n3 || *halt) return;
   us[t] = (float)u[t];
@@ -790,16 +790,16 @@ __device__ __forceinline__ void k_shadow_body(int n3, const double* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_shadow(int n3, const double* __restrict__ u,
-                                                     const double* __restrict__ v,
-                                                     const double* __restrict__ w,
-                                                     const double* __restrict__ th,
-                                                     const double* __restrict__ p,
-                                                     float* __restrict__ us, float* __restrict__ vs,
-                                                     float* __restrict__ ws,
-                                                     float* __restrict__ ths,
-                                                     float* __restrict__ ps,
-                                                     const int* __restrict__ halt) {
+__global__ void __launch_bounds__(kThreads) k_shadow(int n3, const double* HOSC_RESTRICT u,
+                                                     const double* HOSC_RESTRICT v,
+                                                     const double* HOSC_RESTRICT w,
+                                                     const double* HOSC_RESTRICT th,
+                                                     const double* HOSC_RESTRICT p,
+                                                     float* HOSC_RESTRICT us, float* HOSC_RESTRICT vs,
+                                                     float* HOSC_RESTRICT ws,
+                                                     float* HOSC_RESTRICT ths,
+                                                     float* HOSC_RESTRICT ps,
+                                                     const int* HOSC_RESTRICT halt) {
   k_shadow_body(n3, u, v, w, th, p, us, vs, ws, ths, ps, halt, blockIdx.x);
 }
 }  // namespace

@@ -19,7 +19,7 @@ import numpy as np
 from . import hosc as H
 
 
-def request_params(N, Ra, n, Pr=1.0, precision=None, tol_steady=1e-6, tol_div=1e-6):
+def request_params(N, Ra, n, Pr=1.0, precision=None, tol_steady=1e-6, tol_div=None):
     """hosc_params for one cavity solve of a batch or a request stream: the library's steady-solve
     rule (hosc_steady_params: pseudo-time step from the stability estimate of the scheme and the
     pressure relaxation, lambda = 2 Pr min(1, 2 eta_bl), no delta_t^- history), linear tolerance
@@ -27,8 +27,9 @@ def request_params(N, Ra, n, Pr=1.0, precision=None, tol_steady=1e-6, tol_div=1e
     stalls)."""
     p = H.hosc_steady_params(N, Ra, Pr, n)
     p.tol_lin = 1e-10
+    # the steady rule ties tol_div to tol_steady (h / (2 lambda)); an explicit tol_div is kept
+    p.tol_div = p.tol_div * tol_steady / p.tol_steady if tol_div is None else tol_div
     p.tol_steady = tol_steady
-    p.tol_div = tol_div
     p.precision = H.HOSC_MIXED if precision is None else precision
     return p
 

@@ -1,0 +1,52 @@
+"""The time-accurate march of the grid study of Table 1 (Sec. 3.1: n = 0.75, Ra = 1e4, Pr = 1,
+the three-level scheme with the delta_t^- history terms) against the FP64 oracle on the 11^3
+grid: fifty steps from rest at a pseudo-time step inside the stability bound of the printed
+scheme (dt = 5e-4; the printed dt = 0.02 is outside it at this Ra, and the oracle's march with it
+fails within 130 steps), every field after every tenth step within 1e-10 of the oracle's. The
+march to t = 100 itself and its probe values beside the printed ones are a benchmark mode
+(bench.py --mode table1), since it takes 200 000 steps."""
+
+import numpy as np
+import pytest
+
+from oracle import hosc_oracle as O
+
+pytestmark = pytest.mark.gpu
+
+H = pytest.importorskip("paper_2411_06563_gb300.hosc")
+
+FIELDS = (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W), ("th", H.HOSC_THETA),
+          ("p", H.HOSC_P))
+
+
+def table1_params(N, precision=H.HOSC_FP64):
+    """The march of Table 1 on N^3: n = 0.75, Ra = 1e4, Pr = 1, the history terms of Eq. (5) on,
+    dt = 5e-4 and the steady rule's relaxation (at most 0.9 h^2/dt)."""
+    p = H.hosc_default_params(N, 1e4, 1.0, 0.75)
+    p.dt = 5e-4
+    h = 1.0 / (N - 1)
+    p.lambda_ = min(0.9 * h * h / p.dt, H.hosc_steady_params(N, 1e4, 1.0, 0.75).lambda_)
+    p.use_history = 1
+    p.precision = precision
+    return p
+
+
+def test_table1_march_11_against_the_oracle():
+    p = table1_params(11)
+    p.tol_lin = 1e-13
+    p.max_lin_iter = 3000
+    op = O.Params(N=p.N, Ra=p.Ra, Pr=p.Pr, n=p.n, dt=p.dt, lam=p.lambda_, tol_lin=p.tol_lin,
+                  max_lin_iter=p.max_lin_iter, use_history=1)
+    g = O.Grid(p.N)
+    st = O.initial_state(op)
+    with H.Cavity(p) as cav:
+        for block in range(5):
+            info = cav.step(10)
+            assert info["call_status"] == 0
+            for _ in range(10):
+                st, oinfo = O.step(st, op, g)
+                assert oinfo["status"] == 0
+            for name, which in FIELDS:
+                got = cav.get(which)
+                assert np.max(np.abs(got - st[name])) <= 1e-10 * max(np.max(np.abs(st[name])),
+                                                                      1e-300), (block, name)

@@ -142,6 +142,7 @@ def test_steady_params_rule():
         u = max(1.0, 1.5 * c * math.sqrt(Ra))
         assert p.dt * u * u / Pr <= 1.0 + 1e-12   # L = 1/(Pr eta) >= 1/Pr only tightens it
         assert 0 < p.lambda_ <= 2.0 * Pr
+        assert p.tol_div == pytest.approx(0.5 * p.tol_steady * h / p.lambda_, rel=1e-15)
     # thinner fluids and faster flows need smaller steps
     dt = lambda N, Ra, n: H.hosc_steady_params(N, Ra, 1.0, n).dt
     assert dt(41, 1e5, 0.75) < dt(41, 1e5, 1.0)
