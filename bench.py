@@ -25,14 +25,23 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# Pseudo-time step, relaxation and divergence tolerance of each workload: the library's
+# steady-solve rule (hosc_steady_params; the timed steps are those of the steady solve). They are
+# written out here so that the reference arm, which runs the oracle only, needs no part of the
+# library; the GPU arm checks them against the library.
 WORKLOADS = {
-    "cavity101": dict(N=101, Ra=1e5, Pr=1.0, n=0.75, dt=2e-5, spinup=300, history=0,
+    "cavity101": dict(N=101, Ra=1e5, Pr=1.0, n=0.75, dt=1.1503218609060238e-05,
+                      lam=0.5963268526936827, tol_div=8.384663506958269e-09, spinup=300,
+                      history=0,
                       desc="single cavity 101^3, n=0.75, Ra=1e5, Pr=1 (power-law, shear-thinning), "
                            "mixed precision"),
-    "cavity41": dict(N=41, Ra=1e4, Pr=1.0, n=0.75, dt=2e-4, spinup=300, history=0,
-                     desc="cavity 41^3, n=0.75, Ra=1e4, Pr=1, mixed precision"),
+    "cavity41": dict(N=41, Ra=1e4, Pr=1.0, n=0.75, dt=0.0001771411147115303,
+                     lam=0.9182995386645731, tol_div=1.3612116170915195e-08, spinup=300,
+                     history=0, desc="cavity 41^3, n=0.75, Ra=1e4, Pr=1, mixed precision"),
     # out-of-L2 probe: the Krylov working set (2 GB) is 15x the L2
-    "cavity257": dict(N=257, Ra=1e5, Pr=1.0, n=0.75, dt=2e-5, spinup=50, history=0,
+    "cavity257": dict(N=257, Ra=1e5, Pr=1.0, n=0.75, dt=1.1503218609060238e-05,
+                      lam=0.5963268526936827, tol_div=3.2752591824055733e-09, spinup=50,
+                      history=0,
                       desc="single cavity 257^3, n=0.75, Ra=1e5, Pr=1, mixed precision "
                            "(out-of-L2 roofline probe)"),
 }
@@ -110,40 +119,40 @@ class ClockSampler:
 
 
 def run_reference(args, wl):
-    """The oracle (plain FP64 CPU implementation) timed on the host cores: each step is one
-    pseudo-time step of a smaller cavity with the workload's physics (a bounded sample: 51^3 for
-    up to 150 steps in all, 41^3 up to 400, 31^3 beyond, so that the run ends within a few
-    minutes; about 0.66, 0.37 and 0.14 s per step on five x86 host threads)."""
+    """The oracle (plain FP64 CPU implementation) timed on the host cores on the same workload:
+    the same grid, physics, pseudo-time step and relaxation, marched from a seeded developed state
+    of that cavity (the oracle cannot afford the GPU arm's spin-up from rest: one 101^3 step takes
+    about 3.5 s on the machine's host cores). W warm-up steps, then K timed steps (at most 30, so that
+    the run ends within a few minutes)."""
     from paper_2411_06563_gb300 import replicas as R
     ws, rank, _ = R.world()
     if rank != 0:
         return 0
-    import numpy as np
     from oracle import hosc_oracle as O
-    total = args.steps + args.warmup
-    Ns = 51 if total <= 150 else (41 if total <= 400 else 31)
-    h = 1.0 / (Ns - 1)
-    prm = O.Params(N=Ns, Ra=wl["Ra"], Pr=wl["Pr"], n=wl["n"], dt=wl["dt"] * 4,
-                   lam=min(0.25 * h * h / (wl["dt"] * 4), 0.1), tol_lin=1e-10,
-                   use_history=wl["history"])
-    g = O.Grid(Ns)
-    st = O.initial_state(prm)
+    from paper_2411_06563_gb300 import inputs
+    N = wl["N"]
+    prm = O.Params(N=N, Ra=wl["Ra"], Pr=wl["Pr"], n=wl["n"], dt=wl["dt"], lam=wl["lam"],
+                   tol_div=wl["tol_div"], tol_lin=1e-10, use_history=wl["history"])
+    g = O.Grid(N)
+    st = dict(inputs.cavity_state(N, wl["Ra"], seed=2411), prev=None, steps=0)
     for _ in range(args.warmup):
         st, _ = O.step(st, prm, g)
+    k = max(1, min(args.steps, 30))
     t0, c0 = time.perf_counter(), time.process_time()
-    for _ in range(args.steps):
+    for _ in range(k):
         st, _ = O.step(st, prm, g)
     dt = time.perf_counter() - t0
     cores = _cores_used(time.process_time() - c0, dt)
-    val = (Ns - 2) ** 3 * args.steps / dt
+    val = (N - 2) ** 3 * k / dt
+    sample = "%d oracle steps of the %d^3 workload from a seeded developed state" % (k, N)
     out = {"impl": "reference", "metric": "grid-point updates/s", "value": val, "unit": "GPUPS",
-           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+           "n_gpus": args.gpus, "steps": k, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dt / k, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": wl["desc"], "sample": "%d^3 cavity, same physics" % Ns},
+           "config": {"workload": wl["desc"], "N": N, "Ra": wl["Ra"], "n": wl["n"],
+                      "Pr": wl["Pr"], "dt": wl["dt"], "lambda": wl["lam"], "sample": sample},
            "cpu_baseline": dict({"value": val, "unit": "GPUPS", "cores": cores, "kind": "oracle",
-                                 "sample": "%d oracle steps of a %d^3 cavity" % (args.steps, Ns)},
-                                **_host()),
+                                 "sample": sample}, **_host()),
            "e2e": {"value": val, "unit": "GPUPS", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -228,7 +237,8 @@ def run_batch(args):
     return 0
 
 
-def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=None):
+def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=None,
+                 max_seconds=1e9):
     """One steady solve with the library's steady-solve parameters (hosc_steady_params), mixed
     precision with the automatic switch to FP64 defect sweeps, from rest to max|chi^{n+1} -
     chi^n|/dt < 1e-6 and max|div V| < 1e-6. Returns a dict: wall seconds (device-synchronised),
@@ -243,9 +253,19 @@ def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=N
     with H.Cavity(p) as cav:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        info = cav.solve_steady(max_steps)
+        done, info = 0, None
+        while done < max_steps:   # chunks, with progress on stderr
+            info = cav.solve_steady(min(5000, max_steps - done),
+                                    allow=(H.HOSC_ESTEPLIMIT, H.HOSC_ENOCONV, H.HOSC_EDIVERGED))
+            done += info["steps"]
+            print("steady %d^3: %d steps, res/dt %.3e, div %.3e, phase %d, %.0f s" % (
+                N, done, info["res"] / p.dt, info["div_max"], H.hosc_get_phase(cav.h),
+                time.perf_counter() - t0), file=sys.stderr, flush=True)
+            if info["call_status"] != H.HOSC_ESTEPLIMIT or time.perf_counter() - t0 > max_seconds:
+                break
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        info["steps"] = done
         d = cav.diagnostics(with_fields=True)
         phase = H.hosc_get_phase(cav.h)
     el_f = d["E_local_field"]
@@ -273,9 +293,11 @@ def run_steady(args):
     from paper_2411_06563_gb300 import hosc as H
     torch.cuda.set_device(0)
     wl = WORKLOADS[args.workload]
-    r = steady_solve(H, wl["N"], wl["Ra"], wl["n"], wl["Pr"], args.max_steps)
+    r = steady_solve(H, wl["N"], wl["Ra"], wl["n"], wl["Pr"], args.max_steps,
+                     max_seconds=args.max_seconds)
     out = {"metric": "steady solves/s", "value": 1.0 / r["seconds"], "unit": "solves/s",
-           "n_gpus": 1, "steps": r["steps"], "warmup": 0, "ms_per_step": 1e3 * r["seconds"] / max(1, r["steps"]),
+           "n_gpus": 1, "steps": r["steps"], "warmup": 0,
+           "ms_per_step": 1e3 * r["seconds"] / max(1, r["steps"]),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32+f64", "data": "synthetic", "config": {"workload": wl["desc"]},
            "steady": r}
@@ -539,7 +561,7 @@ def cpu_baseline(cav, H, wl):
     N = wl["N"]
     prm = O.Params(N=N, Ra=wl["Ra"], Pr=wl["Pr"], n=wl["n"], dt=wl["dt"],
                    lam=cav.params.lambda_, tol_lin=cav.params.tol_lin,
-                   use_history=wl["history"])
+                   tol_div=cav.params.tol_div, use_history=wl["history"])
     st = dict(u=cav.get(H.HOSC_U), v=cav.get(H.HOSC_V), w=cav.get(H.HOSC_W),
               th=cav.get(H.HOSC_THETA), p=cav.get(H.HOSC_P), steps=0,
               prev=dict(L=cav.get(H.HOSC_PREV_L), u=cav.get(H.HOSC_PREV_U),
@@ -591,6 +613,8 @@ def main():
                          "the pool against one-at-a-time FP64 at equal accuracy")
     ap.add_argument("--equal-cavities", type=int, default=8)
     ap.add_argument("--table1-sizes", default="11,51")
+    ap.add_argument("--max-seconds", type=float, default=1e9,
+                    help="steady mode: stop after this wall time (status: step limit)")
     ap.add_argument("--equal-max-steps", type=int, default=20000)
     ap.add_argument("--pool-mode", default="persistent",
                     choices=["graph", "streams", "persistent"])
@@ -635,11 +659,11 @@ def main():
     spinup = wl["spinup"] if args.spinup is None else args.spinup
 
     def make(precision, precond=0, solver=0):
-        p = H.hosc_default_params(N, wl["Ra"], wl["Pr"], wl["n"])
+        p = H.hosc_steady_params(N, wl["Ra"], wl["Pr"], wl["n"])
+        assert (p.dt, p.lambda_, p.tol_div) == (wl["dt"], wl["lam"], wl["tol_div"]), \
+            "the workload table no longer matches the library's steady-solve rule"
         p.precond = precond
         p.solver = solver
-        p.dt = wl["dt"]
-        p.lambda_ = min(0.25 * h * h / p.dt, 0.1 * wl["Pr"])
         p.tol_lin = 1e-10
         p.use_history = wl["history"]
         p.precision = H.HOSC_MIXED if precision == "mixed" else H.HOSC_FP64

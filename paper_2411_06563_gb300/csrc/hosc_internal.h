@@ -217,12 +217,10 @@ RoundState* round_state_create();
 void round_state_destroy(RoundState* S);
 // Items and Krylov tile shape of a member (sets P.kblock, P.kz for the round kernel).
 void round_member_shape(RoundMember* M);
-// One persistent round of G steps of every member on `stream` (cooperative launch), waited for.
-// HOSC_ECUDA with detail on a CUDA error or when a grid barrier wait gave up.
-hosc_status launch_round(RoundState* S, const std::vector<RoundMember>& members, int G,
-                         cudaStream_t stream, char* detail, size_t detail_len);
-// The same round in the work-list form: each member advances through its own phases, whose
-// tiles any block takes from a shared queue (no grid barrier).
+// One persistent round of G steps of every member on `stream` (one cooperative launch), waited
+// for: each member advances through its own phases, whose tiles any block takes from a shared
+// queue. HOSC_ECUDA with detail on a CUDA error or when a queue wait gave up; HOSC_ENOMEM when
+// one phase of all members has more tiles than the queue holds.
 hosc_status launch_flow(RoundState* S, const std::vector<RoundMember>& members, int G,
                         cudaStream_t stream, char* detail, size_t detail_len);
 

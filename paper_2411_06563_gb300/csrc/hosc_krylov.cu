@@ -1105,6 +1105,25 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
   k_bicg_init<double><<<b, kThreads, 0, s>>>(P, F, b);
 }
 
+// Launch of an interleaved Krylov kernel with programmatic stream serialisation (see
+// pdl_wait_and_release): in a captured step the kernels of the BiCGSTAB loop chain with
+// programmatic edges.
+template <class K>
+void launch_pdl(K kern, dim3 grid, int threads, cudaStream_t s, const DevParams& P,
+                const Fields& F, int pp) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kern, P, F, pp);
+}
+
 void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
   if (P.krylov_fp32 && P.merged) {   // x, r update of the previous iteration, then p, v
     if (P.narrow) k6_a<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
@@ -1116,8 +1135,8 @@ void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
     return;
   }
   if (P.krylov_fp32) {
-    if (P.narrow) k4_pv<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
-    else k4_pv<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    if (P.narrow) launch_pdl(k4_pv<4>, grid4(P), P.kblock, s, P, F, pp);
+    else launch_pdl(k4_pv<2>, grid4(P), P.kblock, s, P, F, pp);
     return;
   }
   const int b = interior_blocks(P);
@@ -1135,8 +1154,8 @@ void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
     return;
   }
   if (P.krylov_fp32) {
-    if (P.narrow) k4_st<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
-    else k4_st<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    if (P.narrow) launch_pdl(k4_st<4>, grid4(P), P.kblock, s, P, F, pp);
+    else launch_pdl(k4_st<2>, grid4(P), P.kblock, s, P, F, pp);
     return;
   }
   const int b = interior_blocks(P);
@@ -1146,8 +1165,8 @@ void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
   if (P.krylov_fp32 && P.merged) return;   // folded into the next k6_a
   if (P.krylov_fp32) {
-    if (P.narrow) k4_xr<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
-    else k4_xr<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    if (P.narrow) launch_pdl(k4_xr<4>, grid4(P), P.kblock, s, P, F, pp);
+    else launch_pdl(k4_xr<2>, grid4(P), P.kblock, s, P, F, pp);
     return;
   }
   const int b = interior_blocks(P);

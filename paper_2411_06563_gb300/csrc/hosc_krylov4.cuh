@@ -214,6 +214,15 @@ __device__ __forceinline__ double bytes4(const DevParams& P, double float4_words
   return 16.0 * float4_words * ni * ni * ni;
 }
 
+// Programmatic dependent launch: the Krylov kernels of the interleaved solve are launched so that
+// each may start while the previous one is finishing (its blocks take SMs as the previous
+// kernel's blocks leave); a kernel waits for the previous grid's completion and memory before its
+// first access, and lets the next kernel launch at once.
+__device__ __forceinline__ void pdl_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // r = r_0, x = 0, p = v = 0 at interior nodes, every vector zero on the walls; ||r_0||^2.
 // Grid-stride over all N^3 nodes: each thread sums several nodes before the one block reduction.
 // Returns true in the block that finished the launch's reduction (its scalars are then final).
@@ -328,6 +337,7 @@ __device__ __forceinline__ void k4_pv_body(const DevParams& P, const Fields& F, 
 template <int MinB>
 __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
     k4_pv(DevParams P, Fields F, int pp) {
+  pdl_wait_and_release();
   k4_pv_body(P, F, pp, hw_grid());
 }
 
@@ -384,6 +394,7 @@ __device__ __forceinline__ void k4_st_body(const DevParams& P, const Fields& F, 
 template <int MinB>
 __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
     k4_st(DevParams P, Fields F, int pp) {
+  pdl_wait_and_release();
   k4_st_body(P, F, pp, hw_grid());
 }
 
@@ -448,6 +459,7 @@ __device__ __forceinline__ bool k4_xr_body(const DevParams& P, const Fields& F, 
 template <int MinB>
 __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
     k4_xr(DevParams P, Fields F, int pp) {
+  pdl_wait_and_release();
   k4_xr_body(P, F, pp, hw_grid());
 }
 

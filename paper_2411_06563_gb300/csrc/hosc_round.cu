@@ -2,18 +2,20 @@
 // a round of G pseudo-time steps (Punia & Ray, arXiv:2411.06563, Sec. 2.2 solution procedure,
 // for many cavities of different sizes at once).
 //
-// The grid is cooperative (every block resident) and walks, phase after phase, a work list of
-// (member, tile) items: for each phase of a step, item q of the phase's list goes to block
-// q mod gridDim, whatever member it belongs to, so that small and large cavities share the SMs.
-// A phase's items run the same device bodies as the per-kernel launches (hosc_step_dev.cuh,
-// hosc_krylov4.cuh) with the member's parameters and arrays; each member's reductions finish in
-// its own last tile (a ticket counter per member, as in the per-kernel path). Phases are
-// separated by a grid barrier. The BiCGSTAB loop runs while any member still has an unconverged
-// system: the last tile of a member's initialisation and of each of its iterations raises the
-// continue flag of the next iteration, which every block reads after the barrier.
+// The grid is cooperative (every block resident). Each member advances through the phases of its
+// own steps (S1, S2, S3/S4, the Krylov initialisation, the p/v, s/t and x/r kernels of each
+// BiCGSTAB iteration, the update kernels, the record, the float copies); a phase's work is a list
+// of tiles (the 256-thread blocks of the per-kernel launches), appended to a queue shared by all
+// members when the member's previous phase completes, and any block takes the next tile of the
+// queue, whatever member it belongs to. The tiles run the same device bodies as the per-kernel
+// launches (hosc_step_dev.cuh, hosc_krylov4.cuh) with the member's parameters and arrays; each
+// member's reductions finish in its own last tile (its ticket counter, as in the per-kernel
+// path), and the block that finishes the last outstanding tile of a phase decides and queues the
+// member's next phase (the BiCGSTAB loop continues while one of its systems has not converged).
+// No block waits for a particular other block.
 //
-// Every wait is bounded: a block that waits at a barrier for longer than kBarrierNs gives up,
-// raises the round's error flag and returns; every other block returns at its next barrier. The
+// Every wait is bounded: a block that waits for a queue position longer than kBarrierNs gives up,
+// raises the round's error flag and returns, and so does every other block at its next wait. The
 // host reports HOSC_ECUDA for such a round.
 
 #include <cuda_runtime.h>
@@ -37,84 +39,10 @@ constexpr unsigned long long kBarrierNs = 5000000000ull;   // 5 s
 constexpr int kRoundThreads = 256;
 constexpr int kRoundMinBlocks = 2;   // resident blocks per SM the register budget is set for
 
-// Item counts per member of each phase class (blocks of 256 threads).
-enum { kNodes = 0, kInterior, kThetaWalls, kPressureWalls, kKrylov, kInit, kOne, kClasses };
-
-struct RoundDev {
-  const RoundMember* m;   // [count]
-  int count;
-  int G;
-  const int* off;         // [kClasses][count + 1]: prefix sums of the members' item counts
-  unsigned* bar;          // [2]: arrivals, generation
-  int* cont;              // [max_it + 2]: an unconverged system remains at iteration it
-  int max_it;
-  int* err;               // 1: a barrier wait gave up
-};
-
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
-}
-
-// Grid-wide barrier with a bounded wait. False when the round is being abandoned.
-__device__ bool grid_sync(const RoundDev& R) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned* gen = R.bar + 1;
-    volatile int* err = R.err;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(R.bar, 1u);
-    ok = 1;
-    if (arrived == gridDim.x - 1) {
-      R.bar[0] = 0u;
-      __threadfence();
-      atomicAdd(R.bar + 1, 1u);
-    } else {
-      const unsigned long long t0 = now_ns();
-      while (*gen == g) {
-        if (*err) {
-          ok = 0;
-          break;
-        }
-        if (now_ns() - t0 > kBarrierNs) {
-          atomicExch(R.err, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    if (*err) ok = 0;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-// Item q of a phase class -> (member, tile). Binary search in the prefix sums.
-__device__ __forceinline__ int member_of(const RoundDev& R, int cls, int q, int* tile) {
-  const int* o = R.off + cls * (R.count + 1);
-  int lo = 0, hi = R.count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (o[mid] <= q) lo = mid;
-    else hi = mid - 1;
-  }
-  *tile = q - o[lo];
-  return lo;
-}
-
-template <class Fn>
-__device__ __forceinline__ void for_items(const RoundDev& R, int cls, Fn&& fn) {
-  const int total = R.off[cls * (R.count + 1) + R.count];
-  for (int q = blockIdx.x; q < total; q += gridDim.x) {
-    int tile;
-    const int mb = member_of(R, cls, q, &tile);
-    fn(R.m[mb], tile);
-  }
 }
 
 __device__ __forceinline__ void shadow_item(const RoundMember& M, int lev, int tile) {
@@ -177,7 +105,8 @@ __device__ __noinline__ void sources_item(const RoundMember& M, int cur, int til
   const Fields& F = M.F;
   if (P.sweep_fp32)
     k_sources_body<float>(P, F.us[cur], F.vs[cur], F.ws[cur], F.ths, F.ps,
-                          reinterpret_cast<const float*>(F.eta), reinterpret_cast<float*>(F.Eu[cur]),
+                          reinterpret_cast<const float*>(F.eta),
+                          reinterpret_cast<float*>(F.Eu[cur]),
                           reinterpret_cast<float*>(F.Ev[cur]), reinterpret_cast<float*>(F.Ew[cur]),
                           F.halt, (unsigned)tile);
   else
@@ -205,75 +134,6 @@ __device__ __noinline__ void update_item(const RoundMember& M, int phase, int cu
     case 3: k_pressure_correct_body(M.P, M.F, (unsigned)tile); break;
     case 4: k_pressure_walls_body(M.P, M.F, (unsigned)tile); break;
     default: k_finish_record_body(M.P, M.F, (unsigned)tile); break;
-  }
-}
-
-// Raise the continue flag of iteration it when a member still has an unconverged system (called
-// in the block that finished the member's initialisation or iteration, whose thread 0 has just
-// written the final scalars).
-__device__ __forceinline__ void raise_continue(const RoundDev& R, const RoundMember& M, int it) {
-  if (threadIdx.x != 0) return;
-  const KrylovScalars* ks = M.F.ks;
-  if (!(ks[0].done && ks[1].done && ks[2].done && ks[3].done)) atomicExch(R.cont + it, 1);
-}
-
-__global__ void __launch_bounds__(kRoundThreads, kRoundMinBlocks) k_round(RoundDev R) {
-  // the round's start: every member runs, stops at its first steady step, no records yet
-  for (int q = blockIdx.x; q < R.count; q += gridDim.x) {
-    if (threadIdx.x == 0) {
-      const Fields& F = R.m[q].F;
-      *F.halt = 0;
-      *F.ring_pos = 0u;
-      *F.steady_stop = 1;
-    }
-  }
-  if (!grid_sync(R)) return;
-  // float copies of the round's first level for the FP32 sweeps
-  for_items(R, kNodes, [&](const RoundMember& M, int tile) {
-    if (M.P.sweep_fp32) shadow_item(M, M.cur, tile);
-  });
-  if (!grid_sync(R)) return;
-  for (int step = 0; step < R.G; ++step) {
-    const int flip = step & 1;
-    if (blockIdx.x == 0)
-      for (int q = threadIdx.x; q <= R.max_it + 1; q += blockDim.x) R.cont[q] = 0;
-    // S1 viscosity and L, S2 momentum sources, S3/S4 right-hand sides and compact operators
-    for_items(R, kNodes, [&](const RoundMember& M, int t) { visc_item(M, M.cur ^ flip, t); });
-    if (!grid_sync(R)) return;
-    for_items(R, kNodes, [&](const RoundMember& M, int t) { sources_item(M, M.cur ^ flip, t); });
-    if (!grid_sync(R)) return;
-    for_items(R, kInterior, [&](const RoundMember& M, int t) { rhs_item(M, M.cur ^ flip, t); });
-    if (!grid_sync(R)) return;
-    // S5: BiCGSTAB, all members' systems together
-    for_items(R, kInit, [&](const RoundMember& M, int t) {
-      if (init_item(M, t)) raise_continue(R, M, 0);
-    });
-    if (!grid_sync(R)) return;
-    for (int it = 0; it <= R.max_it; ++it) {
-      if (!*(volatile int*)(R.cont + it)) break;
-      const int pp = it & 1;
-      for_items(R, kKrylov, [&](const RoundMember& M, int t) { pv_item(M, pp, t); });
-      if (!grid_sync(R)) return;
-      for_items(R, kKrylov, [&](const RoundMember& M, int t) { st_item(M, pp, t); });
-      if (!grid_sync(R)) return;
-      for_items(R, kKrylov, [&](const RoundMember& M, int t) {
-        if (xr_item(M, pp, t)) raise_continue(R, M, it + 1);
-      });
-      if (!grid_sync(R)) return;
-    }
-    // S6-S8: increments, theta walls, divergence, pressure correction and walls, step record
-    const int cls[6] = {kNodes, kThetaWalls, kInterior, kInterior, kPressureWalls, kOne};
-    for (int ph = 0; ph < 6; ++ph) {
-      for_items(R, cls[ph], [&](const RoundMember& M, int t) {
-        update_item(M, ph, M.cur ^ flip, t);
-      });
-      if (!grid_sync(R)) return;
-    }
-    // float copies of the new level
-    for_items(R, kNodes, [&](const RoundMember& M, int t) {
-      shadow_item(M, 1 - (M.cur ^ flip), t);
-    });
-    if (!grid_sync(R)) return;
   }
 }
 
@@ -463,16 +323,7 @@ __global__ void __launch_bounds__(kRoundThreads, kRoundMinBlocks) k_flow(FlowDev
 struct RoundState {
   int device = -1;
   int capacity = 0;       // members the device arrays hold
-  int max_it = 0;
   RoundMember* d_m = nullptr;
-  int* d_off = nullptr;
-  unsigned* d_bar = nullptr;
-  int* d_cont = nullptr;
-  int* d_err = nullptr;
-  int grid = 0;
-  std::vector<RoundMember> h_m;
-  std::vector<int> h_off;
-  // the work-list form
   FlowMember* d_st = nullptr;
   int2* d_items = nullptr;
   unsigned* d_seq = nullptr;
@@ -487,26 +338,11 @@ RoundState* round_state_create() { return new RoundState(); }
 void round_state_destroy(RoundState* S) {
   if (!S) return;
   if (S->d_m) cudaFree(S->d_m);
-  if (S->d_off) cudaFree(S->d_off);
-  if (S->d_bar) cudaFree(S->d_bar);
-  if (S->d_cont) cudaFree(S->d_cont);
-  if (S->d_err) cudaFree(S->d_err);
   if (S->d_st) cudaFree(S->d_st);
   if (S->d_items) cudaFree(S->d_items);
   if (S->d_seq) cudaFree(S->d_seq);
   if (S->d_ctl) cudaFree(S->d_ctl);
   delete S;
-}
-
-// Item counts of one member per phase class.
-static void item_counts(const RoundMember& M, int out[kClasses]) {
-  out[kNodes] = M.nodes;
-  out[kInterior] = M.interior;
-  out[kThetaWalls] = M.theta_walls;
-  out[kPressureWalls] = M.pressure_walls;
-  out[kKrylov] = M.kx * M.ky;
-  out[kInit] = M.init;
-  out[kOne] = 1;
 }
 
 void round_member_shape(RoundMember* M) {
@@ -527,92 +363,6 @@ void round_member_shape(RoundMember* M) {
   M->kx = (int)((ni * ni + kRoundThreads - 1) / kRoundThreads);
   M->ky = (int)((ni + M->P.kz - 1) / M->P.kz);
 }
-
-hosc_status launch_round(RoundState* S, const std::vector<RoundMember>& members, int G,
-                         cudaStream_t stream, char* detail, size_t detail_len) {
-  const int count = (int)members.size();
-  if (count == 0) return HOSC_OK;
-  int max_it = 1;
-  for (const RoundMember& M : members) max_it = M.P.max_lin_iter > max_it ? M.P.max_lin_iter : max_it;
-  auto fail = [&](const char* what, cudaError_t e) {
-    snprintf(detail, detail_len, "round kernel: %s: %s", what, cudaGetErrorString(e));
-    cudaGetLastError();
-    return HOSC_ECUDA;
-  };
-  cudaError_t e = cudaSuccess;
-  int device = 0;
-  if ((e = cudaGetDevice(&device)) != cudaSuccess) return fail("device", e);
-  if (S->device != device || S->capacity < count || S->max_it < max_it) {
-    if (S->d_m) cudaFree(S->d_m);
-    if (S->d_off) cudaFree(S->d_off);
-    if (S->d_bar) cudaFree(S->d_bar);
-    if (S->d_cont) cudaFree(S->d_cont);
-    if (S->d_err) cudaFree(S->d_err);
-    S->d_m = nullptr;
-    S->d_off = nullptr;
-    S->d_bar = nullptr;
-    S->d_cont = nullptr;
-    S->d_err = nullptr;
-    const int cap = count < 16 ? 16 : count * 2;
-    if ((e = cudaMalloc(&S->d_m, cap * sizeof(RoundMember))) != cudaSuccess ||
-        (e = cudaMalloc(&S->d_off, kClasses * (cap + 1) * sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&S->d_bar, 2 * sizeof(unsigned))) != cudaSuccess ||
-        (e = cudaMalloc(&S->d_cont, (max_it + 2) * sizeof(int))) != cudaSuccess ||
-        (e = cudaMalloc(&S->d_err, sizeof(int))) != cudaSuccess) {
-      S->capacity = 0;
-      return fail("allocation", e);
-    }
-    S->capacity = cap;
-    S->max_it = max_it;
-    S->device = device;
-    int per_sm = 0, sms = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_round, kRoundThreads, 0)) !=
-            cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
-      return fail("occupancy", e);
-    if (per_sm < 1) return fail("occupancy", cudaErrorInvalidConfiguration);
-    S->grid = per_sm * sms;
-  }
-  S->h_off.assign(kClasses * (count + 1), 0);
-  for (int c = 0; c < count; ++c) {
-    int n[kClasses];
-    item_counts(members[c], n);
-    for (int k = 0; k < kClasses; ++k)
-      S->h_off[k * (count + 1) + c + 1] = S->h_off[k * (count + 1) + c] + n[k];
-  }
-  if ((e = cudaMemcpyAsync(S->d_m, members.data(), count * sizeof(RoundMember),
-                           cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(S->d_off, S->h_off.data(), S->h_off.size() * sizeof(int),
-                           cudaMemcpyHostToDevice, stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(S->d_bar, 0, 2 * sizeof(unsigned), stream)) != cudaSuccess ||
-      (e = cudaMemsetAsync(S->d_err, 0, sizeof(int), stream)) != cudaSuccess)
-    return fail("table", e);
-  RoundDev R;
-  R.m = S->d_m;
-  R.count = count;
-  R.G = G;
-  R.off = S->d_off;
-  R.bar = S->d_bar;
-  R.cont = S->d_cont;
-  R.max_it = max_it;
-  R.err = S->d_err;
-  void* args[] = {&R};
-  if ((e = cudaLaunchCooperativeKernel((const void*)k_round, dim3(S->grid), dim3(kRoundThreads),
-                                       args, 0, stream)) != cudaSuccess)
-    return fail("launch", e);
-  int err = 0;
-  if ((e = cudaMemcpyAsync(&err, S->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream)) !=
-          cudaSuccess ||
-      (e = cudaStreamSynchronize(stream)) != cudaSuccess)
-    return fail("run", e);
-  if (err) {
-    snprintf(detail, detail_len, "round kernel: a grid barrier wait gave up after %.0f s",
-             kBarrierNs * 1e-9);
-    return HOSC_ECUDA;
-  }
-  return HOSC_OK;
-}
-
 
 hosc_status launch_flow(RoundState* S, const std::vector<RoundMember>& members, int G,
                         cudaStream_t stream, char* detail, size_t detail_len) {

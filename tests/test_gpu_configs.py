@@ -174,7 +174,8 @@ def test_power_law_41_fp64_trajectory(n):
             for name, which in FIELDS:
                 assert _rel(cav.get(which), st[name]) <= 1e-10, name
             for s_, name in enumerate(("u", "v", "w", "th")):
-                assert abs(info["last_iters"][s_] - oinfo["iters"][name]) <= 2 + oinfo["iters"][name] // 10
+                it_o = oinfo["iters"][name]
+                assert abs(info["last_iters"][s_] - it_o) <= 2 + it_o // 10
 
 
 @pytest.mark.parametrize("n", [0.75, 1.25])
@@ -280,7 +281,10 @@ def test_newtonian_21_steady_state_fp64(c1_march):
     assert not (prev["res"] < stop and prev["div_max"] < p.tol_div)
     for name, _ in FIELDS:
         assert _rel(gpu[name], st[name]) <= 1e-10, name
-    assert abs(info["div_max"] - oinfo["div_max"]) <= 1e-8 * p.tol_div
+    # max|div V| is a difference of O(1) velocities over 2h: it agrees to rounding of that scale
+    h = 1.0 / (p.N - 1)
+    vmax = max(np.max(np.abs(st[k])) for k in ("u", "v", "w"))
+    assert abs(info["div_max"] - oinfo["div_max"]) <= 1e-12 * vmax / h
     od = O.diagnostics(st, _oracle_params(p))
     for k_gpu, k_ora in (("Nu_hot_max", "Nu_hot_max"), ("Nu_hot_mean", "Nu_hot_mean"),
                          ("Nu_cold_mean", "Nu_cold_mean"), ("E_total", "E_total"),

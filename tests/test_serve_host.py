@@ -1,5 +1,5 @@
-"""Host logic of the serving loop and the steady-solve parameter rule, on the CPU with a stand-in pool
-and a simulated clock (the native pool itself is exercised by tests/test_gpu_pool.py)."""
+"""Host logic of the serving loop and the steady-solve parameter rule, on the CPU with a stand-in
+pool and a simulated clock (the native pool itself is exercised by tests/test_gpu_pool.py)."""
 
 import math
 

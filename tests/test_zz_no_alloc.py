@@ -5,8 +5,9 @@ Callers that cannot call cudaMalloc (hosts whose allocator or memory pool alread
 memory, solvers held to a device-memory budget fixed at start-up) pass their own input and output
 arrays; the scratch of the solve lives in a fixed device array inside the library. Here the
 inputs are the right-hand sides and operator weights a context computed for one step, copied into
-caller-owned torch buffers, and the outputs must match the increments the context's solve produced (relative 1e-12, the FP64 parity tolerance of the solve is 1e-9), on two
-calls in a row with different grid sizes (the second call finds the first call's scratch).
+caller-owned torch buffers, and the outputs must match the increments the context's solve
+produced (relative 1e-12, the FP64 parity tolerance of the solve is 1e-9), on two calls in a row
+with different grid sizes (the second call finds the first call's scratch).
 """
 
 import numpy as np
