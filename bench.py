@@ -365,10 +365,14 @@ def run_equal(args):
     import numpy as np
     import torch
     from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
-    cavs = inputs.steady_mix(args.equal_cavities)
+    c4 = args.equal_mix == "c4"
+    cavs = (inputs.batch_mix()[:args.equal_cavities] if c4
+            else inputs.steady_mix(args.equal_cavities))
     fields = (("u", H.HOSC_U), ("v", H.HOSC_V), ("w", H.HOSC_W), ("th", H.HOSC_THETA))
 
     def params(c, precision):
+        if c4:   # the steady-solve rule, tol_steady = 1e-6
+            return S.request_params(c["N"], c["Ra"], c["n"], c["Pr"], precision=precision)
         p = S.request_params(c["N"], c["Ra"], c["n"], c["Pr"], precision=precision,
                              tol_steady=1e-6, tol_div=1e-6)
         p.dt = 0.02
@@ -383,6 +387,9 @@ def run_equal(args):
             info = cav.solve_steady(args.equal_max_steps)
             ref.append(dict(info=info, diag=cav.diagnostics(),
                             **{k: cav.get(w) for k, w in fields}))
+            print("fp64 %s: %d steps, %s, %.0f s" % (c, info["steps"], info["call_status"],
+                                                     time.perf_counter() - t0),
+                  file=sys.stderr, flush=True)
     t64 = time.perf_counter() - t0
     budget = sum(H.hosc_workspace_bytes(params(c, H.HOSC_MIXED)) for c in cavs) + (1 << 20)
     mode = {"graph": H.HOSC_POOL_GRAPH, "streams": H.HOSC_POOL_STREAMS,
@@ -406,9 +413,13 @@ def run_equal(args):
            "unit": "solves/s", "n_gpus": 1, "steps": len(cavs), "warmup": 0,
            "ms_per_step": 1e3 * tmx / len(cavs), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-           "config": {"workload": "%d cavities N in {17,21}, Ra log-uniform [1e2,1e3], n uniform "
-                                  "[0.9,1.1], Pr=1, dt=0.02, lambda=0.1, tol_steady=tol_div=1e-6, "
-                                  "seed 20241108" % len(cavs),
+           "config": {"workload": ("the first %d cavities of the 64-cavity mix (N in "
+                                   "{21,31,41,61}, Ra log-uniform [1e2,1e5], n uniform "
+                                   "[0.75,1.25], seed 20241106), steady-solve rule, "
+                                   "tol_steady=1e-6" % len(cavs)) if c4 else
+                                  ("%d cavities N in {17,21}, Ra log-uniform [1e2,1e3], n uniform "
+                                   "[0.9,1.1], Pr=1, dt=0.02, lambda=0.1, tol_steady=tol_div=1e-6, "
+                                   "seed 20241108" % len(cavs)),
                       "pool_mode": args.pool_mode, "steps_per_round": args.round_steps,
                       "captures": pst["captures"]},
            "fp64_one_at_a_time": {"solves_per_s": len(cavs) / t64, "seconds": t64,
@@ -446,16 +457,20 @@ def run_serve(args):
             p.dt = 0.02
             p.lambda_ = 0.1
             return p
-        return S.request_params(r["N"], r["Ra"], r["n"], r["Pr"], tol_steady=args.tol_steady,
-                                tol_div=1e-4)
+        # the steady-solve rule; tol_div follows tol_steady (half the step change a correction
+        # may cause)
+        return S.request_params(r["N"], r["Ra"], r["n"], r["Pr"], tol_steady=args.tol_steady)
 
     max_steps = max(args.max_steps, 20000) if steady_set else args.max_steps
-    base = inputs.request_stream(args.requests, rate=1.0, **kw)
+    # a prefix of the configured stream of 2000 requests (the parameters of request q do not
+    # depend on the rate, only its arrival time does)
+    total = max(args.requests, 2000)
+    base = inputs.request_stream(total, rate=1.0, **kw)[:args.requests]
     sat_reqs = [dict(r, t=0.0) for r in base[:args.saturation_requests]]
     with S.Pool(budget, args.round_steps, mode, True) as pool:
         _, sat = S.serve(sat_reqs, pool, make, max_steps)
     rate = args.rho * sat["solves_per_s"]
-    stream = inputs.request_stream(args.requests, rate=rate, **kw)
+    stream = inputs.request_stream(total, rate=rate, **kw)[:args.requests]
     with S.Pool(budget, args.round_steps, mode, True) as pool:
         res, summ = S.serve(stream, pool, make, max_steps)
         pst = pool.stats()
@@ -464,6 +479,8 @@ def run_serve(args):
            "ms_per_step": 1e3 / summ["solves_per_s"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
+           "seed_prefix": "the first %d requests of the seeded stream (arrival order)"
+                          % args.requests,
            "config": {"workload": ("Poisson stream of %d cavity solves, N in {17,21}, Ra "
                                    "log-uniform [1e2,1e3], n in {0.9,1,1.1}, Pr=1, dt=0.02, "
                                    "lambda=0.1, tol 1e-6, seed 20241107" if steady_set else
@@ -612,11 +629,13 @@ def main():
                          "serve: a Poisson request stream on a pool; equal: steady solves of "
                          "the pool against one-at-a-time FP64 at equal accuracy")
     ap.add_argument("--equal-cavities", type=int, default=8)
+    ap.add_argument("--equal-mix", default="c4", choices=["c4", "small"],
+                    help="equal mode: the head of the 64-cavity mix, or the small steady mix")
     ap.add_argument("--table1-sizes", default="11,51")
     ap.add_argument("--max-seconds", type=float, default=1e9,
                     help="steady mode: stop after this wall time (status: step limit)")
     ap.add_argument("--equal-max-steps", type=int, default=20000)
-    ap.add_argument("--pool-mode", default="persistent",
+    ap.add_argument("--pool-mode", default="graph",
                     choices=["graph", "streams", "persistent"])
     ap.add_argument("--round-steps", type=int, default=8)
     ap.add_argument("--baseline-cavities", type=int, default=16)
@@ -626,7 +645,7 @@ def main():
     ap.add_argument("--rho", type=float, default=0.8)
     ap.add_argument("--stream", default="config", choices=["config", "steady"])
     ap.add_argument("--max-steps", type=int, default=1000)
-    ap.add_argument("--tol-steady", type=float, default=1e-4)
+    ap.add_argument("--tol-steady", type=float, default=1e-6)
     ap.add_argument("--budget-gb", type=float, default=64.0)
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
