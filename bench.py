@@ -253,15 +253,21 @@ def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=N
     with H.Cavity(p) as cav:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        done, info = 0, None
+        done, info, switch, chunk = 0, None, None, 1000
         while done < max_steps:   # chunks, with progress on stderr
-            info = cav.solve_steady(min(5000, max_steps - done),
+            info = cav.solve_steady(min(chunk, max_steps - done),
                                     allow=(H.HOSC_ESTEPLIMIT, H.HOSC_ENOCONV, H.HOSC_EDIVERGED))
             done += info["steps"]
-            print("steady %d^3: %d steps, res/dt %.3e, div %.3e, phase %d, %.0f s" % (
-                N, done, info["res"] / p.dt, info["div_max"], H.hosc_get_phase(cav.h),
-                time.perf_counter() - t0), file=sys.stderr, flush=True)
-            if info["call_status"] != H.HOSC_ESTEPLIMIT or time.perf_counter() - t0 > max_seconds:
+            phase = H.hosc_get_phase(cav.h)
+            if phase == 1 and switch is None:
+                switch = done   # the automatic switch happened within this chunk
+            last = info["call_status"] != H.HOSC_ESTEPLIMIT or \
+                time.perf_counter() - t0 > max_seconds
+            if done % (5 * chunk) == 0 or last:
+                print("steady %d^3: %d steps, res/dt %.3e, div %.3e, phase %d, %.0f s" % (
+                    N, done, info["res"] / p.dt, info["div_max"], phase,
+                    time.perf_counter() - t0), file=sys.stderr, flush=True)
+            if last:
                 break
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
@@ -277,7 +283,10 @@ def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=N
             "GPUPS": (N - 2) ** 3 * info["steps"] / el if el > 0 else None,
             "bicgstab_iters_per_step": info["lin_iters"] / (4.0 * max(1, info["steps"])),
             "res_over_dt": info["res"] / p.dt, "div_max": info["div_max"],
+            "stop": {"tol_steady": p.tol_steady, "div_steady": p.div_steady,
+                     "tol_div_correction": p.tol_div},
             "final_phase": "FP64 defect sweeps" if phase == 1 else "FP32 sweeps",
+            "defect_switch_by_step": switch,
             "Nu_mean": d["Nu_hot_mean"], "Nu_max": d["Nu_hot_max"],
             "Nu_cold_mean": d["Nu_cold_mean"], "E_total": d["E_total"], "E_HT": d["E_HT"],
             "E_FF": d["E_FF"], "Be": d["Be"], "Nu_avg_z_local_maxima": peaks,

@@ -102,8 +102,9 @@ typedef struct {
   double theta_init;  /* initial interior temperature (fluid at rest, constant pressure) */
   double I2_eps;      /* regulariser: eta = (I2 + I2_eps)^((n-1)/2); unused when n == 1 */
   double phi;         /* irreversibility distribution ratio of E_FF (Sec. 4.3), 1e-4 */
-  double tol_steady;  /* hosc_solve_steady stops when max|chi^{n+1}-chi^n| / dt < tol_steady ... */
-  double tol_div;     /* ... and max|div V| < tol_div; the pressure is corrected when above it */
+  double tol_steady;  /* hosc_solve_steady stops when max|chi^{n+1}-chi^n| / dt < tol_steady and
+                         max|div V| < div_steady (below) */
+  double tol_div;     /* the pressure is corrected while max|div V| > tol_div (Sec. 2.2) */
   double tol_lin;     /* BiCGSTAB stops when ||r_k||_2 <= tol_lin ||r_0||_2 */
   int max_lin_iter;   /* BiCGSTAB iteration limit per system and step, >= 1 */
   int precision;      /* hosc_precision */
@@ -118,8 +119,10 @@ typedef struct {
                          first-order pseudo-time march with the same steady state */
   int auto_defect;    /* HOSC_MIXED: 1 switches from FP32 to FP64 defect sweeps by itself when the
                          step change stalls: 200 steps without a 5 % improvement once it is below
-                         1e-3 of the largest step change of the solve, or 2000 steps at any level;
-                         0 keeps the phase chosen with hosc_set_phase */
+                         1e-3 of the largest step change of the solve, or 2000 steps at any level
+                         (counted from the largest step change so far, so a spin-up whose step
+                         change still grows is no stall); 0 keeps the phase chosen with
+                         hosc_set_phase */
   int precond;        /* 0: BiCGSTAB on the systems as assembled (the paper's unpreconditioned
                          solver, the default); 1: Jacobi row scaling, each row of the level-(n+1)
                          system and its right-hand side divided by the row's diagonal before the
@@ -150,6 +153,9 @@ typedef struct {
                          node's apparent viscosity at level n: the relaxation follows the local
                          viscous time scale of the pressure modes (a steady-solve accelerator, not
                          in the paper; the fixed point div V = 0 is the same). */
+  double div_steady;  /* the steady stop's divergence test: max|div V| < div_steady; 0 (the
+                         default) means tol_div, the paper's single threshold. hosc_steady_params
+                         sets it to tol_steady and tol_div, the correction's threshold, far below */
 } hosc_params;
 
 typedef struct {
@@ -181,7 +187,7 @@ typedef struct {
 /* Fill *p with defaults for grid N and (Ra, Pr, n): dt = 0.02, lambda = min(h^2/(4 dt), Pr/10),
  * theta_ref = theta_init = 0.5, I2_eps = 1e-10, phi = 1e-4, tol_steady = 1e-6, tol_div = 1e-6,
  * tol_lin = 1e-10, max_lin_iter = 1000, HOSC_FP64, own stream, a_limit = 0.25, a_boost = 1,
- * use_history = 1, auto_defect = 1. After changing
+ * use_history = 1, auto_defect = 1, div_steady = 0 (the stop tests tol_div). After changing
  * dt, set lambda again (it must stay below h^2/dt). */
 hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, double n);
 
@@ -196,8 +202,10 @@ hosc_status hosc_default_params(hosc_params* p, int N, double Ra, double Pr, dou
  * contract by a fixed fraction of lambda per step; lambda dt must stay below h^2. The rule uses
  * the cube's spacing: for a box (Ly, Lz) set dt and lambda again. tol_div = tol_steady h /
  * (2 lambda): while the pressure correction runs, the step change it causes (about lambda
- * tol_div / h per unit pseudo-time) stays below tol_steady (if tol_steady is changed, set tol_div
- * again). HOSC_EINVAL for N < 5, Ra < 0, Pr <= 0 or n <= 0. */
+ * tol_div / h per unit pseudo-time) stays below tol_steady, so the correction is never switched
+ * off and on around its threshold near the steady state. The stop's divergence test is kept at
+ * the steady criterion itself: div_steady = tol_steady (if tol_steady is changed, set tol_div and
+ * div_steady again). HOSC_EINVAL for N < 5, Ra < 0, Pr <= 0 or n <= 0. */
 hosc_status hosc_steady_params(hosc_params* p, int N, double Ra, double Pr, double n);
 
 /* Bytes of device workspace a context with these parameters needs (0 if invalid). */
@@ -222,7 +230,8 @@ hosc_status hosc_reset(void* ctx);
  * Stops early at the first step whose status is not HOSC_OK and returns that status. */
 hosc_status hosc_step(void* ctx, int nsteps, hosc_info* out);
 
-/* Step until max|chi^{n+1}-chi^n| / dt < tol_steady and max|div V| < tol_div (HOSC_OK), or
+/* Step until max|chi^{n+1}-chi^n| / dt < tol_steady and max|div V| < div_steady (tol_div when
+ * div_steady is 0) (HOSC_OK), or
  * max_steps (HOSC_ESTEPLIMIT), or a numerical failure. */
 hosc_status hosc_solve_steady(void* ctx, long max_steps, hosc_info* out);
 
@@ -293,6 +302,21 @@ hosc_status hosc_get_tiles(void* ctx, int* kblock, int* kz, int* narrow);
 hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz);
 hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz);
 
+/* Bulk-copy (TMA) stencil kernels of the mixed-precision solve: the p/v and s/t kernels with
+ * their reads moved by the GPU's bulk-copy engine (tensor-map box copies of each z-plane into a
+ * ring of three shared-memory stages, one producer thread, mbarrier completion), so that the
+ * bytes in flight do not depend on registers or resident warps. A block owns tty rows of the
+ * plane's interior columns (whole rows up to 252 columns; wider planes are cut into equal
+ * pieces) and tkz consecutive planes (1..N-2). tty == 0 selects the register kernels (the
+ * default); setting tiles here clears hosc_set_stencil_tiles and the reverse. HOSC_EINVAL for a
+ * shape that does not fit (at most 512 threads and 200 KB of shared memory per block, too many
+ * blocks), HOSC_ECUDA when the driver cannot encode the tensor maps, HOSC_ESTATE mid-step.
+ * Three-kernel iteration form only (the merged form keeps its own kernels). Changing it drops
+ * the captured steps. A wait of these kernels that runs out (2 s) ends the step with HOSC_ECUDA
+ * instead of hanging. */
+hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz);
+hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz);
+
 /* Form of the mixed-precision BiCGSTAB iteration: merged = 1 runs two kernels per iteration,
  * folding the x, r update of iteration i-1 into the p, v kernel of iteration i and obtaining
  * r_0.r_{i+1} for beta from r_0.s and r_0.t of the s, t kernel (the same method; the
@@ -312,8 +336,9 @@ int hosc_get_krylov_merged(void* ctx);
  * iteration form (hosc_set_krylov_merged)
  * at that shape and keep the faster; with the three-kernel form, then time the
  * staged p/v and s/t kernels (hosc_set_stencil_tiles) for tiles sx in {8, 16, ..., 64},
- * sy in {4, 8} and skz in 1..33 within 1.5x of their least modelled cost, and keep them when
- * they beat the register kernels. Reports the register shape (any output pointer may be NULL;
+ * sy in {4, 8} and skz in 1..33 within 1.5x of their least modelled cost, and the bulk-copy
+ * kernels (hosc_set_tma_tiles) for tty in 1..8 and tkz in 1..33 within 1.5x of theirs, and keep
+ * the fastest of the three kinds for p/v and s/t. Reports the register shape (any output pointer may be NULL;
  * ms_out = the three kernels' summed mean milliseconds with the chosen kernels). Mixed precision
  * only (HOSC_EINVAL for FP64). The fields keep their values. */
 hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, double* ms_out);

@@ -73,6 +73,8 @@ struct Ctx {
   int merged = 0;                          // two-kernel BiCGSTAB iteration (mixed precision)
   int inner_last = 0;                      // inner pressure passes of the last step
   int sx = 0, sy = 0, skz = 0;             // staged stencil kernels (sx == 0: not used)
+  int tty = 0, tkz = 0;                    // bulk-copy stencil kernels (tty == 0: not used)
+  alignas(64) unsigned char tmap_host[kTmaMaps * kTmaMapBytes];   // their tensor maps
   // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
   // asynchronously into h_ring / h_ring_pos, completion marked by round_ev
   int round_cur0 = 0, round_prev0 = 0;
@@ -90,6 +92,7 @@ hosc_status validate(const hosc_params* p) {
   if (!(p->lambda > 0.0) || !(p->tol_lin > 0.0) || p->max_lin_iter < 1) return HOSC_EINVAL;
   if (!(p->I2_eps >= 0.0) || (p->n != 1.0 && p->n < 1.0 && !(p->I2_eps > 0.0))) return HOSC_EINVAL;
   if (!(p->phi >= 0.0) || !(p->tol_div >= 0.0) || !(p->tol_steady >= 0.0)) return HOSC_EINVAL;
+  if (!(p->div_steady >= 0.0)) return HOSC_EINVAL;
   if (!isfinite(p->theta_ref) || !isfinite(p->theta_init)) return HOSC_EINVAL;
   if (!(p->a_limit >= 0.0) || !(p->a_limit < 1.0)) return HOSC_EINVAL;
   if (!(p->a_boost >= 0.0) || !isfinite(p->a_boost)) return HOSC_EINVAL;
@@ -114,12 +117,14 @@ double kernel_bytes(const DevParams& P, int kid) {
   switch (kid) {
     case HOSC_K_VISC: return n3 * 5 * sb;                        // u, v, w -> eta, L
     case HOSC_K_SOURCES: return n3 * 9 * sb;                     // u, v, w, th, p, eta -> E* x3
-    case HOSC_K_RHS:   // L, u, v, w, theta, E* x3 (+ 7 history arrays) -> rhs x4, 14 weights
-      return ni3 * ((8 + (P.have_prev ? 7 : 0)) * sb + (f4 ? 16.0 * (1 + 4) : 8.0 * 18));
+    // The interleaved operators are stored compact: kwm and kwe (float4) and kL (float), 2.25
+    // float4 words per interior node; the planar FP64 operators are 14 weights.
+    case HOSC_K_RHS:   // L, u, v, w, theta, E* x3 (+ 7 history arrays) -> rhs x4, operators
+      return ni3 * ((8 + (P.have_prev ? 7 : 0)) * sb + (f4 ? 16.0 * (1 + 2.25) : 8.0 * 18));
     case HOSC_K_BICG_PV:   // merged form: the x, r update folded in
-      return ni3 * (f4 ? 16.0 * ((P.merged ? 10 : 6) + 4) : 8.0 * (4 * 6 + 14));
+      return ni3 * (f4 ? 16.0 * ((P.merged ? 10 : 6) + 2.25) : 8.0 * (4 * 6 + 14));
     case HOSC_K_BICG_ST:
-      return ni3 * (f4 ? 16.0 * ((P.merged ? 4 : 3) + 4) : 8.0 * (4 * 3 + 14));
+      return ni3 * (f4 ? 16.0 * ((P.merged ? 4 : 3) + 2.25) : 8.0 * (4 * 3 + 14));
     case HOSC_K_BICG_XR: return ni3 * (f4 ? (P.merged ? 0.0 : 16.0 * 8) : 8.0 * 4 * 8);
     default: return 0.0;
   }
@@ -133,6 +138,9 @@ void apply_tiles(Ctx* c) {
   c->P.sx = c->sx;
   c->P.sy = c->sy;
   c->P.skz = c->skz;
+  c->P.tty = c->tty;
+  c->P.ttx = tma_tile_x(c->prm.N);
+  c->P.tkz = c->tkz;
 }
 
 bool stencil_tiles_valid(const Ctx* c, int sx, int sy, int skz) {
@@ -167,7 +175,9 @@ constexpr double kFp32TolFloor = 3e-6;
 // Mixed precision switches from FP32 to FP64 defect sweeps when the step change has stalled: no
 // 5 % improvement in kStallSteps steps once it is below kStallDrop times the largest step change
 // of the solve (the FP32 noise floor lies far below the start-up transient, whose own plateaus
-// must not trigger the switch), or in kStallLong steps whatever its level.
+// must not trigger the switch), or in kStallLong steps whatever its level. Steps counted from the
+// largest step change so far: a march from rest first grows its step change while the flow
+// spins up, which is no stall.
 constexpr long kStallSteps = 200;
 constexpr long kStallLong = 2000;
 constexpr double kStallDrop = 1e-3;
@@ -213,6 +223,8 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
   d.eta_exp = 0.5 * (p.n - 1.0);
   d.dtf = (float)p.dt;
   d.Prf = (float)p.Pr;
+  d.iPr = 1.0 / p.Pr;
+  d.iPrf = (float)d.iPr;
   d.Raf = (float)p.Ra;
   d.theta_reff = (float)p.theta_ref;
   d.I2_epsf = (float)p.I2_eps;
@@ -239,6 +251,7 @@ DevParams device_params(const hosc_params& p, int have_prev, int phase) {
     d.lambda_cap = 0.9 * hmin * hmin / p.dt;
   }
   d.steady_res = p.tol_steady * p.dt;
+  d.div_steady = p.div_steady > 0.0 ? p.div_steady : p.tol_div;
   return d;
 }
 
@@ -609,7 +622,12 @@ void set_phase(Ctx* c, int phase) {
 
 void watch_stall(Ctx* c, double res) {
   if (c->prm.precision != HOSC_MIXED || c->phase != 0 || !c->prm.auto_defect) return;
-  if (!(res <= c->peak_res)) c->peak_res = res;
+  if (!(res <= c->peak_res)) {   // still spinning up: the watch starts again from the new peak
+    c->peak_res = res;
+    c->best_res = res;
+    c->since_best = 0;
+    return;
+  }
   if (res < 0.95 * c->best_res) {
     c->best_res = res;
     c->since_best = 0;
@@ -770,7 +788,7 @@ hosc_status fold_records(Ctx* c, unsigned n, hosc_info* info, bool* steady) {
       st = (hosc_status)r.status;
       break;
     }
-    if (steady && r.res < c->P.steady_res && r.div_max < c->P.tol_div) *steady = true;
+    if (steady && r.res < c->P.steady_res && r.div_max < c->P.div_steady) *steady = true;
     watch_stall(c, r.res);
   }
   return st;
@@ -865,6 +883,7 @@ hosc_status make_ctx(const hosc_params* p, void* dev_ws, size_t bytes, void** ou
     }
     c->ws_bytes = need;
     workspace_layout(p->N, p->solver == 1, &c->F, c->ws);
+    c->F.tmaps_host = c->tmap_host;
     if (p->cuda_stream) {
       c->stream = (cudaStream_t)p->cuda_stream;
     } else {
@@ -910,9 +929,11 @@ cudaStream_t ctx_branch_stream(void* ctx) { return ((Ctx*)ctx)->cap[0]; }
 // What a captured round assumes about the context: level parity, history, phase, launch shape.
 long ctx_signature(void* ctx) {
   const Ctx* c = (const Ctx*)ctx;
-  return (long)c->cur | ((long)c->P.have_prev << 1) | ((long)c->phase << 2) |
-         ((long)c->kblock << 3) | ((long)c->kz << 13) | ((long)c->narrow << 23) | ((long)c->sx << 24) |
-         ((long)c->sy << 32) | ((long)c->skz << 42) | ((long)c->merged << 52);
+  const long s = (long)c->cur | ((long)c->P.have_prev << 1) | ((long)c->phase << 2) |
+                 ((long)c->kblock << 3) | ((long)c->kz << 13) | ((long)c->narrow << 23) |
+                 ((long)c->sx << 24) | ((long)c->sy << 32) | ((long)c->skz << 42) |
+                 ((long)c->merged << 52);
+  return s ^ ((long)c->tty << 53) ^ ((long)c->tkz << 56);
 }
 
 // Start of a round of n steps from the current level (read back by ctx_collect_round).
@@ -1107,6 +1128,7 @@ size_t workspace_layout(int N, int bicgstab2, Fields* f, char* base) {
   F.steady_stop = (int*)take(sizeof(int));
   F.ring = (StepRecord*)take(kRing * sizeof(StepRecord));
   F.ring_pos = (unsigned int*)take(sizeof(unsigned int));
+  F.tmaps_host = nullptr;
   const size_t ff = n3 * sizeof(float);
   for (int b = 0; b < 2; ++b) {
     F.us[b] = (float*)take(ff);
@@ -1184,6 +1206,8 @@ hosc_status hosc_steady_params(hosc_params* p, int N, double Ra, double Pr, doub
   // tol_div is set so that this is half of tol_steady (else the correction, switched on and off
   // around tol_div, holds the step change above tol_steady on fine grids).
   p->tol_div = 0.5 * p->tol_steady * h / p->lambda;
+  // the stop itself tests the divergence at the steady criterion
+  p->div_steady = p->tol_steady;
   return HOSC_OK;
 }
 
@@ -1270,7 +1294,7 @@ hosc_status hosc_solve_steady(void* ctx, long max_steps, hosc_info* out) {
       st = q;
       break;
     }
-    if (info.res_steady < c->prm.tol_steady * c->prm.dt && info.div_max < c->prm.tol_div) {
+    if (info.res_steady < c->P.steady_res && info.div_max < c->P.div_steady) {
       st = HOSC_OK;
       break;
     }
@@ -1550,13 +1574,53 @@ hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
   CU(cudaSetDevice(c->device));
   if (!stencil_tiles_valid(c, sx, sy, skz)) return HOSC_EINVAL;
   if (sx == 0) sy = skz = 0;
-  if (sx != c->sx || sy != c->sy || skz != c->skz) {
+  if (sx != c->sx || sy != c->sy || skz != c->skz || (sx > 0 && c->tty > 0)) {
     c->sx = sx;
     c->sy = sy;
     c->skz = skz;
+    if (sx > 0) c->tty = c->tkz = 0;   // one kind of stencil kernel at a time
     apply_tiles(c);
     drop_graphs(c);
   }
+  return HOSC_OK;
+}
+
+hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  CU(cudaSetDevice(c->device));
+  if (tty == 0) {
+    tkz = 0;
+  } else {
+    if (!tma_tiles_valid(c->prm.N, tty, tkz)) return HOSC_EINVAL;
+    DevParams P = c->P;
+    P.tty = tty;
+    P.ttx = tma_tile_x(c->prm.N);
+    P.tkz = tkz;
+    if (krylov4_blocks(P) * (P.merged ? 2 : 1) > red_rows((long)c->prm.N * c->prm.N * c->prm.N))
+      return HOSC_EINVAL;
+    if (!tma_prepare(P, c->F, c->tmap_host)) {
+      snprintf(g_detail, sizeof(g_detail),
+               "tensor maps of the bulk-copy stencil kernels could not be encoded");
+      return HOSC_ECUDA;
+    }
+  }
+  if (tty != c->tty || tkz != c->tkz || (tty > 0 && c->sx > 0)) {
+    c->tty = tty;
+    c->tkz = tkz;
+    if (tty > 0) c->sx = c->sy = c->skz = 0;
+    apply_tiles(c);
+    drop_graphs(c);
+  }
+  return HOSC_OK;
+}
+
+hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) return HOSC_EINVAL;
+  if (tty) *tty = c->tty;
+  if (tkz) *tkz = c->tkz;
   return HOSC_OK;
 }
 
@@ -1607,7 +1671,11 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   if (c->stage != 0) return HOSC_ESTATE;
   if (!c->P.krylov_fp32) return HOSC_EINVAL;
   CU(cudaSetDevice(c->device));
-  c->P.sx = 0;   // the register kernels first
+  {   // the register kernels first
+    hosc_status s0 = hosc_set_stencil_tiles(c, 0, 0, 0);
+    if (!s0) s0 = hosc_set_tma_tiles(c, 0, 0);
+    if (s0) return s0;
+  }
   int best_b = c->kblock, best_z = c->kz, best_n = c->narrow;
   double best = INFINITY;
   static const int blocks[] = {64, 96, 128, 160, 192, 256, 320, 384};
@@ -1693,6 +1761,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   }
   if (c->merged) {   // the staged kernels implement the three-kernel form only
     st = hosc_set_stencil_tiles(c, 0, 0, 0);
+    if (!st) st = hosc_set_tma_tiles(c, 0, 0);
     if (st) return st;
     if (kblock_out) *kblock_out = best_b;
     if (kz_out) *kz_out = best_z;
@@ -1753,7 +1822,51 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   c->P.sy = ssy;
   c->P.skz = sskz;
   if (st) return st;
-  if (best_staged < reg_pvst) {
+  // Bulk-copy (TMA) stencil kernels: tiles of whole interior rows (tty rows) and tkz planes
+  // within 1.5x of their least modelled cost.
+  double best_tma = INFINITY;
+  int bty = 0, btkz = 0;
+  {
+    const int N = c->prm.N;
+    const long rows = red_rows((long)N * N * N);
+    double best_tmodel = 1e300;
+    for (int ty = 1; ty <= 8; ++ty)
+      for (int z = 1; z <= 33; ++z) best_tmodel = fmin(best_tmodel, tma_wave_cost(N, ty, z, sms));
+    const DevParams saved = c->P;
+    for (int ty = 1; ty <= 8 && !st && best_tmodel < 1e299; ++ty) {
+      for (int z = 1; z <= 33 && !st; ++z) {
+        if (tma_wave_cost(N, ty, z, sms) > 1.5 * best_tmodel) continue;
+        DevParams trial = saved;
+        trial.sx = 0;
+        trial.tty = ty;
+        trial.ttx = tma_tile_x(N);
+        trial.tkz = z;
+        if (krylov4_blocks(trial) > rows) continue;
+        if (!tma_prepare(trial, c->F, c->tmap_host)) {
+          best_tmodel = 1e300;   // no tensor maps on this driver: keep the other kernels
+          break;
+        }
+        c->P = trial;
+        double tot = 0.0;
+        for (int kid = HOSC_K_BICG_PV; kid <= HOSC_K_BICG_ST && !st; ++kid) {
+          double ms = 0.0;
+          st = time_class(c, kid, reps, &ms);
+          tot += ms;
+        }
+        if (!st && tot < best_tma) {
+          best_tma = tot;
+          bty = ty;
+          btkz = z;
+        }
+      }
+    }
+    c->P = saved;
+  }
+  if (st) return st;
+  if (best_tma < reg_pvst && best_tma < best_staged) {
+    st = hosc_set_tma_tiles(c, bty, btkz);
+    best += best_tma - reg_pvst;
+  } else if (best_staged < reg_pvst) {
     st = hosc_set_stencil_tiles(c, bsx, bsy, bskz);
     best += best_staged - reg_pvst;
   } else {

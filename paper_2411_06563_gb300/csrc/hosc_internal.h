@@ -31,6 +31,8 @@ struct DevParams {
                      // folded into the next p, v kernel) instead of three
   int sx, sy, skz;   // staged stencil kernels (p/v and s/t): tile of sx * sy interior columns,
                      // skz planes per block; sx == 0 selects the register kernels instead
+  int tty, ttx, tkz; // bulk-copy (TMA) stencil kernels (p/v and s/t): tile of ttx * tty interior
+                     // columns, tkz planes per block; tty == 0: not used
   double h, h2;      // grid spacing along x and its square
   double Ly, Lz;     // box 1 x Ly x Lz: lengths along y and z (1 for the cube)
   // Spacing constants of the directions d = x, y, z (spacings h, k, l = h, Ly h, Lz h), in double
@@ -47,14 +49,16 @@ struct DevParams {
   double eta_exp;    // (n - 1)/2, the exponent of the regularised viscosity
   // float copies of the scalars the float sweeps use (converted once on the host)
   float dtf, Prf, Raf, theta_reff, I2_epsf, eta_expf, a_limitf, a_boostf;
+  double iPr;          // 1/Pr, and its float copy
+  float iPrf;
   double Ra, Pr, n, dt, lambda, theta_ref, I2_eps, phi, tol_div, tol_lin, a_limit, a_boost;
   int precond;         // Jacobi row scaling of the level-(n+1) systems
   int solver;          // 0: BiCGSTAB; 1: BiCGSTAB(2) (planar FP64 solve)
   int inner_pass;      // an inner pressure pass: momentum only (theta kept, its system skipped)
   int lambda_mode;     // 0: p -= lambda div V; 1: p -= min(lambda eta, lambda_cap) div V
   double lambda_cap;   // 0.9 h_min^2 / dt
-  double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (and div below tol_div)
-                       // is steady (tol_steady * dt)
+  double steady_res;   // a step with max|chi^{n+1} - chi^n| below this (tol_steady * dt) and
+  double div_steady;   // max|div V| below this (div_steady, else tol_div) is steady
 };
 
 constexpr int kRing = 256;   // step records kept on the device between host reads
@@ -142,6 +146,10 @@ struct Fields {
   float* ws[2];
   float* ths;
   float* ps;
+  // host address of the tensor maps of the bulk-copy stencil kernels (kTmaMaps CUtensorMap
+  // objects encoded for the context's arrays and tile shape; the launches pass them to the
+  // kernels as parameters)
+  const void* tmaps_host;
 };
 
 // Bytes of a context's device workspace (the BiCGSTAB(2) vectors included when bicgstab2);
@@ -164,6 +172,22 @@ double krylov4_wave_cost(int N, int kblock, int kz, int narrow, int merged, int 
 double staged_wave_cost(int N, int sx, int sy, int skz, int sms);
 // Dynamic shared memory of a staged launch (bytes), for tile sx * sy.
 size_t staged_smem_bytes(int sx, int sy, bool pv);
+
+// Bulk-copy (TMA) stencil kernels (hosc_tma.cu). The interior columns of a plane are cut into
+// tiles of ttx * tty (ttx from N: whole interior rows up to 252 columns, else the least even
+// split), a block streams the tile through tkz planes.
+constexpr int kTmaMaps = 8;        // kr, kr0, kp[0], kp[1], kv[0], kv[1], kwm, kwe
+constexpr int kTmaMapBytes = 128;  // sizeof(CUtensorMap)
+int tma_tile_x(int N);
+// False when the shape does not launch (shared memory, threads, block count).
+bool tma_tiles_valid(int N, int tty, int tkz);
+// Encode the tensor maps of P's tile shape for F's arrays into host (kTmaMaps * 128 bytes,
+// 64-byte aligned); false when the driver cannot encode them.
+bool tma_prepare(const DevParams& P, const Fields& F, void* host);
+double tma_wave_cost(int N, int tty, int tkz, int sms);
+void launch_tma_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
+void launch_tma_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
+long tma_blocks(const DevParams& P);
 int device_sms();
 
 // S1: eta and L at every node.

@@ -1130,6 +1130,10 @@ void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
     else k6_a<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
     return;
   }
+  if (P.krylov_fp32 && P.tty > 0) {
+    launch_tma_pv(P, F, pp, s);
+    return;
+  }
   if (P.krylov_fp32 && P.sx > 0) {
     k5_pv<<<grid5(P), P.sx * P.sy, staged_smem_bytes(P.sx, P.sy, true), s>>>(P, F, pp);
     return;
@@ -1147,6 +1151,10 @@ void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
   if (P.krylov_fp32 && P.merged) {
     if (P.narrow) k6_b<4><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
     else k6_b<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
+    return;
+  }
+  if (P.krylov_fp32 && P.tty > 0) {
+    launch_tma_st(P, F, pp, s);
     return;
   }
   if (P.krylov_fp32 && P.sx > 0) {
@@ -1192,7 +1200,8 @@ long krylov4_blocks(const DevParams& P) {
     const long n5 = (long)g5.x * g5.y * g5.z;
     nb = n5 > nb ? n5 : nb;
   }
-  return nb;
+  const long n7 = tma_blocks(P);
+  return n7 > nb ? n7 : nb;
 }
 
 size_t staged_smem_bytes(int sx, int sy, bool pv) {

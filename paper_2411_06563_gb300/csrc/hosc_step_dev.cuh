@@ -189,7 +189,8 @@ __device__ __forceinline__ void k_sources_body(const DevParams& P, const T* HOSC
   const T pz = grad_axis_t<T>(p, t, k, N, sz, sp.i2[2]);
   const T e = eta[t];
   const T exy = T(0.5) * (g.uy + g.vx), exz = T(0.5) * (g.uz + g.wx), eyz = T(0.5) * (g.vz + g.wy);
-  const T a = T(1) / (par<T>(P.Pr, P.Prf) * e), b = T(2) / e;
+  const T ie = T(1) / e;   // one division per node
+  const T a = ie * par<T>(P.iPr, P.iPrf), b = T(2) * ie;
   Eu[t] = -px * a + b * (g.ux * ex + exy * ey + exz * ez);
   Ev[t] = -py * a + b * (exy * ex + g.vy * ey + eyz * ez) +
           par<T>(P.Ra, P.Raf) * ((T)th[t] - par<T>(P.theta_ref, P.theta_reff)) / e;
@@ -401,7 +402,8 @@ __device__ __forceinline__ void k_rhs_body(const DevParams& P, const Tc* HOSC_RE
     rv[2] = system(Ew, Ewp, w);
     // level-(n+1) weights (Eq. 6): M_d = -dt/(2L) + h_d^2/12, M15 = (h^2/(6L)) dx L, ...
     const D7<Tc> dL = diffs7<Tc>(L7, sp);
-    const Tc m0 = -tdt / (Tc(2) * Lc), inv6L = Tc(2) / Lc;   // h_d^2/(6L) = (h_d^2/12) (2/L)
+    const Tc iL = Tc(1) / Lc;   // one division per node
+    const Tc m0 = Tc(-0.5) * tdt * iL, inv6L = Tc(2) * iL;   // h_d^2/(6L) = (h_d^2/12) (2/L)
     const Tc Mx = m0 + sp.s12[0], My = m0 + sp.s12[1], Mz = m0 + sp.s12[2];
     const Tc m15 = sp.s12[0] * inv6L * dL.dx, m16 = sp.s12[1] * inv6L * dL.dy,
              m17 = sp.s12[2] * inv6L * dL.dz;
@@ -741,7 +743,9 @@ __device__ __forceinline__ void k_finish_record_body(const DevParams& P, const F
   for (int s = 0; s < 4; ++s) {
     r->iters[s] = F.ks[s].iters;
     r->lin_status[s] = F.ks[s].status;
-    if (F.ks[s].status != 0) st = HOSC_ENOCONV;
+    // HOSC_ECUDA: a bounded wait inside a Krylov kernel ran out; anything else: no convergence
+    if (F.ks[s].status == HOSC_ECUDA) st = HOSC_ECUDA;
+    else if (F.ks[s].status != 0 && st != HOSC_ECUDA) st = HOSC_ENOCONV;
     const double q = F.ks[s].r0norm > 0.0 ? F.ks[s].rnorm / F.ks[s].r0norm : 0.0;
     lres = fmax(lres, isfinite(q) ? q : INFINITY);
   }
@@ -752,7 +756,7 @@ __device__ __forceinline__ void k_finish_record_body(const DevParams& P, const F
   F.ring[pos % kRing] = *r;
   *F.ring_pos = pos + 1;
   if (st != HOSC_OK) *F.halt = 1;
-  else if (*F.steady_stop && r->res < P.steady_res && r->div_max < P.tol_div) *F.halt = 2;
+  else if (*F.steady_stop && r->res < P.steady_res && r->div_max < P.div_steady) *F.halt = 2;
 }
 
 __global__ void k_finish_record(DevParams P, Fields F) {

@@ -44,7 +44,7 @@ class hosc_params(ctypes.Structure):
                 ("use_history", ctypes.c_int), ("auto_defect", ctypes.c_int),
                 ("precond", ctypes.c_int), ("inner_max", ctypes.c_int),
                 ("Ly", ctypes.c_double), ("Lz", ctypes.c_double), ("solver", ctypes.c_int),
-                ("lambda_mode", ctypes.c_int)]
+                ("lambda_mode", ctypes.c_int), ("div_steady", ctypes.c_double)]
 
 
 class hosc_info(ctypes.Structure):
@@ -139,6 +139,9 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
         "hosc_set_stencil_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "hosc_set_tma_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+        "hosc_get_tma_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
         "hosc_set_krylov_merged": (ctypes.c_int, [_P, ctypes.c_int]),
         "hosc_get_krylov_merged": (ctypes.c_int, [_P]),
         "hosc_get_stencil_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
@@ -326,6 +329,16 @@ def hosc_get_tiles(h):
 
 def hosc_set_stencil_tiles(h, sx, sy, skz):
     return lib().hosc_set_stencil_tiles(h, int(sx), int(sy), int(skz))
+
+
+def hosc_set_tma_tiles(h, tty, tkz):
+    return lib().hosc_set_tma_tiles(h, int(tty), int(tkz))
+
+
+def hosc_get_tma_tiles(h):
+    a, b = ctypes.c_int(), ctypes.c_int()
+    st = lib().hosc_get_tma_tiles(h, ctypes.byref(a), ctypes.byref(b))
+    return st, a.value, b.value
 
 
 def hosc_set_krylov_merged(h, merged):

@@ -27,8 +27,14 @@ def request_params(N, Ra, n, Pr=1.0, precision=None, tol_steady=1e-6, tol_div=No
     stalls)."""
     p = H.hosc_steady_params(N, Ra, Pr, n)
     p.tol_lin = 1e-10
-    # the steady rule ties tol_div to tol_steady (h / (2 lambda)); an explicit tol_div is kept
-    p.tol_div = p.tol_div * tol_steady / p.tol_steady if tol_div is None else tol_div
+    # the steady rule ties the correction threshold tol_div to tol_steady (h / (2 lambda)) and
+    # stops at max|div V| < tol_steady; an explicit tol_div is both (the paper's one threshold)
+    if tol_div is None:
+        p.tol_div = p.tol_div * tol_steady / p.tol_steady
+        p.div_steady = tol_steady
+    else:
+        p.tol_div = tol_div
+        p.div_steady = 0.0
     p.tol_steady = tol_steady
     p.precision = H.HOSC_MIXED if precision is None else precision
     return p

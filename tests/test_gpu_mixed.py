@@ -102,7 +102,7 @@ def test_phase_api():
         assert H.hosc_set_phase(cav.h, 0) == 0
 
 
-def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None, merged=None):
+def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None, merged=None, tma=None):
     p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-12)
     st = inputs.cavity_state(N, Ra, seed=seed)
     with H.Cavity(p) as cav:
@@ -115,6 +115,10 @@ def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None, merged=None):
         if stencil is not None:
             assert H.hosc_set_stencil_tiles(cav.h, *stencil) == 0
             assert H.hosc_get_stencil_tiles(cav.h) == (0,) + tuple(stencil)
+        if tma is not None:
+            assert H.hosc_set_tma_tiles(cav.h, *tma) == 0
+            assert H.hosc_get_tma_tiles(cav.h) == (0,) + tuple(tma)
+            assert H.hosc_get_stencil_tiles(cav.h) == (0, 0, 0, 0)
         for name, which in FIELDS:
             cav.set(which, st[name])
         info = cav.step(1)
@@ -153,6 +157,49 @@ def test_staged_stencil_kernels(stencil):
         assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, stencil)
 
 
+@pytest.mark.parametrize("tma", [(1, 1), (2, 5), (3, 17), (4, 9), (8, 3), (17, 2)])
+def test_tma_stencil_kernels(tma):
+    """The bulk-copy (TMA) p/v and s/t kernels compute what the register kernels compute: the
+    increment equals the default's within the FP32 solve tolerance, for row tiles that overhang
+    the interior in y (17 = 2 x 8 + 1, 3 x 5 + 2, ...), segments that do not divide the interior,
+    single-plane and whole-column segments and a single tile per plane."""
+    N, Ra, n, dt = 19, 1e4, 0.75, 0.002
+    _, _, ref = _one_mixed_step(N, Ra, n, dt, 219)
+    _, _, got = _one_mixed_step(N, Ra, n, dt, 219, tma=tma, merged=0)
+    for name in ref:
+        scale = max(np.max(np.abs(ref[name])), 1e-12)
+        assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, tma)
+
+
+def test_tma_steps_and_shape_switches():
+    """Captured steps with the bulk-copy kernels, then a switch to the staged kernels (which
+    clears the bulk-copy shape) and back: every state equals the register kernels' run within the
+    FP32 solve tolerance after each leg."""
+    N, Ra, n, dt = 21, 1e4, 0.75, 0.002
+    p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-10)
+    st = inputs.cavity_state(N, Ra, seed=5)
+    runs = []
+    for plan in ("register", "switch"):
+        with H.Cavity(p) as cav:
+            for name, which in FIELDS:
+                cav.set(which, st[name])
+            out = []
+            for leg in range(3):
+                if plan == "switch":
+                    if leg == 1:
+                        assert H.hosc_set_stencil_tiles(cav.h, 16, 2, 5) == 0
+                        assert H.hosc_get_tma_tiles(cav.h) == (0, 0, 0)
+                    else:
+                        assert H.hosc_set_tma_tiles(cav.h, 2, 6) == 0
+                        assert H.hosc_get_stencil_tiles(cav.h) == (0, 0, 0, 0)
+                info = cav.step(4)
+                assert info["call_status"] == 0, info
+                out.append(cav.get(H.HOSC_U))
+            runs.append(out)
+    for a, b in zip(*runs):
+        assert np.max(np.abs(a - b)) <= 1e-4 * np.max(np.abs(a)), "state after a leg"
+
+
 def test_tiles_limits_and_autotune():
     N = 21
     p = _params(N, 1e4, 0.75, 0.002, H.HOSC_MIXED)
@@ -163,6 +210,9 @@ def test_tiles_limits_and_autotune():
         for bad in ((4, 4, 1), (32, 16, 1), (32, 4, 0), (32, 4, N - 1), (64, 8, 1), (17, 2, 1)):
             assert H.hosc_set_stencil_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
         assert H.hosc_set_stencil_tiles(cav.h, 0, 0, 0) == 0
+        for bad in ((1, 0), (1, N - 1), (N - 1, 1), (-1, 3), (2, -4)):
+            assert H.hosc_set_tma_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
+        assert H.hosc_set_tma_tiles(cav.h, 0, 5) == 0 and H.hosc_get_tma_tiles(cav.h) == (0, 0, 0)
         assert H.hosc_get_krylov_merged(cav.h) == 0   # the default form: three kernels
         assert H.hosc_set_krylov_merged(cav.h, 2) == H.HOSC_EINVAL
         assert H.hosc_set_tiles(cav.h, 384, 1) == 0

@@ -143,6 +143,7 @@ def test_steady_params_rule():
         assert p.dt * u * u / Pr <= 1.0 + 1e-12   # L = 1/(Pr eta) >= 1/Pr only tightens it
         assert 0 < p.lambda_ <= 2.0 * Pr
         assert p.tol_div == pytest.approx(0.5 * p.tol_steady * h / p.lambda_, rel=1e-15)
+        assert p.div_steady == p.tol_steady   # the stop tests the divergence at 1e-6
     # thinner fluids and faster flows need smaller steps
     dt = lambda N, Ra, n: H.hosc_steady_params(N, Ra, 1.0, n).dt
     assert dt(41, 1e5, 0.75) < dt(41, 1e5, 1.0)
@@ -152,6 +153,13 @@ def test_steady_params_rule():
         H.hosc_steady_params(21, -1.0, 1.0, 1.0)
     r = S.request_params(31, 1e3, 0.75)
     assert r.precision == H.HOSC_MIXED and r.tol_lin == 1e-10 and r.use_history == 0
+    assert r.div_steady == r.tol_steady == 1e-6
+    r = S.request_params(31, 1e3, 0.75, tol_steady=1e-4)
+    q = H.hosc_steady_params(31, 1e3, 1.0, 0.75)
+    assert r.div_steady == 1e-4 and r.tol_div == pytest.approx(100 * q.tol_div, rel=1e-15)
+    r = S.request_params(31, 1e3, 0.75, tol_div=1e-3)
+    assert r.tol_div == 1e-3 and r.div_steady == 0.0   # one threshold for both, as in Sec. 2.2
+    assert H.hosc_default_params(21, 1e3, 1.0, 1.0).div_steady == 0.0
 
 
 def test_batch_and_stream_recipes_are_seeded():
