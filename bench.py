@@ -49,10 +49,61 @@ WORKLOADS = {
 
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum,
 # mean of the captured launches) from ncu captures of the same kernel build, workload and launch
-# shape, summarised under profiles/. Keyed by (workload, kernel class, threads per block, planes
-# per thread, narrow); any other configuration, or a kernel changed since its capture, reports
-# null.
+# shape, summarised under profiles/, over the launches of the uncaptured profiled steps (the
+# in-step launches that `achieved` averages). Keyed by (workload, kernel class, launch shape as
+# _kernel_shape gives it); any other configuration, or a kernel changed since its capture,
+# reports null.
 NCU_TRAFFIC = {}
+
+
+def _kernel_shape(kernel, shape):
+    """The launch shape of a Krylov kernel class, as NCU_TRAFFIC keys it."""
+    t, s, m = shape["tiles"], shape["stencil"], shape["tma"]
+    reg = ("register", t["block"], t["kz"], t["narrow"])
+    if kernel in ("k_bicg_pv", "k_bicg_st"):
+        if m["rows"]:
+            return ("bulk-copy", m["rows"], m["planes"])
+        if s["sx"]:
+            return ("staged", s["sx"], s["sy"], s["skz"])
+        return reg
+    if kernel == "k_bicg_xr":
+        return ("flat",) if shape["xr"] == "flat stream" else reg
+    return None
+
+
+def _fp64_roofline(H, cav, N, steps=3):
+    """The all-FP64 path's kernels against their two ceilings, over a few uncaptured steps: the
+    BiCGSTAB kernels (p/v, s/t, x/r) as FP64 arithmetic, 32 fused multiply-adds per node, system
+    and iteration (p/v: p update 2, operator 7, r_0 . v 1; s/t: s at the 7 stencil nodes 7,
+    operator 7, two dot products 2; x/r: 4 updates, 2 dot products), against the FP64 FMA rate
+    measured by hosc_fp64_peak, and as bytes against the measured copy bandwidth; the sweeps
+    as bytes and time."""
+    import torch
+    names = ["k_viscosity", "k_sources", "k_rhs", "k_bicg_pv", "k_bicg_st", "k_bicg_xr", "update"]
+    H.hosc_profile_enable(cav.h, 1)
+    info = cav.step(steps)
+    kern = {}
+    for kid, name in enumerate(names):
+        _, kms, kl, kb = H.hosc_profile_read(cav.h, kid)
+        kern[name] = dict(ms=kms, launches=kl, bytes=kb)
+    H.hosc_profile_enable(cav.h, 0)
+    torch.cuda.synchronize()
+    rc, tf = H.hosc_fp64_peak(20)
+    peak, _ = _peaks()
+    kry = sum(kern[k]["ms"] for k in ("k_bicg_pv", "k_bicg_st", "k_bicg_xr"))
+    kry_b = sum(kern[k]["bytes"] for k in ("k_bicg_pv", "k_bicg_st", "k_bicg_xr"))
+    flops = 64.0 * (N - 2) ** 3 * info["lin_iters"]
+    out = {"steps": steps, "fp64_peak_tflops_measured": tf if rc == 0 else None,
+           "krylov": {"ms_per_step": kry / steps,
+                      "fp64_tflops": flops / (kry * 1e-3) / 1e12 if kry > 0 else None,
+                      "GBps": kry_b / (kry * 1e-3) / 1e9 if kry > 0 else None},
+           "kernels": {k: {"ms_per_step": v["ms"] / steps,
+                           "GBps": v["bytes"] / (v["ms"] * 1e-3) / 1e9 if v["ms"] else 0.0}
+                       for k, v in kern.items()}}
+    k = out["krylov"]
+    k["fp64_frac"] = k["fp64_tflops"] / tf if (rc == 0 and tf > 0 and k["fp64_tflops"]) else None
+    k["hbm_frac"] = k["GBps"] / peak if k["GBps"] else None
+    return out
 
 
 def _peaks():
@@ -178,6 +229,11 @@ def _one_at_a_time(H, S, cavs, precision, steps, warmup):
 
 
 def run_batch(args):
+    print(json.dumps(batch_line(args)))
+    return 0
+
+
+def batch_line(args):
     """Batched configuration: 64 uneven cavities (N in {21, 31, 41, 61}, log-uniform Ra in
     [1e2, 1e5], n uniform in [0.75, 1.25], Pr = 1, seed 20241106) advancing together in a pool,
     one captured graph launch per round of G steps for all cavities, launch shapes autotuned per
@@ -228,13 +284,12 @@ def run_batch(args):
                       "tuned_sizes": st1["tuned_sizes"],
                       "bicgstab_iters_per_cavity_step":
                           iters / (4.0 * max(1, sum(r["steps"] for r in res))),
-                      "dt": "per cavity from the stability bound (serve.pseudo_time_step)"},
+                      "dt": "per cavity from the steady-solve rule (hosc_steady_params)"},
            "one_at_a_time": {"cavities": len(sub), "steps_each": args.baseline_steps,
                              "mixed_GPUPS": one_mixed, "fp64_GPUPS": one_fp64,
                              "batched_over_fp64": value / one_fp64,
                              "batched_over_mixed": value / one_mixed}}
-    print(json.dumps(out))
-    return 0
+    return out
 
 
 def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=None,
@@ -444,68 +499,89 @@ def run_equal(args):
 
 
 def run_serve(args):
+    print(json.dumps(serve_line(args)))
+    return 0
+
+
+def serve_line(args, saturated_only=False):
     """Serving configuration: a seeded Poisson stream (seed 20241107) of cavity solves, N in
     {21, 31, ..., 101}, log-uniform Ra in [1e2, 1e5], n in {0.75, 1.0, 1.25}, Pr = 1, admitted
-    against a device-memory budget, each solved to steady state (or a step cap) in a pool.
-    First the saturated rate (all requests present at t = 0), then the stream at rho times that
-    rate; p50 / p99 arrival-to-completion times."""
+    against a device-memory budget, each solved to steady state (max|chi^{n+1} - chi^n|/dt and
+    max|div V| below tol_steady, 1e-6) with the library's steady-solve rule, or to a step cap, in
+    a pool. The first `saturation_requests` requests all present at t = 0 give the saturated
+    rate; then (unless saturated_only) the first `requests` requests of the stream arrive at rho
+    times that rate. Solves/s and p50 / p99 arrival-to-completion times."""
     from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
     mode = {"graph": H.HOSC_POOL_GRAPH, "streams": H.HOSC_POOL_STREAMS,
             "persistent": H.HOSC_POOL_PERSISTENT}[args.pool_mode]
     budget = int(args.budget_gb * (1 << 30))
-    steady_set = args.stream == "steady"
-    # "config": the stream of the serving configuration (most requests end at the step cap);
-    # "steady": small, slow cavities that reach steady state (time-to-steady is meaningful)
-    kw = (dict(sizes=(17, 21), indices=(0.9, 1.0, 1.1), ra_log10=(2.0, 3.0)) if steady_set
-          else {})
 
     def make(r):
-        if steady_set:
-            p = S.request_params(r["N"], r["Ra"], r["n"], r["Pr"], tol_steady=1e-6,
-                                 tol_div=1e-6)
-            p.dt = 0.02
-            p.lambda_ = 0.1
-            return p
-        # the steady-solve rule; tol_div follows tol_steady (half the step change a correction
-        # may cause)
         return S.request_params(r["N"], r["Ra"], r["n"], r["Pr"], tol_steady=args.tol_steady)
 
-    max_steps = max(args.max_steps, 20000) if steady_set else args.max_steps
+    max_steps = args.max_steps
     # a prefix of the configured stream of 2000 requests (the parameters of request q do not
     # depend on the rate, only its arrival time does)
-    total = max(args.requests, 2000)
-    base = inputs.request_stream(total, rate=1.0, **kw)[:args.requests]
+    total = max(args.requests, args.saturation_requests, 2000)
+    base = inputs.request_stream(total, rate=1.0)
     sat_reqs = [dict(r, t=0.0) for r in base[:args.saturation_requests]]
     with S.Pool(budget, args.round_steps, mode, True) as pool:
-        _, sat = S.serve(sat_reqs, pool, make, max_steps)
-    rate = args.rho * sat["solves_per_s"]
-    stream = inputs.request_stream(total, rate=rate, **kw)[:args.requests]
-    with S.Pool(budget, args.round_steps, mode, True) as pool:
-        res, summ = S.serve(stream, pool, make, max_steps)
+        sres, sat = S.serve(sat_reqs, pool, make, max_steps)
         pst = pool.stats()
+    if saturated_only:
+        res, summ, n_req, rho = sres, sat, len(sat_reqs), None
+    else:
+        rate = args.rho * sat["solves_per_s"]
+        stream = inputs.request_stream(total, rate=rate)[:args.requests]
+        with S.Pool(budget, args.round_steps, mode, True) as pool:
+            res, summ = S.serve(stream, pool, make, max_steps)
+            pst = pool.stats()
+        n_req, rho = args.requests, args.rho
     out = {"metric": "served cavity solves/s", "value": summ["solves_per_s"], "unit": "solves/s",
-           "n_gpus": 1, "steps": args.requests, "warmup": 0,
+           "n_gpus": 1, "steps": n_req, "warmup": 0,
            "ms_per_step": 1e3 / summ["solves_per_s"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
-           "seed_prefix": "the first %d requests of the seeded stream (arrival order)"
-                          % args.requests,
-           "config": {"workload": ("Poisson stream of %d cavity solves, N in {17,21}, Ra "
-                                   "log-uniform [1e2,1e3], n in {0.9,1,1.1}, Pr=1, dt=0.02, "
-                                   "lambda=0.1, tol 1e-6, seed 20241107" if steady_set else
-                                   "Poisson stream of %d cavity solves, N in {21..101} step 10, "
-                                   "Ra log-uniform [1e2,1e5], n in {0.75,1,1.25}, Pr=1, seed "
-                                   "20241107") % args.requests,
-                      "stream": args.stream,
-                      "rho": args.rho, "saturated_solves_per_s": sat["solves_per_s"],
+           "seed_prefix": "the first %d requests of the seeded stream (arrival order)%s"
+                          % (n_req, ", all present at t = 0" if saturated_only else ""),
+           "config": {"workload": "Poisson stream of cavity solves, N in {21..101} step 10, Ra "
+                                  "log-uniform [1e2,1e5], n in {0.75,1,1.25}, Pr=1, seed "
+                                  "20241107, the library's steady-solve rule",
+                      "rho": rho, "saturated_solves_per_s": sat["solves_per_s"],
                       "saturation_requests": len(sat_reqs), "budget_GB": args.budget_gb,
-                      "max_steps": max_steps,
-                      "tol_steady": 1e-6 if steady_set else args.tol_steady,
+                      "max_steps": max_steps, "tol_steady": args.tol_steady,
                       "pool_mode": args.pool_mode, "steps_per_round": args.round_steps,
                       "completed": summ["completed"], "steady": summ["steady"],
+                      "requests": [{k: r[k] for k in ("N", "Ra", "n")}
+                                   for r in base[:n_req]],
+                      "steps_to_steady": [r.get("steps") if r else None for r in res],
+                      "latency_s": [r.get("latency") if r else None for r in res],
                       "captures": pst["captures"], "capture_ms": pst["capture_ms"]}}
-    print(json.dumps(out))
-    return 0
+    return out
+
+
+def _pool_blocks(args):
+    """Bounded runs of the batching and serving workloads for the default line: the 64-cavity
+    mix advanced 32 steps in rounds of 8 (after 3 warm-up rounds) against 4 of its cavities one
+    at a time, and the first `serve_block_requests` requests of the serving stream, all present
+    at t = 0, each solved to steady state."""
+    import types
+    common = dict(pool_mode="graph", round_steps=8, budget_gb=64.0)
+    t0 = time.perf_counter()
+    b = batch_line(types.SimpleNamespace(steps=32, warmup=3, baseline_cavities=4,
+                                         baseline_steps=20, **common))
+    t1 = time.perf_counter()
+    s = serve_line(types.SimpleNamespace(requests=args.serve_block_requests,
+                                         saturation_requests=args.serve_block_requests,
+                                         rho=None, max_steps=300000, tol_steady=1e-6,
+                                         **common), saturated_only=True)
+    t2 = time.perf_counter()
+    keep = ("metric", "value", "unit", "steps", "ms_per_step")
+    batch = dict({k: b[k] for k in keep}, config=b["config"], one_at_a_time=b["one_at_a_time"],
+                 wall_s=t1 - t0)
+    serve = dict({k: s[k] for k in keep}, p50_s=s["p50_s"], p99_s=s["p99_s"],
+                 seed_prefix=s["seed_prefix"], config=s["config"], wall_s=t2 - t1)
+    return {"batch": batch, "serve": serve}
 
 
 def _host():
@@ -652,7 +728,9 @@ def main():
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--saturation-requests", type=int, default=32)
     ap.add_argument("--rho", type=float, default=0.8)
-    ap.add_argument("--stream", default="config", choices=["config", "steady"])
+    ap.add_argument("--no-pool-blocks", action="store_true",
+                    help="leave the bounded batch and serve blocks out of the default line")
+    ap.add_argument("--serve-block-requests", type=int, default=6)
     ap.add_argument("--max-steps", type=int, default=1000)
     ap.add_argument("--tol-steady", type=float, default=1e-6)
     ap.add_argument("--budget-gb", type=float, default=64.0)
@@ -739,6 +817,8 @@ def main():
                 # 96 words (p/v 38, s/t 26, x/r 32); BiCGSTAB(2) 224 words per two-iteration
                 # cycle (B1 30, B2 50, B3 46, B4 54, B5 44)
                 "krylov_bytes_per_iteration_per_node": 768 if solver == 0 else 896}
+            if solver == 0:
+                fp64_compare[name]["roofline"] = _fp64_roofline(H, c64, N)
             c64.close()
     p, cav = make(args.precision)
 
@@ -816,15 +896,21 @@ def main():
              if mixed else None,
              "stencil": dict(zip(("sx", "sy", "skz"), H.hosc_get_stencil_tiles(cav.h)[1:]))
              if mixed else None,
+             "tma": dict(zip(("rows", "planes"), H.hosc_get_tma_tiles(cav.h)[1:]))
+             if mixed else None,
+             "xr": (("flat stream" if H.hosc_get_xr_form(cav.h) else "column march")
+                    if mixed else None),
              "form": (("merged: 2 kernels per iteration" if H.hosc_get_krylov_merged(cav.h)
                        else "3 kernels per iteration") if mixed else None)}
     traffic = None
     if mixed:
-        t = shape["tiles"]
-        traffic = NCU_TRAFFIC.get((args.workload, dom, t["block"], t["kz"], t["narrow"]))
+        traffic = NCU_TRAFFIC.get((args.workload, dom, _kernel_shape(dom, shape)))
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(cav, H, wl)
+    pool_blocks = None
+    if rank == 0 and ws == 1 and args.precision == "mixed" and not args.no_pool_blocks:
+        pool_blocks = _pool_blocks(args)
 
     # a variant outside the paper's method, for comparison only: the same workload with Jacobi
     # row scaling of the level-(n+1) systems before BiCGSTAB (same solution, fewer iterations)
@@ -874,6 +960,7 @@ def main():
                        # interior nodes x systems x BiCGSTAB iterations per second
                        "sweep_rate_per_s": (N - 2) ** 3 * lin_iters * ws / (ms * 1e-3),
                        "krylov_tiles": shape["tiles"], "stencil_tiles": shape["stencil"],
+                       "tma_tiles": shape["tma"], "xr_form": shape["xr"],
                        "krylov_form": shape["form"],
                        "l2": "no flush: device working set %.0f MB > 129 MB L2"
                              % (H.hosc_workspace_bytes(p) / 1e6),
@@ -893,6 +980,8 @@ def main():
             "cpu_baseline": cpu,
             "variants": variant,
         }
+        if pool_blocks:
+            out.update(pool_blocks)
         print(json.dumps(out))
     cav.close()
     if ws > 1:

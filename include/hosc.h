@@ -317,6 +317,14 @@ hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz);
 hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz);
 hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz);
 
+/* Form of the mixed-precision x/r kernel (three-kernel iteration): flat = 0 (the default) the
+ * column march of hosc_set_tiles; 1 one flat grid-stride stream over the interior planes (the
+ * i and j wall nodes included, where every vector is zero), each thread issuing the loads of
+ * four nodes before their arithmetic. HOSC_EINVAL for another value, HOSC_ESTATE mid-step.
+ * Drops the captured steps. hosc_get_xr_form returns the form (-1 for a NULL context). */
+hosc_status hosc_set_xr_form(void* ctx, int flat);
+int hosc_get_xr_form(void* ctx);
+
 /* Form of the mixed-precision BiCGSTAB iteration: merged = 1 runs two kernels per iteration,
  * folding the x, r update of iteration i-1 into the p, v kernel of iteration i and obtaining
  * r_0.r_{i+1} for beta from r_0.s and r_0.t of the s, t kernel (the same method; the
@@ -338,7 +346,8 @@ int hosc_get_krylov_merged(void* ctx);
  * staged p/v and s/t kernels (hosc_set_stencil_tiles) for tiles sx in {8, 16, ..., 64},
  * sy in {4, 8} and skz in 1..33 within 1.5x of their least modelled cost, and the bulk-copy
  * kernels (hosc_set_tma_tiles) for tty in 1..8 and tkz in 1..33 within 1.5x of theirs, and keep
- * the fastest of the three kinds for p/v and s/t. Reports the register shape (any output pointer may be NULL;
+ * the fastest of the three kinds for p/v and s/t; then the two x/r forms (hosc_set_xr_form) with
+ * 4 reps launches each, keeping the faster. Reports the register shape (any output pointer may be NULL;
  * ms_out = the three kernels' summed mean milliseconds with the chosen kernels). Mixed precision
  * only (HOSC_EINVAL for FP64). The fields keep their values. */
 hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, double* ms_out);

@@ -74,6 +74,7 @@ struct Ctx {
   int inner_last = 0;                      // inner pressure passes of the last step
   int sx = 0, sy = 0, skz = 0;             // staged stencil kernels (sx == 0: not used)
   int tty = 0, tkz = 0;                    // bulk-copy stencil kernels (tty == 0: not used)
+  int xr_flat = 0;                         // x/r as one flat stream (k8_xr)
   alignas(64) unsigned char tmap_host[kTmaMaps * kTmaMapBytes];   // their tensor maps
   // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
   // asynchronously into h_ring / h_ring_pos, completion marked by round_ev
@@ -141,6 +142,7 @@ void apply_tiles(Ctx* c) {
   c->P.tty = c->tty;
   c->P.ttx = tma_tile_x(c->prm.N);
   c->P.tkz = c->tkz;
+  c->P.xr_flat = c->xr_flat;
 }
 
 bool stencil_tiles_valid(const Ctx* c, int sx, int sy, int skz) {
@@ -933,7 +935,7 @@ long ctx_signature(void* ctx) {
                  ((long)c->kblock << 3) | ((long)c->kz << 13) | ((long)c->narrow << 23) |
                  ((long)c->sx << 24) | ((long)c->sy << 32) | ((long)c->skz << 42) |
                  ((long)c->merged << 52);
-  return s ^ ((long)c->tty << 53) ^ ((long)c->tkz << 56);
+  return s ^ ((long)c->tty << 53) ^ ((long)c->tkz << 56) ^ ((long)c->xr_flat << 62);
 }
 
 // Start of a round of n steps from the current level (read back by ctx_collect_round).
@@ -1616,6 +1618,23 @@ hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz) {
   return HOSC_OK;
 }
 
+hosc_status hosc_set_xr_form(void* ctx, int flat) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c || (flat != 0 && flat != 1)) return HOSC_EINVAL;
+  if (c->stage != 0) return HOSC_ESTATE;
+  if (flat != c->xr_flat) {
+    c->xr_flat = flat;
+    apply_tiles(c);
+    drop_graphs(c);
+  }
+  return HOSC_OK;
+}
+
+int hosc_get_xr_form(void* ctx) {
+  const Ctx* c = (const Ctx*)ctx;
+  return c ? c->xr_flat : -1;
+}
+
 hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
@@ -1674,6 +1693,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   {   // the register kernels first
     hosc_status s0 = hosc_set_stencil_tiles(c, 0, 0, 0);
     if (!s0) s0 = hosc_set_tma_tiles(c, 0, 0);
+    if (!s0) s0 = hosc_set_xr_form(c, 0);
     if (s0) return s0;
   }
   int best_b = c->kblock, best_z = c->kz, best_n = c->narrow;
@@ -1762,6 +1782,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   if (c->merged) {   // the staged kernels implement the three-kernel form only
     st = hosc_set_stencil_tiles(c, 0, 0, 0);
     if (!st) st = hosc_set_tma_tiles(c, 0, 0);
+    if (!st) st = hosc_set_xr_form(c, 0);
     if (st) return st;
     if (kblock_out) *kblock_out = best_b;
     if (kz_out) *kz_out = best_z;
@@ -1873,6 +1894,20 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
     st = hosc_set_stencil_tiles(c, 0, 0, 0);
   }
   if (st) return st;
+  // x/r: the column march at the shape found against the flat stream
+  {
+    double col = 0.0, flat = 0.0;
+    const int save = c->xr_flat;
+    c->P.xr_flat = 0;
+    st = time_class(c, HOSC_K_BICG_XR, 4 * reps, &col);
+    c->P.xr_flat = 1;
+    if (!st) st = time_class(c, HOSC_K_BICG_XR, 4 * reps, &flat);
+    c->P.xr_flat = save;
+    if (st) return st;
+    st = hosc_set_xr_form(c, flat < col ? 1 : 0);
+    if (st) return st;
+    best += (flat < col ? flat : col) - (save ? flat : col);
+  }
   if (kblock_out) *kblock_out = best_b;
   if (kz_out) *kz_out = best_z;
   if (ms_out) *ms_out = best;

@@ -33,6 +33,7 @@ struct DevParams {
                      // skz planes per block; sx == 0 selects the register kernels instead
   int tty, ttx, tkz; // bulk-copy (TMA) stencil kernels (p/v and s/t): tile of ttx * tty interior
                      // columns, tkz planes per block; tty == 0: not used
+  int xr_flat;       // x/r as one flat grid-stride stream (k8_xr) instead of the column march
   double h, h2;      // grid spacing along x and its square
   double Ly, Lz;     // box 1 x Ly x Lz: lengths along y and z (1 for the cube)
   // Spacing constants of the directions d = x, y, z (spacings h, k, l = h, Ly h, Lz h), in double
@@ -188,6 +189,8 @@ double tma_wave_cost(int N, int tty, int tkz, int sms);
 void launch_tma_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 void launch_tma_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 long tma_blocks(const DevParams& P);
+// Blocks of the flat x/r kernel (one wave of resident blocks).
+int xr_flat_blocks();
 int device_sms();
 
 // S1: eta and L at every node.

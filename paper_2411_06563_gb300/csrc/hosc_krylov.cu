@@ -1105,6 +1105,80 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
   k_bicg_init<double><<<b, kThreads, 0, s>>>(P, F, b);
 }
 
+// x/r as one flat stream: every node of the interior planes, the i and j walls included (every
+// vector is zero there: k4_init zeroes t and r_0 on the walls), in a grid-stride loop that
+// issues the loads of U nodes before their arithmetic, so that a thread keeps 6 U float4 loads in
+// flight. Same arithmetic and float-float partials as k4_xr; one block partial per block.
+template <int U>
+__global__ void __launch_bounds__(256) k8_xr(DevParams P, Fields F, int pp) {
+  __shared__ double smem[32 * 8];
+  __shared__ Scal4 sc;
+  pdl_wait_and_release();
+  load_scalars(F.ks, sc);
+  if (sc.all_done) return;
+  const int np = 1 - pp;
+  const float4 a = sc.a, om = sc.om, ma = neg4(sc.a), mom = neg4(sc.om);
+  const float4* __restrict__ V = F.kv[np];
+  const float4* __restrict__ Pv = F.kp[np];
+  const float4* __restrict__ T = F.kt;
+  const float4* __restrict__ R0 = F.kr0;
+  float4* __restrict__ X = F.kx;
+  float4* __restrict__ R = F.kr;
+  const unsigned N2 = (unsigned)P.N * (unsigned)P.N, hi = N2 * (unsigned)(P.N - 1);
+  const unsigned stride = gridDim.x * blockDim.x;
+  FF acc[8] = {};
+  unsigned c = N2 + blockIdx.x * blockDim.x + threadIdx.x;
+  for (; c + (U - 1) * stride < hi; c += U * stride) {
+    float4 r[U], v[U], p[U], t[U], r0[U], x[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const unsigned e = c + q * stride;
+      r[q] = R[e];
+      x[q] = X[e];
+      v[q] = __ldg(V + e);
+      p[q] = __ldg(Pv + e);
+      t[q] = __ldg(T + e);
+      r0[q] = __ldg(R0 + e);
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const unsigned e = c + q * stride;
+      const float4 sv = fma4(ma, v[q], r[q]);
+      X[e] = fma4(om, sv, fma4(a, p[q], x[q]));
+      const float4 rn = fma4(mom, t[q], sv);
+      R[e] = rn;
+      ff_dot4(acc, r0[q], rn);
+      ff_dot4(acc + 4, rn, rn);
+    }
+  }
+  for (; c < hi; c += stride) {
+    const float4 sv = fma4(ma, __ldg(V + c), R[c]);
+    X[c] = fma4(om, sv, fma4(a, __ldg(Pv + c), X[c]));
+    const float4 rn = fma4(mom, __ldg(T + c), sv);
+    R[c] = rn;
+    ff_dot4(acc, __ldg(R0 + c), rn);
+    ff_dot4(acc + 4, rn, rn);
+  }
+  double part[8];
+  block_ff<8>(acc, part, smem);
+  if (publish_is_last<8>(part, F.red, F.counter, blockIdx.x, gridDim.x))
+    xr_finish(P, F, gridDim.x, smem);
+}
+
+// Blocks of the flat x/r kernel: resident blocks of one wave.
+int xr_flat_blocks() {
+  static int occ = 0;
+  if (occ == 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k8_xr<4>, 256, 0) != cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      occ = 4;
+    }
+  }
+  return occ * device_sms();
+}
+
+
 // Launch of an interleaved Krylov kernel with programmatic stream serialisation (see
 // pdl_wait_and_release): in a captured step the kernels of the BiCGSTAB loop chain with
 // programmatic edges.
@@ -1172,6 +1246,10 @@ void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
 
 void launch_bicg_xr(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
   if (P.krylov_fp32 && P.merged) return;   // folded into the next k6_a
+  if (P.krylov_fp32 && P.xr_flat) {
+    launch_pdl(k8_xr<4>, dim3(xr_flat_blocks()), 256, s, P, F, pp);
+    return;
+  }
   if (P.krylov_fp32) {
     if (P.narrow) launch_pdl(k4_xr<4>, grid4(P), P.kblock, s, P, F, pp);
     else launch_pdl(k4_xr<2>, grid4(P), P.kblock, s, P, F, pp);

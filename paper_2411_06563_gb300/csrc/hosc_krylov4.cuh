@@ -238,8 +238,12 @@ __device__ __forceinline__ bool k4_init_body(const DevParams& P, const Fields& F
     const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
     const float4 z = f4(0.f);
     const float4 r = inner ? F.kr0[c] : z;
+    if (!inner) {   // t and r_0 zero on the walls: the flat x/r kernel streams wall nodes too
+      F.kt[c] = z;
+      F.kr0[c] = z;
+    }
     F.kr[c] = r;
-    F.kx[c] = z;   // t needs no zeros: k4_st writes it before k4_xr reads it, inside only
+    F.kx[c] = z;   // t inside needs no zeros: k4_st writes it before k4_xr reads it
     F.kp[0][c] = z;
     F.kp[1][c] = z;
     F.kv[0][c] = z;
@@ -398,6 +402,35 @@ __global__ void __launch_bounds__(MinB == 2 ? 384 : 256, MinB)
   k4_st_body(P, F, pp, hw_grid());
 }
 
+// The last block of an x/r launch: totals of (r_0 . r, r . r) per system, then the convergence and
+// breakdown tests, beta and rho of the next iteration.
+__device__ __forceinline__ void xr_finish(const DevParams& P, const Fields& F, unsigned nblocks,
+                                          double* smem) {
+  double tot[8];
+  reduce_partials<8, false>(tot, F.red, nblocks, F.counter, smem);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 4; ++s) {
+      KrylovScalars& k = F.ks[s];
+      if (k.done) continue;
+      const double rho_new = tot[s];
+      k.rnorm = sqrt(tot[4 + s]);
+      k.iters += 1;
+      if (k.rnorm <= P.tol_lin * k.r0norm) {
+        k.done = 1;
+        k.status = 0;
+      } else if (!isfinite(k.rnorm) || k.iters >= P.max_lin_iter || rho_new == 0.0 ||
+                 k.omega == 0.0) {
+        k.done = 1;
+        k.status = HOSC_ENOCONV;
+      } else {
+        k.beta = (rho_new / k.rho) * (k.alpha / k.omega);
+        k.rho = rho_new;
+      }
+    }
+    F.alg_bytes[HOSC_K_BICG_XR] += bytes4(P, 8.0);   // r v p x t r0 in, x r out
+  }
+}
+
 // s = r - alpha v; x += alpha p + omega s; r = s - omega t; partials (r_0 . r, r . r); last block:
 // convergence and breakdown tests, beta and rho of the next iteration.
 // Returns true in the block that finished the launch's reduction (convergence decided).
@@ -428,31 +461,7 @@ __device__ __forceinline__ bool k4_xr_body(const DevParams& P, const Fields& F, 
   double part[8];
   block_ff<8>(acc, part, smem);
   if (!publish_is_last<8>(part, F.red, F.counter, block_id(vg), block_count(vg))) return false;
-  {
-    double tot[8];
-    reduce_partials<8, false>(tot, F.red, block_count(vg), F.counter, smem);
-    if (threadIdx.x == 0) {
-      for (int s = 0; s < 4; ++s) {
-        KrylovScalars& k = F.ks[s];
-        if (k.done) continue;
-        const double rho_new = tot[s];
-        k.rnorm = sqrt(tot[4 + s]);
-        k.iters += 1;
-        if (k.rnorm <= P.tol_lin * k.r0norm) {
-          k.done = 1;
-          k.status = 0;
-        } else if (!isfinite(k.rnorm) || k.iters >= P.max_lin_iter || rho_new == 0.0 ||
-                   k.omega == 0.0) {
-          k.done = 1;
-          k.status = HOSC_ENOCONV;
-        } else {
-          k.beta = (rho_new / k.rho) * (k.alpha / k.omega);
-          k.rho = rho_new;
-        }
-      }
-      F.alg_bytes[HOSC_K_BICG_XR] += bytes4(P, 8.0);   // r v p x t r0 in, x r out
-    }
-  }
+  xr_finish(P, F, block_count(vg), smem);
   return true;
 }
 

@@ -142,6 +142,8 @@ def lib():
         "hosc_set_tma_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
         "hosc_get_tma_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
+        "hosc_set_xr_form": (ctypes.c_int, [_P, ctypes.c_int]),
+        "hosc_get_xr_form": (ctypes.c_int, [_P]),
         "hosc_set_krylov_merged": (ctypes.c_int, [_P, ctypes.c_int]),
         "hosc_get_krylov_merged": (ctypes.c_int, [_P]),
         "hosc_get_stencil_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
@@ -339,6 +341,14 @@ def hosc_get_tma_tiles(h):
     a, b = ctypes.c_int(), ctypes.c_int()
     st = lib().hosc_get_tma_tiles(h, ctypes.byref(a), ctypes.byref(b))
     return st, a.value, b.value
+
+
+def hosc_set_xr_form(h, flat):
+    return lib().hosc_set_xr_form(h, int(flat))
+
+
+def hosc_get_xr_form(h):
+    return int(lib().hosc_get_xr_form(h))
 
 
 def hosc_set_krylov_merged(h, merged):

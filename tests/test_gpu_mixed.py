@@ -102,7 +102,8 @@ def test_phase_api():
         assert H.hosc_set_phase(cav.h, 0) == 0
 
 
-def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None, merged=None, tma=None):
+def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None, merged=None, tma=None,
+                    xr=None):
     p = _params(N, Ra, n, dt, H.HOSC_MIXED, tol_lin=1e-12)
     st = inputs.cavity_state(N, Ra, seed=seed)
     with H.Cavity(p) as cav:
@@ -119,6 +120,8 @@ def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None, merged=None, t
             assert H.hosc_set_tma_tiles(cav.h, *tma) == 0
             assert H.hosc_get_tma_tiles(cav.h) == (0,) + tuple(tma)
             assert H.hosc_get_stencil_tiles(cav.h) == (0, 0, 0, 0)
+        if xr is not None:
+            assert H.hosc_set_xr_form(cav.h, xr) == 0 and H.hosc_get_xr_form(cav.h) == xr
         for name, which in FIELDS:
             cav.set(which, st[name])
         info = cav.step(1)
@@ -171,6 +174,19 @@ def test_tma_stencil_kernels(tma):
         assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, tma)
 
 
+@pytest.mark.parametrize("N,tma", [(19, None), (19, (2, 5)), (12, None), (31, (3, 7))])
+def test_flat_xr_kernel(N, tma):
+    """The flat x/r stream (every node of the interior planes, walls included) computes what the
+    column march computes, alone and with the bulk-copy stencil kernels: the increment equals the
+    default's within the FP32 solve tolerance."""
+    Ra, n, dt = 1e4, 0.75, 0.002
+    _, _, ref = _one_mixed_step(N, Ra, n, dt, 219)
+    _, _, got = _one_mixed_step(N, Ra, n, dt, 219, tma=tma, merged=0, xr=1)
+    for name in ref:
+        scale = max(np.max(np.abs(ref[name])), 1e-12)
+        assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, N, tma)
+
+
 def test_tma_steps_and_shape_switches():
     """Captured steps with the bulk-copy kernels, then a switch to the staged kernels (which
     clears the bulk-copy shape) and back: every state equals the register kernels' run within the
@@ -213,6 +229,7 @@ def test_tiles_limits_and_autotune():
         for bad in ((1, 0), (1, N - 1), (N - 1, 1), (-1, 3), (2, -4)):
             assert H.hosc_set_tma_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
         assert H.hosc_set_tma_tiles(cav.h, 0, 5) == 0 and H.hosc_get_tma_tiles(cav.h) == (0, 0, 0)
+        assert H.hosc_set_xr_form(cav.h, 2) == H.HOSC_EINVAL and H.hosc_get_xr_form(cav.h) == 0
         assert H.hosc_get_krylov_merged(cav.h) == 0   # the default form: three kernels
         assert H.hosc_set_krylov_merged(cav.h, 2) == H.HOSC_EINVAL
         assert H.hosc_set_tiles(cav.h, 384, 1) == 0
