@@ -53,7 +53,11 @@ WORKLOADS = {
 # in-step launches that `achieved` averages). Keyed by (workload, kernel class, launch shape as
 # _kernel_shape gives it); any other configuration, or a kernel changed since its capture,
 # reports null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/k4_pv_cavity101_mixed.md, "In-step DRAM traffic" (40 launches each)
+    ("cavity101", "k_bicg_pv", ("register", 256, 9, 0)): 105.0e6,
+    ("cavity101", "k_bicg_pv", ("register", 384, 9, 0)): 104.7e6,
+}
 
 
 def _kernel_shape(kernel, shape):
@@ -308,11 +312,12 @@ def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=N
     with H.Cavity(p) as cav:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        done, info, switch, chunk = 0, None, None, 1000
+        done, info, switch, chunk, lin = 0, None, None, 1000, 0
         while done < max_steps:   # chunks, with progress on stderr
             info = cav.solve_steady(min(chunk, max_steps - done),
                                     allow=(H.HOSC_ESTEPLIMIT, H.HOSC_ENOCONV, H.HOSC_EDIVERGED))
             done += info["steps"]
+            lin += info["lin_iters"]
             phase = H.hosc_get_phase(cav.h)
             if phase == 1 and switch is None:
                 switch = done   # the automatic switch happened within this chunk
@@ -336,7 +341,7 @@ def steady_solve(H, N, Ra, n, Pr=1.0, max_steps=200000, precision=None, stream=N
             "status": H.hosc_strerror(info["call_status"]), "steady": info["call_status"] == 0,
             "steps": info["steps"], "seconds": el,
             "GPUPS": (N - 2) ** 3 * info["steps"] / el if el > 0 else None,
-            "bicgstab_iters_per_step": info["lin_iters"] / (4.0 * max(1, info["steps"])),
+            "bicgstab_iters_per_step": lin / (4.0 * max(1, done)),
             "res_over_dt": info["res"] / p.dt, "div_max": info["div_max"],
             "stop": {"tol_steady": p.tol_steady, "div_steady": p.div_steady,
                      "tol_div_correction": p.tol_div},

@@ -306,7 +306,7 @@ hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz);
  * their reads moved by the GPU's bulk-copy engine (tensor-map box copies of each z-plane into a
  * ring of three shared-memory stages, one producer thread, mbarrier completion), so that the
  * bytes in flight do not depend on registers or resident warps. A block owns tty rows of the
- * plane's interior columns (whole rows up to 252 columns; wider planes are cut into equal
+ * plane's interior columns (whole rows up to 126 columns; wider planes are cut into equal
  * pieces) and tkz consecutive planes (1..N-2). tty == 0 selects the register kernels (the
  * default); setting tiles here clears hosc_set_stencil_tiles and the reverse. HOSC_EINVAL for a
  * shape that does not fit (at most 512 threads and 200 KB of shared memory per block, too many

@@ -175,7 +175,7 @@ double staged_wave_cost(int N, int sx, int sy, int skz, int sms);
 size_t staged_smem_bytes(int sx, int sy, bool pv);
 
 // Bulk-copy (TMA) stencil kernels (hosc_tma.cu). The interior columns of a plane are cut into
-// tiles of ttx * tty (ttx from N: whole interior rows up to 252 columns, else the least even
+// tiles of ttx * tty (ttx from N: whole interior rows up to 126 columns, else the least even
 // split), a block streams the tile through tkz planes.
 constexpr int kTmaMaps = 8;        // kr, kr0, kp[0], kp[1], kv[0], kv[1], kwm, kwe
 constexpr int kTmaMapBytes = 128;  // sizeof(CUtensorMap)

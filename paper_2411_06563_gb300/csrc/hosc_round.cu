@@ -37,7 +37,7 @@ namespace {
 
 constexpr unsigned long long kBarrierNs = 5000000000ull;   // 5 s
 constexpr int kRoundThreads = 256;
-constexpr int kRoundMinBlocks = 2;   // resident blocks per SM the register budget is set for
+constexpr int kRoundMinBlocks = 4;   // resident blocks per SM the register budget is set for
 
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;

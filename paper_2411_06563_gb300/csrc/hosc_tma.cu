@@ -7,7 +7,8 @@
 // producer thread (the block's last warp) streams the planes of the segment, one ahead of the
 // plane being computed, into a ring of kTmaStages shared-memory stages: per plane the haloed
 // (ttx + 2) x (tty + 2) box of each stencil vector and the tile boxes of the compact operators
-// (and r_0) by tensor-map copies (cp.async.bulk.tensor, zero fill outside the grid), and the
+// (and r_0) by tensor-map copies (cp.async.bulk.tensor over 8-byte elements, so that each box row
+// is one contiguous run; zero fill outside the grid), and the
 // momentum L of each tile row by a plain bulk copy (its rows are not 16-byte aligned in general,
 // which a tensor map requires). A stage's copies complete a "full" mbarrier (transaction count);
 // the consumer warps mark a stage free on an "empty" mbarrier once they have read it. No load
@@ -116,13 +117,15 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity
     if (gpu_ns() - t0 > kTmaWaitNs) return false;
   return true;
 }
-// Tensor-map copy of a 4-D box (float4 arrays as {4, N, N, N} floats) into shared memory.
+// Tensor-map copy of a 3-D box into shared memory. The float4 arrays are described as
+// {2N, N, N} tensors of 8-byte elements (two per node), so that a box row is one contiguous run
+// of 16 (tx + 2) bytes and its x coordinate, 2i, is always a 16-byte boundary.
 __device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, int i, int j, int k,
                                         unsigned long long* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-      "l"(map), "r"(0), "r"(i), "r"(j), "r"(k), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(map), "r"(2 * i), "r"(j), "r"(k), "r"(smem_u32(bar))
       : "memory");
 }
 // Plain bulk copy: 16-byte aligned source and destination, size a multiple of 16.
@@ -342,15 +345,17 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// A float4 array of N^3 nodes as a 4-D tensor {4, N, N, N} of floats; box {4, bw, bh, 1}.
+// A float4 array of N^3 nodes as a 3-D tensor {2N, N, N} of 8-byte elements (the bits are
+// copied as they are; outside the tensor the box is filled with zero bits, 0.0f); box
+// {2 bw, bh, 1}.
 bool encode_vec(CUtensorMap* m, const float4* a, int N, int bw, int bh) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  const cuuint64_t dims[4] = {4, (cuuint64_t)N, (cuuint64_t)N, (cuuint64_t)N};
-  const cuuint64_t strides[3] = {16, 16ull * N, 16ull * N * N};
-  const cuuint32_t box[4] = {4, (cuuint32_t)bw, (cuuint32_t)bh, 1};
-  const cuuint32_t es[4] = {1, 1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)a, dims, strides, box, es,
+  const cuuint64_t dims[3] = {2ull * N, (cuuint64_t)N, (cuuint64_t)N};
+  const cuuint64_t strides[2] = {16ull * N, 16ull * N * N};
+  const cuuint32_t box[3] = {(cuuint32_t)(2 * bw), (cuuint32_t)bh, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)a, dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -399,7 +404,8 @@ void launch_k7(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
 
 int tma_tile_x(int N) {
   const int ni = N - 2;
-  const int parts = (ni + 251) / 252;   // whole rows up to 252 columns (box dimensions <= 256)
+  // whole rows up to 126 columns: a haloed row is 2 (tx + 2) <= 256 elements of a box dimension
+  const int parts = (ni + 125) / 126;
   return (ni + parts - 1) / parts;
 }
 
