@@ -66,7 +66,7 @@ def _kernel_shape(kernel, shape):
     reg = ("register", t["block"], t["kz"], t["narrow"])
     if kernel in ("k_bicg_pv", "k_bicg_st"):
         if m["rows"]:
-            return ("bulk-copy", m["rows"], m["planes"])
+            return ("bulk-copy", m["rows"], m["planes"], m["stages"])
         if s["sx"]:
             return ("staged", s["sx"], s["sy"], s["skz"])
         return reg
@@ -504,18 +504,20 @@ def run_equal(args):
 
 
 def run_serve(args):
-    print(json.dumps(serve_line(args)))
+    print(json.dumps(serve_line(args, newtonian_only=args.newtonian_only)))
     return 0
 
 
-def serve_line(args, saturated_only=False):
+def serve_line(args, saturated_only=False, newtonian_only=False):
     """Serving configuration: a seeded Poisson stream (seed 20241107) of cavity solves, N in
     {21, 31, ..., 101}, log-uniform Ra in [1e2, 1e5], n in {0.75, 1.0, 1.25}, Pr = 1, admitted
     against a device-memory budget, each solved to steady state (max|chi^{n+1} - chi^n|/dt and
     max|div V| below tol_steady, 1e-6) with the library's steady-solve rule, or to a step cap, in
     a pool. The first `saturation_requests` requests all present at t = 0 give the saturated
     rate; then (unless saturated_only) the first `requests` requests of the stream arrive at rho
-    times that rate. Solves/s and p50 / p99 arrival-to-completion times."""
+    times that rate. newtonian_only keeps the stream's n = 1 requests, in their order (the
+    power-law requests at low Ra need 10^5 steps and more to reach the stop). Solves/s and p50 /
+    p99 arrival-to-completion times."""
     from paper_2411_06563_gb300 import hosc as H, inputs, serve as S
     mode = {"graph": H.HOSC_POOL_GRAPH, "streams": H.HOSC_POOL_STREAMS,
             "persistent": H.HOSC_POOL_PERSISTENT}[args.pool_mode]
@@ -528,7 +530,8 @@ def serve_line(args, saturated_only=False):
     # a prefix of the configured stream of 2000 requests (the parameters of request q do not
     # depend on the rate, only its arrival time does)
     total = max(args.requests, args.saturation_requests, 2000)
-    base = inputs.request_stream(total, rate=1.0)
+    keep = (lambda r: r["n"] == 1.0) if newtonian_only else (lambda r: True)
+    base = [r for r in inputs.request_stream(total, rate=1.0) if keep(r)]
     sat_reqs = [dict(r, t=0.0) for r in base[:args.saturation_requests]]
     with S.Pool(budget, args.round_steps, mode, True) as pool:
         sres, sat = S.serve(sat_reqs, pool, make, max_steps)
@@ -537,7 +540,7 @@ def serve_line(args, saturated_only=False):
         res, summ, n_req, rho = sres, sat, len(sat_reqs), None
     else:
         rate = args.rho * sat["solves_per_s"]
-        stream = inputs.request_stream(total, rate=rate)[:args.requests]
+        stream = [r for r in inputs.request_stream(total, rate=rate) if keep(r)][:args.requests]
         with S.Pool(budget, args.round_steps, mode, True) as pool:
             res, summ = S.serve(stream, pool, make, max_steps)
             pst = pool.stats()
@@ -547,8 +550,9 @@ def serve_line(args, saturated_only=False):
            "ms_per_step": 1e3 / summ["solves_per_s"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
            "p50_s": summ["p50_s"], "p99_s": summ["p99_s"],
-           "seed_prefix": "the first %d requests of the seeded stream (arrival order)%s"
-                          % (n_req, ", all present at t = 0" if saturated_only else ""),
+           "seed_prefix": "the first %d %srequests of the seeded stream (arrival order)%s"
+                          % (n_req, "Newtonian (n = 1) " if newtonian_only else "",
+                             ", all present at t = 0" if saturated_only else ""),
            "config": {"workload": "Poisson stream of cavity solves, N in {21..101} step 10, Ra "
                                   "log-uniform [1e2,1e5], n in {0.75,1,1.25}, Pr=1, seed "
                                   "20241107, the library's steady-solve rule",
@@ -568,8 +572,8 @@ def serve_line(args, saturated_only=False):
 def _pool_blocks(args):
     """Bounded runs of the batching and serving workloads for the default line: the 64-cavity
     mix advanced 32 steps in rounds of 8 (after 3 warm-up rounds) against 4 of its cavities one
-    at a time, and the first `serve_block_requests` requests of the serving stream, all present
-    at t = 0, each solved to steady state."""
+    at a time, and the first `serve_block_requests` Newtonian requests of the serving stream, all
+    present at t = 0, each solved to steady state."""
     import types
     common = dict(pool_mode="graph", round_steps=8, budget_gb=64.0)
     t0 = time.perf_counter()
@@ -579,7 +583,7 @@ def _pool_blocks(args):
     s = serve_line(types.SimpleNamespace(requests=args.serve_block_requests,
                                          saturation_requests=args.serve_block_requests,
                                          rho=None, max_steps=300000, tol_steady=1e-6,
-                                         **common), saturated_only=True)
+                                         **common), saturated_only=True, newtonian_only=True)
     t2 = time.perf_counter()
     keep = ("metric", "value", "unit", "steps", "ms_per_step")
     batch = dict({k: b[k] for k in keep}, config=b["config"], one_at_a_time=b["one_at_a_time"],
@@ -711,6 +715,10 @@ def main():
     ap.add_argument("--tiles", default=None,
                     help="launch shape of the mixed-precision solve as BLOCK,KZ,NARROW "
                          "(instead of the autotuner)")
+    ap.add_argument("--tma-tiles", default=None,
+                    help="bulk-copy stencil kernels as ROWS,PLANES,STAGES (with --tiles)")
+    ap.add_argument("--xr-form", type=int, default=None, choices=[0, 1],
+                    help="x/r kernel: 0 column march, 1 flat stream (with --tiles)")
     ap.add_argument("--spinup", type=int, default=None,
                     help="untimed steps from rest before the warm-up (default: per workload)")
     ap.add_argument("--mode", default="step",
@@ -736,6 +744,8 @@ def main():
     ap.add_argument("--no-pool-blocks", action="store_true",
                     help="leave the bounded batch and serve blocks out of the default line")
     ap.add_argument("--serve-block-requests", type=int, default=6)
+    ap.add_argument("--newtonian-only", action="store_true",
+                    help="serve mode: keep the stream's n = 1 requests")
     ap.add_argument("--max-steps", type=int, default=1000)
     ap.add_argument("--tol-steady", type=float, default=1e-6)
     ap.add_argument("--budget-gb", type=float, default=64.0)
@@ -789,6 +799,12 @@ def main():
             kb, kz, nr = (int(x) for x in args.tiles.split(","))
             rc = H.hosc_set_tiles(cav.h, kb, kz, nr)
             assert rc == 0, ("launch shape", args.tiles, rc)
+            if args.tma_tiles:
+                ty, tz, ts = (int(x) for x in args.tma_tiles.split(","))
+                rc = H.hosc_set_tma_tiles(cav.h, ty, tz, ts)
+                assert rc == 0, ("bulk-copy shape", args.tma_tiles, rc)
+            if args.xr_form is not None:
+                assert H.hosc_set_xr_form(cav.h, args.xr_form) == 0
         elif precision == "mixed" and not args.no_autotune:
             rc, kb, kz, _ = H.hosc_autotune(cav.h, 5)
             assert rc == 0, rc
@@ -901,7 +917,7 @@ def main():
              if mixed else None,
              "stencil": dict(zip(("sx", "sy", "skz"), H.hosc_get_stencil_tiles(cav.h)[1:]))
              if mixed else None,
-             "tma": dict(zip(("rows", "planes"), H.hosc_get_tma_tiles(cav.h)[1:]))
+             "tma": dict(zip(("rows", "planes", "stages"), H.hosc_get_tma_tiles(cav.h)[1:]))
              if mixed else None,
              "xr": (("flat stream" if H.hosc_get_xr_form(cav.h) else "column march")
                     if mixed else None),

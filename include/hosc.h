@@ -304,18 +304,20 @@ hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz);
 
 /* Bulk-copy (TMA) stencil kernels of the mixed-precision solve: the p/v and s/t kernels with
  * their reads moved by the GPU's bulk-copy engine (tensor-map box copies of each z-plane into a
- * ring of three shared-memory stages, one producer thread, mbarrier completion), so that the
- * bytes in flight do not depend on registers or resident warps. A block owns tty rows of the
+ * ring of `stages` shared-memory stages, 3, 4, 6 or 8, stages - 2 planes ahead of the one being
+ * computed; one producer thread, mbarrier completion), so that the bytes in flight do not
+ * depend on registers or resident warps. A block owns tty rows of the
  * plane's interior columns (whole rows up to 126 columns; wider planes are cut into equal
  * pieces) and tkz consecutive planes (1..N-2). tty == 0 selects the register kernels (the
- * default); setting tiles here clears hosc_set_stencil_tiles and the reverse. HOSC_EINVAL for a
+ * default; tkz and stages are then ignored); setting tiles here clears hosc_set_stencil_tiles
+ * and the reverse. HOSC_EINVAL for a
  * shape that does not fit (at most 512 threads and 200 KB of shared memory per block, too many
  * blocks), HOSC_ECUDA when the driver cannot encode the tensor maps, HOSC_ESTATE mid-step.
  * Three-kernel iteration form only (the merged form keeps its own kernels). Changing it drops
  * the captured steps. A wait of these kernels that runs out (2 s) ends the step with HOSC_ECUDA
  * instead of hanging. */
-hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz);
-hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz);
+hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages);
+hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz, int* stages);
 
 /* Form of the mixed-precision x/r kernel (three-kernel iteration): flat = 0 (the default) the
  * column march of hosc_set_tiles; 1 one flat grid-stride stream over the interior planes (the
@@ -345,7 +347,8 @@ int hosc_get_krylov_merged(void* ctx);
  * at that shape and keep the faster; with the three-kernel form, then time the
  * staged p/v and s/t kernels (hosc_set_stencil_tiles) for tiles sx in {8, 16, ..., 64},
  * sy in {4, 8} and skz in 1..33 within 1.5x of their least modelled cost, and the bulk-copy
- * kernels (hosc_set_tma_tiles) for tty in 1..8 and tkz in 1..33 within 1.5x of theirs, and keep
+ * kernels (hosc_set_tma_tiles) for stages in {3, 4, 6, 8}, tty in 1..8 and tkz in 1..50 within
+ * 1.5x of their least modelled cost (waves times planes streamed over planes in flight), and keep
  * the fastest of the three kinds for p/v and s/t; then the two x/r forms (hosc_set_xr_form) with
  * 4 reps launches each, keeping the faster. Reports the register shape (any output pointer may be NULL;
  * ms_out = the three kernels' summed mean milliseconds with the chosen kernels). Mixed precision

@@ -73,7 +73,7 @@ struct Ctx {
   int merged = 0;                          // two-kernel BiCGSTAB iteration (mixed precision)
   int inner_last = 0;                      // inner pressure passes of the last step
   int sx = 0, sy = 0, skz = 0;             // staged stencil kernels (sx == 0: not used)
-  int tty = 0, tkz = 0;                    // bulk-copy stencil kernels (tty == 0: not used)
+  int tty = 0, tkz = 0, tstages = 3;       // bulk-copy stencil kernels (tty == 0: not used)
   int xr_flat = 0;                         // x/r as one flat stream (k8_xr)
   alignas(64) unsigned char tmap_host[kTmaMaps * kTmaMapBytes];   // their tensor maps
   // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
@@ -142,6 +142,7 @@ void apply_tiles(Ctx* c) {
   c->P.tty = c->tty;
   c->P.ttx = tma_tile_x(c->prm.N);
   c->P.tkz = c->tkz;
+  c->P.tstages = c->tstages;
   c->P.xr_flat = c->xr_flat;
 }
 
@@ -935,7 +936,8 @@ long ctx_signature(void* ctx) {
                  ((long)c->kblock << 3) | ((long)c->kz << 13) | ((long)c->narrow << 23) |
                  ((long)c->sx << 24) | ((long)c->sy << 32) | ((long)c->skz << 42) |
                  ((long)c->merged << 52);
-  return s ^ ((long)c->tty << 53) ^ ((long)c->tkz << 56) ^ ((long)c->xr_flat << 62);
+  return s ^ ((long)c->tty << 53) ^ ((long)c->tkz << 56) ^ ((long)c->xr_flat << 62) ^
+         ((long)c->tstages << 45);
 }
 
 // Start of a round of n steps from the current level (read back by ctx_collect_round).
@@ -1587,19 +1589,21 @@ hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
   return HOSC_OK;
 }
 
-hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz) {
+hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
   if (c->stage != 0) return HOSC_ESTATE;
   CU(cudaSetDevice(c->device));
   if (tty == 0) {
     tkz = 0;
+    stages = 3;
   } else {
-    if (!tma_tiles_valid(c->prm.N, tty, tkz)) return HOSC_EINVAL;
+    if (!tma_tiles_valid(c->prm.N, tty, tkz, stages)) return HOSC_EINVAL;
     DevParams P = c->P;
     P.tty = tty;
     P.ttx = tma_tile_x(c->prm.N);
     P.tkz = tkz;
+    P.tstages = stages;
     if (krylov4_blocks(P) * (P.merged ? 2 : 1) > red_rows((long)c->prm.N * c->prm.N * c->prm.N))
       return HOSC_EINVAL;
     if (!tma_prepare(P, c->F, c->tmap_host)) {
@@ -1608,9 +1612,10 @@ hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz) {
       return HOSC_ECUDA;
     }
   }
-  if (tty != c->tty || tkz != c->tkz || (tty > 0 && c->sx > 0)) {
+  if (tty != c->tty || tkz != c->tkz || stages != c->tstages || (tty > 0 && c->sx > 0)) {
     c->tty = tty;
     c->tkz = tkz;
+    c->tstages = stages;
     if (tty > 0) c->sx = c->sy = c->skz = 0;
     apply_tiles(c);
     drop_graphs(c);
@@ -1635,11 +1640,12 @@ int hosc_get_xr_form(void* ctx) {
   return c ? c->xr_flat : -1;
 }
 
-hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz) {
+hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz, int* stages) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
   if (tty) *tty = c->tty;
   if (tkz) *tkz = c->tkz;
+  if (stages) *stages = c->tstages;
   return HOSC_OK;
 }
 
@@ -1692,7 +1698,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   CU(cudaSetDevice(c->device));
   {   // the register kernels first
     hosc_status s0 = hosc_set_stencil_tiles(c, 0, 0, 0);
-    if (!s0) s0 = hosc_set_tma_tiles(c, 0, 0);
+    if (!s0) s0 = hosc_set_tma_tiles(c, 0, 0, 3);
     if (!s0) s0 = hosc_set_xr_form(c, 0);
     if (s0) return s0;
   }
@@ -1781,7 +1787,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   }
   if (c->merged) {   // the staged kernels implement the three-kernel form only
     st = hosc_set_stencil_tiles(c, 0, 0, 0);
-    if (!st) st = hosc_set_tma_tiles(c, 0, 0);
+    if (!st) st = hosc_set_tma_tiles(c, 0, 0, 3);
     if (!st) st = hosc_set_xr_form(c, 0);
     if (st) return st;
     if (kblock_out) *kblock_out = best_b;
@@ -1846,22 +1852,27 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   // Bulk-copy (TMA) stencil kernels: tiles of whole interior rows (tty rows) and tkz planes
   // within 1.5x of their least modelled cost.
   double best_tma = INFINITY;
-  int bty = 0, btkz = 0;
+  int bty = 0, btkz = 0, bts = 3;
   {
     const int N = c->prm.N;
     const long rows = red_rows((long)N * N * N);
+    static const int ring[] = {3, 4, 6, 8};
     double best_tmodel = 1e300;
-    for (int ty = 1; ty <= 8; ++ty)
-      for (int z = 1; z <= 33; ++z) best_tmodel = fmin(best_tmodel, tma_wave_cost(N, ty, z, sms));
+    for (int ts : ring)
+      for (int ty = 1; ty <= 8; ++ty)
+        for (int z = 1; z <= 50; ++z)
+          best_tmodel = fmin(best_tmodel, tma_wave_cost(N, ty, z, ts, sms));
     const DevParams saved = c->P;
+    for (int ts : ring)
     for (int ty = 1; ty <= 8 && !st && best_tmodel < 1e299; ++ty) {
-      for (int z = 1; z <= 33 && !st; ++z) {
-        if (tma_wave_cost(N, ty, z, sms) > 1.5 * best_tmodel) continue;
+      for (int z = 1; z <= 50 && !st; ++z) {
+        if (tma_wave_cost(N, ty, z, ts, sms) > 1.5 * best_tmodel) continue;
         DevParams trial = saved;
         trial.sx = 0;
         trial.tty = ty;
         trial.ttx = tma_tile_x(N);
         trial.tkz = z;
+        trial.tstages = ts;
         if (krylov4_blocks(trial) > rows) continue;
         if (!tma_prepare(trial, c->F, c->tmap_host)) {
           best_tmodel = 1e300;   // no tensor maps on this driver: keep the other kernels
@@ -1878,6 +1889,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
           best_tma = tot;
           bty = ty;
           btkz = z;
+          bts = ts;
         }
       }
     }
@@ -1885,7 +1897,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   }
   if (st) return st;
   if (best_tma < reg_pvst && best_tma < best_staged) {
-    st = hosc_set_tma_tiles(c, bty, btkz);
+    st = hosc_set_tma_tiles(c, bty, btkz, bts);
     best += best_tma - reg_pvst;
   } else if (best_staged < reg_pvst) {
     st = hosc_set_stencil_tiles(c, bsx, bsy, bskz);

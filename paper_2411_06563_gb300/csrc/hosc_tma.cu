@@ -4,8 +4,8 @@
 // apply_op), with their reads moved by the bulk-copy engine instead of load instructions.
 //
 // A block owns a tile of ttx * tty interior (i, j) columns and a segment of tkz planes. One
-// producer thread (the block's last warp) streams the planes of the segment, one ahead of the
-// plane being computed, into a ring of kTmaStages shared-memory stages: per plane the haloed
+// producer thread (the block's last warp) streams the planes of the segment, S - 2 ahead of the
+// plane being computed, into a ring of S shared-memory stages (S = 3, 4, 6 or 8): per plane the haloed
 // (ttx + 2) x (tty + 2) box of each stencil vector and the tile boxes of the compact operators
 // (and r_0) by tensor-map copies (cp.async.bulk.tensor over 8-byte elements, so that each box row
 // is one contiguous run; zero fill outside the grid), and the
@@ -25,7 +25,6 @@ namespace hosc {
 
 namespace {
 
-constexpr int kTmaStages = 3;
 constexpr int kTmaMaxThreads = 512;
 constexpr unsigned long long kTmaWaitNs = 2000000000ull;   // 2 s
 enum { kMapR = 0, kMapR0 = 1, kMapP0 = 2, kMapV0 = 4, kMapWM = 6, kMapWE = 7 };
@@ -69,8 +68,8 @@ __host__ __device__ inline int tma_consumers(int tx, int ty) { return tx * ty; }
 __host__ __device__ inline int tma_threads(int tx, int ty) {
   return ((tma_consumers(tx, ty) + 31) / 32 + 1) * 32;   // consumer warps + the producer warp
 }
-inline size_t tma_smem(int tx, int ty, bool pv) {
-  return (size_t)kTmaStages * tma_layout(tx, ty, pv).stage + 128;   // + alignment slack
+inline size_t tma_smem(int tx, int ty, bool pv, int stages) {
+  return (size_t)stages * tma_layout(tx, ty, pv).stage + 128;   // + alignment slack
 }
 
 // ------------------------------------------------------------------ PTX wrappers
@@ -148,11 +147,10 @@ struct TmaMaps {
   CUtensorMap m[kTmaMaps];
 };
 
-template <bool PV>
+template <bool PV, int S>
 __global__ void __launch_bounds__(kTmaMaxThreads)
     k7_stencil(DevParams P, Fields F, int pp, const __grid_constant__ TmaMaps tm) {
   constexpr int M = PV ? 4 : 8;
-  constexpr int S = kTmaStages;
   extern __shared__ unsigned char tdyn[];
   __shared__ double smem[32 * 8];
   __shared__ Scal4 sc;
@@ -360,18 +358,32 @@ bool encode_vec(CUtensorMap* m, const float4* a, int N, int bw, int bh) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The instantiations: ring depths of 3, 4, 6 and 8 stages (planes 1, 2, 4 and 6 ahead).
+template <bool PV>
+const void* k7_fn(int stages) {
+  switch (stages) {
+    case 3: return (const void*)k7_stencil<PV, 3>;
+    case 4: return (const void*)k7_stencil<PV, 4>;
+    case 6: return (const void*)k7_stencil<PV, 6>;
+    case 8: return (const void*)k7_stencil<PV, 8>;
+    default: return nullptr;
+  }
+}
+
 bool tma_attrs_ready() {
   static int done[64] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
   if (!done[dev]) {
     const int cap = 200 * 1024;
-    if (cudaFuncSetAttribute(k7_stencil<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, cap) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k7_stencil<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             cap) != cudaSuccess) {
-      cudaGetLastError();
-      return false;
+    for (int st : {3, 4, 6, 8}) {
+      if (cudaFuncSetAttribute(k7_fn<true>(st), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               cap) != cudaSuccess ||
+          cudaFuncSetAttribute(k7_fn<false>(st), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+      }
     }
     done[dev] = 1;
   }
@@ -383,12 +395,12 @@ dim3 tma_grid(const DevParams& P) {
   return dim3((ni + P.ttx - 1) / P.ttx, (ni + P.tty - 1) / P.tty, (ni + P.tkz - 1) / P.tkz);
 }
 
-template <bool PV>
+template <bool PV, int S>
 void launch_k7(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = tma_grid(P);
   cfg.blockDim = dim3(tma_threads(P.ttx, P.tty));
-  cfg.dynamicSmemBytes = tma_smem(P.ttx, P.tty, PV);
+  cfg.dynamicSmemBytes = tma_smem(P.ttx, P.tty, PV, S);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -397,7 +409,17 @@ void launch_k7(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
   cfg.numAttrs = 1;
   TmaMaps tm;
   memcpy(&tm, F.tmaps_host, sizeof(tm));
-  cudaLaunchKernelEx(&cfg, k7_stencil<PV>, P, F, pp, tm);
+  cudaLaunchKernelEx(&cfg, k7_stencil<PV, S>, P, F, pp, tm);
+}
+
+template <bool PV>
+void launch_k7(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
+  switch (P.tstages) {
+    case 4: launch_k7<PV, 4>(P, F, pp, s); break;
+    case 6: launch_k7<PV, 6>(P, F, pp, s); break;
+    case 8: launch_k7<PV, 8>(P, F, pp, s); break;
+    default: launch_k7<PV, 3>(P, F, pp, s); break;
+  }
 }
 
 }  // namespace
@@ -409,11 +431,12 @@ int tma_tile_x(int N) {
   return (ni + parts - 1) / parts;
 }
 
-bool tma_tiles_valid(int N, int tty, int tkz) {
+bool tma_tiles_valid(int N, int tty, int tkz, int stages) {
   const int ni = N - 2, tx = tma_tile_x(N);
   if (tty < 1 || tty > ni || tkz < 1 || tkz > ni) return false;
+  if (stages != 3 && stages != 4 && stages != 6 && stages != 8) return false;
   if (tma_threads(tx, tty) > kTmaMaxThreads) return false;
-  if (tma_smem(tx, tty, true) > 200 * 1024) return false;
+  if (tma_smem(tx, tty, true, stages) > 200 * 1024) return false;
   if (tty + 2 > 256) return false;
   const long nb = (long)((ni + tx - 1) / tx) * ((ni + tty - 1) / tty) * ((ni + tkz - 1) / tkz);
   const long n3 = (long)N * N * N;
@@ -442,12 +465,14 @@ bool tma_prepare(const DevParams& P, const Fields& F, void* host) {
   return ok;
 }
 
-double tma_wave_cost(int N, int tty, int tkz, int sms) {
-  if (!tma_tiles_valid(N, tty, tkz) || !tma_attrs_ready()) return 1e300;
+double tma_wave_cost(int N, int tty, int tkz, int stages, int sms) {
+  if (!tma_tiles_valid(N, tty, tkz, stages) || !tma_attrs_ready()) return 1e300;
   const int tx = tma_tile_x(N), ni = N - 2;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k7_stencil<true>, tma_threads(tx, tty),
-                                                    tma_smem(tx, tty, true)) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k7_fn<true>(stages),
+                                                    tma_threads(tx, tty),
+                                                    tma_smem(tx, tty, true, stages)) !=
+          cudaSuccess ||
       occ < 1) {
     cudaGetLastError();
     return 1e300;
@@ -455,7 +480,8 @@ double tma_wave_cost(int N, int tty, int tkz, int sms) {
   const long items = (long)((ni + tx - 1) / tx) * ((ni + tty - 1) / tty) * ((ni + tkz - 1) / tkz);
   const long slots = (long)occ * sms;
   const long waves = (items + slots - 1) / slots;
-  return (double)waves * (tkz + 2);
+  // a block streams tkz + 2 planes, stages - 2 of them ahead of the one it computes
+  return (double)waves * (tkz + 2) / (double)(stages - 2);
 }
 
 void launch_tma_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {

@@ -139,8 +139,9 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int),
                                           ctypes.POINTER(ctypes.c_int)]),
         "hosc_set_stencil_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
-        "hosc_set_tma_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+        "hosc_set_tma_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "hosc_get_tma_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int),
                                               ctypes.POINTER(ctypes.c_int)]),
         "hosc_set_xr_form": (ctypes.c_int, [_P, ctypes.c_int]),
         "hosc_get_xr_form": (ctypes.c_int, [_P]),
@@ -333,14 +334,14 @@ def hosc_set_stencil_tiles(h, sx, sy, skz):
     return lib().hosc_set_stencil_tiles(h, int(sx), int(sy), int(skz))
 
 
-def hosc_set_tma_tiles(h, tty, tkz):
-    return lib().hosc_set_tma_tiles(h, int(tty), int(tkz))
+def hosc_set_tma_tiles(h, tty, tkz, stages=3):
+    return lib().hosc_set_tma_tiles(h, int(tty), int(tkz), int(stages))
 
 
 def hosc_get_tma_tiles(h):
-    a, b = ctypes.c_int(), ctypes.c_int()
-    st = lib().hosc_get_tma_tiles(h, ctypes.byref(a), ctypes.byref(b))
-    return st, a.value, b.value
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    st = lib().hosc_get_tma_tiles(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return st, a.value, b.value, c.value
 
 
 def hosc_set_xr_form(h, flat):
