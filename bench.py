@@ -635,15 +635,17 @@ if int(z["hist"]):
     prev = {k: z["prev_" + k] for k in ("L", "u", "v", "w", "Eu", "Ev", "Ew")}
 st = dict(u=z["u"], v=z["v"], w=z["w"], th=z["th"], p=z["p"], steps=0, prev=prev)
 g = O.Grid(prm.N)
+k = int(sys.argv[3]) if len(sys.argv) > 3 else 1
 t0 = time.perf_counter()
-O.step(st, prm, g)
-print(time.perf_counter() - t0)
+for _ in range(k):
+    st, _info = O.step(st, prm, g)
+print((time.perf_counter() - t0) / k)
 """
 
 
-def _one_thread_step(st, prm, path):
-    """Wall time of one oracle step of the same state in a child process held to one thread
-    (OMP, OpenBLAS and MKL thread pools of numpy and scipy set to 1)."""
+def _one_thread_step(st, prm, path, steps=1):
+    """Wall time per oracle step (mean over `steps` steps from the same state) in a child process
+    held to one thread (OMP, OpenBLAS and MKL thread pools of numpy and scipy set to 1)."""
     arrays = {k: st[k] for k in ("u", "v", "w", "th", "p")}
     hist = st.get("prev") is not None
     if hist:
@@ -652,8 +654,8 @@ def _one_thread_step(st, prm, path):
     np.savez(path, N=prm.N, Ra=prm.Ra, Pr=prm.Pr, n=prm.n, dt=prm.dt, lam=prm.lam,
              tol=prm.tol_lin, hist=int(hist), **arrays)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    out = subprocess.run([sys.executable, "-c", _ONE_THREAD_STEP, ROOT, path], env=env,
-                         capture_output=True, text=True, timeout=600)
+    out = subprocess.run([sys.executable, "-c", _ONE_THREAD_STEP, ROOT, path, str(steps)],
+                         env=env, capture_output=True, text=True, timeout=600)
     if out.returncode != 0:
         return None
     return float(out.stdout.strip().splitlines()[-1])
@@ -693,9 +695,43 @@ def cpu_baseline(cav, H, wl):
     out = {"value": (N - 2) ** 3 / dt, "unit": "GPUPS", "cores": cores, "kind": "oracle",
            "sample": "1 oracle step of the %d^3 workload from the GPU state (%.1f s)" % (N, dt),
            "one_thread": ({"value": (N - 2) ** 3 / dt1, "unit": "GPUPS", "cores": 1,
-                           "seconds": dt1} if dt1 else None)}
+                           "seconds": dt1} if dt1 else None),
+           "by_config": _oracle_config_timings(H)}
     out.update(_host())
     return out
+
+
+def _oracle_config_timings(H, steps=3):
+    """The oracle on the other single-cavity configurations: the Newtonian 21^3 cavity (Ra = 1e3)
+    and the 41^3 power-law cavities (Ra = 1e4, n = 0.75 and 1.25), each from a seeded developed
+    state at the steady-solve rule's step, `steps` steps with numpy's threads and on one thread."""
+    from oracle import hosc_oracle as O
+    from paper_2411_06563_gb300 import inputs
+    rows = {}
+    for name, N, Ra, n in (("C1 21^3 n=1 Ra=1e3", 21, 1e3, 1.0),
+                           ("C2 41^3 n=0.75 Ra=1e4", 41, 1e4, 0.75),
+                           ("C2 41^3 n=1.25 Ra=1e4", 41, 1e4, 1.25)):
+        p = H.hosc_steady_params(N, Ra, 1.0, n)
+        prm = O.Params(N=N, Ra=Ra, Pr=1.0, n=n, dt=p.dt, lam=p.lambda_, tol_lin=1e-12,
+                       tol_div=p.tol_div, use_history=0)
+        st = dict(inputs.cavity_state(N, Ra, seed=2024), steps=0, prev=None)
+        g = O.Grid(N)
+        s0, c0 = time.perf_counter(), time.process_time()
+        cur = st
+        for _ in range(steps):
+            cur, _ = O.step(cur, prm, g)
+        wall = (time.perf_counter() - s0) / steps
+        cores = _cores_used(time.process_time() - c0, wall * steps)
+        fd, path = tempfile.mkstemp(suffix=".npz")
+        os.close(fd)
+        try:
+            one = _one_thread_step(st, prm, path, steps)
+        finally:
+            os.unlink(path)
+        rows[name] = {"GPUPS": (N - 2) ** 3 / wall, "cores": cores,
+                      "one_thread_GPUPS": (N - 2) ** 3 / one if one else None,
+                      "steps": steps}
+    return rows
 
 
 def main():

@@ -1582,7 +1582,10 @@ hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
     c->sx = sx;
     c->sy = sy;
     c->skz = skz;
-    if (sx > 0) c->tty = c->tkz = 0;   // one kind of stencil kernel at a time
+    if (sx > 0) {   // one kind of stencil kernel at a time
+      c->tty = c->tkz = 0;
+      c->tstages = 3;
+    }
     apply_tiles(c);
     drop_graphs(c);
   }

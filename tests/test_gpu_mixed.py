@@ -176,7 +176,7 @@ def test_tma_stencil_kernels(tma):
         assert np.max(np.abs(got[name] - ref[name])) <= 1e-5 * scale, (name, tma)
 
 
-@pytest.mark.parametrize("N,tma", [(19, None), (19, (2, 5)), (12, None), (31, (3, 7))])
+@pytest.mark.parametrize("N,tma", [(19, None), (19, (2, 5, 4)), (12, None), (31, (3, 7, 6))])
 def test_flat_xr_kernel(N, tma):
     """The flat x/r stream (every node of the interior planes, walls included) computes what the
     column march computes, alone and with the bulk-copy stencil kernels: the increment equals the
