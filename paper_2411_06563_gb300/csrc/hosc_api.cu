@@ -74,6 +74,7 @@ struct Ctx {
   int inner_last = 0;                      // inner pressure passes of the last step
   int sx = 0, sy = 0, skz = 0;             // staged stencil kernels (sx == 0: not used)
   int tty = 0, tkz = 0, tstages = 3;       // bulk-copy stencil kernels (tty == 0: not used)
+  int tkernels = 3;                        // which of them run (1 p/v, 2 s/t, 3 both)
   int xr_flat = 0;                         // x/r as one flat stream (k8_xr)
   alignas(64) unsigned char tmap_host[kTmaMaps * kTmaMapBytes];   // their tensor maps
   // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
@@ -143,6 +144,7 @@ void apply_tiles(Ctx* c) {
   c->P.ttx = tma_tile_x(c->prm.N);
   c->P.tkz = c->tkz;
   c->P.tstages = c->tstages;
+  c->P.tkernels = c->tkernels;
   c->P.xr_flat = c->xr_flat;
 }
 
@@ -937,7 +939,7 @@ long ctx_signature(void* ctx) {
                  ((long)c->sx << 24) | ((long)c->sy << 32) | ((long)c->skz << 42) |
                  ((long)c->merged << 52);
   return s ^ ((long)c->tty << 53) ^ ((long)c->tkz << 56) ^ ((long)c->xr_flat << 62) ^
-         ((long)c->tstages << 45);
+         ((long)c->tstages << 45) ^ ((long)c->tkernels << 48);
 }
 
 // Start of a round of n steps from the current level (read back by ctx_collect_round).
@@ -1585,6 +1587,7 @@ hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
     if (sx > 0) {   // one kind of stencil kernel at a time
       c->tty = c->tkz = 0;
       c->tstages = 3;
+      c->tkernels = 3;
     }
     apply_tiles(c);
     drop_graphs(c);
@@ -1592,7 +1595,7 @@ hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
   return HOSC_OK;
 }
 
-hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages) {
+hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages, int kernels) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
   if (c->stage != 0) return HOSC_ESTATE;
@@ -1600,7 +1603,9 @@ hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages) {
   if (tty == 0) {
     tkz = 0;
     stages = 3;
+    kernels = 3;
   } else {
+    if (kernels < 1 || kernels > 3) return HOSC_EINVAL;
     if (!tma_tiles_valid(c->prm.N, tty, tkz, stages)) return HOSC_EINVAL;
     DevParams P = c->P;
     P.tty = tty;
@@ -1615,10 +1620,12 @@ hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages) {
       return HOSC_ECUDA;
     }
   }
-  if (tty != c->tty || tkz != c->tkz || stages != c->tstages || (tty > 0 && c->sx > 0)) {
+  if (tty != c->tty || tkz != c->tkz || stages != c->tstages || kernels != c->tkernels ||
+      (tty > 0 && c->sx > 0)) {
     c->tty = tty;
     c->tkz = tkz;
     c->tstages = stages;
+    c->tkernels = kernels;
     if (tty > 0) c->sx = c->sy = c->skz = 0;
     apply_tiles(c);
     drop_graphs(c);
@@ -1643,12 +1650,13 @@ int hosc_get_xr_form(void* ctx) {
   return c ? c->xr_flat : -1;
 }
 
-hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz, int* stages) {
+hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz, int* stages, int* kernels) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
   if (tty) *tty = c->tty;
   if (tkz) *tkz = c->tkz;
   if (stages) *stages = c->tstages;
+  if (kernels) *kernels = c->tkernels;
   return HOSC_OK;
 }
 
@@ -1701,7 +1709,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   CU(cudaSetDevice(c->device));
   {   // the register kernels first
     hosc_status s0 = hosc_set_stencil_tiles(c, 0, 0, 0);
-    if (!s0) s0 = hosc_set_tma_tiles(c, 0, 0, 3);
+    if (!s0) s0 = hosc_set_tma_tiles(c, 0, 0, 3, 3);
     if (!s0) s0 = hosc_set_xr_form(c, 0);
     if (s0) return s0;
   }
@@ -1790,7 +1798,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   }
   if (c->merged) {   // the staged kernels implement the three-kernel form only
     st = hosc_set_stencil_tiles(c, 0, 0, 0);
-    if (!st) st = hosc_set_tma_tiles(c, 0, 0, 3);
+    if (!st) st = hosc_set_tma_tiles(c, 0, 0, 3, 3);
     if (!st) st = hosc_set_xr_form(c, 0);
     if (st) return st;
     if (kblock_out) *kblock_out = best_b;
@@ -1799,7 +1807,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
     return HOSC_OK;
   }
   // Staged stencil kernels for p/v and s/t: against the register kernels at the shape found.
-  double reg_pvst = 0.0;
+  double reg_pvst = 0.0, reg_k[2] = {0.0, 0.0};
   {
     const int ssx = c->sx, ssy = c->sy, sskz = c->skz;
     c->P.sx = 0;
@@ -1807,6 +1815,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
       double ms = 0.0;
       st = time_class(c, kid, reps, &ms);
       reg_pvst += ms;
+      reg_k[kid - HOSC_K_BICG_PV] = ms;
     }
     c->P.sx = ssx;
     c->P.sy = ssy;
@@ -1853,9 +1862,10 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   c->P.skz = sskz;
   if (st) return st;
   // Bulk-copy (TMA) stencil kernels: tiles of whole interior rows (tty rows) and tkz planes
-  // within 1.5x of their least modelled cost.
-  double best_tma = INFINITY;
-  int bty = 0, btkz = 0, bts = 3;
+  // within 1.5x of their least modelled cost; the pair at its best shape, and the p/v kernel
+  // alone at its best shape beside the register s/t.
+  double best_tma = INFINITY, best_tpv = INFINITY;
+  int bty = 0, btkz = 0, bts = 3, pty = 0, ptkz = 0, pts = 3;
   {
     const int N = c->prm.N;
     const long rows = red_rows((long)N * N * N);
@@ -1881,12 +1891,14 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
           best_tmodel = 1e300;   // no tensor maps on this driver: keep the other kernels
           break;
         }
+        trial.tkernels = 3;
         c->P = trial;
-        double tot = 0.0;
+        double tot = 0.0, pv = 0.0;
         for (int kid = HOSC_K_BICG_PV; kid <= HOSC_K_BICG_ST && !st; ++kid) {
           double ms = 0.0;
           st = time_class(c, kid, reps, &ms);
           tot += ms;
+          if (kid == HOSC_K_BICG_PV) pv = ms;
         }
         if (!st && tot < best_tma) {
           best_tma = tot;
@@ -1894,13 +1906,23 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
           btkz = z;
           bts = ts;
         }
+        if (!st && pv < best_tpv) {
+          best_tpv = pv;
+          pty = ty;
+          ptkz = z;
+          pts = ts;
+        }
       }
     }
     c->P = saved;
   }
   if (st) return st;
-  if (best_tma < reg_pvst && best_tma < best_staged) {
-    st = hosc_set_tma_tiles(c, bty, btkz, bts);
+  const double tma_pv_reg_st = best_tpv + reg_k[1];
+  if (tma_pv_reg_st < best_tma && tma_pv_reg_st < reg_pvst && tma_pv_reg_st < best_staged) {
+    st = hosc_set_tma_tiles(c, pty, ptkz, pts, 1);
+    best += tma_pv_reg_st - reg_pvst;
+  } else if (best_tma < reg_pvst && best_tma < best_staged) {
+    st = hosc_set_tma_tiles(c, bty, btkz, bts, 3);
     best += best_tma - reg_pvst;
   } else if (best_staged < reg_pvst) {
     st = hosc_set_stencil_tiles(c, bsx, bsy, bskz);

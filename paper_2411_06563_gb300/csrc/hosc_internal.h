@@ -34,6 +34,7 @@ struct DevParams {
   int tty, ttx, tkz; // bulk-copy (TMA) stencil kernels (p/v and s/t): tile of ttx * tty interior
                      // columns, tkz planes per block; tty == 0: not used
   int tstages;       // their ring of shared-memory stages (3, 4, 6 or 8)
+  int tkernels;      // which of them run: 1 p/v, 2 s/t, 3 both
   int xr_flat;       // x/r as one flat grid-stride stream (k8_xr) instead of the column march
   double h, h2;      // grid spacing along x and its square
   double Ly, Lz;     // box 1 x Ly x Lz: lengths along y and z (1 for the cube)

@@ -1204,7 +1204,7 @@ void launch_bicg_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
     else k6_a<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
     return;
   }
-  if (P.krylov_fp32 && P.tty > 0) {
+  if (P.krylov_fp32 && P.tty > 0 && (P.tkernels & 1)) {
     launch_tma_pv(P, F, pp, s);
     return;
   }
@@ -1227,7 +1227,7 @@ void launch_bicg_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s)
     else k6_b<2><<<grid4(P), P.kblock, 0, s>>>(P, F, pp);
     return;
   }
-  if (P.krylov_fp32 && P.tty > 0) {
+  if (P.krylov_fp32 && P.tty > 0 && (P.tkernels & 2)) {
     launch_tma_st(P, F, pp, s);
     return;
   }

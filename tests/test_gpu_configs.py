@@ -117,13 +117,15 @@ def _increment_residuals(st0, got, op):
 @pytest.mark.parametrize("precision,phase,shape", [(H.HOSC_FP64, 0, None),
                                                    (H.HOSC_MIXED, 0, "autotuned"),
                                                    (H.HOSC_MIXED, 1, "autotuned"),
-                                                   (H.HOSC_MIXED, 1, (2, 17, 6))])
+                                                   (H.HOSC_MIXED, 1, (2, 33, 6, 1)),
+                                                   (H.HOSC_MIXED, 0, (2, 17, 4, 3))])
 def test_benched_cavity_101_one_step(step101, precision, phase, shape):
     """One step of the benched cavity from a seeded developed state against the oracle's step:
     FP64 fields within 1e-10; mixed precision at the autotuner's launch shape for this grid (the
-    one the benchmark times) and with the bulk-copy stencil kernels forced (2 rows x 17 planes per
-    block, a ring of six stages), within the FP32 solve's tolerance and, with FP64 sweeps, by
-    residual in the oracle's system."""
+    one the benchmark times) and with the bulk-copy stencil kernels forced (p/v alone, 2 rows x
+    33 planes per block in a ring of six stages; both, 2 rows x 17 planes in a ring of four),
+    within the FP32 solve's tolerance and, with FP64 sweeps, by residual in the oracle's
+    system."""
     st0, ref, oinfo = step101
     tol_lin = 1e-12 if precision == H.HOSC_FP64 else 1e-10
     p = _params(N101, RA101, N_IDX101, DT101, LAM101, precision, tol_lin)
