@@ -57,6 +57,10 @@ NCU_TRAFFIC = {
     # profiles/k4_pv_cavity101_mixed.md, "In-step DRAM traffic" (40 launches each)
     ("cavity101", "k_bicg_pv", ("register", 256, 9, 0)): 105.0e6,
     ("cavity101", "k_bicg_pv", ("register", 384, 9, 0)): 104.7e6,
+    # profiles/k7_pv_bulk_copy_cavity101_mixed.md (50 in-step launches each)
+    ("cavity101", "k_bicg_pv", ("bulk-copy", 2, 33, 6)): 96.2e6,
+    ("cavity101", "k_bicg_st", ("register", 384, 9, 0)): 57.3e6,
+    ("cavity101", "k_bicg_xr", ("flat",)): 98.7e6,
 }
 
 

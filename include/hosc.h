@@ -353,9 +353,10 @@ int hosc_get_krylov_merged(void* ctx);
  * 1.5x of their least modelled cost (waves times planes streamed over planes in flight), and keep
  * the fastest of: both register, both staged, both bulk-copy at their best shape, bulk-copy p/v
  * at its best shape with the register s/t; then the two x/r forms (hosc_set_xr_form) with
- * 4 reps launches each, keeping the faster. Reports the register shape (any output pointer may be NULL;
- * ms_out = the three kernels' summed mean milliseconds with the chosen kernels). Mixed precision
- * only (HOSC_EINVAL for FP64). The fields keep their values. */
+ * 4 reps launches each, keeping the flat stream only when it is at least 5 % faster. Reports
+ * the register shape (any output pointer may be NULL; ms_out = the three kernels' summed mean
+ * milliseconds with the chosen kernels). Mixed precision only (HOSC_EINVAL for FP64). The fields
+ * keep their values. */
 hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, double* ms_out);
 
 /* Kernel classes for hosc_profile_read and hosc_time_kernel. */

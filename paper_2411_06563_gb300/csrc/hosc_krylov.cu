@@ -1106,7 +1106,8 @@ void launch_bicg_init(const DevParams& P, const Fields& F, cudaStream_t s) {
 }
 
 // x/r as one flat stream: every node of the interior planes, the i and j walls included (every
-// vector is zero there: k4_init zeroes t and r_0 on the walls), in a grid-stride loop that
+// vector is zero there: the workspace is zeroed at creation, k4_init zeroes x, r, p and v
+// everywhere, and no kernel writes the wall entries of t or r_0), in a grid-stride loop that
 // issues the loads of U nodes before their arithmetic, so that a thread keeps 6 U float4 loads in
 // flight. Same arithmetic and float-float partials as k4_xr; one block partial per block.
 template <int U>

@@ -238,12 +238,10 @@ __device__ __forceinline__ bool k4_init_body(const DevParams& P, const Fields& F
     const bool inner = i > 0 && j > 0 && k > 0 && i < N - 1 && j < N - 1 && k < N - 1;
     const float4 z = f4(0.f);
     const float4 r = inner ? F.kr0[c] : z;
-    if (!inner) {   // t and r_0 zero on the walls: the flat x/r kernel streams wall nodes too
-      F.kt[c] = z;
-      F.kr0[c] = z;
-    }
     F.kr[c] = r;
-    F.kx[c] = z;   // t inside needs no zeros: k4_st writes it before k4_xr reads it
+    // t needs no zeros: inside, k4_st writes it before k4_xr reads it; its wall entries (and those
+    // of r_0) are zero from the workspace's zeroing at creation, and no kernel writes them
+    F.kx[c] = z;
     F.kp[0][c] = z;
     F.kp[1][c] = z;
     F.kv[0][c] = z;
