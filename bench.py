@@ -70,8 +70,7 @@ def _kernel_shape(kernel, shape):
     reg = ("register", t["block"], t["kz"], t["narrow"])
     if kernel in ("k_bicg_pv", "k_bicg_st"):
         if m["rows"] and m["kernels"] & (1 if kernel == "k_bicg_pv" else 2):
-            return ("bulk-copy", m["rows"], m["planes"], m["stages"]) + (
-                (m["nodes"],) if m["nodes"] != 1 else ())
+            return ("bulk-copy", m["rows"], m["planes"], m["stages"])
         if s["sx"]:
             return ("staged", s["sx"], s["sy"], s["skz"])
         return reg
@@ -757,8 +756,8 @@ def main():
                     help="launch shape of the mixed-precision solve as BLOCK,KZ,NARROW "
                          "(instead of the autotuner)")
     ap.add_argument("--tma-tiles", default=None,
-                    help="bulk-copy stencil kernels as ROWS,PLANES,STAGES,KERNELS[,NODES] (with "
-                         "--tiles; KERNELS 1 p/v, 2 s/t, 3 both; NODES per computing thread)")
+                    help="bulk-copy stencil kernels as ROWS,PLANES,STAGES,KERNELS (with --tiles; "
+                         "KERNELS 1 p/v, 2 s/t, 3 both)")
     ap.add_argument("--xr-form", type=int, default=None, choices=[0, 1],
                     help="x/r kernel: 0 column march, 1 flat stream (with --tiles)")
     ap.add_argument("--spinup", type=int, default=None,
@@ -842,8 +841,8 @@ def main():
             rc = H.hosc_set_tiles(cav.h, kb, kz, nr)
             assert rc == 0, ("launch shape", args.tiles, rc)
             if args.tma_tiles:
-                vals = [int(x) for x in args.tma_tiles.split(",")]
-                rc = H.hosc_set_tma_tiles(cav.h, *vals)
+                ty, tz, ts, tk = (int(x) for x in args.tma_tiles.split(","))
+                rc = H.hosc_set_tma_tiles(cav.h, ty, tz, ts, tk)
                 assert rc == 0, ("bulk-copy shape", args.tma_tiles, rc)
             if args.xr_form is not None:
                 assert H.hosc_set_xr_form(cav.h, args.xr_form) == 0
@@ -959,7 +958,7 @@ def main():
              if mixed else None,
              "stencil": dict(zip(("sx", "sy", "skz"), H.hosc_get_stencil_tiles(cav.h)[1:]))
              if mixed else None,
-             "tma": dict(zip(("rows", "planes", "stages", "kernels", "nodes"),
+             "tma": dict(zip(("rows", "planes", "stages", "kernels"),
                              H.hosc_get_tma_tiles(cav.h)[1:]))
              if mixed else None,
              "xr": (("flat stream" if H.hosc_get_xr_form(cav.h) else "column march")

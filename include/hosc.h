@@ -314,15 +314,12 @@ hosc_status hosc_get_stencil_tiles(void* ctx, int* sx, int* sy, int* skz);
  * shape that does not fit (at most 512 threads and 200 KB of shared memory per block, too many
  * blocks), HOSC_ECUDA when the driver cannot encode the tensor maps, HOSC_ESTATE mid-step.
  * kernels selects which of the two run in this form: 1 p/v only (s/t keeps the register kernel
- * of hosc_set_tiles), 2 s/t only, 3 both (HOSC_EINVAL otherwise). nodes = 1 or 2: nodes of a
- * plane each computing thread takes (2 halves the computing warps and gives each thread two
- * independent nodes; HOSC_EINVAL otherwise).
+ * of hosc_set_tiles), 2 s/t only, 3 both (HOSC_EINVAL otherwise).
  * Three-kernel iteration form only (the merged form keeps its own kernels). Changing it drops
  * the captured steps. A wait of these kernels that runs out (2 s) ends the step with HOSC_ECUDA
  * instead of hanging. */
-hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages, int kernels, int nodes);
-hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz, int* stages, int* kernels,
-                               int* nodes);
+hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages, int kernels);
+hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz, int* stages, int* kernels);
 
 /* Form of the mixed-precision x/r kernel (three-kernel iteration): flat = 0 (the default) the
  * column march of hosc_set_tiles; 1 one flat grid-stride stream over the interior planes (the
@@ -352,8 +349,7 @@ int hosc_get_krylov_merged(void* ctx);
  * at that shape and keep the faster; with the three-kernel form, then time the
  * staged p/v and s/t kernels (hosc_set_stencil_tiles) for tiles sx in {8, 16, ..., 64},
  * sy in {4, 8} and skz in 1..33 within 1.5x of their least modelled cost, and the bulk-copy
- * kernels (hosc_set_tma_tiles) for nodes in {1, 2}, stages in {3, 4, 6, 8}, tty in 1..8 and
- * tkz in 1..50 within
+ * kernels (hosc_set_tma_tiles) for stages in {3, 4, 6, 8}, tty in 1..8 and tkz in 1..50 within
  * 1.5x of their least modelled cost (waves times planes streamed over planes in flight), and keep
  * the fastest of: both register, both staged, both bulk-copy at their best shape, bulk-copy p/v
  * at its best shape with the register s/t; then the two x/r forms (hosc_set_xr_form) with

@@ -75,7 +75,6 @@ struct Ctx {
   int sx = 0, sy = 0, skz = 0;             // staged stencil kernels (sx == 0: not used)
   int tty = 0, tkz = 0, tstages = 3;       // bulk-copy stencil kernels (tty == 0: not used)
   int tkernels = 3;                        // which of them run (1 p/v, 2 s/t, 3 both)
-  int tnpt = 1;                            // nodes of a plane per consumer thread
   int xr_flat = 0;                         // x/r as one flat stream (k8_xr)
   alignas(64) unsigned char tmap_host[kTmaMaps * kTmaMapBytes];   // their tensor maps
   // a round of steps enqueued for a pool (hosc_pool.cu): level and length, records read back
@@ -146,7 +145,6 @@ void apply_tiles(Ctx* c) {
   c->P.tkz = c->tkz;
   c->P.tstages = c->tstages;
   c->P.tkernels = c->tkernels;
-  c->P.tnpt = c->tnpt;
   c->P.xr_flat = c->xr_flat;
 }
 
@@ -941,7 +939,7 @@ long ctx_signature(void* ctx) {
                  ((long)c->sx << 24) | ((long)c->sy << 32) | ((long)c->skz << 42) |
                  ((long)c->merged << 52);
   return s ^ ((long)c->tty << 53) ^ ((long)c->tkz << 56) ^ ((long)c->xr_flat << 62) ^
-         ((long)c->tstages << 45) ^ ((long)c->tkernels << 48) ^ ((long)c->tnpt << 50);
+         ((long)c->tstages << 45) ^ ((long)c->tkernels << 48);
 }
 
 // Start of a round of n steps from the current level (read back by ctx_collect_round).
@@ -1590,7 +1588,6 @@ hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
       c->tty = c->tkz = 0;
       c->tstages = 3;
       c->tkernels = 3;
-      c->tnpt = 1;
     }
     apply_tiles(c);
     drop_graphs(c);
@@ -1598,7 +1595,7 @@ hosc_status hosc_set_stencil_tiles(void* ctx, int sx, int sy, int skz) {
   return HOSC_OK;
 }
 
-hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages, int kernels, int nodes) {
+hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages, int kernels) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
   if (c->stage != 0) return HOSC_ESTATE;
@@ -1607,10 +1604,9 @@ hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages, int kern
     tkz = 0;
     stages = 3;
     kernels = 3;
-    nodes = 1;
   } else {
     if (kernels < 1 || kernels > 3) return HOSC_EINVAL;
-    if (!tma_tiles_valid(c->prm.N, tty, tkz, stages, nodes)) return HOSC_EINVAL;
+    if (!tma_tiles_valid(c->prm.N, tty, tkz, stages)) return HOSC_EINVAL;
     DevParams P = c->P;
     P.tty = tty;
     P.ttx = tma_tile_x(c->prm.N);
@@ -1625,12 +1621,11 @@ hosc_status hosc_set_tma_tiles(void* ctx, int tty, int tkz, int stages, int kern
     }
   }
   if (tty != c->tty || tkz != c->tkz || stages != c->tstages || kernels != c->tkernels ||
-      nodes != c->tnpt || (tty > 0 && c->sx > 0)) {
+      (tty > 0 && c->sx > 0)) {
     c->tty = tty;
     c->tkz = tkz;
     c->tstages = stages;
     c->tkernels = kernels;
-    c->tnpt = nodes;
     if (tty > 0) c->sx = c->sy = c->skz = 0;
     apply_tiles(c);
     drop_graphs(c);
@@ -1655,15 +1650,13 @@ int hosc_get_xr_form(void* ctx) {
   return c ? c->xr_flat : -1;
 }
 
-hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz, int* stages, int* kernels,
-                               int* nodes) {
+hosc_status hosc_get_tma_tiles(void* ctx, int* tty, int* tkz, int* stages, int* kernels) {
   Ctx* c = (Ctx*)ctx;
   if (!c) return HOSC_EINVAL;
   if (tty) *tty = c->tty;
   if (tkz) *tkz = c->tkz;
   if (stages) *stages = c->tstages;
   if (kernels) *kernels = c->tkernels;
-  if (nodes) *nodes = c->tnpt;
   return HOSC_OK;
 }
 
@@ -1716,7 +1709,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   CU(cudaSetDevice(c->device));
   {   // the register kernels first
     hosc_status s0 = hosc_set_stencil_tiles(c, 0, 0, 0);
-    if (!s0) s0 = hosc_set_tma_tiles(c, 0, 0, 3, 3, 1);
+    if (!s0) s0 = hosc_set_tma_tiles(c, 0, 0, 3, 3);
     if (!s0) s0 = hosc_set_xr_form(c, 0);
     if (s0) return s0;
   }
@@ -1805,7 +1798,7 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   }
   if (c->merged) {   // the staged kernels implement the three-kernel form only
     st = hosc_set_stencil_tiles(c, 0, 0, 0);
-    if (!st) st = hosc_set_tma_tiles(c, 0, 0, 3, 3, 1);
+    if (!st) st = hosc_set_tma_tiles(c, 0, 0, 3, 3);
     if (!st) st = hosc_set_xr_form(c, 0);
     if (st) return st;
     if (kblock_out) *kblock_out = best_b;
@@ -1872,30 +1865,27 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   // within 1.5x of their least modelled cost; the pair at its best shape, and the p/v kernel
   // alone at its best shape beside the register s/t.
   double best_tma = INFINITY, best_tpv = INFINITY;
-  int bty = 0, btkz = 0, bts = 3, bnp = 1, pty = 0, ptkz = 0, pts = 3, pnp = 1;
+  int bty = 0, btkz = 0, bts = 3, pty = 0, ptkz = 0, pts = 3;
   {
     const int N = c->prm.N;
     const long rows = red_rows((long)N * N * N);
     static const int ring[] = {3, 4, 6, 8};
     double best_tmodel = 1e300;
-    for (int np = 1; np <= 2; ++np)
-      for (int ts : ring)
-        for (int ty = 1; ty <= 8; ++ty)
-          for (int z = 1; z <= 50; ++z)
-            best_tmodel = fmin(best_tmodel, tma_wave_cost(N, ty, z, ts, np, sms));
+    for (int ts : ring)
+      for (int ty = 1; ty <= 8; ++ty)
+        for (int z = 1; z <= 50; ++z)
+          best_tmodel = fmin(best_tmodel, tma_wave_cost(N, ty, z, ts, sms));
     const DevParams saved = c->P;
-    for (int np = 1; np <= 2; ++np)
     for (int ts : ring)
     for (int ty = 1; ty <= 8 && !st && best_tmodel < 1e299; ++ty) {
       for (int z = 1; z <= 50 && !st; ++z) {
-        if (tma_wave_cost(N, ty, z, ts, np, sms) > 1.5 * best_tmodel) continue;
+        if (tma_wave_cost(N, ty, z, ts, sms) > 1.5 * best_tmodel) continue;
         DevParams trial = saved;
         trial.sx = 0;
         trial.tty = ty;
         trial.ttx = tma_tile_x(N);
         trial.tkz = z;
         trial.tstages = ts;
-        trial.tnpt = np;
         if (krylov4_blocks(trial) > rows) continue;
         if (!tma_prepare(trial, c->F, c->tmap_host)) {
           best_tmodel = 1e300;   // no tensor maps on this driver: keep the other kernels
@@ -1915,14 +1905,12 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
           bty = ty;
           btkz = z;
           bts = ts;
-          bnp = np;
         }
         if (!st && pv < best_tpv) {
           best_tpv = pv;
           pty = ty;
           ptkz = z;
           pts = ts;
-          pnp = np;
         }
       }
     }
@@ -1931,10 +1919,10 @@ hosc_status hosc_autotune(void* ctx, int reps, int* kblock_out, int* kz_out, dou
   if (st) return st;
   const double tma_pv_reg_st = best_tpv + reg_k[1];
   if (tma_pv_reg_st < best_tma && tma_pv_reg_st < reg_pvst && tma_pv_reg_st < best_staged) {
-    st = hosc_set_tma_tiles(c, pty, ptkz, pts, 1, pnp);
+    st = hosc_set_tma_tiles(c, pty, ptkz, pts, 1);
     best += tma_pv_reg_st - reg_pvst;
   } else if (best_tma < reg_pvst && best_tma < best_staged) {
-    st = hosc_set_tma_tiles(c, bty, btkz, bts, 3, bnp);
+    st = hosc_set_tma_tiles(c, bty, btkz, bts, 3);
     best += best_tma - reg_pvst;
   } else if (best_staged < reg_pvst) {
     st = hosc_set_stencil_tiles(c, bsx, bsy, bskz);

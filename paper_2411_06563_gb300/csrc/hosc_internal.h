@@ -35,7 +35,6 @@ struct DevParams {
                      // columns, tkz planes per block; tty == 0: not used
   int tstages;       // their ring of shared-memory stages (3, 4, 6 or 8)
   int tkernels;      // which of them run: 1 p/v, 2 s/t, 3 both
-  int tnpt;          // nodes of a plane per consumer thread (1 or 2)
   int xr_flat;       // x/r as one flat grid-stride stream (k8_xr) instead of the column march
   double h, h2;      // grid spacing along x and its square
   double Ly, Lz;     // box 1 x Ly x Lz: lengths along y and z (1 for the cube)
@@ -184,11 +183,11 @@ constexpr int kTmaMaps = 8;        // kr, kr0, kp[0], kp[1], kv[0], kv[1], kwm, 
 constexpr int kTmaMapBytes = 128;  // sizeof(CUtensorMap)
 int tma_tile_x(int N);
 // False when the shape does not launch (shared memory, threads, block count).
-bool tma_tiles_valid(int N, int tty, int tkz, int stages, int npt);
+bool tma_tiles_valid(int N, int tty, int tkz, int stages);
 // Encode the tensor maps of P's tile shape for F's arrays into host (kTmaMaps * 128 bytes,
 // 64-byte aligned); false when the driver cannot encode them.
 bool tma_prepare(const DevParams& P, const Fields& F, void* host);
-double tma_wave_cost(int N, int tty, int tkz, int stages, int npt, int sms);
+double tma_wave_cost(int N, int tty, int tkz, int stages, int sms);
 void launch_tma_pv(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 void launch_tma_st(const DevParams& P, const Fields& F, int pp, cudaStream_t s);
 long tma_blocks(const DevParams& P);

@@ -69,8 +69,8 @@ struct Pool {
   cudaGraphExec_t exec = nullptr;
   bool dirty = true;                          // membership changed since the capture
   // tuned launch shapes per N: kblock, kz, narrow, sx, sy, skz, tty, tkz, merged, x/r form,
-  // ring stages, kernels and nodes per thread of the bulk-copy kernels
-  std::map<int, std::array<int, 13>> tiles;
+  // ring stages and kernels of the bulk-copy kernels
+  std::map<int, std::array<int, 12>> tiles;
   long rounds = 0, captures = 0;
   double capture_ms = 0.0;
   RoundState* rs = nullptr;                   // persistent mode: the round kernel's tables
@@ -125,11 +125,11 @@ bool needs_capture(const Pool* P) {
   return false;
 }
 
-hosc_status apply_shape(void* ctx, const std::array<int, 13>& t) {
+hosc_status apply_shape(void* ctx, const std::array<int, 12>& t) {
   hosc_status st = hosc_set_krylov_merged(ctx, t[8]);
   if (!st) st = hosc_set_tiles(ctx, t[0], t[1], t[2]);
   if (!st) st = hosc_set_stencil_tiles(ctx, t[3], t[4], t[5]);
-  if (!st) st = hosc_set_tma_tiles(ctx, t[6], t[7], t[10], t[11], t[12]);
+  if (!st) st = hosc_set_tma_tiles(ctx, t[6], t[7], t[10], t[11]);
   if (!st) st = hosc_set_xr_form(ctx, t[9]);
   return st;
 }
@@ -178,10 +178,10 @@ hosc_status settle(Pool* P, int slot, hosc_status st, bool steady, const hosc_in
       auto it = P->tiles.find(q.N);
       if (it == P->tiles.end()) {
         hosc_status ts = hosc_autotune(q.ctx, 3, nullptr, nullptr, nullptr);
-        std::array<int, 13> t = {};
+        std::array<int, 12> t = {};
         if (!ts) ts = hosc_get_tiles(q.ctx, &t[0], &t[1], &t[2]);
         if (!ts) ts = hosc_get_stencil_tiles(q.ctx, &t[3], &t[4], &t[5]);
-        if (!ts) ts = hosc_get_tma_tiles(q.ctx, &t[6], &t[7], &t[10], &t[11], &t[12]);
+        if (!ts) ts = hosc_get_tma_tiles(q.ctx, &t[6], &t[7], &t[10], &t[11]);
         if (!ts) t[8] = hosc_get_krylov_merged(q.ctx);
         if (!ts) t[9] = hosc_get_xr_form(q.ctx);
         if (ts) return ts;

@@ -64,12 +64,9 @@ __host__ __device__ inline TmaLayout tma_layout(int tx, int ty, bool pv) {
   return L;
 }
 
-// Consumer warps of a tile when each consumer thread computes npt nodes of a plane.
-__host__ __device__ inline int tma_consumer_warps(int tx, int ty, int npt) {
-  return (tx * ty + 32 * npt - 1) / (32 * npt);
-}
-__host__ __device__ inline int tma_threads(int tx, int ty, int npt) {
-  return (tma_consumer_warps(tx, ty, npt) + 1) * 32;   // consumer warps + the producer warp
+__host__ __device__ inline int tma_consumers(int tx, int ty) { return tx * ty; }
+__host__ __device__ inline int tma_threads(int tx, int ty) {
+  return ((tma_consumers(tx, ty) + 31) / 32 + 1) * 32;   // consumer warps + the producer warp
 }
 inline size_t tma_smem(int tx, int ty, bool pv, int stages) {
   return (size_t)stages * tma_layout(tx, ty, pv).stage + 128;   // + alignment slack
@@ -150,10 +147,7 @@ struct TmaMaps {
   CUtensorMap m[kTmaMaps];
 };
 
-// NPT: nodes of a plane per consumer thread (node e of the tile for thread t: e = t + q C,
-// q < NPT, C the consumer threads), independent work that hides arithmetic and shared-memory
-// latency when few warps fit on an SM.
-template <bool PV, int S, int NPT>
+template <bool PV, int S>
 __global__ void __launch_bounds__(kTmaMaxThreads)
     k7_stencil(DevParams P, Fields F, int pp, const __grid_constant__ TmaMaps tm) {
   constexpr int M = PV ? 4 : 8;
@@ -172,7 +166,7 @@ __global__ void __launch_bounds__(kTmaMaxThreads)
   const int i0 = 1 + (int)blockIdx.x * L.tx, j0 = 1 + (int)blockIdx.y * L.ty;
   const int k0 = 1 + (int)blockIdx.z * P.tkz, k1 = min(k0 + P.tkz, N - 1);
   const int nplanes = k1 - k0 + 2;   // planes k0 - 1 .. k1
-  const int nwc = tma_consumer_warps(L.tx, L.ty, NPT);
+  const int nwc = (tma_consumers(L.tx, L.ty) + 31) >> 5;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char* base = tdyn + ((128u - (smem_u32(tdyn) & 127u)) & 127u);
   const CUtensorMap* maps = tm.m;   // kernel parameters: generic addresses in param space
@@ -233,17 +227,10 @@ __global__ void __launch_bounds__(kTmaMaxThreads)
     }
   } else {
     // ---------------------------------------------------------------- consumers
-    const int hx = L.tx + 2, C = nwc * 32;
-    int h[NPT], e[NPT], txq[NPT], tyq[NPT];
-    bool mine[NPT];
-#pragma unroll
-    for (int q = 0; q < NPT; ++q) {
-      e[q] = (int)threadIdx.x + q * C;
-      txq[q] = e[q] % L.tx;
-      tyq[q] = e[q] / L.tx;
-      mine[q] = e[q] < L.tx * L.ty && i0 + txq[q] <= N - 2 && j0 + tyq[q] <= N - 2;
-      h[q] = (tyq[q] + 1) * hx + (txq[q] + 1);
-    }
+    const int t = threadIdx.x, tx = t % L.tx, ty = t / L.tx;
+    const bool mine = t < L.tx * L.ty && i0 + tx <= N - 2 && j0 + ty <= N - 2;
+    const int hx = L.tx + 2;
+    const int h = (ty + 1) * hx + (tx + 1), e = ty * L.tx + tx;
     const float4 zero = f4(0.f);
     const float4 b = sc.b, mom = neg4(sc.om), ma = neg4(sc.a);
     auto vec = [&](int u, int v) {
@@ -254,52 +241,45 @@ __global__ void __launch_bounds__(kTmaMaxThreads)
       if (PV) return fma4(b, fma4(mom, vec(u, 2)[x], vec(u, 1)[x]), vec(u, 0)[x]);
       return fma4(ma, vec(u, 1)[x], vec(u, 0)[x]);
     };
-    float4 pm[NPT], pc[NPT];
     bool ok = mbar_wait(&full[0], 0u);
-#pragma unroll
-    for (int q = 0; q < NPT; ++q) pm[q] = (ok && mine[q]) ? val(0, h[q]) : zero;
+    float4 pm = (ok && mine) ? val(0, h) : zero;
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[0]);
     ok = ok && mbar_wait(&full[1 % S], (unsigned)((1 / S) & 1));
-#pragma unroll
-    for (int q = 0; q < NPT; ++q) pc[q] = (ok && mine[q]) ? val(1, h[q]) : zero;
+    float4 pc = (ok && mine) ? val(1, h) : zero;
     for (int u = 1; ok && u < nplanes - 1; ++u) {   // plane k = k0 - 1 + u
       const int un = u + 1;
       if (!mbar_wait(&full[un % S], (unsigned)((un / S) & 1))) {
         ok = false;
         break;
       }
-      const unsigned char* st = base + (u % S) * L.stage;
-      const int k = k0 - 1 + u;
-#pragma unroll
-      for (int q = 0; q < NPT; ++q) {
-        const float4 pz = mine[q] ? val(un, h[q]) : zero;
-        if (mine[q]) {
-          const long lin = (long)i0 + (long)N * (j0 + tyq[q]) + (long)N2 * k;
-          Op4 op;
-          op.m = ((const float4*)(st + L.off_m))[e[q]];
-          op.e = ene ? ((const float4*)(st + L.off_e))[e[q]] : zero;
-          op.l12 = ((const float*)(st + L.off_l + tyq[q] * L.lrow))[(int)(lin & 3L) + txq[q]] *
-                   (1.f / 12.f);
-          const int x = h[q];
-          const float4 y = apply_op(P, op, pc[q], val(u, x + 1), val(u, x - 1), val(u, x + hx),
-                                    val(u, x - hx), pz, pm[q]);
-          const int c = (i0 + txq[q]) + N * (j0 + tyq[q]) + N2 * k;
-          if (PV) {
-            F.kp[1 - pp][c] = pc[q];
-            F.kv[1 - pp][c] = y;
-            ff_dot4(acc, ((const float4*)(st + L.off_r0))[e[q]], y);
-          } else {
-            F.kt[c] = y;
-            ff_dot4(acc, y, pc[q]);
-            ff_dot4(acc + 4, y, y);
-          }
+      const float4 pz = mine ? val(un, h) : zero;
+      if (mine) {
+        const unsigned char* st = base + (u % S) * L.stage;
+        const int k = k0 - 1 + u;
+        const long lin = (long)i0 + (long)N * (j0 + ty) + (long)N2 * k;
+        Op4 op;
+        op.m = ((const float4*)(st + L.off_m))[e];
+        op.e = ene ? ((const float4*)(st + L.off_e))[e] : zero;
+        op.l12 = ((const float*)(st + L.off_l + ty * L.lrow))[(int)(lin & 3L) + tx] *
+                 (1.f / 12.f);
+        const float4 y = apply_op(P, op, pc, val(u, h + 1), val(u, h - 1), val(u, h + hx),
+                                  val(u, h - hx), pz, pm);
+        const int c = (i0 + tx) + N * (j0 + ty) + N2 * k;
+        if (PV) {
+          F.kp[1 - pp][c] = pc;
+          F.kv[1 - pp][c] = y;
+          ff_dot4(acc, ((const float4*)(st + L.off_r0))[e], y);
+        } else {
+          F.kt[c] = y;
+          ff_dot4(acc, y, pc);
+          ff_dot4(acc + 4, y, y);
         }
-        pm[q] = pc[q];
-        pc[q] = pz;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[u % S]);
+      pm = pc;
+      pc = pz;
     }
     if (!ok) failed = 1;
   }
@@ -378,21 +358,16 @@ bool encode_vec(CUtensorMap* m, const float4* a, int N, int bw, int bh) {
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The instantiations: ring depths of 3, 4, 6 and 8 stages (planes 1, 2, 4 and 6 ahead), one or
-// two nodes per consumer thread.
-template <bool PV, int NPT>
-const void* k7_fn_n(int stages) {
+// The instantiations: ring depths of 3, 4, 6 and 8 stages (planes 1, 2, 4 and 6 ahead).
+template <bool PV>
+const void* k7_fn(int stages) {
   switch (stages) {
-    case 3: return (const void*)k7_stencil<PV, 3, NPT>;
-    case 4: return (const void*)k7_stencil<PV, 4, NPT>;
-    case 6: return (const void*)k7_stencil<PV, 6, NPT>;
-    case 8: return (const void*)k7_stencil<PV, 8, NPT>;
+    case 3: return (const void*)k7_stencil<PV, 3>;
+    case 4: return (const void*)k7_stencil<PV, 4>;
+    case 6: return (const void*)k7_stencil<PV, 6>;
+    case 8: return (const void*)k7_stencil<PV, 8>;
     default: return nullptr;
   }
-}
-template <bool PV>
-const void* k7_fn(int stages, int npt) {
-  return npt == 2 ? k7_fn_n<PV, 2>(stages) : k7_fn_n<PV, 1>(stages);
 }
 
 bool tma_attrs_ready() {
@@ -401,15 +376,13 @@ bool tma_attrs_ready() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
   if (!done[dev]) {
     const int cap = 200 * 1024;
-    for (int npt : {1, 2}) {
-      for (int st : {3, 4, 6, 8}) {
-        if (cudaFuncSetAttribute(k7_fn<true>(st, npt),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess ||
-            cudaFuncSetAttribute(k7_fn<false>(st, npt),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, cap) != cudaSuccess) {
-          cudaGetLastError();
-          return false;
-        }
+    for (int st : {3, 4, 6, 8}) {
+      if (cudaFuncSetAttribute(k7_fn<true>(st), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               cap) != cudaSuccess ||
+          cudaFuncSetAttribute(k7_fn<false>(st), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
       }
     }
     done[dev] = 1;
@@ -422,11 +395,11 @@ dim3 tma_grid(const DevParams& P) {
   return dim3((ni + P.ttx - 1) / P.ttx, (ni + P.tty - 1) / P.tty, (ni + P.tkz - 1) / P.tkz);
 }
 
-template <bool PV, int S, int NPT>
+template <bool PV, int S>
 void launch_k7(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = tma_grid(P);
-  cfg.blockDim = dim3(tma_threads(P.ttx, P.tty, NPT));
+  cfg.blockDim = dim3(tma_threads(P.ttx, P.tty));
   cfg.dynamicSmemBytes = tma_smem(P.ttx, P.tty, PV, S);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -436,23 +409,17 @@ void launch_k7(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
   cfg.numAttrs = 1;
   TmaMaps tm;
   memcpy(&tm, F.tmaps_host, sizeof(tm));
-  cudaLaunchKernelEx(&cfg, k7_stencil<PV, S, NPT>, P, F, pp, tm);
-}
-
-template <bool PV, int NPT>
-void launch_k7_n(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
-  switch (P.tstages) {
-    case 4: launch_k7<PV, 4, NPT>(P, F, pp, s); break;
-    case 6: launch_k7<PV, 6, NPT>(P, F, pp, s); break;
-    case 8: launch_k7<PV, 8, NPT>(P, F, pp, s); break;
-    default: launch_k7<PV, 3, NPT>(P, F, pp, s); break;
-  }
+  cudaLaunchKernelEx(&cfg, k7_stencil<PV, S>, P, F, pp, tm);
 }
 
 template <bool PV>
 void launch_k7(const DevParams& P, const Fields& F, int pp, cudaStream_t s) {
-  if (P.tnpt == 2) launch_k7_n<PV, 2>(P, F, pp, s);
-  else launch_k7_n<PV, 1>(P, F, pp, s);
+  switch (P.tstages) {
+    case 4: launch_k7<PV, 4>(P, F, pp, s); break;
+    case 6: launch_k7<PV, 6>(P, F, pp, s); break;
+    case 8: launch_k7<PV, 8>(P, F, pp, s); break;
+    default: launch_k7<PV, 3>(P, F, pp, s); break;
+  }
 }
 
 }  // namespace
@@ -464,12 +431,11 @@ int tma_tile_x(int N) {
   return (ni + parts - 1) / parts;
 }
 
-bool tma_tiles_valid(int N, int tty, int tkz, int stages, int npt) {
+bool tma_tiles_valid(int N, int tty, int tkz, int stages) {
   const int ni = N - 2, tx = tma_tile_x(N);
   if (tty < 1 || tty > ni || tkz < 1 || tkz > ni) return false;
   if (stages != 3 && stages != 4 && stages != 6 && stages != 8) return false;
-  if (npt != 1 && npt != 2) return false;
-  if (tma_threads(tx, tty, npt) > kTmaMaxThreads) return false;
+  if (tma_threads(tx, tty) > kTmaMaxThreads) return false;
   if (tma_smem(tx, tty, true, stages) > 200 * 1024) return false;
   if (tty + 2 > 256) return false;
   const long nb = (long)((ni + tx - 1) / tx) * ((ni + tty - 1) / tty) * ((ni + tkz - 1) / tkz);
@@ -499,12 +465,12 @@ bool tma_prepare(const DevParams& P, const Fields& F, void* host) {
   return ok;
 }
 
-double tma_wave_cost(int N, int tty, int tkz, int stages, int npt, int sms) {
-  if (!tma_tiles_valid(N, tty, tkz, stages, npt) || !tma_attrs_ready()) return 1e300;
+double tma_wave_cost(int N, int tty, int tkz, int stages, int sms) {
+  if (!tma_tiles_valid(N, tty, tkz, stages) || !tma_attrs_ready()) return 1e300;
   const int tx = tma_tile_x(N), ni = N - 2;
   int occ = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k7_fn<true>(stages, npt),
-                                                    tma_threads(tx, tty, npt),
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k7_fn<true>(stages),
+                                                    tma_threads(tx, tty),
                                                     tma_smem(tx, tty, true, stages)) !=
           cudaSuccess ||
       occ < 1) {

@@ -140,8 +140,11 @@ def lib():
                                           ctypes.POINTER(ctypes.c_int)]),
         "hosc_set_stencil_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "hosc_set_tma_tiles": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                              ctypes.c_int, ctypes.c_int]),
-        "hosc_get_tma_tiles": (ctypes.c_int, [_P] + [ctypes.POINTER(ctypes.c_int)] * 5),
+                                              ctypes.c_int]),
+        "hosc_get_tma_tiles": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int),
+                                              ctypes.POINTER(ctypes.c_int)]),
         "hosc_set_xr_form": (ctypes.c_int, [_P, ctypes.c_int]),
         "hosc_get_xr_form": (ctypes.c_int, [_P]),
         "hosc_set_krylov_merged": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -333,15 +336,16 @@ def hosc_set_stencil_tiles(h, sx, sy, skz):
     return lib().hosc_set_stencil_tiles(h, int(sx), int(sy), int(skz))
 
 
-def hosc_set_tma_tiles(h, tty, tkz, stages=3, kernels=3, nodes=1):
-    return lib().hosc_set_tma_tiles(h, int(tty), int(tkz), int(stages), int(kernels), int(nodes))
+def hosc_set_tma_tiles(h, tty, tkz, stages=3, kernels=3):
+    return lib().hosc_set_tma_tiles(h, int(tty), int(tkz), int(stages), int(kernels))
 
 
 def hosc_get_tma_tiles(h):
-    """(status, rows, planes, stages, kernels, nodes)."""
-    v = [ctypes.c_int() for _ in range(5)]
-    st = lib().hosc_get_tma_tiles(h, *(ctypes.byref(x) for x in v))
-    return (st,) + tuple(x.value for x in v)
+    """(status, rows, planes, stages, kernels)."""
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    st = lib().hosc_get_tma_tiles(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                  ctypes.byref(d))
+    return st, a.value, b.value, c.value, d.value
 
 
 def hosc_set_xr_form(h, flat):

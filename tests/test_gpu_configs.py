@@ -117,14 +117,13 @@ def _increment_residuals(st0, got, op):
 @pytest.mark.parametrize("precision,phase,shape", [(H.HOSC_FP64, 0, None),
                                                    (H.HOSC_MIXED, 0, "autotuned"),
                                                    (H.HOSC_MIXED, 1, "autotuned"),
-                                                   (H.HOSC_MIXED, 1, (2, 33, 6, 1, 1)),
-                                                   (H.HOSC_MIXED, 0, (2, 17, 4, 3, 2))])
+                                                   (H.HOSC_MIXED, 1, (2, 33, 6, 1)),
+                                                   (H.HOSC_MIXED, 0, (2, 17, 4, 3))])
 def test_benched_cavity_101_one_step(step101, precision, phase, shape):
     """One step of the benched cavity from a seeded developed state against the oracle's step:
     FP64 fields within 1e-10; mixed precision at the autotuner's launch shape for this grid (the
     one the benchmark times) and with the bulk-copy stencil kernels forced (p/v alone, 2 rows x
-    33 planes per block in a ring of six stages; both, 2 rows x 17 planes in a ring of four, two
-    nodes per computing thread),
+    33 planes per block in a ring of six stages; both, 2 rows x 17 planes in a ring of four),
     within the FP32 solve's tolerance and, with FP64 sweeps, by residual in the oracle's
     system."""
     st0, ref, oinfo = step101

@@ -117,8 +117,7 @@ def _one_mixed_step(N, Ra, n, dt, seed, tiles=None, stencil=None, merged=None, t
             assert H.hosc_set_stencil_tiles(cav.h, *stencil) == 0
             assert H.hosc_get_stencil_tiles(cav.h) == (0,) + tuple(stencil)
         if tma is not None:
-            # rows, planes, stages (3), kernels (3: both), nodes per thread (1)
-            full = tuple(tma) + (3, 3, 1)[len(tma) - 2:]
+            full = tuple(tma) + (3,) * (4 - len(tma))   # rows, planes, stages, kernels
             assert H.hosc_set_tma_tiles(cav.h, *full) == 0
             assert H.hosc_get_tma_tiles(cav.h) == (0,) + full
             assert H.hosc_get_stencil_tiles(cav.h) == (0, 0, 0, 0)
@@ -163,16 +162,14 @@ def test_staged_stencil_kernels(stencil):
 
 
 @pytest.mark.parametrize("tma", [(1, 1, 3), (2, 5, 4), (3, 17, 3), (4, 9, 6), (8, 3, 8),
-                                 (17, 2, 3), (1, 17, 8), (2, 7, 6), (2, 9, 6, 1), (3, 5, 4, 2),
-                                 (2, 9, 6, 1, 2), (3, 5, 4, 3, 2), (17, 2, 3, 3, 2),
-                                 (1, 17, 8, 2, 2)])
+                                 (17, 2, 3), (1, 17, 8), (2, 7, 6), (2, 9, 6, 1), (3, 5, 4, 2)])
 def test_tma_stencil_kernels(tma):
     """The bulk-copy (TMA) p/v and s/t kernels compute what the register kernels compute: the
     increment equals the default's within the FP32 solve tolerance, for row tiles that overhang
     the interior in y (17 = 2 x 8 + 1, 3 x 5 + 2, ...), segments that do not divide the interior,
     single-plane and whole-column segments, a single tile per plane, rings of 3, 4, 6 and 8
-    stages (segments shorter and longer than the ring), either kernel alone beside the register
-    form of the other, and two nodes per computing thread (tiles of an odd node count)."""
+    stages (segments shorter and longer than the ring), and either kernel alone beside the
+    register form of the other."""
     N, Ra, n, dt = 19, 1e4, 0.75, 0.002
     _, _, ref = _one_mixed_step(N, Ra, n, dt, 219)
     _, _, got = _one_mixed_step(N, Ra, n, dt, 219, tma=tma, merged=0)
@@ -211,9 +208,9 @@ def test_tma_steps_and_shape_switches():
                 if plan == "switch":
                     if leg == 1:
                         assert H.hosc_set_stencil_tiles(cav.h, 16, 2, 5) == 0
-                        assert H.hosc_get_tma_tiles(cav.h) == (0, 0, 0, 3, 3, 1)
+                        assert H.hosc_get_tma_tiles(cav.h) == (0, 0, 0, 3, 3)
                     else:
-                        assert H.hosc_set_tma_tiles(cav.h, 2, 6, 4, 3, 2) == 0
+                        assert H.hosc_set_tma_tiles(cav.h, 2, 6, 4, 3) == 0
                         assert H.hosc_get_stencil_tiles(cav.h) == (0, 0, 0, 0)
                 info = cav.step(4)
                 assert info["call_status"] == 0, info
@@ -233,12 +230,12 @@ def test_tiles_limits_and_autotune():
         for bad in ((4, 4, 1), (32, 16, 1), (32, 4, 0), (32, 4, N - 1), (64, 8, 1), (17, 2, 1)):
             assert H.hosc_set_stencil_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
         assert H.hosc_set_stencil_tiles(cav.h, 0, 0, 0) == 0
-        for bad in ((1, 0, 3, 3, 1), (1, N - 1, 3, 3, 1), (N - 1, 1, 3, 3, 1), (-1, 3, 3, 3, 1),
-                    (2, -4, 3, 3, 1), (2, 4, 5, 3, 1), (2, 4, 2, 3, 1), (2, 4, 16, 3, 1),
-                    (2, 4, 3, 0, 1), (2, 4, 3, 4, 1), (2, 4, 3, 3, 0), (2, 4, 3, 3, 3)):
+        for bad in ((1, 0, 3, 3), (1, N - 1, 3, 3), (N - 1, 1, 3, 3), (-1, 3, 3, 3),
+                    (2, -4, 3, 3), (2, 4, 5, 3), (2, 4, 2, 3), (2, 4, 16, 3), (2, 4, 3, 0),
+                    (2, 4, 3, 4)):
             assert H.hosc_set_tma_tiles(cav.h, *bad) == H.HOSC_EINVAL, bad
-        assert H.hosc_set_tma_tiles(cav.h, 0, 5, 7, 1, 2) == 0
-        assert H.hosc_get_tma_tiles(cav.h) == (0, 0, 0, 3, 3, 1)
+        assert H.hosc_set_tma_tiles(cav.h, 0, 5, 7, 1) == 0
+        assert H.hosc_get_tma_tiles(cav.h) == (0, 0, 0, 3, 3)
         assert H.hosc_set_xr_form(cav.h, 2) == H.HOSC_EINVAL and H.hosc_get_xr_form(cav.h) == 0
         assert H.hosc_get_krylov_merged(cav.h) == 0   # the default form: three kernels
         assert H.hosc_set_krylov_merged(cav.h, 2) == H.HOSC_EINVAL
